@@ -1,0 +1,302 @@
+"""Pins of the oracle's dynamic program (paper Eq. 5-6), backtracking (Sec. 3.3)
+and prior reading against exhaustive enumeration, direct re-evaluation,
+the prefix-sum identity of Sec. 3.4, closed special cases and planted scenes."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+# A short, steep camera so that the ground line spans many disparities over a
+# dozen rows: alpha = 1.0 * cos(0) / 0.5 = 2 px per row, horizon at image row 3.
+SHORT = dict(dmax=24, horizon_row=3, baseline_m=1.0, camera_height_m=0.5, pitch_rad=0.0)
+
+
+def _random_column(rng, H, dmax, kind):
+    if kind == "uniform":
+        return rng.integers(0, 16 * dmax + 1, size=H).astype(np.int16)
+    # piecewise: random runs of constant disparity or of the ground line, plus outliers
+    q = np.zeros(H, np.int64)
+    v = 0
+    while v < H:
+        n = int(rng.integers(1, H - v + 1))
+        mode = rng.integers(0, 3)
+        if mode == 0:
+            q[v:v + n] = 16 * rng.integers(0, dmax + 1)
+        elif mode == 1:
+            r = H - 1 - np.arange(v, v + n)
+            q[v:v + n] = np.clip(np.rint(16 * 2.0 * (r - 3)), 0, 16 * dmax)
+        else:
+            q[v:v + n] = 0
+        v += n
+    noise = rng.integers(-8, 9, size=H)
+    q = np.clip(q + noise, 0, 16 * dmax)
+    out = rng.random(H) < 0.15
+    q[out] = rng.integers(0, 16 * dmax + 1, size=int(out.sum()))
+    return q.astype(np.int16)
+
+
+def _key(st):
+    return [(int(s["v_bottom"]), int(s["v_top"]), int(s["cls"])) for s in st]
+
+
+@pytest.mark.parametrize("kind", ["uniform", "piecewise"])
+def test_dp_equals_exhaustive_minimum_without_ordering(kind):
+    """With the ordering prior off, the priors are Markov in (row, class), so the DP
+    (Eq. 6) is exact: its cost equals the minimum over all 3 * 4^(H-1) segmentations,
+    and when that minimum is unique the segmentations coincide."""
+    rng = np.random.default_rng(100 if kind == "uniform" else 200)
+    p = oracle.make_params(**SHORT, cost_order=0.0, quantize=1)
+    unique = 0
+    for trial in range(160):
+        H = int(rng.integers(1, 11)) if trial < 150 else 12
+        q = _random_column(rng, H, SHORT["dmax"], kind)
+        dp = oracle.column(p, q)
+        bf_cost, count, bf_st = oracle.brute_force(p, q)
+        assert dp.cost == bf_cost, (H, q.tolist())
+        if count == 1:
+            unique += 1
+            assert _key(dp.stixels) == _key(bf_st), (H, q.tolist())
+    assert unique > 100
+
+
+def test_dp_equals_exhaustive_minimum_real_arithmetic():
+    rng = np.random.default_rng(300)
+    p = oracle.make_params(**SHORT, cost_order=0.0, quantize=0)
+    for _ in range(80):
+        H = int(rng.integers(1, 10))
+        q = _random_column(rng, H, SHORT["dmax"], "piecewise")
+        dp = oracle.column(p, q)
+        bf_cost, _, _ = oracle.brute_force(p, q)
+        assert abs(dp.cost - bf_cost) <= 1e-12 * max(1.0, abs(bf_cost))
+
+
+def test_dp_with_ordering_is_consistent_upper_bound():
+    """With the ordering prior on, Eq. 6 keeps only the best object stixel per end
+    row, so the DP cost is >= the exhaustive minimum, and it equals the true cost
+    of the segmentation it returns."""
+    rng = np.random.default_rng(400)
+    p = oracle.make_params(**SHORT, cost_order=2.0, eps_order=0.0, quantize=1)
+    strictly_worse = 0
+    for _ in range(150):
+        H = int(rng.integers(1, 11))
+        q = _random_column(rng, H, SHORT["dmax"], "piecewise")
+        dp = oracle.column(p, q)
+        bf_cost, _, _ = oracle.brute_force(p, q)
+        assert dp.cost >= bf_cost
+        strictly_worse += dp.cost > bf_cost
+        assert oracle.eval_segmentation(p, q, dp.stixels) == dp.cost
+
+
+def _grid(x):
+    return x if math.isinf(x) else round(4096.0 * x) / 4096.0 if x >= 0 else -round(-4096.0 * x) / 4096.0
+
+
+def _my_cost(d, q, st, H):
+    """Independent evaluation of a segmentation's total cost from per-pixel costs and
+    this test's own reading of the five prior constraints."""
+    p = oracle.make_params(**d)
+    fg = oracle.model_constants(p, H)["fg"]
+    f32 = lambda x: float(np.float32(x))
+    bic = f32(d["cost_new_stixel"])
+    total, prev = 0.0, None
+    for s in st:
+        b, k, c = int(s["v_bottom"]), int(s["v_top"]), int(s["cls"])
+        n = k - b + 1
+        S = int(np.sum(q[b:k + 1].astype(np.int64)))
+        f = (S + 8 * n) // (16 * n)
+        total += sum(oracle.pixel_cost(p, H, c, v, int(q[v]), f) for v in range(b, k + 1))
+        if prev is None:
+            total += _grid(f32(d["prior_first"][c]) + bic)
+        else:
+            pc, pf = prev
+            total += _grid(f32(d["prior_trans"][c][pc]) + bic)
+            if c == oracle.OBJECT and pc == oracle.GROUND:
+                gq = 16 * fg[b]
+                if 16 * f > gq + round(16 * f32(d["eps_gravity"])):
+                    total += _grid(f32(d["cost_gravity"]))
+                if 16 * f < gq - round(16 * f32(d["eps_diving"])):
+                    total += _grid(f32(d["cost_diving"]))
+            if c == oracle.OBJECT and pc == oracle.OBJECT:
+                if 16 * f > 16 * pf + round(16 * f32(d["eps_order"])):
+                    total += _grid(f32(d["cost_order"]))
+        prev = (c, f)
+    return total
+
+
+def test_segmentation_cost_reading_independent():
+    """The oracle's direct evaluation equals this test's own evaluation of the same
+    segmentation (same per-pixel costs, independently coded priors)."""
+    rng = np.random.default_rng(500)
+    d = dict(oracle.DEFAULTS); d.update(SHORT); d["quantize"] = 1
+    d["prior_trans"] = ((1.5, 1.0, 4.0), (1.5, 7.0, 8.0), (0.5, 0.5, 9.0))   # all finite here
+    p = oracle.make_params(**d)
+    for _ in range(200):
+        H = int(rng.integers(1, 14))
+        q = _random_column(rng, H, SHORT["dmax"], "piecewise")
+        cuts = np.sort(rng.choice(np.arange(1, H), size=int(rng.integers(0, H)), replace=False)) if H > 1 else []
+        bounds = [0] + list(cuts) + [H]
+        st = np.zeros(len(bounds) - 1, oracle.STIXEL_DTYPE)
+        for i in range(len(bounds) - 1):
+            st[i]["v_bottom"], st[i]["v_top"] = bounds[i], bounds[i + 1] - 1
+            st[i]["cls"] = rng.integers(0, 3)
+        assert oracle.eval_segmentation(p, q, st) == _my_cost(d, q, st, H)
+
+
+def test_prefix_identity():
+    """Sec. 3.4: a stixel's data cost is the difference of two prefix entries."""
+    rng = np.random.default_rng(600)
+    p = oracle.make_params(dmax=40, horizon_row=30, quantize=1)
+    H = 57
+    q = rng.integers(0, 16 * 40 + 1, size=H).astype(np.int16)
+    pd, pg, ps, po = oracle.prefix(p, q)
+    assert np.array_equal(pd, np.concatenate([[0], np.cumsum(q.astype(np.int64))]))
+    for _ in range(200):
+        b = int(rng.integers(0, H)); k = int(rng.integers(b, H)); f = int(rng.integers(0, 41))
+        direct_o = sum(oracle.pixel_cost(p, H, oracle.OBJECT, v, int(q[v]), f) for v in range(b, k + 1))
+        direct_g = sum(oracle.pixel_cost(p, H, oracle.GROUND, v, int(q[v])) for v in range(b, k + 1))
+        direct_s = sum(oracle.pixel_cost(p, H, oracle.SKY, v, int(q[v])) for v in range(b, k + 1))
+        assert po[f, k + 1] - po[f, b] == direct_o
+        assert pg[k + 1] - pg[b] == direct_g
+        assert ps[k + 1] - ps[b] == direct_s
+
+
+def _check_frame_invariants(p, fr, H):
+    forbidden = {(c, pc) for c in range(3) for pc in range(3)
+                 if math.isinf(oracle.DEFAULTS["prior_trans"][c][pc])}
+    for c in range(fr.q.shape[0]):
+        n = fr.counts[c]
+        st = fr.stixels[c, :n]
+        assert 1 <= n <= H
+        assert st[0]["v_bottom"] == 0 and st[-1]["v_top"] == H - 1
+        for i in range(n):
+            b, k = int(st[i]["v_bottom"]), int(st[i]["v_top"])
+            assert b <= k
+            if i:
+                assert b == st[i - 1]["v_top"] + 1
+                assert (int(st[i]["cls"]), int(st[i - 1]["cls"])) not in forbidden
+            S = int(fr.q[c, b:k + 1].astype(np.int64).sum())
+            assert st[i]["sum_q"] == S
+            assert st[i]["f"] == (S + 8 * (k - b + 1)) // (16 * (k - b + 1))
+            assert st[i]["disparity"] == S / (16.0 * (k - b + 1))
+        assert oracle.eval_segmentation(p, fr.q[c], st) == fr.cost[c]
+
+
+@pytest.mark.parametrize("seed", [1000, 1001, 1002])
+def test_frame_invariants_config1(seed):
+    cam = scenes.CONFIG1
+    sc = scenes.make_scene(cam, seed, n_obstacles=(3, 6))
+    p = oracle.make_params(cam)
+    fr = oracle.frame(p, sc.disparity, cap=cam.height)
+    _check_frame_invariants(p, fr, cam.height)
+
+
+def test_special_constant_column_is_one_object():
+    cam = scenes.Camera(40, 100, stixel_width=5, dmax=64, horizon_row=95)   # ground line 0..1 px
+    for d in [7, 20, 45]:
+        p = oracle.make_params(cam)
+        q = np.full(100, 16 * d, np.int16)
+        out = oracle.column(p, q)
+        assert _key(out.stixels) == [(0, 99, oracle.OBJECT)] and out.stixels[0]["f"] == d
+
+
+def test_special_ground_then_sky():
+    """A noise-free ground ramp below the horizon and zeros above it gives exactly
+    [ground, sky].  Near disparity 0 the truncated normaliser A_norm makes sky
+    cheaper than ground for disparities up to about 1.3 sigma, so the boundary
+    lies at most 2 sigma / alpha rows below the horizon (and never above it)."""
+    cam = scenes.CONFIG1
+    sc = scenes.make_scene(cam, 7, n_obstacles=(0, 0), noise_sigma=0, p_outlier=0, p_invalid=0)
+    p = oracle.make_params(cam)
+    fr = oracle.frame(p, sc.disparity)
+    H, hz = cam.height, cam.horizon_row
+    for c in range(fr.q.shape[0]):
+        st = fr.stixels[c, :fr.counts[c]]
+        assert [int(s["cls"]) for s in st] == [oracle.GROUND, oracle.SKY]
+        top_ground_row = H - 1 - int(st[0]["v_top"])
+        assert hz <= top_ground_row + 1 and top_ground_row - hz <= math.ceil(2.0 / cam.alpha)
+
+
+def test_special_all_zero_column_is_sky_when_sky_first_is_cheapest():
+    p = oracle.make_params(dmax=64, horizon_row=200, prior_first=(1.0, 0.2, 0.5))
+    out = oracle.column(p, np.zeros(80, np.int16))
+    assert _key(out.stixels) == [(0, 79, oracle.SKY)]
+
+
+def _truth_object_runs(sc, c):
+    """Maximal runs (image rows) of one obstacle disparity in reduced column c, top->bottom."""
+    s = sc.camera.stixel_width
+    col = sc.obj_disp[:, c * s]
+    lab = sc.labels[:, c * s]
+    runs, r = [], 0
+    H = col.shape[0]
+    while r < H:
+        if lab[r] == 0:
+            e = r
+            while e + 1 < H and lab[e + 1] == 0 and col[e + 1] == col[r]:
+                e += 1
+            runs.append((r, e, int(col[r])))
+            r = e + 1
+        else:
+            r += 1
+    return runs
+
+
+def _ground_run(lab, r, step):
+    """Length of the run of ground labels starting at image row r going in `step`."""
+    n = 0
+    while 0 <= r < lab.shape[0] and lab[r] == 1:
+        n += 1
+        r += step
+    return n
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_planted_obstacles_recovered(seed):
+    """Noise-free scenes with integer obstacle disparities (>= 8 rows tall, spans on
+    stixel columns): every obstacle comes back as one object stixel with the exact
+    disparity; its boundaries are exact next to sky or another object and within
+    one row next to a ground run of 8 or more rows."""
+    cam = scenes.CONFIG1
+    sc = scenes.make_scene(cam, 4242 + seed, n_obstacles=(3, 6), integer_disp=True, min_height=8,
+                           noise_sigma=0, p_outlier=0, p_invalid=0)
+    p = oracle.make_params(cam)
+    fr = oracle.frame(p, sc.disparity, cap=cam.height)
+    H = cam.height
+    s = cam.stixel_width
+    checked = 0
+    for c in range(fr.q.shape[0]):
+        st = fr.stixels[c, :fr.counts[c]]
+        objs = [(H - 1 - int(x["v_top"]), H - 1 - int(x["v_bottom"]), int(x["f"]))
+                for x in st if x["cls"] == oracle.OBJECT]
+        lab = sc.labels[:, c * s]
+        for top, bot, d in _truth_object_runs(sc, c):
+            if bot - top + 1 < 8:
+                continue
+            match = [o for o in objs if o[2] == d and not (o[1] < top or o[0] > bot)]
+            assert len(match) == 1, (c, (top, bot, d), objs)
+            t, b, _ = match[0]
+            # next to ground the boundary may move by one row; a ground strip shorter
+            # than 8 rows may be absorbed by the object (a stixel costs more priors
+            # than the strip's small residual), so that side is not checked
+            up = _ground_run(lab, top - 1, -1)
+            down = _ground_run(lab, bot + 1, +1)
+            if up == 0 or up >= 8:
+                assert abs(t - top) <= (1 if up else 0), (c, (top, bot, d), match[0])
+            if down == 0 or down >= 8:
+                assert abs(b - bot) <= (1 if down else 0), (c, (top, bot, d), match[0])
+            checked += 1
+    assert checked > 0
+
+
+def test_fixed_grid_effect_is_small():
+    """The fixed-point grids move a column's optimum by little: costs agree with the
+    plain-real model to 1e-3 relative on a noisy frame."""
+    cam = scenes.CONFIG1
+    sc = scenes.make_scene(cam, 1000)
+    fq = oracle.frame(oracle.make_params(cam, quantize=1), sc.disparity)
+    fu = oracle.frame(oracle.make_params(cam, quantize=0), sc.disparity)
+    rel = np.abs(fq.cost - fu.cost) / np.maximum(1.0, np.abs(fu.cost))
+    assert rel.max() < 1e-3

@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the stixel pipeline on GB300.
+
+Default workload: one 1024 x 440 FP32 disparity frame, stixel width 5,
+dmax 128 (the paper's headline size), through the plain per-frame launch:
+column reduction -> prefix LUTs -> DP + backtracking.  One step = one frame.
+Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (oracle/) on the host cores for the same
+workload and metric.  With N > 1 (torchrun) every rank runs an independent
+replica on its own GPU; there is no data exchange between ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "frames/s @1024x440 w=5"
+PAPER_FPS = 413.0          # Titan X (Maxwell), 1024x440, s = 5 (paper Sec. 6): context only
+OPS_PER_CELL = 20          # algorithmic integer ops per object DP candidate
+L2_FLUSH_BYTES = 256 << 20
+
+# DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by the sha1 of the kernel's source file at the time of the capture.  A
+# kernel whose source changed since reports null.
+NCU_TRAFFIC = {}
+
+
+def _sha(path):
+    with open(path, "rb") as fh:
+        return hashlib.sha1(fh.read()).hexdigest()[:12]
+
+
+def _traffic(kernel_file):
+    rec = NCU_TRAFFIC.get(os.path.basename(kernel_file))
+    if not rec:
+        return None
+    sha, nbytes = rec
+    return nbytes if sha == _sha(kernel_file) else None
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample budget")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_rate(cam, scene_fn, seconds, max_frames=64):
+    """Frames/s of the CPU oracle on host cores, over a bounded sample."""
+    import oracle
+    p = oracle.make_params(cam)
+    frames, t0 = 0, time.perf_counter()
+    while True:
+        sc = scene_fn(frames)
+        oracle.frame(p, sc.disparity, cap=64)
+        frames += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or frames >= max_frames:
+            return frames / el, frames, el
+
+
+# ----------------------------------------------------------------------------- ours
+
+def bench_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1610_04124_gb300 as S
+    import scenes
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    cam = scenes.CONFIG2
+    H, W, s, dmax = cam.height, cam.width, cam.stixel_width, cam.dmax
+    sc = scenes.make_scene(cam, 2000 + rank, n_obstacles=(8, 20))
+    params = S.default_params(cam)
+    h = S.Stixels(params)
+    h.reserve(H, W)
+    ncols, cap = h.output_shape(H, W)
+    P, F = S.lut_pitch(H), dmax + 1
+    disp = torch.from_numpy(sc.disparity).to(dev)
+    q = torch.zeros((ncols, H), dtype=torch.int16, device=dev)
+    pd = torch.zeros((ncols, P), dtype=torch.int32, device=dev)
+    pg, ps = torch.zeros_like(pd), torch.zeros_like(pd)
+    po = torch.zeros((ncols, F, P), dtype=torch.int32, device=dev)
+    out = h.alloc_output(H, W, dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        h.reduce(disp, q, stream)
+        S._check(S.lib().stixels_build_luts(h.handle, S._ptr(q), H, ncols, S._stream_ptr(stream), S._ptr(pd),
+                                            S._ptr(pg), S._ptr(ps), S._ptr(po)), "build_luts")
+        h.solve(pd, pg, ps, po, H, ncols, out, stream)
+
+    for i in range(args.warmup):
+        flush.fill_(float(i))
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    for i in range(K):
+        flush.fill_(float(i))                   # L2 flush between steps (not timed)
+        e = ev[i]
+        e[0].record(stream)
+        h.reduce(disp, q, stream)
+        e[1].record(stream)
+        S._check(S.lib().stixels_build_luts(h.handle, S._ptr(q), H, ncols, S._stream_ptr(stream), S._ptr(pd),
+                                            S._ptr(pg), S._ptr(ps), S._ptr(po)), "build_luts")
+        e[2].record(stream)
+        h.solve(pd, pg, ps, po, H, ncols, out, stream)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_step = [ev[i][0].elapsed_time(ev[i][3]) for i in range(K)]
+    t_red = [ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]
+    t_lut = [ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]
+    t_dp = [ev[i][2].elapsed_time(ev[i][3]) for i in range(K)]
+    total_ms = sum(t_step)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    frames = K * world
+    value = frames / (total_ms / 1000.0)
+    err = h.get_error(stream)
+
+    # end to end through the C ABI, host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(sc.disparity).pin_memory().numpy()
+        host_out = h.alloc_host_output(H, W, pinned=True)
+        for _ in range(3):
+            h.compute_host(host_in, host_out)
+        n_e2e = max(10, min(K, 200))
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            h.compute_host(host_in, host_out)
+        el = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([el], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = float(tt.item())
+        e2e = {"value": n_e2e * world / el, "unit": "frames/s", "h2d_bytes_per_step": H * W * 4,
+               "d2h_bytes_per_step": ncols * cap * 12 + ncols * 4 + ncols * 4, "steps": n_e2e}
+
+    if rank != 0:
+        h.close()
+        return None
+
+    peaks, peak_src = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    alu_peak = sms * 128 * sm_max * 1e6 / 1e12          # Tops/s, 128 INT32/FP32 lanes per SM
+    cells = ncols * H * (H + 1) // 2
+    dp_ms = statistics.mean(t_dp)
+    dp_tops = cells * OPS_PER_CELL / (dp_ms / 1000.0) / 1e12
+    lut_bytes = ncols * (F + 3) * P * 4 + ncols * H * 2
+    lut_ms = statistics.mean(t_lut)
+    lut_gbs = lut_bytes / (lut_ms / 1000.0) / 1e9
+    red_bytes = H * W * 4 + ncols * H * 2
+    red_ms = statistics.mean(t_red)
+    hbm = float(peaks.get("hbm_gbs") or 6800.0)
+    kdir = os.path.join(ROOT, "paper_1610_04124_gb300", "csrc")
+
+    cpu = None
+    if not args.no_cpu_baseline and args.cpu_seconds > 0:
+        fps, nfr, el = oracle_rate(cam, lambda i: scenes.make_scene(cam, 2100 + i, n_obstacles=(8, 20)),
+                                   args.cpu_seconds)
+        cpu = {"value": fps, "unit": "frames/s", "cores": host_cores(), "kind": "oracle",
+               "sample": f"{nfr} frames of 1024x440 s=5 dmax=128 (seeds 2100..{2100 + nfr - 1}), "
+                         f"columns spread over all host cores with OpenMP, {el:.1f} s"}
+
+    rec = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_FPS,
+        "vs_baseline_ref": "paper: 413 fps on a Titan X (Maxwell) at 1024x440, s=5 (other hardware; context)",
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "1024x440 s=5 dmax=128, one frame per launch sequence (paper-sized frame)",
+                   "H": H, "W": W, "stixel_width": s, "dmax": dmax, "frames_per_step": 1,
+                   "l2": "flushed between steps (256 MB write, untimed)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"kernel": "stixel_dp_kernel", "bound": "alu", "achieved": dp_tops, "peak": alu_peak,
+                     "unit": "Tops/s", "frac": dp_tops / alu_peak,
+                     "traffic": _traffic(os.path.join(kdir, "kernels_dp.cu")),
+                     "peak_source": f"{sms} SMs x 128 int32/fp32 lanes x {sm_max:.0f} MHz (max SM clock, {peak_src})",
+                     "work": f"{cells} object DP cells x {OPS_PER_CELL} ops"},
+        "roofline_luts": {"kernel": "prefix_lut_kernel", "bound": "hbm", "achieved": lut_gbs, "peak": hbm,
+                          "unit": "GB/s", "frac": lut_gbs / hbm, "traffic": _traffic(os.path.join(kdir, "kernels_luts.cu")),
+                          "peak_source": f"hbm_gbs ({peak_src})", "bytes": lut_bytes},
+        "roofline_reduce": {"kernel": "reduce_transpose_kernel", "bound": "hbm",
+                            "achieved": red_bytes / (red_ms / 1000.0) / 1e9, "peak": hbm, "unit": "GB/s",
+                            "frac": red_bytes / (red_ms / 1000.0) / 1e9 / hbm, "bytes": red_bytes},
+        "stages_ms": {"reduce": red_ms, "luts": lut_ms, "dp": dp_ms,
+                      "step_median": statistics.median(t_step), "step_p99": sorted(t_step)[int(0.99 * (K - 1))]},
+        "dp_cells_per_s": cells / (dp_ms / 1000.0),
+        "gpu_launches": 3 * K,
+        "clocks": clk,
+        "device_error_word": err,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+    }
+    h.close()
+    return rec
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def bench_reference(args, world, rank):
+    """The CPU oracle as the reference arm: same workload and metric, host cores."""
+    if rank != 0:
+        return None
+    import oracle
+    import scenes
+    cam = scenes.CONFIG2
+    p = oracle.make_params(cam)
+    sc = scenes.make_scene(cam, 2000, n_obstacles=(8, 20))
+    ncols = cam.width // cam.stixel_width
+    t0 = time.perf_counter()
+    oracle.frame(p, sc.disparity, cap=64)
+    t_frame = time.perf_counter() - t0
+    total = args.steps + args.warmup
+    budget = 150.0                                     # seconds for the whole run
+    frac = min(1.0, budget / max(total * t_frame, 1e-9))
+    sample_cols = max(1, min(ncols, int(math.ceil(frac * ncols))))
+    W_s = sample_cols * cam.stixel_width
+    sub = sc.disparity[:, :W_s].copy()
+    for _ in range(args.warmup):
+        oracle.frame(p, sub, cap=64)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.frame(p, sub, cap=64)
+    el = time.perf_counter() - t0
+    frames = args.steps * sample_cols / ncols
+    value = frames / el
+    sample = (f"each step: {sample_cols} of the {ncols} columns of a 1024x440 s=5 dmax=128 frame "
+              f"(seed 2000), scaled to frames; all host cores (OpenMP)")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_FPS, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "1024x440 s=5 dmax=128, one frame per step (paper-sized frame)",
+                       "H": cam.height, "W": cam.width, "stixel_width": cam.stixel_width, "dmax": cam.dmax},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": host_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_info()
+    if args.impl == "reference":
+        rec = bench_reference(args, world, rank)
+    else:
+        rec = bench_ours(args, world, rank, local)
+    if rec is not None and rank == 0:
+        print(json.dumps(rec), flush=True)
+
+
+if __name__ == "__main__":
+    main()

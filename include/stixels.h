@@ -1,0 +1,245 @@
+/*
+ * stixels.h -- C ABI of a GB300 (sm_103a) implementation of multi-stixel
+ * estimation, the method of "GPU-accelerated real-time stixel computation"
+ * (Hernandez-Juarez et al., arXiv 1610.04124).
+ *
+ * The library takes an FP32 disparity map (e.g. from semi-global matching),
+ * reduces every stixel-width column to one pixel per row (Sec. 5.1), builds the
+ * per-column cost look-up tables (Sec. 3.4, Sec. 5.2), and solves, per column,
+ * the MAP segmentation into ground, object and sky stixels with the dynamic
+ * program of Eq. 5-6 (Sec. 3.3, Sec. 5.3), followed by backtracking (Sec. 5.4).
+ *
+ * Conventions used throughout:
+ *   - Image rows: 0 = top row.  Columns are independent (Sec. 3).
+ *   - A disparity map is H x W FP32, row-major, contiguous (pitch W).
+ *     ncols = floor(W / stixel_width); the last W mod stixel_width pixels of
+ *     every row are ignored.
+ *   - Disparities are clamped to [0, dmax] (NaN -> 0) and put on a 1/16-pixel
+ *     grid ("Q4 code" = round-half-even(16 d)) before any other step.
+ *   - Costs are carried in exact fixed point: every per-pixel term and every
+ *     prior is rounded to a multiple of 2^-12 cost units, sums are exact int32
+ *     arithmetic (internal unit 2^-14).  Results are therefore deterministic
+ *     and independent of thread scheduling, and ties are broken exactly.
+ *   - "Device pointer" = memory the CUDA device can address (cudaMalloc,
+ *     torch CUDA tensors, managed memory).  Streams are cudaStream_t passed as
+ *     void*; NULL = the legacy default stream.
+ *
+ * Errors: every function returns an int status (enum stixels_status).  No
+ * function throws, aborts, or traps on the device.  Kernels that detect a
+ * per-column condition (output capacity exceeded, no feasible segmentation)
+ * record it in a per-handle device error word that stixels_get_error() reads.
+ *
+ * Threading: a stixels_t handle is not re-entrant -- do not call compute-type
+ * functions on one handle from several host threads at once.  Different
+ * handles are independent.  The server functions (stixels_submit/poll) are
+ * thread-safe.
+ */
+#ifndef STIXELS_H
+#define STIXELS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STIXELS_ABI_VERSION 1
+#define STIXELS_MAX_STIXEL_WIDTH 16
+#define STIXELS_MAX_DMAX 255
+#define STIXELS_MAX_HEIGHT 2048
+
+/* Status codes. */
+enum stixels_status {
+    STIXELS_OK = 0,
+    STIXELS_E_INVALID_ARG = 1,   /* a parameter or size is out of range (see each function) */
+    STIXELS_E_OOM = 2,           /* device or pinned host allocation failed, or over budget */
+    STIXELS_E_CUDA = 3,          /* a CUDA runtime call failed (launch, copy, sync) */
+    STIXELS_E_CAPACITY = 4,      /* a column had more stixels than the output capacity */
+    STIXELS_E_NOT_READY = 5,     /* the ticket's result is not finished yet */
+    STIXELS_E_TIMEOUT = 6,       /* a wait ran out of time */
+    STIXELS_E_REJECTED = 7,      /* admission refused (no slot / memory budget) */
+    STIXELS_E_DEVICE_FAULT = 8   /* a kernel reported an internal error (e.g. infeasible column) */
+};
+
+/* Stixel classes (Sec. 3.1); this order is also the tie-break order. */
+enum stixels_class { STIXELS_OBJECT = 0, STIXELS_GROUND = 1, STIXELS_SKY = 2 };
+
+/* Bits of the device error word. */
+#define STIXELS_ERR_CAPACITY 1u    /* some column's stixel count exceeded the capacity */
+#define STIXELS_ERR_INFEASIBLE 2u  /* some column has no finite-cost segmentation */
+
+/*
+ * Model parameters (Sec. 3; Eq. 3 for the sensor model; the five prior
+ * constraints of Sec. 3: BIC, gravity, ordering, staggering, diving).  The
+ * paper takes the prior values from Pfeiffer's thesis, which it does not
+ * reproduce; stixels_params_default() returns this library's own defaults.
+ * All priors are -ln P costs >= 0; INFINITY marks a forbidden configuration.
+ */
+typedef struct stixels_params {
+    float focal_px;            /* focal length in px (only for reported depth; not used by the DP) */
+    float baseline_m;          /* stereo baseline in m */
+    float camera_height_m;     /* camera height above the ground plane in m (> 0) */
+    float pitch_rad;           /* camera pitch in rad */
+    int32_t horizon_row;       /* image row (0 = top) of the horizon */
+    int32_t stixel_width;      /* s in [1, STIXELS_MAX_STIXEL_WIDTH] */
+    int32_t dmax;              /* largest disparity, [1, STIXELS_MAX_DMAX]; d_range = dmax */
+    float p_out;               /* outlier rate of the sensor model, (0, 1) */
+    float sigma_ground;        /* disparity noise (px) of each class model, > 0 */
+    float sigma_object;
+    float sigma_sky;
+    float prior_first[3];      /* cost of the class of the bottom stixel: object, ground, sky */
+    float prior_trans[3][3];   /* [class above][class below] transition cost */
+    float cost_new_stixel;     /* BIC: cost added once per stixel */
+    float cost_gravity;        /* object directly above ground, nearer than the ground at its base */
+    float eps_gravity;         /*   tolerance (px) */
+    float cost_diving;         /* object directly above ground, farther than the ground at its base */
+    float eps_diving;          /*   tolerance (px) */
+    float cost_order;          /* object directly above an object, nearer than it */
+    float eps_order;           /*   tolerance (px) */
+    int32_t reduce_mode;       /* 0 = median of the s pixels (default), 1 = mean (paper Sec. 5.1) */
+    int32_t max_stixels_per_col; /* output capacity per column, >= 1 */
+} stixels_params_t;
+
+/* One output stixel: 12 bytes. */
+typedef struct stixel {
+    int16_t row_top;           /* image row of the stixel's top pixel (0 = top of image) */
+    int16_t row_bottom;        /* image row of its bottom pixel (row_top <= row_bottom) */
+    uint8_t cls;               /* enum stixels_class */
+    uint8_t flags;             /* reserved, 0 */
+    int16_t reserved;          /* 0 */
+    float disparity;           /* exact mean of the stixel's Q4 disparities, in px */
+} stixel_t;
+
+/* Output buffers of one frame.  All pointers are device pointers owned by the
+ * caller.  stixels: ncols * capacity records, column c at [c * capacity],
+ * listed bottom -> top.  counts[c] = number of stixels of column c (it may
+ * exceed capacity; then only the bottom `capacity` are written and the error
+ * word gets STIXELS_ERR_CAPACITY).  column_cost (optional, may be NULL): the
+ * column's minimum cost in cost units.  column_cost_fixed (optional): the same
+ * cost exactly, as an integer in units of 2^-14. */
+typedef struct stixels_output {
+    stixel_t* stixels;
+    int32_t* counts;
+    float* column_cost;
+    int32_t* column_cost_fixed;
+    int32_t ncols;
+    int32_t capacity;
+} stixels_output_t;
+
+typedef struct stixels_s* stixels_t;
+
+/* Fill *p with the library's default parameters (320x120 camera of the test
+ * workload; adjust the camera fields for your own).  Returns OK, or
+ * INVALID_ARG if p is NULL. */
+int stixels_params_default(stixels_params_t* p);
+
+/* Create a handle for one camera / parameter set (Sec. 3.4: the offline LUTs
+ * -- sensor-model constants and per-class residual tables -- are built here in
+ * FP64 and uploaded once to the current CUDA device, where they stay resident).
+ * Fails with INVALID_ARG for out-of-range parameters (ranges above; first and
+ * transition priors in [0, 1000] or +INFINITY; BIC and the gravity, diving and
+ * ordering costs finite in [0, 1000]; eps_gravity, eps_diving in [0, 100];
+ * |eps_order| <= 100; the residual tables must reach the outlier cost within
+ * dmax px), OOM, or CUDA.  The handle is bound to
+ * the device that was current at creation; call it with that device current. */
+int stixels_create(const stixels_params_t* params, stixels_t* out_handle);
+
+/* Release the handle and all its device memory.  Waits for work the handle
+ * launched to finish.  NULL is accepted. */
+int stixels_destroy(stixels_t h);
+
+/* Output shape for an H x W frame: *ncols = floor(W / s), *capacity =
+ * max_stixels_per_col. */
+int stixels_output_shape(stixels_t h, int H, int W, int* ncols, int* capacity);
+
+/* Pre-allocate the handle's workspace and per-height tables for frames up to
+ * H x W, so that later compute calls allocate nothing (and can be captured in a
+ * CUDA graph).  Synchronous.  INVALID_ARG if H > STIXELS_MAX_HEIGHT or the
+ * fixed-point budget check fails: H * max(C_out, -min K) + 3 * (largest prior
+ * of one stixel incl. penalties) must stay below 16384 cost units (about
+ * H <= 2000 with the default model). */
+int stixels_reserve(stixels_t h, int H, int W);
+
+/*
+ * Full pipeline on one frame (Sec. 5.1 -> 5.2 -> 5.3 -> 5.4), asynchronous on
+ * `stream`: column reduction + transpose, prefix LUTs, DP + backtracking.
+ * d_disparity: device pointer, H x W FP32 row-major; must stay valid until the
+ * stream reaches this work.  out: device buffers sized per stixels_output_shape
+ * (out->ncols and out->capacity must equal it).  If the workspace is too small
+ * it is grown first (a synchronous allocation).  H == 0 or ncols == 0 is a no-op.
+ * Returns OK once the kernels are enqueued; per-column conditions are reported
+ * through stixels_get_error().
+ */
+int stixels_compute(stixels_t h, const float* d_disparity, int H, int W, void* stream,
+                    const stixels_output_t* out);
+
+/*
+ * Same pipeline from HOST memory to HOST memory, synchronous: copies the frame
+ * to the device, runs stixels_compute on the handle's own stream, copies the
+ * results back and waits.  h_stixels: ncols * capacity records; h_counts:
+ * ncols; h_cost (optional): ncols floats.  Pinned (page-locked) host buffers
+ * give full copy bandwidth; pageable ones work but are slower.  Returns the
+ * compute status, or CAPACITY / DEVICE_FAULT if the error word was set.
+ */
+int stixels_compute_host(stixels_t h, const float* h_disparity, int H, int W,
+                         stixel_t* h_stixels, int32_t* h_counts, float* h_cost);
+
+/* Read and clear the handle's device error word (STIXELS_ERR_* bits) after
+ * synchronising `stream`. */
+int stixels_get_error(stixels_t h, void* stream, uint32_t* flags);
+
+/* ---- individual stages (the same kernels stixels_compute launches) ---- */
+
+/* Row pitch (in int32 elements) of the prefix LUTs for height H:
+ * the smallest multiple of 4 that is >= H + 1. */
+int stixels_lut_pitch(int H);
+
+/* Stage 1 (Sec. 5.1): column reduction + transpose.  d_q: device, ncols x H
+ * int16 Q4 codes, column c at d_q[c * H + v], v = H-1-r (v = 0 is the bottom
+ * image row). */
+int stixels_reduce(stixels_t h, const float* d_disparity, int H, int W, void* stream, int16_t* d_q);
+
+/* Stage 2 (Sec. 3.4, Sec. 5.2): per-column prefix LUTs from Q4 codes d_q
+ * (layout of stixels_reduce).  With P = stixels_lut_pitch(H) and F = dmax + 1:
+ *   d_pd[c * P + j]             = sum of q over rows v < j           (Q4 units)
+ *   d_pg[c * P + j], d_ps[...]  = sum of ground / sky pixel costs over v < j
+ *   d_po[(c * F + f) * P + j]   = sum of object pixel costs at integer
+ *                                 disparity f over v < j
+ * Costs in units of 2^-14 (every pixel cost is a multiple of 4).  Entries
+ * j in (H, P) repeat the total. */
+int stixels_build_luts(stixels_t h, const int16_t* d_q, int H, int ncols, void* stream,
+                       int32_t* d_pd, int32_t* d_pg, int32_t* d_ps, int32_t* d_po);
+
+/* Stage 3 (Sec. 3.3, Sec. 5.3-5.4): DP + backtracking from the LUTs of stage 2
+ * (same layout); writes `out` as stixels_compute does. */
+int stixels_solve(stixels_t h, const int32_t* d_pd, const int32_t* d_pg, const int32_t* d_ps,
+                  const int32_t* d_po, int H, int ncols, void* stream, const stixels_output_t* out);
+
+/* Build, on the host only (no CUDA call), the fixed-point model tables that
+ * stixels_create would upload for `params`, plus the row tables for height H,
+ * into caller-owned host arrays (for inspection and tests).  Returns
+ * INVALID_ARG for parameters stixels_create would reject, or for H outside
+ * [0, STIXELS_MAX_HEIGHT].  Cost values in 2^-14 units, forbidden /
+ * infinite entries = 2^29.  Sizes and meaning:
+ *   k_obj[dmax+1]    normalisation constant K (Eq. 4) of the object model at integer f
+ *   g_obj, g_ground, g_sky [16*dmax+1]   residual term (e/16)^2 / (2 sigma^2) of each
+ *                    class at Q4 residual e
+ *   fgq[H]           ground-model disparity at bottom-up row v, Q4 code
+ *   k_ground[H]      K of the ground model at row v
+ *   scalars[STIXELS_N_SCALARS] = { C_out, K_sky, first[object, ground, sky],
+ *                    trans[above][below] row-major (9), gravity, diving, ordering
+ *                    penalties, eps_gravity, eps_diving, eps_order (Q4 codes) }
+ * Any pointer may be NULL. */
+#define STIXELS_N_SCALARS 20
+int stixels_model_tables(const stixels_params_t* params, int H, int32_t* k_obj, int32_t* g_obj,
+                         int32_t* g_ground, int32_t* g_sky, int32_t* fgq, int32_t* k_ground,
+                         int32_t* scalars);
+
+/* Human-readable name of a status code (static storage). */
+const char* stixels_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STIXELS_H */

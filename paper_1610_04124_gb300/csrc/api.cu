@@ -1,0 +1,432 @@
+// api.cu -- the C ABI of stixels.h: handles, workspace, per-frame pipeline.
+#include <stdlib.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+#include "model.h"
+
+using namespace stx;
+
+namespace {
+
+// Per-height row tables resident on the device.
+struct RowsBuf {
+    int32_t* d = nullptr;   // fgq[H] followed by k_ground[H]
+    int H = 0;
+};
+
+struct Workspace {
+    void* base = nullptr;
+    size_t bytes = 0;
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Layout of one frame's intermediates inside a workspace.
+struct FrameLayout {
+    size_t q, pd, pg, ps, po, total;
+};
+
+FrameLayout frame_layout(int H, int ncols, int F)
+{
+    const int P = lut_pitch(H);
+    FrameLayout L;
+    size_t off = 0;
+    L.q = off;  off = align_up(off + sizeof(int16_t) * (size_t)ncols * H, 256);
+    L.pd = off; off = align_up(off + sizeof(int32_t) * (size_t)ncols * P, 256);
+    L.pg = off; off = align_up(off + sizeof(int32_t) * (size_t)ncols * P, 256);
+    L.ps = off; off = align_up(off + sizeof(int32_t) * (size_t)ncols * P, 256);
+    L.po = off; off = align_up(off + sizeof(int32_t) * (size_t)ncols * F * P, 256);
+    L.total = off;
+    return L;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? STIXELS_OK : (e == cudaErrorMemoryAllocation ? STIXELS_E_OOM : STIXELS_E_CUDA); }
+
+}  // namespace
+
+struct stixels_s {
+    int device = 0;
+    HostModel hm;
+    int32_t* d_tables = nullptr;       // k_obj | g_obj | g_ground | g_sky
+    ModelDev md;
+    std::map<int, RowsBuf> rows;       // per height
+    Workspace ws;
+    uint32_t* d_err = nullptr;
+    cudaStream_t stream = nullptr;     // own stream for compute_host
+    // device buffers for compute_host
+    float* d_in = nullptr;
+    size_t in_bytes = 0;
+    void* d_out = nullptr;
+    size_t out_bytes = 0;
+};
+
+namespace {
+
+int ensure_rows(stixels_t h, int H, RowsDev* out)
+{
+    auto it = h->rows.find(H);
+    if (it == h->rows.end()) {
+        std::vector<int32_t> fgq, kg;
+        build_rows(h->hm, H, &fgq, &kg);
+        if (!budget_ok(h->hm, H, kg)) return STIXELS_E_INVALID_ARG;
+        RowsBuf rb;
+        rb.H = H;
+        cudaError_t e = cudaMalloc(&rb.d, sizeof(int32_t) * 2 * (size_t)H);
+        if (e != cudaSuccess) return cuda_status(e);
+        std::vector<int32_t> buf(2 * (size_t)H);
+        memcpy(buf.data(), fgq.data(), sizeof(int32_t) * H);
+        memcpy(buf.data() + H, kg.data(), sizeof(int32_t) * H);
+        e = cudaMemcpy(rb.d, buf.data(), sizeof(int32_t) * 2 * (size_t)H, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cudaFree(rb.d); return cuda_status(e); }
+        it = h->rows.emplace(H, rb).first;
+    }
+    out->fgq = it->second.d;
+    out->k_ground = it->second.d + H;
+    return STIXELS_OK;
+}
+
+int ensure_workspace(stixels_t h, size_t bytes)
+{
+    if (h->ws.bytes >= bytes) return STIXELS_OK;
+    if (h->ws.base) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_status(e);
+        cudaFree(h->ws.base);
+        h->ws.base = nullptr;
+        h->ws.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&h->ws.base, bytes);
+    if (e != cudaSuccess) { h->ws.base = nullptr; return cuda_status(e); }
+    h->ws.bytes = bytes;
+    return STIXELS_OK;
+}
+
+int check_frame(stixels_t h, int H, int W)
+{
+    if (!h) return STIXELS_E_INVALID_ARG;
+    if (H < 0 || W < 0 || H > STIXELS_MAX_HEIGHT) return STIXELS_E_INVALID_ARG;
+    if (W > (1 << 24)) return STIXELS_E_INVALID_ARG;
+    return STIXELS_OK;
+}
+
+FrameGeom geom(stixels_t h, int H, int W)
+{
+    FrameGeom g;
+    g.H = H;
+    g.W = W;
+    g.s = h->hm.p.stixel_width;
+    g.ncols = W / g.s;
+    g.P = lut_pitch(H);
+    return g;
+}
+
+int check_output(stixels_t h, const FrameGeom& g, const stixels_output_t* out)
+{
+    if (!out) return STIXELS_E_INVALID_ARG;
+    if (out->ncols != g.ncols || out->capacity != h->hm.p.max_stixels_per_col) return STIXELS_E_INVALID_ARG;
+    if (g.ncols > 0 && (!out->stixels || !out->counts)) return STIXELS_E_INVALID_ARG;
+    return STIXELS_OK;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int stixels_params_default(stixels_params_t* p)
+{
+    if (!p) return STIXELS_E_INVALID_ARG;
+    default_params(p);
+    return STIXELS_OK;
+}
+
+int stixels_create(const stixels_params_t* params, stixels_t* out_handle)
+{
+    if (!params || !out_handle) return STIXELS_E_INVALID_ARG;
+    *out_handle = nullptr;
+    stixels_s* h = new (std::nothrow) stixels_s();
+    if (!h) return STIXELS_E_OOM;
+    int rc = build_model(params, &h->hm);
+    if (rc != STIXELS_OK) { delete h; return rc; }
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) { delete h; return cuda_status(e); }
+    const HostModel& m = h->hm;
+    const size_t n_tab = (size_t)(m.dmax + 1) + 3 * (size_t)(m.emax + 1);
+    e = cudaMalloc(&h->d_tables, sizeof(int32_t) * n_tab);
+    if (e == cudaSuccess) {
+        std::vector<int32_t> buf;
+        buf.reserve(n_tab);
+        buf.insert(buf.end(), m.k_obj.begin(), m.k_obj.end());
+        buf.insert(buf.end(), m.g_obj.begin(), m.g_obj.end());
+        buf.insert(buf.end(), m.g_ground.begin(), m.g_ground.end());
+        buf.insert(buf.end(), m.g_sky.begin(), m.g_sky.end());
+        e = cudaMemcpy(h->d_tables, buf.data(), sizeof(int32_t) * n_tab, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        stixels_destroy(h);
+        return cuda_status(e);
+    }
+    ModelDev& d = h->md;
+    d.dmax = m.dmax;
+    d.emax = m.emax;
+    d.c_out = m.c_out;
+    d.k_sky = m.k_sky;
+    for (int c = 0; c < 3; ++c) {
+        d.first[c] = m.first[c];
+        for (int q = 0; q < 3; ++q) d.trans[c][q] = m.trans[c][q];
+    }
+    d.pen_grav = m.pen_grav;
+    d.pen_div = m.pen_div;
+    d.pen_ord = m.pen_ord;
+    d.eps_g = m.eps_g;
+    d.eps_d = m.eps_d;
+    d.eps_o = m.eps_o;
+    d.k_obj = h->d_tables;
+    d.g_obj = d.k_obj + (m.dmax + 1);
+    d.g_ground = d.g_obj + (m.emax + 1);
+    d.g_sky = d.g_ground + (m.emax + 1);
+    *out_handle = h;
+    return STIXELS_OK;
+}
+
+int stixels_destroy(stixels_t h)
+{
+    if (!h) return STIXELS_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : h->rows) cudaFree(kv.second.d);
+    cudaFree(h->ws.base);
+    cudaFree(h->d_tables);
+    cudaFree(h->d_err);
+    cudaFree(h->d_in);
+    cudaFree(h->d_out);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete h;
+    return STIXELS_OK;
+}
+
+int stixels_output_shape(stixels_t h, int H, int W, int* ncols, int* capacity)
+{
+    int rc = check_frame(h, H, W);
+    if (rc) return rc;
+    if (ncols) *ncols = W / h->hm.p.stixel_width;
+    if (capacity) *capacity = h->hm.p.max_stixels_per_col;
+    return STIXELS_OK;
+}
+
+int stixels_lut_pitch(int H) { return H < 0 ? 0 : lut_pitch(H); }
+
+int stixels_reserve(stixels_t h, int H, int W)
+{
+    int rc = check_frame(h, H, W);
+    if (rc) return rc;
+    if (H == 0) return STIXELS_OK;
+    RowsDev r;
+    rc = ensure_rows(h, H, &r);
+    if (rc) return rc;
+    const FrameGeom g = geom(h, H, W);
+    return ensure_workspace(h, frame_layout(H, g.ncols, h->hm.dmax + 1).total);
+}
+
+int stixels_reduce(stixels_t h, const float* d_disparity, int H, int W, void* stream, int16_t* d_q)
+{
+    int rc = check_frame(h, H, W);
+    if (rc) return rc;
+    const FrameGeom g = geom(h, H, W);
+    if (g.H == 0 || g.ncols == 0) return STIXELS_OK;
+    if (!d_disparity || !d_q) return STIXELS_E_INVALID_ARG;
+    return cuda_status(launch_reduce(d_disparity, g, h->hm.dmax, h->hm.p.reduce_mode, d_q, (cudaStream_t)stream));
+}
+
+int stixels_build_luts(stixels_t h, const int16_t* d_q, int H, int ncols, void* stream, int32_t* d_pd,
+                       int32_t* d_pg, int32_t* d_ps, int32_t* d_po)
+{
+    if (!h || H < 0 || H > STIXELS_MAX_HEIGHT || ncols < 0) return STIXELS_E_INVALID_ARG;
+    if (H == 0 || ncols == 0) return STIXELS_OK;
+    if (!d_q || !d_pd || !d_pg || !d_ps || !d_po) return STIXELS_E_INVALID_ARG;
+    if (!aligned16(d_pd) || !aligned16(d_pg) || !aligned16(d_ps) || !aligned16(d_po)) return STIXELS_E_INVALID_ARG;
+    RowsDev r;
+    int rc = ensure_rows(h, H, &r);
+    if (rc) return rc;
+    FrameGeom g;
+    g.H = H; g.W = ncols * h->hm.p.stixel_width; g.s = h->hm.p.stixel_width; g.ncols = ncols; g.P = lut_pitch(H);
+    return cuda_status(launch_luts(d_q, g, h->md, r, d_pd, d_pg, d_ps, d_po, (cudaStream_t)stream));
+}
+
+int stixels_solve(stixels_t h, const int32_t* d_pd, const int32_t* d_pg, const int32_t* d_ps, const int32_t* d_po,
+                  int H, int ncols, void* stream, const stixels_output_t* out)
+{
+    if (!h || H < 0 || H > STIXELS_MAX_HEIGHT || ncols < 0) return STIXELS_E_INVALID_ARG;
+    FrameGeom g;
+    g.H = H; g.W = ncols * h->hm.p.stixel_width; g.s = h->hm.p.stixel_width; g.ncols = ncols; g.P = lut_pitch(H);
+    int rc = check_output(h, g, out);
+    if (rc) return rc;
+    if (H == 0 || ncols == 0) return STIXELS_OK;
+    if (!d_pd || !d_pg || !d_ps || !d_po) return STIXELS_E_INVALID_ARG;
+    RowsDev r;
+    rc = ensure_rows(h, H, &r);
+    if (rc) return rc;
+    return cuda_status(launch_dp(d_pd, d_pg, d_ps, d_po, g, h->md, r, *out, h->d_err, (cudaStream_t)stream));
+}
+
+int stixels_compute(stixels_t h, const float* d_disparity, int H, int W, void* stream, const stixels_output_t* out)
+{
+    int rc = check_frame(h, H, W);
+    if (rc) return rc;
+    const FrameGeom g = geom(h, H, W);
+    rc = check_output(h, g, out);
+    if (rc) return rc;
+    if (g.H == 0 || g.ncols == 0) return STIXELS_OK;
+    if (!d_disparity) return STIXELS_E_INVALID_ARG;
+    RowsDev r;
+    rc = ensure_rows(h, H, &r);
+    if (rc) return rc;
+    const FrameLayout L = frame_layout(H, g.ncols, h->hm.dmax + 1);
+    rc = ensure_workspace(h, L.total);
+    if (rc) return rc;
+    char* ws = (char*)h->ws.base;
+    int16_t* q = (int16_t*)(ws + L.q);
+    int32_t* pd = (int32_t*)(ws + L.pd);
+    int32_t* pg = (int32_t*)(ws + L.pg);
+    int32_t* ps = (int32_t*)(ws + L.ps);
+    int32_t* po = (int32_t*)(ws + L.po);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_reduce(d_disparity, g, h->hm.dmax, h->hm.p.reduce_mode, q, st);
+    if (e == cudaSuccess) e = launch_luts(q, g, h->md, r, pd, pg, ps, po, st);
+    if (e == cudaSuccess) e = launch_dp(pd, pg, ps, po, g, h->md, r, *out, h->d_err, st);
+    return cuda_status(e);
+}
+
+int stixels_get_error(stixels_t h, void* stream, uint32_t* flags)
+{
+    if (!h || !flags) return STIXELS_E_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    uint32_t v = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&v, h->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(uint32_t));
+    if (e != cudaSuccess) return cuda_status(e);
+    *flags = v;
+    return STIXELS_OK;
+}
+
+int stixels_compute_host(stixels_t h, const float* h_disparity, int H, int W, stixel_t* h_stixels,
+                         int32_t* h_counts, float* h_cost)
+{
+    int rc = check_frame(h, H, W);
+    if (rc) return rc;
+    const FrameGeom g = geom(h, H, W);
+    if (g.H == 0 || g.ncols == 0) return STIXELS_OK;
+    if (!h_disparity || !h_stixels || !h_counts) return STIXELS_E_INVALID_ARG;
+    const size_t in_bytes = sizeof(float) * (size_t)H * W;
+    const int cap = h->hm.p.max_stixels_per_col;
+    const size_t st_bytes = align_up(sizeof(stixel_t) * (size_t)g.ncols * cap, 256);
+    const size_t cnt_bytes = align_up(sizeof(int32_t) * (size_t)g.ncols, 256);
+    const size_t cost_bytes = align_up(sizeof(float) * (size_t)g.ncols, 256);
+    const size_t out_bytes = st_bytes + cnt_bytes + cost_bytes;
+    cudaError_t e = cudaSuccess;
+    if (h->in_bytes < in_bytes) {
+        cudaFree(h->d_in);
+        h->d_in = nullptr;
+        h->in_bytes = 0;
+        e = cudaMalloc(&h->d_in, in_bytes);
+        if (e != cudaSuccess) return cuda_status(e);
+        h->in_bytes = in_bytes;
+    }
+    if (h->out_bytes < out_bytes) {
+        cudaFree(h->d_out);
+        h->d_out = nullptr;
+        h->out_bytes = 0;
+        e = cudaMalloc(&h->d_out, out_bytes);
+        if (e != cudaSuccess) return cuda_status(e);
+        h->out_bytes = out_bytes;
+    }
+    stixels_output_t out;
+    out.stixels = (stixel_t*)h->d_out;
+    out.counts = (int32_t*)((char*)h->d_out + st_bytes);
+    out.column_cost = (float*)((char*)h->d_out + st_bytes + cnt_bytes);
+    out.column_cost_fixed = nullptr;
+    out.ncols = g.ncols;
+    out.capacity = cap;
+    e = cudaMemcpyAsync(h->d_in, h_disparity, in_bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    rc = stixels_compute(h, h->d_in, H, W, h->stream, &out);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(h_counts, out.counts, sizeof(int32_t) * g.ncols, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h_stixels, out.stixels, sizeof(stixel_t) * (size_t)g.ncols * cap, cudaMemcpyDeviceToHost,
+                            h->stream);
+    if (e == cudaSuccess && h_cost)
+        e = cudaMemcpyAsync(h_cost, out.column_cost, sizeof(float) * g.ncols, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    uint32_t flags = 0;
+    rc = stixels_get_error(h, h->stream, &flags);
+    if (rc) return rc;
+    if (flags & STIXELS_ERR_INFEASIBLE) return STIXELS_E_DEVICE_FAULT;
+    if (flags & STIXELS_ERR_CAPACITY) return STIXELS_E_CAPACITY;
+    return STIXELS_OK;
+}
+
+int stixels_model_tables(const stixels_params_t* params, int H, int32_t* k_obj, int32_t* g_obj,
+                         int32_t* g_ground, int32_t* g_sky, int32_t* fgq, int32_t* k_ground, int32_t* scalars)
+{
+    if (!params || H < 0 || H > STIXELS_MAX_HEIGHT) return STIXELS_E_INVALID_ARG;
+    HostModel m;
+    int rc = build_model(params, &m);
+    if (rc) return rc;
+    if (k_obj) memcpy(k_obj, m.k_obj.data(), sizeof(int32_t) * m.k_obj.size());
+    if (g_obj) memcpy(g_obj, m.g_obj.data(), sizeof(int32_t) * m.g_obj.size());
+    if (g_ground) memcpy(g_ground, m.g_ground.data(), sizeof(int32_t) * m.g_ground.size());
+    if (g_sky) memcpy(g_sky, m.g_sky.data(), sizeof(int32_t) * m.g_sky.size());
+    if (fgq || k_ground) {
+        std::vector<int32_t> f, k;
+        build_rows(m, H, &f, &k);
+        if (fgq) memcpy(fgq, f.data(), sizeof(int32_t) * H);
+        if (k_ground) memcpy(k_ground, k.data(), sizeof(int32_t) * H);
+    }
+    if (scalars) {
+        int32_t* s = scalars;
+        s[0] = m.c_out;
+        s[1] = m.k_sky;
+        for (int c = 0; c < 3; ++c) s[2 + c] = m.first[c];
+        for (int c = 0; c < 3; ++c)
+            for (int q = 0; q < 3; ++q) s[5 + 3 * c + q] = m.trans[c][q];
+        s[14] = m.pen_grav;
+        s[15] = m.pen_div;
+        s[16] = m.pen_ord;
+        s[17] = m.eps_g;
+        s[18] = m.eps_d;
+        s[19] = m.eps_o;
+    }
+    return STIXELS_OK;
+}
+
+const char* stixels_status_string(int status)
+{
+    switch (status) {
+        case STIXELS_OK: return "ok";
+        case STIXELS_E_INVALID_ARG: return "invalid argument";
+        case STIXELS_E_OOM: return "out of memory";
+        case STIXELS_E_CUDA: return "CUDA error";
+        case STIXELS_E_CAPACITY: return "stixel capacity exceeded";
+        case STIXELS_E_NOT_READY: return "not ready";
+        case STIXELS_E_TIMEOUT: return "timeout";
+        case STIXELS_E_REJECTED: return "rejected by admission control";
+        case STIXELS_E_DEVICE_FAULT: return "device-side error";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,61 @@
+// internal.h -- shared declarations of the stixel library's host code and kernels.
+#pragma once
+
+#include <stdint.h>
+
+#include <cuda_runtime.h>
+
+#include "stixels.h"
+
+namespace stx {
+
+// Fixed-point cost arithmetic.  Costs are int32 in units of 2^-14; every
+// per-pixel term and every prior is a multiple of 4 (i.e. on the 2^-12 grid),
+// so the two low bits of a candidate cost are free to carry the code of the
+// previous class (0 object, 1 ground, 2 sky, 3 none = first stixel).  A
+// packed value (cost + code) then orders candidates by (cost, code).
+constexpr int32_t kUnitsPerCost = 16384;         // 2^14
+constexpr int32_t kBig = 1 << 29;                // infeasible / forbidden
+constexpr int32_t kFiniteBudget = 1 << 28;       // |finite cost| bound checked by the host
+constexpr int32_t kNoneCode = 3;
+
+// Per-handle model, resident on the device (the "offline" LUTs of Sec. 3.4)
+// plus the scalars every kernel needs.  Passed to kernels by value.
+struct ModelDev {
+    int32_t dmax;            // F = dmax + 1 object disparities
+    int32_t emax;            // 16 * dmax: largest tabulated Q4 residual
+    int32_t c_out;           // outlier branch of Eq. 4
+    int32_t k_sky;           // K of the sky model (f = 0)
+    int32_t first[3];        // first-stixel prior + BIC, per class
+    int32_t trans[3][3];     // [above][below] transition prior + BIC
+    int32_t pen_grav, pen_div, pen_ord;
+    int32_t eps_g, eps_d, eps_o;     // Q4 tolerances
+    const int32_t* k_obj;    // [dmax + 1]
+    const int32_t* g_obj;    // [emax + 1]
+    const int32_t* g_ground; // [emax + 1]
+    const int32_t* g_sky;    // [emax + 1]
+};
+
+// Per-(handle, H) row tables.
+struct RowsDev {
+    const int32_t* fgq;      // [H] ground-model Q4 disparity at bottom-up row v
+    const int32_t* k_ground; // [H]
+};
+
+struct FrameGeom {
+    int H, W, s, ncols;
+    int P;                   // LUT pitch (int32 elements), multiple of 4, >= H + 1
+};
+
+inline int lut_pitch(int H) { return ((H + 1) + 3) & ~3; }
+
+// ---- kernel launchers (kernels_*.cu); all return cudaGetLastError() ----
+cudaError_t launch_reduce(const float* disp, const FrameGeom& g, int dmax, int mode, int16_t* q,
+                          cudaStream_t st);
+cudaError_t launch_luts(const int16_t* q, const FrameGeom& g, const ModelDev& m, const RowsDev& r,
+                        int32_t* pd, int32_t* pg, int32_t* ps, int32_t* po, cudaStream_t st);
+cudaError_t launch_dp(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po,
+                      const FrameGeom& g, const ModelDev& m, const RowsDev& r,
+                      const stixels_output_t& out, uint32_t* err, cudaStream_t st);
+
+}  // namespace stx

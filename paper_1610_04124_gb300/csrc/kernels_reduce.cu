@@ -1,0 +1,120 @@
+// kernels_reduce.cu -- column reduction and transpose (paper Sec. 5.1).
+//
+// Every stixel-width column of the H x W disparity map becomes one column of
+// H Q4 codes: each pixel is clamped to [0, dmax] (NaN -> 0) and rounded to the
+// 1/16-px grid, then the s codes of a row are reduced to their lower median
+// (rank (s-1)/2; the median commutes with the monotone quantisation) or to
+// their mean rounded half up (the paper's average).  The output is stored
+// column-major and bottom-up (q[c * H + v], v = H-1-r) -- the layout the LUT
+// and DP stages read.
+//
+// A 256-thread CTA reduces a tile of 32 columns x 32 rows: a warp reads 32
+// consecutive groups of s pixels of one row (32 s contiguous floats, so the
+// warp's loads cover whole cache lines), the 32 x 32 results are transposed
+// through shared memory, and each warp then writes 32 consecutive bottom-up
+// rows of one column (a contiguous 64-byte store).  The kernel moves 4 W H
+// bytes in and 2 ncols H bytes out and is bandwidth / launch bound.
+#include "internal.h"
+
+namespace stx {
+namespace {
+
+__device__ __forceinline__ int q4_code(float d, int dmax)
+{
+    if (!(d > 0.0f)) return 0;               // NaN, negative, zero
+    if (d >= (float)dmax) return 16 * dmax;
+    return __float2int_rn(16.0f * d);        // 16 d is exact; halves to even
+}
+
+template <int S, int MODE>
+__device__ __forceinline__ int reduce_group(const float* __restrict__ px, int dmax)
+{
+    int v[S];
+#pragma unroll
+    for (int i = 0; i < S; ++i) v[i] = q4_code(__ldg(px + i), dmax);
+    if (MODE == 1) {
+        int sum = 0;
+#pragma unroll
+        for (int i = 0; i < S; ++i) sum += v[i];
+        return (2 * sum + S) / (2 * S);      // mean, halves up
+    }
+    // lower median by rank selection: v[i] is the answer iff
+    // #{v < v[i]} <= m < #{v <= v[i]}, m = (S-1)/2
+    constexpr int m = (S - 1) / 2;
+    int out = 0;
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+        int lt = 0, le = 0;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            lt += v[j] < v[i];
+            le += v[j] <= v[i];
+        }
+        if (lt <= m && m < le) out = v[i];
+    }
+    return out;
+}
+
+template <int S, int MODE>
+__global__ void __launch_bounds__(256) reduce_transpose_kernel(const float* __restrict__ disp, int H, int W,
+                                                               int ncols, int dmax, int16_t* __restrict__ q)
+{
+    __shared__ int16_t tile[32][34];                 // [column][row], padded
+    const int tx = threadIdx.x, ty = threadIdx.y;    // 32 x 8
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int c = c0 + tx;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = r0 + ty + 8 * i;
+        int val = 0;
+        if (c < ncols && r < H) val = reduce_group<S, MODE>(disp + (size_t)r * W + (size_t)c * S, dmax);
+        tile[tx][ty + 8 * i] = (int16_t)val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int cc = c0 + ty + 8 * j;              // this warp's column
+        const int r = r0 + tx;                       // lane = row within the tile
+        if (cc < ncols && r < H) q[(size_t)cc * H + (H - 1 - r)] = tile[ty + 8 * j][tx];
+    }
+}
+
+template <int S>
+cudaError_t launch_s(const float* disp, const FrameGeom& g, int dmax, int mode, int16_t* q, cudaStream_t st)
+{
+    dim3 block(32, 8), grid((g.ncols + 31) / 32, (g.H + 31) / 32);
+    if (mode == 1)
+        reduce_transpose_kernel<S, 1><<<grid, block, 0, st>>>(disp, g.H, g.W, g.ncols, dmax, q);
+    else
+        reduce_transpose_kernel<S, 0><<<grid, block, 0, st>>>(disp, g.H, g.W, g.ncols, dmax, q);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_reduce(const float* disp, const FrameGeom& g, int dmax, int mode, int16_t* q,
+                          cudaStream_t st)
+{
+    if (g.H <= 0 || g.ncols <= 0) return cudaSuccess;
+    switch (g.s) {
+        case 1: return launch_s<1>(disp, g, dmax, mode, q, st);
+        case 2: return launch_s<2>(disp, g, dmax, mode, q, st);
+        case 3: return launch_s<3>(disp, g, dmax, mode, q, st);
+        case 4: return launch_s<4>(disp, g, dmax, mode, q, st);
+        case 5: return launch_s<5>(disp, g, dmax, mode, q, st);
+        case 6: return launch_s<6>(disp, g, dmax, mode, q, st);
+        case 7: return launch_s<7>(disp, g, dmax, mode, q, st);
+        case 8: return launch_s<8>(disp, g, dmax, mode, q, st);
+        case 9: return launch_s<9>(disp, g, dmax, mode, q, st);
+        case 10: return launch_s<10>(disp, g, dmax, mode, q, st);
+        case 11: return launch_s<11>(disp, g, dmax, mode, q, st);
+        case 12: return launch_s<12>(disp, g, dmax, mode, q, st);
+        case 13: return launch_s<13>(disp, g, dmax, mode, q, st);
+        case 14: return launch_s<14>(disp, g, dmax, mode, q, st);
+        case 15: return launch_s<15>(disp, g, dmax, mode, q, st);
+        case 16: return launch_s<16>(disp, g, dmax, mode, q, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace stx

@@ -1,0 +1,210 @@
+// model.cpp -- the input-independent ("offline") part of the stixel model
+// (Sec. 3.4), built once per parameter set on the host in FP64 and rounded to
+// the fixed-point grid used by the kernels.
+//
+// Sensor model (Eq. 3) and per-pixel cost (Eq. 4):
+//   cost(d | f) = min( C_out , K(f) + (d - f)^2 / (2 sigma^2) )
+//   C_out = ln d_range - ln p_out
+//   K(f)  = ln A_norm(f) + ln(sigma sqrt(2 pi)) - ln(1 - p_out)
+//   A_norm(f) = Phi((d_range - f)/sigma) - Phi(-f/sigma), f clamped to [0, d_range]
+// with d_range = dmax and sigma a per-class constant (the paper's noise model
+// sigma^c(f, v) is not specified further).  The class models (Sec. 3.1): object
+// f = rounded mean disparity of the stixel; ground f(v) = alpha (v_hor - v), i.e.
+// alpha (r - horizon_row) at image row r, alpha = baseline cos(pitch) / height,
+// put on the 1/16-px grid; sky f = 0.
+//
+// Fixed point: each of C_out, K and the residual term is rounded to the
+// nearest multiple of 2^-12 (halves away from zero) and stored in 2^-14 units
+// (so as a multiple of 4).  The residual term is tabulated over the Q4
+// residual e = |q - 16 f| in [0, 16 dmax]; larger residuals clamp to the last
+// entry, which create() checks is already past the outlier branch.  The
+// expressions below are evaluated in IEEE FP64 exactly as written (the build
+// disables floating-point contraction), which makes the tables reproducible.
+#include "model.h"
+
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace stx {
+
+namespace {
+
+double std_normal_cdf(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
+
+double norm_mass(double f, double sigma, double d_range)
+{
+    double fc = f < 0.0 ? 0.0 : (f > d_range ? d_range : f);
+    return std_normal_cdf((d_range - fc) / sigma) - std_normal_cdf((0.0 - fc) / sigma);
+}
+
+double gauss_const(double f, double sigma, double p_out, double d_range)
+{
+    return log(norm_mass(f, sigma, d_range)) + log(sigma * sqrt(2.0 * M_PI)) - log(1.0 - p_out);
+}
+
+double resid(double dpx, double sigma) { return dpx * dpx / (2.0 * sigma * sigma); }
+
+// Residual terms are capped at 65536 cost units before rounding: every capped
+// entry is far past the outlier branch (C_out - K is at most a few hundred),
+// so min(C_out, K + term) is unchanged and the table stays inside int32.
+double resid_capped(double dpx, double sigma)
+{
+    double r = resid(dpx, sigma);
+    return r < 65536.0 ? r : 65536.0;
+}
+
+// multiple of 2^-12, in 2^-14 units
+int32_t to_fixed(double x) { return (int32_t)(4 * llround(4096.0 * x)); }
+
+bool finite_pos(float x) { return std::isfinite(x) && x > 0.0f; }
+
+bool sigma_ok(float x) { return finite_pos(x) && x <= 1000.0f; }
+
+// a prior: >= 0, and finite <= 1000 or +inf
+bool prior_ok(float x) { return !std::isnan(x) && x >= 0.0f && (std::isinf(x) || x <= 1000.0f); }
+
+int32_t fixed_prior(double x) { return std::isinf(x) ? kBig : to_fixed(x); }
+
+}  // namespace
+
+void default_params(stixels_params_t* p)
+{
+    std::memset(p, 0, sizeof(*p));
+    p->focal_px = 700.0f;
+    p->baseline_m = 0.3f;
+    p->camera_height_m = 1.2f;
+    p->pitch_rad = 0.0f;
+    p->horizon_row = 40;
+    p->stixel_width = 5;
+    p->dmax = 64;
+    p->p_out = 0.05f;
+    p->sigma_ground = p->sigma_object = p->sigma_sky = 1.0f;
+    // first stixel: object, ground, sky
+    p->prior_first[0] = 1.0f; p->prior_first[1] = 0.2f; p->prior_first[2] = 5.0f;
+    // [above][below]; ground above ground / sky and sky above sky are impossible
+    const float inf = INFINITY;
+    const float t[3][3] = {{1.5f, 1.0f, 4.0f}, {1.5f, inf, inf}, {0.5f, 0.5f, inf}};
+    std::memcpy(p->prior_trans, t, sizeof(t));
+    p->cost_new_stixel = 3.0f;
+    p->cost_gravity = 2.0f; p->eps_gravity = 1.0f;
+    p->cost_diving = 10.0f; p->eps_diving = 1.0f;
+    p->cost_order = 2.0f; p->eps_order = 0.0f;
+    p->reduce_mode = 0;
+    p->max_stixels_per_col = 64;
+}
+
+int build_model(const stixels_params_t* p, HostModel* m)
+{
+    if (!p || !m) return STIXELS_E_INVALID_ARG;
+    if (p->dmax < 1 || p->dmax > STIXELS_MAX_DMAX) return STIXELS_E_INVALID_ARG;
+    if (p->stixel_width < 1 || p->stixel_width > STIXELS_MAX_STIXEL_WIDTH) return STIXELS_E_INVALID_ARG;
+    if (!(p->p_out > 0.0f && p->p_out < 1.0f)) return STIXELS_E_INVALID_ARG;
+    if (!sigma_ok(p->sigma_ground) || !sigma_ok(p->sigma_object) || !sigma_ok(p->sigma_sky))
+        return STIXELS_E_INVALID_ARG;
+    if (!finite_pos(p->camera_height_m) || !std::isfinite(p->baseline_m) || !std::isfinite(p->pitch_rad) ||
+        std::fabs(p->pitch_rad) >= 1.5f)
+        return STIXELS_E_INVALID_ARG;
+    for (int c = 0; c < 3; ++c) {
+        if (!prior_ok(p->prior_first[c])) return STIXELS_E_INVALID_ARG;
+        for (int q = 0; q < 3; ++q)
+            if (!prior_ok(p->prior_trans[c][q])) return STIXELS_E_INVALID_ARG;
+    }
+    if (!prior_ok(p->cost_new_stixel) || std::isinf(p->cost_new_stixel)) return STIXELS_E_INVALID_ARG;
+    // the data-dependent penalties must be finite: a feasible segmentation then
+    // never needs more than three stixels to reach any class, which bounds every
+    // feasible cost (see budget_ok)
+    for (float c : {p->cost_gravity, p->cost_diving, p->cost_order})
+        if (!prior_ok(c) || std::isinf(c)) return STIXELS_E_INVALID_ARG;
+    const float eps[3] = {p->eps_gravity, p->eps_diving, p->eps_order};
+    for (float e : eps)
+        if (!std::isfinite(e) || std::fabs(e) > 100.0f) return STIXELS_E_INVALID_ARG;
+    // gravity (f above the ground line + eps) and diving (f below it - eps) must
+    // exclude each other
+    if (p->eps_gravity < 0.0f || p->eps_diving < 0.0f) return STIXELS_E_INVALID_ARG;
+    if (p->reduce_mode != 0 && p->reduce_mode != 1) return STIXELS_E_INVALID_ARG;
+    if (p->max_stixels_per_col < 1 || p->max_stixels_per_col > STIXELS_MAX_HEIGHT) return STIXELS_E_INVALID_ARG;
+
+    m->p = *p;
+    m->dmax = p->dmax;
+    m->emax = 16 * p->dmax;
+    const double d_range = (double)p->dmax;
+    const double p_out = (double)p->p_out;
+    const double s_obj = (double)p->sigma_object, s_gnd = (double)p->sigma_ground, s_sky = (double)p->sigma_sky;
+
+    m->c_out = to_fixed(log(d_range) - log(p_out));
+    m->k_obj.resize(m->dmax + 1);
+    for (int f = 0; f <= m->dmax; ++f) m->k_obj[f] = to_fixed(gauss_const((double)f, s_obj, p_out, d_range));
+    m->k_sky = to_fixed(gauss_const(0.0, s_sky, p_out, d_range));
+    m->g_obj.resize(m->emax + 1);
+    m->g_ground.resize(m->emax + 1);
+    m->g_sky.resize(m->emax + 1);
+    for (int e = 0; e <= m->emax; ++e) {
+        const double dpx = e / 16.0;
+        m->g_obj[e] = to_fixed(resid_capped(dpx, s_obj));
+        m->g_ground[e] = to_fixed(resid_capped(dpx, s_gnd));
+        m->g_sky[e] = to_fixed(resid_capped(dpx, s_sky));
+    }
+    // the residual table must reach the outlier branch before it ends, for every
+    // class and every K (K is smallest at the clamped ends of [0, d_range])
+    const int32_t kmin[3] = {to_fixed(gauss_const(0.0, s_obj, p_out, d_range)),
+                             to_fixed(gauss_const(0.0, s_gnd, p_out, d_range)),
+                             to_fixed(gauss_const(0.0, s_sky, p_out, d_range))};
+    const int32_t glast[3] = {m->g_obj[m->emax], m->g_ground[m->emax], m->g_sky[m->emax]};
+    for (int c = 0; c < 3; ++c)
+        if ((int64_t)kmin[c] + glast[c] < m->c_out) return STIXELS_E_INVALID_ARG;
+
+    m->alpha = (double)p->baseline_m * cos((double)p->pitch_rad) / (double)p->camera_height_m;
+
+    const double bic = (double)p->cost_new_stixel;
+    int32_t maxp = 0;
+    for (int c = 0; c < 3; ++c) {
+        m->first[c] = fixed_prior((double)p->prior_first[c] + bic);
+        if (m->first[c] < kBig && m->first[c] > maxp) maxp = m->first[c];
+        for (int q = 0; q < 3; ++q) {
+            m->trans[c][q] = fixed_prior((double)p->prior_trans[c][q] + bic);
+            if (m->trans[c][q] < kBig && m->trans[c][q] > maxp) maxp = m->trans[c][q];
+        }
+    }
+    m->pen_grav = fixed_prior((double)p->cost_gravity);
+    m->pen_div = fixed_prior((double)p->cost_diving);
+    m->pen_ord = fixed_prior((double)p->cost_order);
+    m->max_finite_prior = maxp + m->pen_grav + m->pen_div + m->pen_ord;
+    m->eps_g = (int32_t)llround(16.0 * (double)p->eps_gravity);
+    m->eps_d = (int32_t)llround(16.0 * (double)p->eps_diving);
+    m->eps_o = (int32_t)llround(16.0 * (double)p->eps_order);
+    return STIXELS_OK;
+}
+
+void build_rows(const HostModel& m, int H, std::vector<int32_t>* fgq, std::vector<int32_t>* k_ground)
+{
+    fgq->resize(H);
+    k_ground->resize(H);
+    const double d_range = (double)m.dmax;
+    const double p_out = (double)m.p.p_out;
+    const double s_gnd = (double)m.p.sigma_ground;
+    for (int v = 0; v < H; ++v) {
+        const int r = H - 1 - v;                       // image row of bottom-up row v
+        const long long code = llround(16.0 * m.alpha * (double)(r - m.p.horizon_row));
+        (*fgq)[v] = (int32_t)code;
+        (*k_ground)[v] = to_fixed(gauss_const((double)code / 16.0, s_gnd, p_out, d_range));
+    }
+}
+
+// A feasible cell of the cost table is reached by some segmentation of at most
+// three stixels (one per class change), so every feasible cost is below
+// H * max|pixel cost| + 3 * (largest prior of one stixel).  Keeping that below
+// 2^28 units keeps feasible costs below the 2^29 "infeasible" marker and every
+// candidate sum (cost <= 2^29, transition <= 2^29, penalty, data) inside int32.
+bool budget_ok(const HostModel& m, int H, const std::vector<int32_t>& k_ground)
+{
+    int64_t kmin = m.k_sky;
+    for (int32_t k : m.k_obj) kmin = k < kmin ? k : kmin;
+    for (int32_t k : k_ground) kmin = k < kmin ? k : kmin;
+    int64_t per_pixel = m.c_out > -kmin ? m.c_out : -kmin;
+    int64_t worst = (int64_t)H * per_pixel + 3 * (int64_t)m.max_finite_prior;
+    return worst < kFiniteBudget;
+}
+
+}  // namespace stx

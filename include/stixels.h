@@ -68,6 +68,7 @@ enum stixels_class { STIXELS_OBJECT = 0, STIXELS_GROUND = 1, STIXELS_SKY = 2 };
 /* Bits of the device error word. */
 #define STIXELS_ERR_CAPACITY 1u    /* some column's stixel count exceeded the capacity */
 #define STIXELS_ERR_INFEASIBLE 2u  /* some column has no finite-cost segmentation */
+#define STIXELS_ERR_TIMEOUT 4u     /* an internal wait of a kernel gave up (bounded spin); column left empty */
 
 /*
  * Model parameters (Sec. 3; Eq. 3 for the sensor model; the five prior

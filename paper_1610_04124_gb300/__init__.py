@@ -20,7 +20,7 @@ __all__ = ["Params", "Stixels", "STIXEL_DTYPE", "StixelsError", "lib", "default_
 
 OBJECT, GROUND, SKY = 0, 1, 2
 OK, E_INVALID_ARG, E_OOM, E_CUDA, E_CAPACITY, E_NOT_READY, E_TIMEOUT, E_REJECTED, E_DEVICE_FAULT = range(9)
-ERR_CAPACITY, ERR_INFEASIBLE = 1, 2
+ERR_CAPACITY, ERR_INFEASIBLE, ERR_TIMEOUT = 1, 2, 4
 MAX_HEIGHT = 2048
 N_SCALARS = 20
 UNITS_PER_COST = 16384

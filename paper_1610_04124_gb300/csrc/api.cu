@@ -191,6 +191,9 @@ int stixels_create(const stixels_params_t* params, stixels_t* out_handle)
     d.eps_g = m.eps_g;
     d.eps_d = m.eps_d;
     d.eps_o = m.eps_o;
+    d.esat_obj = m.esat[0];
+    d.esat_ground = m.esat[1];
+    d.esat_sky = m.esat[2];
     d.k_obj = h->d_tables;
     d.g_obj = d.k_obj + (m.dmax + 1);
     d.g_ground = d.g_obj + (m.emax + 1);

@@ -30,6 +30,9 @@ struct ModelDev {
     int32_t trans[3][3];     // [above][below] transition prior + BIC
     int32_t pen_grav, pen_div, pen_ord;
     int32_t eps_g, eps_d, eps_o;     // Q4 tolerances
+    // saturation residual per class: for e >= esat, K + G[e] >= C_out for every K
+    // of that class, so min(C_out, K + G[min(e, esat)]) equals the unclamped cost
+    int32_t esat_obj, esat_ground, esat_sky;
     const int32_t* k_obj;    // [dmax + 1]
     const int32_t* g_obj;    // [emax + 1]
     const int32_t* g_ground; // [emax + 1]

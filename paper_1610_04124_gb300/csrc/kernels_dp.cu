@@ -17,25 +17,50 @@
 //   V_c[k] = PC[k + 1] + min_{b <= k} ( min_p (V_p[b - 1] + T_cp) - PC[b] )
 // is a running minimum: O(1) per row.  Objects are the O(H^2) part.
 //
-// Parallel scheme (a redesign of the paper's one-thread-per-row CTA): rows are
-// cut into blocks of 32.  For block t,
-//   1. all warps gather the data terms of the block's 528 intra-block (b, k)
-//      pairs into shared memory (no dependence on the DP),
-//   2. warp 0 solves the block's triangle: 32 sequential starts, lane l owns
-//      end row 32 t + l; after each start the owner's running minimum is
-//      broadcast with a shuffle and every lane derives the next start's
-//      context (no shared-memory round trip on the dependency chain),
-//   3. all warps apply the 32 starts of block t to every later end row
-//      (rectangles of 32 x 32 independent candidates, one per lane and start;
-//      chunk j of end rows always goes to the same warp, so updates of one cell
-//      happen in start order).
-// The data terms come from the object LUT in global memory (L2-resident).
+// Parallel scheme (a redesign of the paper's one-thread-per-row CTA with a
+// barrier per row), one 256-thread CTA per column, rows cut into blocks of 32:
+//   - the chain warp finalises the blocks in order.  For block j it applies the
+//     32 starts of block j-1 to block j's end rows, then solves the block's
+//     triangle: 32 sequential starts, lane l owning end row 32 j + l; after each
+//     start the owner's running minimum is broadcast with a shuffle and every
+//     lane derives the next start's context in registers.  Lane l keeps row
+//     32 j + l's results in registers (predicated selects, no per-row stores)
+//     and the warp writes the block's back-pointers and start contexts with one
+//     coalesced store each at the end of the block.  The chain's data terms
+//     (with the input-only gravity / diving penalties already added) were
+//     gathered into shared memory beforehand, so the sequential chain never
+//     waits on global memory.
+//   - the 7 bulk warps apply the starts of every finalised block t to the end
+//     rows of blocks t+2, t+3, ... (independent 32 x 32 tiles).  End-row block c
+//     receives c - 1 tiles; blocks are dealt to the bulk warps largest first
+//     to the least-loaded warp, and a block always stays with its warp, so a
+//     cell's updates happen in start order.  Right after block t is final they
+//     first do what the chain needs next -- the tile (t, t+2) and, shared among
+//     all of them, the chain's data gathers for block t+2 -- and only then the
+//     tiles of later blocks.
+// The two sides synchronise through progress counters in shared memory
+// instead of CTA barriers, so neither waits for the other's non-critical work.
+// Every wait is a bounded spin: on expiry the CTA records STIXELS_ERR_TIMEOUT,
+// leaves the column empty and exits (no wait can hang the device).
+// The object LUT is read from global memory (L2-resident).
+//
+// The kernel is specialised for the standard staggering constraints (ground
+// never directly above ground or sky, sky never directly above sky): those
+// transitions then drop out of the ground / sky running minima.  Any other
+// transition table uses the general instantiation.
 #include <climits>
 
 #include "internal.h"
 
 namespace stx {
 namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kBulk = kWarps - 1;    // warps besides the chain warp
+constexpr int kMaxBlocks = (STIXELS_MAX_HEIGHT + 31) / 32;
+constexpr int kSpinLimit = 1 << 24;  // polls (~20 ns apart) before a wait gives up
 
 struct DpArgs {
     const int32_t* pd;
@@ -53,14 +78,40 @@ struct DpArgs {
     uint32_t* err;
 };
 
-// Context of one start row b, shared by every end row k >= b.
+// Context of one start row b, shared by every end row k >= b: the three
+// previous-class terms V_p[b-1] + T(object | p) + code(p) and the ordering
+// threshold (penalty iff f > ford).
 struct __align__(16) StartCtx {
-    int32_t pdb;        // PD[b]
-    int32_t bo, bg, bs; // V_p[b-1] + T(object | p) + code(p), p = object, ground, sky
-    int32_t ford;       // ordering penalty iff f > ford
-    int32_t fhi;        // gravity penalty iff f > fhi
-    int32_t flo;        // diving penalty iff f < flo
-    int32_t b;
+    int32_t bo, bg, bs, ford;
+};
+
+// Input-only data of row v: pd8 = PD[v] + 8 v (so that S + 8 n of a stixel
+// [b, k] is pd8[k + 1] - pd8[b]) and the gravity / diving thresholds at row v
+// (penalty iff f > fhi, iff f < flo).
+struct __align__(16) RowInfo {
+    int32_t pd8, fhi, flo, pad;
+};
+
+// Ground and sky prefix entries of rows v and v + 1, read by the chain in one load.
+struct __align__(16) GS4 {
+    int32_t pg0, ps0, pg1, ps1;
+};
+
+// Chain data of one block: for each (start i, end row l) slot e = 32 i + l,
+// {d, e_g} = the object data cost and the same plus the ground-below
+// penalties, and f = the rounded mean; part 0 = starts of the previous block,
+// part 1 = the block's own triangle.
+struct ChainBuf {
+    int2 de[2][1024];
+    uint8_t f[2][1024];
+};
+
+struct SyncState {
+    int final_blocks;            // blocks the chain warp has finalised
+    int abort;                   // set when a wait gave up
+    int ready[kMaxBlocks];       // ready[c]: bulk tiles applied to end-row block c
+    int gathered[kMaxBlocks];    // gathered[j]: bulk warps done gathering block j's chain data
+    int owner[kMaxBlocks];       // bulk warp that owns end-row block c
 };
 
 __device__ __forceinline__ int32_t min3(int32_t a, int32_t b, int32_t c) { return min(min(a, b), c); }
@@ -76,172 +127,359 @@ __device__ __forceinline__ uint2 div_magic(int n)
     return make_uint2((uint32_t)((num + d - 1) / d), (uint32_t)s);
 }
 
-// Rounded mean disparity of a stixel, clamped to the LUT's rows: valid Q4 input
-// always gives f <= dmax; the clamp only keeps malformed caller-built LUTs
-// (stixels_solve) inside the table.
-__device__ __forceinline__ int mean_f(int32_t S, int n, const uint2* s_div, int dmax)
+// Rounded mean disparity of a stixel of n rows from x = S + 8 n, clamped to
+// the LUT's rows: valid Q4 input always gives f <= dmax; the clamp only keeps
+// malformed caller-built LUTs (stixels_solve) inside the table.
+__device__ __forceinline__ int mean_f(int32_t x, int n, const uint2* s_div, int dmax)
 {
     const uint2 dm = s_div[n];
-    return (int)min(__umulhi((uint32_t)(S + 8 * n), dm.x) >> dm.y, (uint32_t)dmax);
+    return (int)min(__umulhi((uint32_t)x, dm.x) >> dm.y, (uint32_t)dmax);
 }
 
-// Object candidate of start context c for a stixel with rounded mean f and data cost d.
-__device__ __forceinline__ int32_t obj_cand(const StartCtx& c, int f, int32_t d, const ModelDev& m)
+// Minimum of N candidates (cost, start << 8 | f) listed in ascending start
+// order, ties to the earlier start, by a pairwise tree (depth log2 N instead of
+// a serial chain of N compare-selects).  Result in v[0], bf[0].
+template <int N>
+__device__ __forceinline__ void tree_min(int32_t (&v)[N], int32_t (&bf)[N])
 {
-    const int32_t co = c.bo + (f > c.ford ? m.pen_ord : 0);
-    const int32_t cg = c.bg + (f > c.fhi ? m.pen_grav : 0) + (f < c.flo ? m.pen_div : 0);
-    return min3(co, cg, c.bs) + d;
+#pragma unroll
+    for (int s = 1; s < N; s *= 2)
+#pragma unroll
+        for (int i = 0; i + s < N; i += 2 * s) {
+            const bool take = v[i + s] < v[i];
+            v[i] = take ? v[i + s] : v[i];
+            bf[i] = take ? bf[i + s] : bf[i];
+        }
 }
 
-template <int NW>
-__global__ void __launch_bounds__(NW * 32) stixel_dp_kernel(DpArgs a)
+// Gravity / diving penalties of an object with rounded mean f directly above
+// ground, base row thresholds r (input-only).
+__device__ __forceinline__ int32_t ground_pen(const RowInfo& r, int f, const ModelDev& m)
 {
-    constexpr unsigned FULL = 0xffffffffu;
+    return (f > r.fhi ? m.pen_grav : 0) + (f < r.flo ? m.pen_div : 0);
+}
+
+// Warp-wide bounded wait until *p >= target (lane 0 polls).  Returns false if
+// the wait gave up or another warp did; the caller then stops.
+__device__ __forceinline__ bool wait_geq(volatile int* p, int target, volatile int* abort_flag)
+{
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) {
+        int it = 0;
+        while (*p < target) {
+            if (*abort_flag) { ok = 0; break; }
+            if (++it > kSpinLimit) { *abort_flag = 1; ok = 0; break; }
+            __nanosleep(20);
+        }
+    }
+    ok = __shfl_sync(kFull, ok, 0);
+    __threadfence_block();
+    return ok != 0;
+}
+
+size_t dp_smem_bytes(int H)
+{
+    const size_t HP = (size_t)((H + 3) & ~3);
+    return sizeof(StartCtx) * HP + sizeof(RowInfo) * (HP + 4) + sizeof(GS4) * HP + sizeof(uint2) * (HP + 4) +
+           sizeof(int32_t) * 5 * HP + sizeof(ChainBuf) * 2 + sizeof(SyncState);
+}
+
+template <bool kStdTrans>
+__global__ void __launch_bounds__(kThreads, 2) stixel_dp_kernel(DpArgs a)
+{
     const int col = blockIdx.x;
     const int H = a.H, P = a.P, F = a.F;
     const int HP = (H + 3) & ~3;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const ModelDev& m = a.m;
+    // rotate the chain warp between CTAs so that two CTAs sharing an SM are
+    // less likely to put their chain warps on the same scheduler; the other
+    // warps are bulk warps 0 .. kBulk-1
+    const int chain = blockIdx.x & 3;
+    const int bulk_id = (warp - chain - 1 + kWarps) % kWarps;
 
     extern __shared__ __align__(16) int32_t sm[];
-    StartCtx* s_ctx = reinterpret_cast<StartCtx*>(sm);          // [HP]
-    int32_t* s_pd = sm + 8 * HP;                                 // [P]
-    int32_t* s_pg = s_pd + P;                                    // [P]
-    int32_t* s_ps = s_pg + P;                                    // [P]
-    uint2* s_div = reinterpret_cast<uint2*>(s_ps + P);           // [HP + 4], index n = 1..H
-    int32_t* s_fhi = reinterpret_cast<int32_t*>(s_div + HP + 4); // [HP]
-    int32_t* s_flo = s_fhi + HP;
-    int32_t* s_bp = s_flo + HP;                                  // [3][HP] back-pointers b << 2 | p
-    int32_t* s_runv = s_bp + 3 * HP;                             // [HP] object running minimum
-    int32_t* s_runb = s_runv + HP;
-    int32_t* s_runf = s_runb + HP;
-    int32_t* s_tri_d = s_runf + HP;                              // [32][32]
-    int32_t* s_tri_f = s_tri_d + 1024;                           // [32][32]
-
-    const int32_t* po_col = a.po + (size_t)col * F * P;
-    for (int j = threadIdx.x; j < P; j += blockDim.x) {
-        s_pd[j] = a.pd[(size_t)col * P + j];
-        s_pg[j] = a.pg[(size_t)col * P + j];
-        s_ps[j] = a.ps[(size_t)col * P + j];
-    }
-    for (int v = threadIdx.x; v < H; v += blockDim.x) {
-        const int32_t g = a.rows.fgq[v];
-        s_fhi[v] = (g + m.eps_g) >> 4;              // 16 f > g + eps  <=>  f > floor((g + eps) / 16)
-        s_flo[v] = -((m.eps_d - g) >> 4);           // 16 f < g - eps  <=>  f < ceil((g - eps) / 16)
-        s_runv[v] = INT_MAX;
-        s_runb[v] = -1;
-        s_runf[v] = 0;
-    }
-    for (int n = 1 + threadIdx.x; n <= H; n += blockDim.x) s_div[n] = div_magic(n);
-    __syncthreads();
-
-    const int ord_off = m.eps_o >> 4;               // 16 f > 16 f' + eps  <=>  f > f' + floor(eps / 16)
+    StartCtx* s_ctx = reinterpret_cast<StartCtx*>(sm);                // [HP]
+    RowInfo* s_row = reinterpret_cast<RowInfo*>(s_ctx + HP);          // [HP + 4], row H holds pd8[H]
+    GS4* s_gs = reinterpret_cast<GS4*>(s_row + HP + 4);               // [HP]
+    uint2* s_div = reinterpret_cast<uint2*>(s_gs + HP);               // [HP + 4], index n = 1..H
+    int32_t* s_bp = reinterpret_cast<int32_t*>(s_div + HP + 4);        // [3][HP] back-pointers b << 2 | p
+    int32_t* s_runv = s_bp + 3 * HP;                                   // [HP] object running minimum
+    int32_t* s_runbf = s_runv + HP;                                    // [HP] its start << 8 | f
+    ChainBuf* s_cb = reinterpret_cast<ChainBuf*>(s_runbf + HP);        // [2]
+    SyncState* sync = reinterpret_cast<SyncState*>(s_cb + 2);
+    volatile int* v_final = &sync->final_blocks;
+    volatile int* v_abort = &sync->abort;
     const int NB = (H + 31) >> 5;
 
-    // warp 0's carried state: V of the last finalised row, f of its best object
-    // stixel, and the ground / sky running minima (all uniform across lanes)
+    const int32_t* po_col = a.po + (size_t)col * F * P;
+    const int32_t* pg_col = a.pg + (size_t)col * P;
+    const int32_t* ps_col = a.ps + (size_t)col * P;
+    for (int v = threadIdx.x; v <= H; v += kThreads) {
+        RowInfo r;
+        r.pd8 = a.pd[(size_t)col * P + v] + 8 * v;
+        r.fhi = r.flo = r.pad = 0;
+        if (v < H) {
+            const int32_t g = a.rows.fgq[v];
+            r.fhi = (g + m.eps_g) >> 4;             // 16 f > g + eps  <=>  f > floor((g + eps) / 16)
+            r.flo = -((m.eps_d - g) >> 4);          // 16 f < g - eps  <=>  f < ceil((g - eps) / 16)
+            GS4 q;
+            q.pg0 = pg_col[v]; q.ps0 = ps_col[v]; q.pg1 = pg_col[v + 1]; q.ps1 = ps_col[v + 1];
+            s_gs[v] = q;
+            s_runv[v] = INT_MAX;
+            s_runbf[v] = 0;
+        }
+        s_row[v] = r;
+    }
+    for (int n = 1 + threadIdx.x; n <= H; n += kThreads) s_div[n] = div_magic(n);
+    if (threadIdx.x < kMaxBlocks) {
+        sync->ready[threadIdx.x] = 0;
+        sync->gathered[threadIdx.x] = 0;
+    }
+    if (threadIdx.x == 0) {
+        sync->final_blocks = 0;
+        sync->abort = 0;
+        // end-row block c receives c - 1 bulk tiles; hand the blocks, largest
+        // first, to the least-loaded bulk warp (balanced per-warp work)
+        int load[kBulk];
+        for (int w = 0; w < kBulk; ++w) load[w] = 0;
+        for (int c = NB - 1; c >= 2; --c) {
+            int best = 0;
+            for (int w = 1; w < kBulk; ++w)
+                if (load[w] < load[best]) best = w;
+            sync->owner[c] = best;
+            load[best] += c - 1;
+        }
+        // start 0 carries the first-stixel prior (code 3 = no previous stixel)
+        s_ctx[0] = StartCtx{m.first[0] + kNoneCode, kBig, kBig, INT_MAX};
+    }
+    __syncthreads();
+
+    // Gather the data terms the chain warp needs for block jn into chain buffer
+    // jn & 1: part 0 = starts of block jn-1 x end rows of block jn, part 1 =
+    // starts and end rows of block jn (start <= end row).  All loads of a pass
+    // are issued before any store.
+    auto gather_chain = [&](int jn, int tid, int nthreads) {
+        ChainBuf* cb = s_cb + (jn & 1);
+        for (int base = tid; base < 2048; base += 5 * nthreads) {
+            int32_t lo[5], hi[5], fv[5];
+            bool ok[5];
+#pragma unroll
+            for (int r = 0; r < 5; ++r) {
+                const int idx = base + r * nthreads;
+                const int part = idx >> 10, e = idx & 1023, i = e >> 5, l = e & 31;
+                const int k = 32 * jn + l;
+                const int b = part == 0 ? 32 * (jn - 1) + i : 32 * jn + i;
+                ok[r] = idx < 2048 && k < H && (part == 0 ? jn >= 1 : i <= l);
+                lo[r] = hi[r] = fv[r] = 0;
+                if (ok[r]) {
+                    const int f = mean_f(s_row[k + 1].pd8 - s_row[b].pd8, k - b + 1, s_div, m.dmax);
+                    const int32_t* row = po_col + (size_t)f * P;
+                    lo[r] = __ldg(row + b);
+                    hi[r] = __ldg(row + k + 1);
+                    fv[r] = f;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 5; ++r) {
+                const int idx = base + r * nthreads;
+                if (ok[r]) {
+                    const int part = idx >> 10, e = idx & 1023;
+                    const int b = part == 0 ? 32 * (jn - 1) + (e >> 5) : 32 * jn + (e >> 5);
+                    const int32_t d = hi[r] - lo[r];
+                    cb->de[part][e] = make_int2(d, d + ground_pen(s_row[b], fv[r], m));
+                    cb->f[part][e] = (uint8_t)fv[r];
+                }
+            }
+        }
+    };
+
+    // Apply the 32 starts of finalised block t to end-row block jc (a bulk tile).
+    auto bulk_tile = [&](int t, int jc) {
+        const int k = 32 * jc + lane;
+        const bool kv = k < H;
+        const int kk = kv ? k : H - 1;
+        int32_t run = INT_MAX, runbf = 0;
+        if (kv) { run = s_runv[k]; runbf = s_runbf[k]; }
+        const int32_t x1 = s_row[kk + 1].pd8;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {          // two groups of 16 starts: 32 gathers in flight
+            int32_t lo[16], hi[16], fv[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int b = 32 * t + 16 * h + i;
+                const int f = mean_f(x1 - s_row[b].pd8, kk + 1 - b, s_div, m.dmax);
+                const int32_t* row = po_col + (size_t)f * P;
+                lo[i] = __ldg(row + b);
+                hi[i] = __ldg(row + kk + 1);
+                fv[i] = f;
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int b = 32 * t + 16 * h + i;
+                const StartCtx c = s_ctx[b];
+                const int32_t d = hi[i] - lo[i];
+                const int f = fv[i];
+                const int32_t cand = min3(c.bo + d + (f > c.ford ? m.pen_ord : 0),
+                                          c.bg + d + ground_pen(s_row[b], f, m), c.bs + d);
+                if (cand < run) { run = cand; runbf = (b << 8) | f; }
+            }
+        }
+        if (kv) { s_runv[k] = run; s_runbf[k] = runbf; }
+    };
+
+    // chain data of blocks 0 and 1 depend on the input only
+    gather_chain(0, threadIdx.x, kThreads);
+    if (NB > 1) gather_chain(1, threadIdx.x, kThreads);
+    __syncthreads();
+
+    if (warp != chain) {
+        // ---------------------------------------------------------------- bulk warps
+        for (int t = 0; t + 2 < NB; ++t) {
+            if (!wait_geq(v_final, t + 1, v_abort)) return;         // block t is final
+            const int jn = t + 2;
+            if (sync->owner[jn] == bulk_id) {                         // the tile the chain needs next
+                bulk_tile(t, jn);
+                __threadfence_block();
+                __syncwarp();
+                if (lane == 0) sync->ready[jn] = t + 1;
+            }
+            gather_chain(jn, bulk_id * 32 + lane, kBulk * 32);        // the chain's data for block t+2
+            __threadfence_block();
+            __syncwarp();
+            if (lane == 0) atomicAdd(&sync->gathered[jn], 1);
+            for (int jc = jn + 1; jc < NB; ++jc) {                    // tiles of later blocks
+                if (sync->owner[jc] != bulk_id) continue;
+                bulk_tile(t, jc);
+                __threadfence_block();
+                __syncwarp();
+                if (lane == 0) sync->ready[jc] = t + 1;
+            }
+        }
+        return;
+    }
+
+    // -------------------------------------------------------------------- chain warp
+    // transition priors with the previous-class codes folded in
+    const int32_t T_oo = m.trans[0][0], T_og = m.trans[0][1] + 1, T_os = m.trans[0][2] + 2;
+    const int32_t T_go = m.trans[1][0], T_gg = m.trans[1][1] + 1, T_gs = m.trans[1][2] + 2;
+    const int32_t T_so = m.trans[2][0], T_sg = m.trans[2][1] + 1, T_ss = m.trans[2][2] + 2;
+    const int ord_off = m.eps_o >> 4;               // 16 f > 16 f' + eps  <=>  f > f' + floor(eps / 16)
+    // carried state (uniform across lanes): V of the last finalised row, f of
+    // its best object stixel, and the ground / sky running minima
     int32_t vo_p = 0, vg_p = 0, vs_p = 0, fo_p = 0;
     int32_t rg = INT_MAX, rgb = 0, rs = INT_MAX, rsb = 0;
+    bool aborted = false;
 
-    for (int t = 0; t < NB; ++t) {
-        const int B = 32 * t;
+    for (int j = 0; j < NB; ++j) {
+        const int B = 32 * j;
+        if (j >= 2) {
+            if (!wait_geq(&sync->ready[j], j - 1, v_abort) || !wait_geq(&sync->gathered[j], kBulk, v_abort)) {
+                aborted = true;
+                break;
+            }
+        }
+        const ChainBuf* cb = s_cb + (j & 1);
         const int nb = min(32, H - B);
-        // 1. intra-block data terms
-        for (int idx = threadIdx.x; idx < 1024; idx += blockDim.x) {
-            const int i = idx >> 5, l = idx & 31;
-            if (i <= l && l < nb) {
-                const int b = B + i, k = B + l, n = k - b + 1;
-                const int f = mean_f(s_pd[k + 1] - s_pd[b], n, s_div, m.dmax);
-                const int32_t* row = po_col + (size_t)f * P;
-                s_tri_d[idx] = __ldg(row + k + 1) - __ldg(row + b);
-                s_tri_f[idx] = f;
+        const int k = B + lane;
+        const bool kv = lane < nb;
+        int32_t run = kv ? s_runv[k] : INT_MAX;
+        int32_t runbf = kv ? s_runbf[k] : 0;
+        if (j > 0) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                int32_t cv[16], cbf[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int e = (16 * h + i) * 32 + lane;
+                    const int b = B - 32 + 16 * h + i;
+                    const StartCtx c = s_ctx[b];
+                    const int2 de = cb->de[0][e];
+                    const int f = cb->f[0][e];
+                    cv[i] = min3(c.bo + de.x + (f > c.ford ? m.pen_ord : 0), c.bg + de.y, c.bs + de.x);
+                    cbf[i] = (b << 8) | f;
+                }
+                tree_min<16>(cv, cbf);
+                if (cv[0] < run) { run = cv[0]; runbf = cbf[0]; }
             }
         }
-        __syncthreads();
-        // 2. triangle
-        if (warp == 0) {
-            const int k = B + lane;
-            const bool kv = lane < nb;
-            int32_t run = kv ? s_runv[k] : INT_MAX;
-            int32_t runb = kv ? s_runb[k] : -1;
-            int32_t runf = kv ? s_runf[k] : 0;
-            for (int i = 0; i < nb; ++i) {
-                const int b = B + i;
-                StartCtx c;
-                int32_t ag, as;
-                c.pdb = s_pd[b];
-                c.b = b;
-                if (b == 0) {
-                    c.bo = m.first[0] + kNoneCode;
-                    c.bg = kBig;
-                    c.bs = kBig;
-                    c.ford = INT_MAX; c.fhi = INT_MAX; c.flo = INT_MIN;
-                    ag = m.first[1] + kNoneCode;
-                    as = m.first[2] + kNoneCode;
+        // lane l's copy of row B + l's results
+        int32_t my_r = 0, my_bf = 0, my_gr = 0, my_rgb = 0, my_sk = 0, my_rsb = 0;
+        // one start of the triangle, start row b = B + i; `first` is set only for
+        // b = 0, whose candidates carry the first-stixel prior
+        auto step = [&](int i, bool first) {
+            const int b = B + i;
+            const GS4 gs = s_gs[b];
+            const int2 de = cb->de[1][i * 32 + lane];
+            const int ff = cb->f[1][i * 32 + lane];
+            int32_t bo, bg, bs, ford, ag, as;
+            if (first) {
+                bo = m.first[0] + kNoneCode; bg = kBig; bs = kBig; ford = INT_MAX;
+                ag = m.first[1] + kNoneCode - gs.pg0;
+                as = m.first[2] + kNoneCode - gs.ps0;
+            } else {
+                bo = vo_p + T_oo; bg = vg_p + T_og; bs = vs_p + T_os; ford = fo_p + ord_off;
+                if (kStdTrans) {
+                    ag = vo_p + T_go - gs.pg0;
+                    as = min(vo_p + T_so, vg_p + T_sg) - gs.ps0;
                 } else {
-                    c.bo = vo_p + m.trans[0][0];
-                    c.bg = vg_p + m.trans[0][1] + 1;
-                    c.bs = vs_p + m.trans[0][2] + 2;
-                    c.ford = fo_p + ord_off;
-                    c.fhi = s_fhi[b];
-                    c.flo = s_flo[b];
-                    ag = min3(vo_p + m.trans[1][0], vg_p + m.trans[1][1] + 1, vs_p + m.trans[1][2] + 2);
-                    as = min3(vo_p + m.trans[2][0], vg_p + m.trans[2][1] + 1, vs_p + m.trans[2][2] + 2);
-                }
-                if (lane == 0) s_ctx[b] = c;
-                ag -= s_pg[b];
-                as -= s_ps[b];
-                if (ag < rg) { rg = ag; rgb = b; }
-                if (as < rs) { rs = as; rsb = b; }
-                if (kv && lane >= i) {
-                    const int f = s_tri_f[i * 32 + lane];
-                    const int32_t cand = obj_cand(c, f, s_tri_d[i * 32 + lane], m);
-                    if (cand < run) { run = cand; runb = b; runf = f; }
-                }
-                // row b is complete: every lane derives its values
-                const int32_t r = __shfl_sync(FULL, run, i);
-                const int32_t rb = __shfl_sync(FULL, runb, i);
-                const int32_t rf = __shfl_sync(FULL, runf, i);
-                const int32_t gr = s_pg[b + 1] + rg;
-                const int32_t sk = s_ps[b + 1] + rs;
-                vo_p = min(r & ~3, kBig);
-                vg_p = min(gr & ~3, kBig);
-                vs_p = min(sk & ~3, kBig);
-                fo_p = rf;
-                if (lane == 0) {
-                    s_bp[b] = (rb << 2) | (r & 3);
-                    s_bp[HP + b] = (rgb << 2) | (gr & 3);
-                    s_bp[2 * HP + b] = (rsb << 2) | (sk & 3);
-                }
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        // 3. rectangles: starts of block t applied to end rows of blocks j > t
-        for (int j = t + 1 + warp; j < NB; j += NW) {
-            const int k = 32 * j + lane;
-            const bool kv = k < H;
-            int32_t run = INT_MAX, runb = -1, runf = 0, pdk1 = 0;
-            if (kv) { run = s_runv[k]; runb = s_runb[k]; runf = s_runf[k]; pdk1 = s_pd[k + 1]; }
-#pragma unroll 4
-            for (int i = 0; i < 32; ++i) {
-                const StartCtx c = s_ctx[B + i];
-                if (kv) {
-                    const int n = k + 1 - c.b;
-                    const int f = mean_f(pdk1 - c.pdb, n, s_div, m.dmax);
-                    const int32_t* row = po_col + (size_t)f * P;
-                    const int32_t d = __ldg(row + k + 1) - __ldg(row + c.b);
-                    const int32_t cand = obj_cand(c, f, d, m);
-                    if (cand < run) { run = cand; runb = c.b; runf = f; }
+                    ag = min3(vo_p + T_go, vg_p + T_gg, vs_p + T_gs) - gs.pg0;
+                    as = min3(vo_p + T_so, vg_p + T_sg, vs_p + T_ss) - gs.ps0;
                 }
             }
-            if (kv) { s_runv[k] = run; s_runb[k] = runb; s_runf[k] = runf; }
+            if (ag < rg) { rg = ag; rgb = b; }
+            if (as < rs) { rs = as; rsb = b; }
+            const int32_t cand = min3(bo + de.x + (ff > ford ? m.pen_ord : 0), bg + de.y, bs + de.x);
+            if (cand < run) { run = cand; runbf = (b << 8) | ff; }
+            // row b is complete: every lane derives its values, lane i keeps them
+            const int32_t r = __shfl_sync(kFull, run, i);
+            const int32_t bf = __shfl_sync(kFull, runbf, i);
+            const int32_t gr = gs.pg1 + rg;
+            const int32_t sk = gs.ps1 + rs;
+            vo_p = min(r & ~3, kBig);
+            vg_p = min(gr & ~3, kBig);
+            vs_p = min(sk & ~3, kBig);
+            fo_p = bf & 255;
+            const bool mine = lane == i;
+            my_r = mine ? r : my_r;
+            my_bf = mine ? bf : my_bf;
+            my_gr = mine ? gr : my_gr;
+            my_rgb = mine ? rgb : my_rgb;
+            my_sk = mine ? sk : my_sk;
+            my_rsb = mine ? rsb : my_rsb;
+        };
+        int i0 = 0;
+        if (j == 0) { step(0, true); i0 = 1; }
+        if (nb == 32) {
+#pragma unroll 8
+            for (int i = i0; i < 32; ++i) step(i, false);
+        } else {
+#pragma unroll 1
+            for (int i = i0; i < nb; ++i) step(i, false);
         }
-        __syncthreads();
+        // the block's back-pointers and the contexts of the starts that follow its rows
+        if (kv) {
+            s_bp[k] = ((my_bf >> 8) << 2) | (my_r & 3);
+            s_bp[HP + k] = (my_rgb << 2) | (my_gr & 3);
+            s_bp[2 * HP + k] = (my_rsb << 2) | (my_sk & 3);
+            if (k + 1 < H)
+                s_ctx[k + 1] = StartCtx{min(my_r & ~3, kBig) + T_oo, min(my_gr & ~3, kBig) + T_og,
+                                        min(my_sk & ~3, kBig) + T_os, (my_bf & 255) + ord_off};
+        }
+        __threadfence_block();
+        __syncwarp();
+        if (lane == 0) *v_final = j + 1;
     }
 
     // backtracking from the top row (Sec. 3.3, Sec. 5.4)
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
+        if (aborted) {
+            a.counts[col] = 0;
+            if (a.cost) a.cost[col] = __int_as_float(0x7f800000);
+            if (a.cost_fixed) a.cost_fixed[col] = kBig;
+            atomicOr(a.err, STIXELS_ERR_TIMEOUT);
+            return;
+        }
         int c = 0;
         int32_t best = vo_p;
         if (vg_p < best) { best = vg_p; c = 1; }
@@ -266,14 +504,15 @@ __global__ void __launch_bounds__(NW * 32) stixel_dp_kernel(DpArgs a)
             const int32_t bp = s_bp[cc * HP + k];
             const int b = bp >> 2;
             if (idx < a.cap) {
-                const int32_t S = s_pd[k + 1] - s_pd[b];
+                const int nrows = k - b + 1;
+                const int32_t S = s_row[k + 1].pd8 - s_row[b].pd8 - 8 * nrows;
                 stixel_t st;
                 st.row_top = (int16_t)(H - 1 - k);
                 st.row_bottom = (int16_t)(H - 1 - b);
                 st.cls = (uint8_t)cc;
                 st.flags = 0;
                 st.reserved = 0;
-                st.disparity = __fdiv_rn(__int2float_rn(S), __int2float_rn(16 * (k - b + 1)));
+                st.disparity = __fdiv_rn(__int2float_rn(S), __int2float_rn(16 * nrows));
                 out[idx] = st;
             }
             k = b - 1;
@@ -286,12 +525,22 @@ __global__ void __launch_bounds__(NW * 32) stixel_dp_kernel(DpArgs a)
     }
 }
 
-constexpr int kDpWarps = 4;
-
-size_t dp_smem_bytes(int H, int P)
+template <bool kStd>
+cudaError_t launch_variant(const DpArgs& a, int ncols, size_t smem, cudaStream_t st)
 {
-    const size_t HP = (size_t)((H + 3) & ~3);
-    return sizeof(int32_t) * (8 * HP + 3 * (size_t)P + 2 * (HP + 4) + 2 * HP + 3 * HP + 3 * HP + 2048);
+    // opt in to large dynamic shared memory once per device
+    static bool configured[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!configured[dev]) {
+        e = cudaFuncSetAttribute(stixel_dp_kernel<kStd>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    stixel_dp_kernel<kStd><<<ncols, kThreads, smem, st>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -301,18 +550,7 @@ cudaError_t launch_dp(const int32_t* pd, const int32_t* pg, const int32_t* ps, c
                       uint32_t* err, cudaStream_t st)
 {
     if (g.H <= 0 || g.ncols <= 0) return cudaSuccess;
-    // opt in to large dynamic shared memory once per device
-    static bool configured[64] = {false};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!configured[dev]) {
-        e = cudaFuncSetAttribute(stixel_dp_kernel<kDpWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 227 * 1024);
-        if (e != cudaSuccess) return e;
-        configured[dev] = true;
-    }
+    if (g.H > STIXELS_MAX_HEIGHT) return cudaErrorInvalidValue;
     DpArgs a;
     a.pd = pd; a.pg = pg; a.ps = ps; a.po = po;
     a.H = g.H; a.P = g.P; a.F = m.dmax + 1;
@@ -320,9 +558,9 @@ cudaError_t launch_dp(const int32_t* pd, const int32_t* pg, const int32_t* ps, c
     a.stixels = out.stixels; a.counts = out.counts; a.cost = out.column_cost; a.cost_fixed = out.column_cost_fixed;
     a.cap = out.capacity;
     a.err = err;
-    const size_t smem = dp_smem_bytes(g.H, g.P);
-    stixel_dp_kernel<kDpWarps><<<g.ncols, kDpWarps * 32, smem, st>>>(a);
-    return cudaGetLastError();
+    const bool std_trans = m.trans[1][1] >= kBig && m.trans[1][2] >= kBig && m.trans[2][2] >= kBig;
+    const size_t smem = dp_smem_bytes(g.H);
+    return std_trans ? launch_variant<true>(a, g.ncols, smem, st) : launch_variant<false>(a, g.ncols, smem, st);
 }
 
 }  // namespace stx

@@ -7,15 +7,17 @@
 //   - the object per-pixel cost at every integer model disparity f in [0, dmax]
 //     (PO, the paper's LUT_object: (dmax+1) rows per column)
 // so that any stixel's data cost is the difference of two table entries.
-// Per-pixel cost: min(C_out, K + G[min(|q - 16 f|, 16 dmax)]), all int32 in
+// Per-pixel cost: min(C_out, K + G[min(|q - 16 f|, esat)]), all int32 in
 // 2^-14 units (see stixels.h); G is the per-class residual table built at
-// create time.
+// create time and esat the residual from which every pixel of the class costs
+// C_out (so the clamp changes no cost and the staged table is small: ~64
+// entries for sigma = 1 px).
 //
-// Work split: one warp per LUT row (as in the paper's Sec. 5.2), 16 rows per
-// 256-thread CTA, grid = (ncols, ceil((dmax + 4) / 16)).  A lane owns 4
-// consecutive outputs, so one chunk of the row is 128 entries: 4 in-register
-// adds, a 5-step shuffle scan of the lane totals, and one 16-byte store per
-// lane (512 contiguous bytes per warp store).  Rows are padded to a multiple
+// Work split: one warp per LUT row (as in the paper's Sec. 5.2), 32 rows per
+// 256-thread CTA, grid = (ncols, ceil((dmax + 4) / 32)).  A lane owns 8
+// consecutive outputs, so one chunk of the row is 256 entries: 7 in-register
+// adds, a 5-step shuffle scan of the lane totals, and two 16-byte stores per
+// lane.  Rows are padded to a multiple
 // of 4 entries (pitch P) so every store is aligned.  The kernel is bound by
 // the write bandwidth of the ncols x (dmax + 4) x P x 4-byte output.
 #include "internal.h"
@@ -23,7 +25,9 @@
 namespace stx {
 namespace {
 
-constexpr int kRowsPerCta = 16;
+constexpr int kRowsPerCta = 32;
+constexpr int kPerLane = 8;                    // consecutive outputs per lane
+constexpr int kChunk = 32 * kPerLane;          // outputs per warp iteration
 
 enum RowKind { kObject = 0, kDisp = 1, kGround = 2, kSky = 3 };
 
@@ -33,16 +37,19 @@ __global__ void __launch_bounds__(256) prefix_lut_kernel(const int16_t* __restri
                                                          int32_t* __restrict__ po)
 {
     extern __shared__ __align__(16) int32_t sm[];
-    const int HP = (H + 3) & ~3;
-    int32_t* s_q = sm;            // [HP]
-    int32_t* s_g = sm + HP;       // [emax + 1] object residual table
+    const int QP = (P + kChunk - 1) / kChunk * kChunk;
+    int32_t* s_q = sm;                           // [QP]: s_q[j] = q[j - 1] (j = 1..H), 0 elsewhere
+    int32_t* s_go = s_q + QP;                    // [esat_obj + 1]   residual tables, clamped at saturation
+    int32_t* s_gg = s_go + m.esat_obj + 1;       // [esat_ground + 1]
+    int32_t* s_gs = s_gg + m.esat_ground + 1;    // [esat_sky + 1]
     const int col = blockIdx.x;
     const int row0 = blockIdx.y * kRowsPerCta;
     const int R = F + 3;
 
-    for (int v = threadIdx.x; v < H; v += blockDim.x) s_q[v] = q[(size_t)col * H + v];
-    if (row0 < F)
-        for (int e = threadIdx.x; e <= m.emax; e += blockDim.x) s_g[e] = __ldg(m.g_obj + e);
+    for (int j = threadIdx.x; j < QP; j += blockDim.x) s_q[j] = (j >= 1 && j <= H) ? q[(size_t)col * H + j - 1] : 0;
+    for (int e = threadIdx.x; e <= m.esat_obj; e += blockDim.x) s_go[e] = __ldg(m.g_obj + e);
+    for (int e = threadIdx.x; e <= m.esat_ground; e += blockDim.x) s_gg[e] = __ldg(m.g_ground + e);
+    for (int e = threadIdx.x; e <= m.esat_sky; e += blockDim.x) s_gs[e] = __ldg(m.g_sky + e);
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -64,42 +71,47 @@ __global__ void __launch_bounds__(256) prefix_lut_kernel(const int16_t* __restri
         }
         const int f16 = 16 * f;
         int32_t carry = 0;
-        for (int base = 0; base < P; base += 128) {
-            const int j0 = base + 4 * lane;              // outputs j0 .. j0+3 hold sums over v < j
-            int32_t c[4];
+        for (int base = 0; base < P; base += kChunk) {
+            const int j0 = base + kPerLane * lane;       // outputs j0 .. j0+7 hold sums over v < j
+            // the lane's 8 codes in two 16-byte reads (conflict-free)
+            const int4 qa = *reinterpret_cast<const int4*>(s_q + j0);
+            const int4 qb = *reinterpret_cast<const int4*>(s_q + j0 + 4);
+            const int32_t qs[kPerLane] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+            int32_t c[kPerLane];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < kPerLane; ++i) {
                 const int v = j0 + i - 1;                 // pixel that enters at output j
                 int32_t x = 0;
                 if (v >= 0 && v < H) {
-                    const int32_t qv = s_q[v];
+                    const int32_t qv = qs[i];
                     if (kind == kObject) {
-                        const int e = min(abs(qv - f16), m.emax);
-                        x = min(m.c_out, kf + s_g[e]);
+                        x = min(m.c_out, kf + s_go[min(abs(qv - f16), m.esat_obj)]);
                     } else if (kind == kDisp) {
                         x = qv;
                     } else if (kind == kGround) {
-                        const int e = min(abs(qv - __ldg(rows.fgq + v)), m.emax);
-                        x = min(m.c_out, __ldg(rows.k_ground + v) + __ldg(m.g_ground + e));
+                        const int e = min(abs(qv - __ldg(rows.fgq + v)), m.esat_ground);
+                        x = min(m.c_out, __ldg(rows.k_ground + v) + s_gg[e]);
                     } else {
-                        x = min(m.c_out, m.k_sky + __ldg(m.g_sky + min(abs(qv), m.emax)));
+                        x = min(m.c_out, m.k_sky + s_gs[min(abs(qv), m.esat_sky)]);
                     }
                 }
                 c[i] = x;
             }
-            c[1] += c[0];
-            c[2] += c[1];
-            c[3] += c[2];
-            int32_t tot = c[3];
+#pragma unroll
+            for (int i = 1; i < kPerLane; ++i) c[i] += c[i - 1];
+            int32_t tot = c[kPerLane - 1];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int32_t t = __shfl_up_sync(0xffffffffu, tot, o);
                 if (lane >= o) tot += t;
             }
-            const int32_t add = carry + tot - c[3];       // exclusive prefix of this lane
-            if (j0 < P) {
-                int4 w = make_int4(c[0] + add, c[1] + add, c[2] + add, c[3] + add);
-                *reinterpret_cast<int4*>(out + j0) = w;
+            const int32_t add = carry + tot - c[kPerLane - 1];   // exclusive prefix of this lane
+#pragma unroll
+            for (int h = 0; h < kPerLane; h += 4) {
+                if (j0 + h < P) {
+                    int4 w = make_int4(c[h] + add, c[h + 1] + add, c[h + 2] + add, c[h + 3] + add);
+                    *reinterpret_cast<int4*>(out + j0 + h) = w;
+                }
             }
             carry += __shfl_sync(0xffffffffu, tot, 31);
         }
@@ -113,8 +125,8 @@ cudaError_t launch_luts(const int16_t* q, const FrameGeom& g, const ModelDev& m,
 {
     if (g.H <= 0 || g.ncols <= 0) return cudaSuccess;
     const int F = m.dmax + 1;
-    const int HP = (g.H + 3) & ~3;
-    const size_t smem = sizeof(int32_t) * ((size_t)HP + m.emax + 1);
+    const int QP = (g.P + kChunk - 1) / kChunk * kChunk;
+    const size_t smem = sizeof(int32_t) * ((size_t)QP + m.esat_obj + m.esat_ground + m.esat_sky + 3);
     dim3 grid(g.ncols, (F + 3 + kRowsPerCta - 1) / kRowsPerCta);
     prefix_lut_kernel<<<grid, 256, smem, st>>>(q, g.H, g.P, F, m, r, pd, pg, ps, po);
     return cudaGetLastError();

@@ -8,11 +8,11 @@
 // column-major and bottom-up (q[c * H + v], v = H-1-r) -- the layout the LUT
 // and DP stages read.
 //
-// A 256-thread CTA reduces a tile of 32 columns x 32 rows: a warp reads 32
-// consecutive groups of s pixels of one row (32 s contiguous floats, so the
-// warp's loads cover whole cache lines), the 32 x 32 results are transposed
-// through shared memory, and each warp then writes 32 consecutive bottom-up
-// rows of one column (a contiguous 64-byte store).  The kernel moves 4 W H
+// A 512-thread CTA reduces a tile of 32 columns x 16 rows, one output per
+// thread: a warp reads 32 consecutive groups of s pixels of one row (32 s
+// contiguous floats, so the warp's loads cover whole cache lines), the 32 x 16
+// results are transposed through shared memory, and each half-warp then writes
+// 16 consecutive bottom-up rows of one column (a contiguous 32-byte store).  The kernel moves 4 W H
 // bytes in and 2 ncols H bytes out and is bandwidth / launch bound.
 #include "internal.h"
 
@@ -56,33 +56,27 @@ __device__ __forceinline__ int reduce_group(const float* __restrict__ px, int dm
 }
 
 template <int S, int MODE>
-__global__ void __launch_bounds__(256) reduce_transpose_kernel(const float* __restrict__ disp, int H, int W,
+__global__ void __launch_bounds__(512) reduce_transpose_kernel(const float* __restrict__ disp, int H, int W,
                                                                int ncols, int dmax, int16_t* __restrict__ q)
 {
-    __shared__ int16_t tile[32][34];                 // [column][row], padded
-    const int tx = threadIdx.x, ty = threadIdx.y;    // 32 x 8
-    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-    const int c = c0 + tx;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int r = r0 + ty + 8 * i;
-        int val = 0;
-        if (c < ncols && r < H) val = reduce_group<S, MODE>(disp + (size_t)r * W + (size_t)c * S, dmax);
-        tile[tx][ty + 8 * i] = (int16_t)val;
-    }
+    __shared__ int16_t tile[32][18];                 // [column][row], padded
+    const int tx = threadIdx.x, ty = threadIdx.y;    // 32 x 16
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 16;
+    const int c = c0 + tx, r = r0 + ty;
+    int val = 0;
+    if (c < ncols && r < H) val = reduce_group<S, MODE>(disp + (size_t)r * W + (size_t)c * S, dmax);
+    tile[tx][ty] = (int16_t)val;
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int cc = c0 + ty + 8 * j;              // this warp's column
-        const int r = r0 + tx;                       // lane = row within the tile
-        if (cc < ncols && r < H) q[(size_t)cc * H + (H - 1 - r)] = tile[ty + 8 * j][tx];
-    }
+    // warp ty writes columns 2 ty and 2 ty + 1 of the tile: 16 bottom-up rows each
+    const int cc = c0 + 2 * ty + (tx >> 4);
+    const int rr = r0 + (tx & 15);
+    if (cc < ncols && rr < H) q[(size_t)cc * H + (H - 1 - rr)] = tile[2 * ty + (tx >> 4)][tx & 15];
 }
 
 template <int S>
 cudaError_t launch_s(const float* disp, const FrameGeom& g, int dmax, int mode, int16_t* q, cudaStream_t st)
 {
-    dim3 block(32, 8), grid((g.ncols + 31) / 32, (g.H + 31) / 32);
+    dim3 block(32, 16), grid((g.ncols + 31) / 32, (g.H + 15) / 16);
     if (mode == 1)
         reduce_transpose_kernel<S, 1><<<grid, block, 0, st>>>(disp, g.H, g.W, g.ncols, dmax, q);
     else

@@ -154,6 +154,14 @@ int build_model(const stixels_params_t* p, HostModel* m)
     const int32_t glast[3] = {m->g_obj[m->emax], m->g_ground[m->emax], m->g_sky[m->emax]};
     for (int c = 0; c < 3; ++c)
         if ((int64_t)kmin[c] + glast[c] < m->c_out) return STIXELS_E_INVALID_ARG;
+    // first residual from which every pixel of the class costs C_out (the tables
+    // are non-decreasing in e, and K >= kmin)
+    const std::vector<int32_t>* gtab[3] = {&m->g_obj, &m->g_ground, &m->g_sky};
+    for (int c = 0; c < 3; ++c) {
+        int e = 0;
+        while (e < m->emax && (int64_t)kmin[c] + (*gtab[c])[e] < m->c_out) ++e;
+        m->esat[c] = e;
+    }
 
     m->alpha = (double)p->baseline_m * cos((double)p->pitch_rad) / (double)p->camera_height_m;
 

@@ -24,6 +24,7 @@ struct HostModel {
     int32_t pen_grav = 0, pen_div = 0, pen_ord = 0;
     int32_t eps_g = 0, eps_d = 0, eps_o = 0;
     int32_t max_finite_prior = 0;       // largest finite prior + penalty sum for one stixel
+    int32_t esat[3] = {0, 0, 0};        // saturation residual (Q4) per class: object, ground, sky
 };
 
 // Validate params and build the model; returns a stixels_status.

@@ -237,6 +237,42 @@ int stixels_model_tables(const stixels_params_t* params, int H, int32_t* k_obj, 
                          int32_t* g_ground, int32_t* g_sky, int32_t* fgq, int32_t* k_ground,
                          int32_t* scalars);
 
+/*
+ * Scratch-free variant of stixels_compute (this library's addition; the paper
+ * has no counterpart).  For callers that cannot allocate device memory when
+ * they process a frame -- real-time loops where an allocation could stall or
+ * fail, code running inside another framework's memory pool or under a strict
+ * memory budget, or code that must not synchronise the device the way
+ * cudaMalloc / cudaFree can.  Such callers create the handle and call
+ * stixels_reserve(h, H, W) once at start-up; stixels_compute_noalloc then
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library call).
+ *
+ * Same computation, arguments and output as stixels_compute (device input,
+ * device output buffers, asynchronous on `stream`), but the frame's
+ * intermediate buffers (reduced column codes and prefix LUTs, the same bytes
+ * stixels_compute keeps in the handle's workspace) live in one fixed device
+ * array inside the library, STIXELS_NOALLOC_SCRATCH_BYTES large, which every
+ * device that loads the library keeps until the process exits.
+ *   - Size limit: frames whose intermediates exceed the array (about
+ *     ncols * (dmax + 4) * (H + 4) * 4 bytes) are rejected with
+ *     STIXELS_E_INVALID_ARG; 1024 x 440 at stixel width 5, dmax 128 fits.
+ *   - The handle must already hold the row tables for height H (from
+ *     stixels_reserve or an earlier stixels_compute with that height);
+ *     otherwise STIXELS_E_INVALID_ARG (creating them would allocate).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call uses the same array, which keeps the previous call's
+ *     contents; the pipeline overwrites every byte it reads, so nothing needs
+ *     clearing, but calls whose work overlaps on the same GPU (issued on
+ *     different streams or from different host threads) race on it: order
+ *     them on one stream or synchronise between them.  Each device has its own
+ *     copy of the array.
+ */
+#define STIXELS_NOALLOC_SCRATCH_BYTES (48u << 20)
+int stixels_compute_noalloc(stixels_t h, const float* d_disparity, int H, int W, void* stream,
+                            const stixels_output_t* out);
+
 /* Human-readable name of a status code (static storage). */
 const char* stixels_status_string(int status);
 

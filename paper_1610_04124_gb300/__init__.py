@@ -22,6 +22,7 @@ OBJECT, GROUND, SKY = 0, 1, 2
 OK, E_INVALID_ARG, E_OOM, E_CUDA, E_CAPACITY, E_NOT_READY, E_TIMEOUT, E_REJECTED, E_DEVICE_FAULT = range(9)
 ERR_CAPACITY, ERR_INFEASIBLE, ERR_TIMEOUT = 1, 2, 4
 MAX_HEIGHT = 2048
+NOALLOC_SCRATCH_BYTES = 48 << 20
 N_SCALARS = 20
 UNITS_PER_COST = 16384
 
@@ -94,6 +95,7 @@ def lib():
         L.stixels_build_luts.argtypes = [V, V, I, I, V, V, V, V, V]
         L.stixels_solve.argtypes = [V, V, V, V, V, I, I, V, P(Output)]
         L.stixels_model_tables.argtypes = [P(Params), I, V, V, V, V, V, V, V]
+        L.stixels_compute_noalloc.argtypes = [V, V, I, I, V, P(Output)]
         L.stixels_status_string.argtypes = [I]
         L.stixels_status_string.restype = C.c_char_p
         _lib = L
@@ -228,6 +230,15 @@ class Stixels:
             counts = np.zeros(max(ncols, 1), np.int32)
             cost = np.zeros(max(ncols, 1), np.float32)
         return st, counts, cost
+
+    def compute_noalloc(self, disparity, out, stream=None):
+        """stixels_compute_noalloc: same as compute(), intermediates in the library's
+        fixed scratch array (no device allocation; call reserve(H, W) first)."""
+        H, W = disparity.shape
+        o = self._out_struct(out)
+        _check(lib().stixels_compute_noalloc(self._h, _ptr(disparity), H, W, _stream_ptr(stream), C.byref(o)),
+               "stixels_compute_noalloc")
+        return out
 
     def compute_host(self, disparity: np.ndarray, out=None):
         """Host -> host pipeline (synchronous).  Returns (stixels, counts, cost, status)."""

@@ -138,6 +138,28 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace
 
+namespace stx {
+
+// Read-only view of a handle for a frame of height H, without creating
+// anything: fails with INVALID_ARG if the row tables for H do not exist yet.
+int handle_view(stixels_t h, int H, HandleView* v)
+{
+    if (!h || !v) return STIXELS_E_INVALID_ARG;
+    auto it = h->rows.find(H);
+    if (it == h->rows.end()) return STIXELS_E_INVALID_ARG;
+    v->device = h->device;
+    v->model = h->md;
+    v->rows.fgq = it->second.d;
+    v->rows.k_ground = it->second.d + H;
+    v->err = h->d_err;
+    v->stixel_width = h->hm.p.stixel_width;
+    v->reduce_mode = h->hm.p.reduce_mode;
+    v->capacity = h->hm.p.max_stixels_per_col;
+    return STIXELS_OK;
+}
+
+}  // namespace stx
+
 extern "C" {
 
 int stixels_params_default(stixels_params_t* p)

@@ -52,6 +52,16 @@ struct FrameGeom {
 
 inline int lut_pitch(int H) { return ((H + 1) + 3) & ~3; }
 
+// What the scratch-free entry point needs from a prepared handle.
+struct HandleView {
+    int device;
+    ModelDev model;
+    RowsDev rows;
+    uint32_t* err;
+    int stixel_width, reduce_mode, capacity;
+};
+int handle_view(stixels_t h, int H, HandleView* v);
+
 // ---- kernel launchers (kernels_*.cu); all return cudaGetLastError() ----
 cudaError_t launch_reduce(const float* disp, const FrameGeom& g, int dmax, int mode, int16_t* q,
                           cudaStream_t st);

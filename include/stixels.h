@@ -237,6 +237,59 @@ int stixels_model_tables(const stixels_params_t* params, int H, int32_t* k_obj, 
                          int32_t* g_ground, int32_t* g_sky, int32_t* fgq, int32_t* k_ground,
                          int32_t* scalars);
 
+/* ---- batched mode: many frames, one graph-captured launch sequence ---- */
+
+/*
+ * A batch is a fixed set of frames -- each with its own camera handle and its
+ * own size -- processed together: one launch per pipeline stage covers every
+ * column of every frame (columns are independent, Sec. 3), and the DP runs as
+ * one persistent kernel whose CTAs take columns from a shared work list,
+ * longest first.  The sequence is captured once as a CUDA graph and replayed by
+ * stixels_batch_launch.  The batch owns a device input slot and device output
+ * buffers per frame; the caller writes frames into the input slots and reads
+ * the outputs after the launch completes.  Not part of the paper (an
+ * execution mode of the same computation: each frame's results equal
+ * stixels_compute's).
+ */
+typedef struct stixels_batch_s* stixels_batch_t;
+typedef struct stixels_frame_desc {
+    stixels_t camera;          /* handle whose parameters the frame uses */
+    int32_t H, W;              /* frame size, 1 <= H <= STIXELS_MAX_HEIGHT */
+} stixels_frame_desc_t;
+typedef struct stixels_batch_config {
+    int32_t dp_warps;          /* warps per DP CTA: 8 (two CTAs per SM) or 16 (one) */
+    int32_t dp_ctas_per_sm;    /* persistent DP grid = SMs x this, 1..4 */
+} stixels_batch_config_t;
+
+/* Plan a batch: validates every frame, allocates all device memory at once
+ * (inputs, intermediates, outputs, work lists), and captures the graph with a
+ * default configuration.  The camera handles must outlive the batch.
+ * INVALID_ARG (bad frame / handle on another device), OOM, CUDA. */
+int stixels_batch_create(const stixels_frame_desc_t* frames, int nframes, stixels_batch_t* out);
+/* Device pointer of frame i's input slot (H x W FP32, row-major). */
+int stixels_batch_input(stixels_batch_t b, int i, float** d_frame);
+/* Device output buffers of frame i (valid until stixels_batch_destroy). */
+int stixels_batch_output(stixels_batch_t b, int i, stixels_output_t* out);
+/* Copy a frame (H x W FP32, host or device memory) into frame i's input slot,
+ * asynchronously on `stream` (cudaMemcpyDefault). */
+int stixels_batch_set_input(stixels_batch_t b, int i, const float* src, void* stream);
+/* Copy frame i's results out (host or device destinations; any may be NULL):
+ * stixels ncols * capacity records, counts / cost / cost_fixed ncols each. */
+int stixels_batch_get_output(stixels_batch_t b, int i, stixel_t* stixels, int32_t* counts, float* cost,
+                             int32_t* cost_fixed, void* stream);
+/* Replay the captured pipeline for all frames on `stream` (asynchronous). */
+int stixels_batch_launch(stixels_batch_t b, void* stream);
+/* Change the DP launch shape and re-capture the graph (synchronous). */
+int stixels_batch_set_config(stixels_batch_t b, const stixels_batch_config_t* cfg);
+int stixels_batch_get_config(stixels_batch_t b, stixels_batch_config_t* cfg);
+/* Autotuner: times every supported launch shape on this batch (a few
+ * launches each, CUDA events on `stream`) and keeps the fastest.  With a cache
+ * file (may be NULL), a previous result for the same device and batch shape
+ * (the multiset of frame sizes, stixel widths and dmax) is reused instead, and
+ * new results are appended.  *chosen (may be NULL) receives the choice. */
+int stixels_batch_tune(stixels_batch_t b, void* stream, const char* cache_path, stixels_batch_config_t* chosen);
+int stixels_batch_destroy(stixels_batch_t b);
+
 /*
  * Scratch-free variant of stixels_compute (this library's addition; the paper
  * has no counterpart).  For callers that cannot allocate device memory when
@@ -275,6 +328,9 @@ int stixels_compute_noalloc(stixels_t h, const float* d_disparity, int H, int W,
 
 /* Human-readable name of a status code (static storage). */
 const char* stixels_status_string(int status);
+/* Text of the CUDA error behind this thread's most recent STIXELS_E_CUDA /
+ * STIXELS_E_OOM status (static storage; "no error" if none). */
+const char* stixels_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

@@ -64,9 +64,20 @@ class Output(C.Structure):
                 ("column_cost_fixed", C.c_void_p), ("ncols", C.c_int32), ("capacity", C.c_int32)]
 
 
+class FrameDesc(C.Structure):
+    _fields_ = [("camera", C.c_void_p), ("H", C.c_int32), ("W", C.c_int32)]
+
+
+class BatchConfig(C.Structure):
+    _fields_ = [("dp_warps", C.c_int32), ("dp_ctas_per_sm", C.c_int32)]
+
+
 class StixelsError(RuntimeError):
     def __init__(self, status: int, what: str):
-        super().__init__(f"{what}: {lib().stixels_status_string(status).decode()} (status {status})")
+        detail = ""
+        if status in (E_CUDA, E_OOM):
+            detail = f" [{lib().stixels_last_cuda_error().decode()}]"
+        super().__init__(f"{what}: {lib().stixels_status_string(status).decode()} (status {status}){detail}")
         self.status = status
 
 
@@ -96,8 +107,20 @@ def lib():
         L.stixels_solve.argtypes = [V, V, V, V, V, I, I, V, P(Output)]
         L.stixels_model_tables.argtypes = [P(Params), I, V, V, V, V, V, V, V]
         L.stixels_compute_noalloc.argtypes = [V, V, I, I, V, P(Output)]
+        L.stixels_batch_create.argtypes = [P(FrameDesc), I, P(V)]
+        L.stixels_batch_input.argtypes = [V, I, P(V)]
+        L.stixels_batch_output.argtypes = [V, I, P(Output)]
+        L.stixels_batch_set_input.argtypes = [V, I, V, V]
+        L.stixels_batch_get_output.argtypes = [V, I, V, V, V, V, V]
+        L.stixels_batch_launch.argtypes = [V, V]
+        L.stixels_batch_set_config.argtypes = [V, P(BatchConfig)]
+        L.stixels_batch_get_config.argtypes = [V, P(BatchConfig)]
+        L.stixels_batch_tune.argtypes = [V, V, C.c_char_p, P(BatchConfig)]
+        L.stixels_batch_destroy.argtypes = [V]
         L.stixels_status_string.argtypes = [I]
         L.stixels_status_string.restype = C.c_char_p
+        L.stixels_last_cuda_error.argtypes = []
+        L.stixels_last_cuda_error.restype = C.c_char_p
         _lib = L
     return _lib
 
@@ -294,3 +317,64 @@ class Stixels:
         st = out["stixels"].cpu().numpy().view(STIXEL_DTYPE)[:ncols * cap].reshape(ncols, cap)
         return (st, out["counts"].cpu().numpy()[:ncols], out["cost"].cpu().numpy()[:ncols],
                 out["cost_fixed"].cpu().numpy()[:ncols])
+
+
+class Batch:
+    """A fixed set of frames (camera handle, H, W) run by one graph-captured launch."""
+
+    def __init__(self, frames):
+        self.frames = [(h, int(H), int(W)) for h, H, W in frames]
+        arr = (FrameDesc * len(self.frames))(*[FrameDesc(h.handle, H, W) for h, H, W in self.frames])
+        b = C.c_void_p()
+        _check(lib().stixels_batch_create(arr, len(self.frames), C.byref(b)), "stixels_batch_create")
+        self._b = b
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().stixels_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_input(self, i, src, stream=None):
+        """src: a CUDA tensor or a contiguous float32 numpy array (H, W)."""
+        ptr = src.data_ptr() if hasattr(src, "data_ptr") else np.ascontiguousarray(src, np.float32).ctypes.data
+        _check(lib().stixels_batch_set_input(self._b, i, ptr, _stream_ptr(stream)), "stixels_batch_set_input")
+
+    def launch(self, stream=None):
+        _check(lib().stixels_batch_launch(self._b, _stream_ptr(stream)), "stixels_batch_launch")
+
+    def output(self, i, stream=None):
+        """Frame i's results copied to host numpy: (stixels[ncols, cap], counts, cost, cost_fixed)."""
+        o = Output()
+        _check(lib().stixels_batch_output(self._b, i, C.byref(o)), "stixels_batch_output")
+        st = np.zeros(max(o.ncols * o.capacity, 1), STIXEL_DTYPE)
+        cnt = np.zeros(max(o.ncols, 1), np.int32)
+        cost = np.zeros(max(o.ncols, 1), np.float32)
+        fix = np.zeros(max(o.ncols, 1), np.int32)
+        _check(lib().stixels_batch_get_output(self._b, i, st.ctypes.data, cnt.ctypes.data, cost.ctypes.data,
+                                              fix.ctypes.data, _stream_ptr(stream)), "stixels_batch_get_output")
+        import torch
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        n = o.ncols
+        return st[:n * o.capacity].reshape(n, o.capacity), cnt[:n], cost[:n], fix[:n]
+
+    @property
+    def config(self):
+        c = BatchConfig()
+        _check(lib().stixels_batch_get_config(self._b, C.byref(c)), "stixels_batch_get_config")
+        return (c.dp_warps, c.dp_ctas_per_sm)
+
+    def set_config(self, dp_warps, dp_ctas_per_sm):
+        c = BatchConfig(dp_warps, dp_ctas_per_sm)
+        _check(lib().stixels_batch_set_config(self._b, C.byref(c)), "stixels_batch_set_config")
+
+    def tune(self, cache_path=None, stream=None):
+        c = BatchConfig()
+        path = cache_path.encode() if cache_path else None
+        _check(lib().stixels_batch_tune(self._b, _stream_ptr(stream), path, C.byref(c)), "stixels_batch_tune")
+        return (c.dp_warps, c.dp_ctas_per_sm)

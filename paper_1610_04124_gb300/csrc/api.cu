@@ -46,7 +46,7 @@ FrameLayout frame_layout(int H, int ncols, int F)
     return L;
 }
 
-int cuda_status(cudaError_t e) { return e == cudaSuccess ? STIXELS_OK : (e == cudaErrorMemoryAllocation ? STIXELS_E_OOM : STIXELS_E_CUDA); }
+int cuda_status(cudaError_t e) { return stx::status_from_cuda(e); }
 
 }  // namespace
 
@@ -140,6 +140,19 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 namespace stx {
 
+namespace {
+thread_local const char* t_last_cuda_error = "no error";
+}
+
+const char* t_last_cuda_error_string() { return t_last_cuda_error; }
+
+int status_from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return STIXELS_OK;
+    t_last_cuda_error = cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? STIXELS_E_OOM : STIXELS_E_CUDA;
+}
+
 // Read-only view of a handle for a frame of height H, without creating
 // anything: fails with INVALID_ARG if the row tables for H do not exist yet.
 int handle_view(stixels_t h, int H, HandleView* v)
@@ -156,6 +169,16 @@ int handle_view(stixels_t h, int H, HandleView* v)
     v->reduce_mode = h->hm.p.reduce_mode;
     v->capacity = h->hm.p.max_stixels_per_col;
     return STIXELS_OK;
+}
+
+// As handle_view, creating the row tables for H first if needed (allocates).
+int handle_prepare(stixels_t h, int H, HandleView* v)
+{
+    if (!h || H < 1 || H > STIXELS_MAX_HEIGHT) return STIXELS_E_INVALID_ARG;
+    RowsDev r;
+    int rc = ensure_rows(h, H, &r);
+    if (rc) return rc;
+    return handle_view(h, H, v);
 }
 
 }  // namespace stx
@@ -437,6 +460,8 @@ int stixels_model_tables(const stixels_params_t* params, int H, int32_t* k_obj, 
     }
     return STIXELS_OK;
 }
+
+const char* stixels_last_cuda_error(void) { return stx::t_last_cuda_error_string(); }
 
 const char* stixels_status_string(int status)
 {

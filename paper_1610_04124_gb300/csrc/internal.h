@@ -52,6 +52,42 @@ struct FrameGeom {
 
 inline int lut_pitch(int H) { return ((H + 1) + 3) & ~3; }
 
+// One frame's arguments for the reduction kernel (batch table entry).
+struct ReduceArgs {
+    const float* disp;
+    int H, W, ncols, dmax;
+    int16_t* q;
+};
+
+// One frame's arguments for the LUT kernel.
+struct LutArgs {
+    const int16_t* q;
+    int H, P, F;
+    ModelDev m;
+    RowsDev rows;
+    int32_t* pd;
+    int32_t* pg;
+    int32_t* ps;
+    int32_t* po;
+};
+
+// One frame's arguments for the DP kernel (per-frame launch or batch table entry).
+struct DpArgs {
+    const int32_t* pd;
+    const int32_t* pg;
+    const int32_t* ps;
+    const int32_t* po;
+    int H, P, F;
+    ModelDev m;
+    RowsDev rows;
+    stixel_t* stixels;
+    int32_t* counts;
+    float* cost;
+    int32_t* cost_fixed;
+    int cap;
+    uint32_t* err;
+};
+
 // What the scratch-free entry point needs from a prepared handle.
 struct HandleView {
     int device;
@@ -61,14 +97,33 @@ struct HandleView {
     int stixel_width, reduce_mode, capacity;
 };
 int handle_view(stixels_t h, int H, HandleView* v);
+// stixels status for a CUDA error, remembering its text for stixels_last_cuda_error()
+int status_from_cuda(cudaError_t e);
+const char* t_last_cuda_error_string();
+int handle_prepare(stixels_t h, int H, HandleView* v);
+int sm_count();
 
 // ---- kernel launchers (kernels_*.cu); all return cudaGetLastError() ----
 cudaError_t launch_reduce(const float* disp, const FrameGeom& g, int dmax, int mode, int16_t* q,
                           cudaStream_t st);
 cudaError_t launch_luts(const int16_t* q, const FrameGeom& g, const ModelDev& m, const RowsDev& r,
                         int32_t* pd, int32_t* pg, int32_t* ps, int32_t* po, cudaStream_t st);
+size_t lut_shared_bytes(int H, const ModelDev& m);
+int lut_row_groups(int F);
+cudaError_t launch_luts_batch(const LutArgs* d_frames, const int2* d_items, int nitems, int max_groups,
+                              size_t smem, cudaStream_t st);
+cudaError_t launch_reduce_batch(const ReduceArgs* d_frames, const int4* d_tiles, int ntiles, int s, int mode,
+                                cudaStream_t st);
 cudaError_t launch_dp(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po,
                       const FrameGeom& g, const ModelDev& m, const RowsDev& r,
                       const stixels_output_t& out, uint32_t* err, cudaStream_t st);
+void dp_frame_args(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po, const FrameGeom& g,
+                   const ModelDev& m, const RowsDev& r, const stixels_output_t& out, uint32_t* err, DpArgs* a);
+size_t dp_shared_bytes(int H);
+// Sets the DP kernels' shared-memory attributes (call outside stream capture).
+cudaError_t prepare_dp_kernels();
+// Persistent DP over a work list of (frame, column) items; *d_counter must be 0.
+cudaError_t launch_dp_batch(const DpArgs* d_frames, const int2* d_items, int nitems, int* d_counter, int maxH,
+                            int warps, bool std_trans, int grid, cudaStream_t st);
 
 }  // namespace stx

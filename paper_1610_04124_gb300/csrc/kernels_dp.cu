@@ -56,27 +56,8 @@ namespace stx {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kWarps = 8;
-constexpr int kThreads = kWarps * 32;
-constexpr int kBulk = kWarps - 1;    // warps besides the chain warp
 constexpr int kMaxBlocks = (STIXELS_MAX_HEIGHT + 31) / 32;
 constexpr int kSpinLimit = 1 << 24;  // polls (~20 ns apart) before a wait gives up
-
-struct DpArgs {
-    const int32_t* pd;
-    const int32_t* pg;
-    const int32_t* ps;
-    const int32_t* po;
-    int H, P, F;
-    ModelDev m;
-    RowsDev rows;
-    stixel_t* stixels;
-    int32_t* counts;
-    float* cost;
-    int32_t* cost_fixed;
-    int cap;
-    uint32_t* err;
-};
 
 // Context of one start row b, shared by every end row k >= b: the three
 // previous-class terms V_p[b-1] + T(object | p) + code(p) and the ordering
@@ -184,10 +165,16 @@ size_t dp_smem_bytes(int H)
            sizeof(int32_t) * 5 * HP + sizeof(ChainBuf) * 2 + sizeof(SyncState);
 }
 
-template <bool kStdTrans>
-__global__ void __launch_bounds__(kThreads, 2) stixel_dp_kernel(DpArgs a)
+// Solves column `col` of frame `a` with all NW warps of the CTA (one chain
+// warp, NW - 1 bulk warps); `sm` is the CTA's dynamic shared memory
+// (dp_smem_bytes).  Every warp returns from here; the caller synchronises
+// before reusing `sm`.
+template <int NW, bool kStdTrans>
+__device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_t* sm)
 {
-    const int col = blockIdx.x;
+    constexpr int kWarps = NW;
+    constexpr int kThreads = NW * 32;
+    constexpr int kBulk = NW - 1;                   // warps besides the chain warp
     const int H = a.H, P = a.P, F = a.F;
     const int HP = (H + 3) & ~3;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -195,10 +182,9 @@ __global__ void __launch_bounds__(kThreads, 2) stixel_dp_kernel(DpArgs a)
     // rotate the chain warp between CTAs so that two CTAs sharing an SM are
     // less likely to put their chain warps on the same scheduler; the other
     // warps are bulk warps 0 .. kBulk-1
-    const int chain = blockIdx.x & 3;
+    const int chain = col & 3;
     const int bulk_id = (warp - chain - 1 + kWarps) % kWarps;
 
-    extern __shared__ __align__(16) int32_t sm[];
     StartCtx* s_ctx = reinterpret_cast<StartCtx*>(sm);                // [HP]
     RowInfo* s_row = reinterpret_cast<RowInfo*>(s_ctx + HP);          // [HP + 4], row H holds pd8[H]
     GS4* s_gs = reinterpret_cast<GS4*>(s_row + HP + 4);               // [HP]
@@ -336,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, 2) stixel_dp_kernel(DpArgs a)
     if (warp != chain) {
         // ---------------------------------------------------------------- bulk warps
         for (int t = 0; t + 2 < NB; ++t) {
-            if (!wait_geq(v_final, t + 1, v_abort)) return;         // block t is final
+            if (!wait_geq(v_final, t + 1, v_abort)) break;          // block t is final
             const int jn = t + 2;
             if (sync->owner[jn] == bulk_id) {                         // the tile the chain needs next
                 bulk_tile(t, jn);
@@ -525,25 +511,118 @@ __global__ void __launch_bounds__(kThreads, 2) stixel_dp_kernel(DpArgs a)
     }
 }
 
-template <bool kStd>
-cudaError_t launch_variant(const DpArgs& a, int ncols, size_t smem, cudaStream_t st)
+template <int NW, bool kStd>
+__global__ void __launch_bounds__(NW * 32, 16 / NW) stixel_dp_kernel(DpArgs a)
 {
-    // opt in to large dynamic shared memory once per device
-    static bool configured[64] = {false};
+    extern __shared__ __align__(16) int32_t sm[];
+    dp_column<NW, kStd>(a, blockIdx.x, sm);
+}
+
+// Persistent form: each CTA takes columns from a work list (one shared atomic
+// counter, reset before the launch) until the list is empty.  The list is
+// ordered longest column first, so the last columns to start are the short ones.
+template <int NW, bool kStd>
+__global__ void __launch_bounds__(NW * 32, 16 / NW)
+    stixel_dp_batch_kernel(const DpArgs* __restrict__ frames, const int2* __restrict__ items, int nitems,
+                           int* counter)
+{
+    extern __shared__ __align__(16) int32_t sm[];
+    __shared__ DpArgs s_args;
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const int2 w = items[it];                        // (frame, column)
+        // the frame's arguments, staged in shared memory for the whole CTA
+        const int* src = reinterpret_cast<const int*>(frames + w.x);
+        int* dst = reinterpret_cast<int*>(&s_args);
+        for (int i = threadIdx.x; i < (int)(sizeof(DpArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+        dp_column<NW, kStd>(s_args, w.y, sm);
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+int sm_count()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!cached[dev]) cudaDeviceGetAttribute(&cached[dev], cudaDevAttrMultiProcessorCount, dev);
+    return cached[dev];
+}
+
+namespace {
+
+// opt a kernel in to large dynamic shared memory once per device
+template <typename K>
+cudaError_t allow_smem(K kernel, bool* done)
+{
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!configured[dev]) {
-        e = cudaFuncSetAttribute(stixel_dp_kernel<kStd>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (!done[dev]) {
+        // the per-block limit (227 KB) covers static + dynamic shared memory
+        cudaFuncAttributes attr;
+        e = cudaFuncGetAttributes(&attr, kernel);
         if (e != cudaSuccess) return e;
-        configured[dev] = true;
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 227 * 1024 - (int)attr.sharedSizeBytes);
+        if (e != cudaSuccess) return e;
+        done[dev] = true;
     }
-    stixel_dp_kernel<kStd><<<ncols, kThreads, smem, st>>>(a);
+    return cudaSuccess;
+}
+
+// per-instantiation "attribute set" flags, one per device
+template <int NW, bool kStd>
+bool* frame_flags() { static bool f[64] = {false}; return f; }
+template <int NW, bool kStd>
+bool* batch_flags() { static bool f[64] = {false}; return f; }
+
+template <int NW, bool kStd>
+cudaError_t launch_frame(const DpArgs& a, int ncols, size_t smem, cudaStream_t st)
+{
+    cudaError_t e = allow_smem(stixel_dp_kernel<NW, kStd>, frame_flags<NW, kStd>());
+    if (e != cudaSuccess) return e;
+    stixel_dp_kernel<NW, kStd><<<ncols, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
+template <int NW, bool kStd>
+cudaError_t launch_batch(const DpArgs* frames, const int2* items, int nitems, int* counter, int grid, size_t smem,
+                         cudaStream_t st)
+{
+    cudaError_t e = allow_smem(stixel_dp_batch_kernel<NW, kStd>, batch_flags<NW, kStd>());
+    if (e != cudaSuccess) return e;
+    stixel_dp_batch_kernel<NW, kStd><<<grid, NW * 32, smem, st>>>(frames, items, nitems, counter);
+    return cudaGetLastError();
+}
+
+bool standard_transitions(const ModelDev& m)
+{
+    return m.trans[1][1] >= kBig && m.trans[1][2] >= kBig && m.trans[2][2] >= kBig;
+}
+
 }  // namespace
+
+size_t dp_shared_bytes(int H) { return dp_smem_bytes(H); }
+
+void dp_frame_args(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po, const FrameGeom& g,
+                   const ModelDev& m, const RowsDev& r, const stixels_output_t& out, uint32_t* err, DpArgs* a)
+{
+    a->pd = pd; a->pg = pg; a->ps = ps; a->po = po;
+    a->H = g.H; a->P = g.P; a->F = m.dmax + 1;
+    a->m = m; a->rows = r;
+    a->stixels = out.stixels; a->counts = out.counts; a->cost = out.column_cost; a->cost_fixed = out.column_cost_fixed;
+    a->cap = out.capacity;
+    a->err = err;
+}
 
 cudaError_t launch_dp(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po,
                       const FrameGeom& g, const ModelDev& m, const RowsDev& r, const stixels_output_t& out,
@@ -552,15 +631,42 @@ cudaError_t launch_dp(const int32_t* pd, const int32_t* pg, const int32_t* ps, c
     if (g.H <= 0 || g.ncols <= 0) return cudaSuccess;
     if (g.H > STIXELS_MAX_HEIGHT) return cudaErrorInvalidValue;
     DpArgs a;
-    a.pd = pd; a.pg = pg; a.ps = ps; a.po = po;
-    a.H = g.H; a.P = g.P; a.F = m.dmax + 1;
-    a.m = m; a.rows = r;
-    a.stixels = out.stixels; a.counts = out.counts; a.cost = out.column_cost; a.cost_fixed = out.column_cost_fixed;
-    a.cap = out.capacity;
-    a.err = err;
-    const bool std_trans = m.trans[1][1] >= kBig && m.trans[1][2] >= kBig && m.trans[2][2] >= kBig;
+    dp_frame_args(pd, pg, ps, po, g, m, r, out, err, &a);
     const size_t smem = dp_smem_bytes(g.H);
-    return std_trans ? launch_variant<true>(a, g.ncols, smem, st) : launch_variant<false>(a, g.ncols, smem, st);
+    // with no more columns than SMs, each column gets a whole SM: 16 warps
+    // (15 bulk); otherwise two 8-warp CTAs share an SM
+    const bool wide = g.ncols <= sm_count();
+    if (standard_transitions(m))
+        return wide ? launch_frame<16, true>(a, g.ncols, smem, st) : launch_frame<8, true>(a, g.ncols, smem, st);
+    return wide ? launch_frame<16, false>(a, g.ncols, smem, st) : launch_frame<8, false>(a, g.ncols, smem, st);
+}
+
+cudaError_t prepare_dp_kernels()
+{
+    // attribute changes are not stream operations: do them before any capture
+    cudaError_t e = allow_smem(stixel_dp_batch_kernel<8, true>, batch_flags<8, true>());
+    if (e == cudaSuccess) e = allow_smem(stixel_dp_batch_kernel<8, false>, batch_flags<8, false>());
+    if (e == cudaSuccess) e = allow_smem(stixel_dp_batch_kernel<16, true>, batch_flags<16, true>());
+    if (e == cudaSuccess) e = allow_smem(stixel_dp_batch_kernel<16, false>, batch_flags<16, false>());
+    if (e == cudaSuccess) e = allow_smem(stixel_dp_kernel<8, true>, frame_flags<8, true>());
+    if (e == cudaSuccess) e = allow_smem(stixel_dp_kernel<8, false>, frame_flags<8, false>());
+    if (e == cudaSuccess) e = allow_smem(stixel_dp_kernel<16, true>, frame_flags<16, true>());
+    if (e == cudaSuccess) e = allow_smem(stixel_dp_kernel<16, false>, frame_flags<16, false>());
+    if (e == cudaSuccess && sm_count() <= 0) e = cudaErrorInvalidDevice;
+    return e;
+}
+
+cudaError_t launch_dp_batch(const DpArgs* d_frames, const int2* d_items, int nitems, int* d_counter, int maxH,
+                            int warps, bool std_trans, int grid, cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    if (maxH <= 0 || maxH > STIXELS_MAX_HEIGHT || grid <= 0) return cudaErrorInvalidValue;
+    const size_t smem = dp_smem_bytes(maxH);
+    if (warps == 16)
+        return std_trans ? launch_batch<16, true>(d_frames, d_items, nitems, d_counter, grid, smem, st)
+                         : launch_batch<16, false>(d_frames, d_items, nitems, d_counter, grid, smem, st);
+    return std_trans ? launch_batch<8, true>(d_frames, d_items, nitems, d_counter, grid, smem, st)
+                     : launch_batch<8, false>(d_frames, d_items, nitems, d_counter, grid, smem, st);
 }
 
 }  // namespace stx

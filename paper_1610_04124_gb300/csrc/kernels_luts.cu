@@ -31,19 +31,23 @@ constexpr int kChunk = 32 * kPerLane;          // outputs per warp iteration
 
 enum RowKind { kObject = 0, kDisp = 1, kGround = 2, kSky = 3 };
 
-__global__ void __launch_bounds__(256) prefix_lut_kernel(const int16_t* __restrict__ q, int H, int P, int F,
-                                                         ModelDev m, RowsDev rows, int32_t* __restrict__ pd,
-                                                         int32_t* __restrict__ pg, int32_t* __restrict__ ps,
-                                                         int32_t* __restrict__ po)
+// Rows [row0, row0 + kRowsPerCta) of column `col`'s LUTs (row f < F: object
+// at disparity f; F: disparities; F + 1: ground; F + 2: sky), by one CTA.
+__device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const int row0, int32_t* sm)
 {
-    extern __shared__ __align__(16) int32_t sm[];
+    const int16_t* __restrict__ q = a.q;
+    const int H = a.H, P = a.P, F = a.F;
+    const ModelDev& m = a.m;
+    const RowsDev& rows = a.rows;
+    int32_t* __restrict__ pd = a.pd;
+    int32_t* __restrict__ pg = a.pg;
+    int32_t* __restrict__ ps = a.ps;
+    int32_t* __restrict__ po = a.po;
     const int QP = (P + kChunk - 1) / kChunk * kChunk;
     int32_t* s_q = sm;                           // [QP]: s_q[j] = q[j - 1] (j = 1..H), 0 elsewhere
     int32_t* s_go = s_q + QP;                    // [esat_obj + 1]   residual tables, clamped at saturation
     int32_t* s_gg = s_go + m.esat_obj + 1;       // [esat_ground + 1]
     int32_t* s_gs = s_gg + m.esat_ground + 1;    // [esat_sky + 1]
-    const int col = blockIdx.x;
-    const int row0 = blockIdx.y * kRowsPerCta;
     const int R = F + 3;
 
     for (int j = threadIdx.x; j < QP; j += blockDim.x) s_q[j] = (j >= 1 && j <= H) ? q[(size_t)col * H + j - 1] : 0;
@@ -118,17 +122,57 @@ __global__ void __launch_bounds__(256) prefix_lut_kernel(const int16_t* __restri
     }
 }
 
+__global__ void __launch_bounds__(256) prefix_lut_kernel(LutArgs a)
+{
+    extern __shared__ __align__(16) int32_t sm[];
+    lut_rows(a, blockIdx.x, blockIdx.y * kRowsPerCta, sm);
+}
+
+// Batch form: blockIdx.x indexes a list of (frame, column) items, blockIdx.y
+// the row group; groups beyond a frame's F + 3 rows return at once.
+__global__ void __launch_bounds__(256) prefix_lut_batch_kernel(const LutArgs* __restrict__ frames,
+                                                               const int2* __restrict__ items)
+{
+    extern __shared__ __align__(16) int32_t sm[];
+    __shared__ LutArgs s_args;
+    const int2 w = items[blockIdx.x];
+    const int* src = reinterpret_cast<const int*>(frames + w.x);
+    int* dst = reinterpret_cast<int*>(&s_args);
+    for (int i = threadIdx.x; i < (int)(sizeof(LutArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    if ((int)blockIdx.y * kRowsPerCta >= s_args.F + 3) return;
+    lut_rows(s_args, w.y, blockIdx.y * kRowsPerCta, sm);
+}
+
 }  // namespace
+
+size_t lut_shared_bytes(int H, const ModelDev& m)
+{
+    const int P = lut_pitch(H);
+    const int QP = (P + kChunk - 1) / kChunk * kChunk;
+    return sizeof(int32_t) * ((size_t)QP + m.esat_obj + m.esat_ground + m.esat_sky + 3);
+}
+
+int lut_row_groups(int F) { return (F + 3 + kRowsPerCta - 1) / kRowsPerCta; }
 
 cudaError_t launch_luts(const int16_t* q, const FrameGeom& g, const ModelDev& m, const RowsDev& r,
                         int32_t* pd, int32_t* pg, int32_t* ps, int32_t* po, cudaStream_t st)
 {
     if (g.H <= 0 || g.ncols <= 0) return cudaSuccess;
-    const int F = m.dmax + 1;
-    const int QP = (g.P + kChunk - 1) / kChunk * kChunk;
-    const size_t smem = sizeof(int32_t) * ((size_t)QP + m.esat_obj + m.esat_ground + m.esat_sky + 3);
-    dim3 grid(g.ncols, (F + 3 + kRowsPerCta - 1) / kRowsPerCta);
-    prefix_lut_kernel<<<grid, 256, smem, st>>>(q, g.H, g.P, F, m, r, pd, pg, ps, po);
+    LutArgs a;
+    a.q = q; a.H = g.H; a.P = g.P; a.F = m.dmax + 1; a.m = m; a.rows = r;
+    a.pd = pd; a.pg = pg; a.ps = ps; a.po = po;
+    dim3 grid(g.ncols, lut_row_groups(a.F));
+    prefix_lut_kernel<<<grid, 256, lut_shared_bytes(g.H, m), st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_luts_batch(const LutArgs* d_frames, const int2* d_items, int nitems, int max_groups,
+                              size_t smem, cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    dim3 grid(nitems, max_groups);
+    prefix_lut_batch_kernel<<<grid, 256, smem, st>>>(d_frames, d_items);
     return cudaGetLastError();
 }
 

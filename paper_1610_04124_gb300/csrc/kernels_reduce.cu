@@ -73,6 +73,38 @@ __global__ void __launch_bounds__(512) reduce_transpose_kernel(const float* __re
     if (cc < ncols && rr < H) q[(size_t)cc * H + (H - 1 - rr)] = tile[2 * ty + (tx >> 4)][tx & 15];
 }
 
+// Batch form: blockIdx.x indexes a list of (frame, column tile, row tile)
+// items of frames that share stixel width S and reduction mode.
+template <int S, int MODE>
+__global__ void __launch_bounds__(512) reduce_transpose_batch_kernel(const ReduceArgs* __restrict__ frames,
+                                                                     const int4* __restrict__ tiles)
+{
+    __shared__ int16_t tile[32][18];
+    const int4 w = tiles[blockIdx.x];                // (frame, first column, first row, -)
+    const ReduceArgs a = frames[w.x];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int c0 = w.y, r0 = w.z;
+    const int c = c0 + tx, r = r0 + ty;
+    int val = 0;
+    if (c < a.ncols && r < a.H) val = reduce_group<S, MODE>(a.disp + (size_t)r * a.W + (size_t)c * S, a.dmax);
+    tile[tx][ty] = (int16_t)val;
+    __syncthreads();
+    const int cc = c0 + 2 * ty + (tx >> 4);
+    const int rr = r0 + (tx & 15);
+    if (cc < a.ncols && rr < a.H) a.q[(size_t)cc * a.H + (a.H - 1 - rr)] = tile[2 * ty + (tx >> 4)][tx & 15];
+}
+
+template <int S>
+cudaError_t launch_batch_s(const ReduceArgs* frames, const int4* tiles, int ntiles, int mode, cudaStream_t st)
+{
+    dim3 block(32, 16);
+    if (mode == 1)
+        reduce_transpose_batch_kernel<S, 1><<<ntiles, block, 0, st>>>(frames, tiles);
+    else
+        reduce_transpose_batch_kernel<S, 0><<<ntiles, block, 0, st>>>(frames, tiles);
+    return cudaGetLastError();
+}
+
 template <int S>
 cudaError_t launch_s(const float* disp, const FrameGeom& g, int dmax, int mode, int16_t* q, cudaStream_t st)
 {
@@ -107,6 +139,31 @@ cudaError_t launch_reduce(const float* disp, const FrameGeom& g, int dmax, int m
         case 14: return launch_s<14>(disp, g, dmax, mode, q, st);
         case 15: return launch_s<15>(disp, g, dmax, mode, q, st);
         case 16: return launch_s<16>(disp, g, dmax, mode, q, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_reduce_batch(const ReduceArgs* d_frames, const int4* d_tiles, int ntiles, int s, int mode,
+                                cudaStream_t st)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    switch (s) {
+        case 1: return launch_batch_s<1>(d_frames, d_tiles, ntiles, mode, st);
+        case 2: return launch_batch_s<2>(d_frames, d_tiles, ntiles, mode, st);
+        case 3: return launch_batch_s<3>(d_frames, d_tiles, ntiles, mode, st);
+        case 4: return launch_batch_s<4>(d_frames, d_tiles, ntiles, mode, st);
+        case 5: return launch_batch_s<5>(d_frames, d_tiles, ntiles, mode, st);
+        case 6: return launch_batch_s<6>(d_frames, d_tiles, ntiles, mode, st);
+        case 7: return launch_batch_s<7>(d_frames, d_tiles, ntiles, mode, st);
+        case 8: return launch_batch_s<8>(d_frames, d_tiles, ntiles, mode, st);
+        case 9: return launch_batch_s<9>(d_frames, d_tiles, ntiles, mode, st);
+        case 10: return launch_batch_s<10>(d_frames, d_tiles, ntiles, mode, st);
+        case 11: return launch_batch_s<11>(d_frames, d_tiles, ntiles, mode, st);
+        case 12: return launch_batch_s<12>(d_frames, d_tiles, ntiles, mode, st);
+        case 13: return launch_batch_s<13>(d_frames, d_tiles, ntiles, mode, st);
+        case 14: return launch_batch_s<14>(d_frames, d_tiles, ntiles, mode, st);
+        case 15: return launch_batch_s<15>(d_frames, d_tiles, ntiles, mode, st);
+        case 16: return launch_batch_s<16>(d_frames, d_tiles, ntiles, mode, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -290,6 +290,50 @@ int stixels_batch_get_config(stixels_batch_t b, stixels_batch_config_t* cfg);
 int stixels_batch_tune(stixels_batch_t b, void* stream, const char* cache_path, stixels_batch_config_t* chosen);
 int stixels_batch_destroy(stixels_batch_t b);
 
+/* ---- serving: continuous batching of frames from many cameras ---- */
+
+/*
+ * A server admits frames from any number of camera handles as they arrive and
+ * runs them with continuous batching: a scheduler thread takes every admitted
+ * frame whose input has been copied in, runs them together as one batch (the
+ * kernels of the batched mode, tables rebuilt per iteration), and alternates
+ * between two CUDA streams, so frames admitted while another iteration is on
+ * the GPU start in the next iteration and the two overlap on the device.
+ * Device memory comes from one arena of mem_budget_bytes allocated at
+ * creation: a frame is admitted only if a slot and arena space for its input,
+ * intermediates and outputs are free, else stixels_submit returns
+ * STIXELS_E_REJECTED at once.  Results are bit-identical to stixels_compute on
+ * the same frame alone.  submit and poll are thread-safe.  A camera handle in
+ * use by a server must not be used concurrently outside it.
+ */
+typedef struct stixels_server_s* stixels_server_t;
+typedef struct stixels_server_stats {
+    uint64_t submitted, admitted, rejected, completed, iterations;
+    uint64_t frames_in_iterations;     /* sum of batch sizes (mean batch = this / iterations) */
+    uint64_t bytes_in_use, bytes_budget;
+    int32_t slots_in_use, max_slots;
+} stixels_server_stats_t;
+
+/* Create a server on the current device: allocates the arena (mem_budget_bytes,
+ * >= 1 MiB) and starts the scheduler thread.  max_slots in [1, 4096]. */
+int stixels_server_create(size_t mem_budget_bytes, int max_slots, stixels_server_t* out);
+/* Admit one frame (H x W FP32 in host or device memory) for `camera`: copies it
+ * into the server (the caller may reuse the buffer on return) and queues it.
+ * *ticket identifies the request.  STIXELS_E_REJECTED if no slot or not enough
+ * arena memory is free right now; INVALID_ARG for a bad frame or handle. */
+int stixels_submit(stixels_server_t s, stixels_t camera, const float* disparity, int H, int W, uint64_t* ticket);
+/* Wait up to timeout_us (0 = just check) for the ticket's result.  On success
+ * copies the result into `out` (host or device buffers, ncols / capacity as
+ * stixels_output_shape; column_cost, column_cost_fixed optional), frees the
+ * frame's slot and retires the ticket.  STIXELS_E_NOT_READY if timeout_us == 0
+ * and the frame is not done, STIXELS_E_TIMEOUT if a positive wait ran out,
+ * INVALID_ARG for an unknown ticket or mismatched buffers. */
+int stixels_poll(stixels_server_t s, uint64_t ticket, const stixels_output_t* out, int timeout_us);
+int stixels_server_stats(stixels_server_t s, stixels_server_stats_t* stats);
+/* Stop the scheduler, wait for frames on the GPU, release everything.  Tickets
+ * not yet polled are dropped. */
+int stixels_server_destroy(stixels_server_t s);
+
 /*
  * Scratch-free variant of stixels_compute (this library's addition; the paper
  * has no counterpart).  For callers that cannot allocate device memory when

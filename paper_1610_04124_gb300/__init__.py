@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build_mod
 
-__all__ = ["Params", "Stixels", "STIXEL_DTYPE", "StixelsError", "lib", "default_params",
+__all__ = ["Params", "Stixels", "Batch", "Server", "STIXEL_DTYPE", "StixelsError", "lib", "default_params",
            "model_tables", "lut_pitch", "OBJECT", "GROUND", "SKY"]
 
 OBJECT, GROUND, SKY = 0, 1, 2
@@ -72,6 +72,13 @@ class BatchConfig(C.Structure):
     _fields_ = [("dp_warps", C.c_int32), ("dp_ctas_per_sm", C.c_int32)]
 
 
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("admitted", C.c_uint64), ("rejected", C.c_uint64),
+                ("completed", C.c_uint64), ("iterations", C.c_uint64), ("frames_in_iterations", C.c_uint64),
+                ("bytes_in_use", C.c_uint64), ("bytes_budget", C.c_uint64),
+                ("slots_in_use", C.c_int32), ("max_slots", C.c_int32)]
+
+
 class StixelsError(RuntimeError):
     def __init__(self, status: int, what: str):
         detail = ""
@@ -117,6 +124,11 @@ def lib():
         L.stixels_batch_get_config.argtypes = [V, P(BatchConfig)]
         L.stixels_batch_tune.argtypes = [V, V, C.c_char_p, P(BatchConfig)]
         L.stixels_batch_destroy.argtypes = [V]
+        L.stixels_server_create.argtypes = [C.c_size_t, I, P(V)]
+        L.stixels_submit.argtypes = [V, V, V, I, I, P(C.c_uint64)]
+        L.stixels_poll.argtypes = [V, C.c_uint64, P(Output), I]
+        L.stixels_server_stats.argtypes = [V, P(ServerStats)]
+        L.stixels_server_destroy.argtypes = [V]
         L.stixels_status_string.argtypes = [I]
         L.stixels_status_string.restype = C.c_char_p
         L.stixels_last_cuda_error.argtypes = []
@@ -378,3 +390,64 @@ class Batch:
         path = cache_path.encode() if cache_path else None
         _check(lib().stixels_batch_tune(self._b, _stream_ptr(stream), path, C.byref(c)), "stixels_batch_tune")
         return (c.dp_warps, c.dp_ctas_per_sm)
+
+
+class Server:
+    """Continuous-batching server over many camera handles (stixels_server_*)."""
+
+    def __init__(self, mem_budget_bytes: int, max_slots: int = 256):
+        s = C.c_void_p()
+        _check(lib().stixels_server_create(int(mem_budget_bytes), int(max_slots), C.byref(s)),
+               "stixels_server_create")
+        self._s = s
+        self._shape = {}                         # ticket -> (ncols, capacity)
+
+    def close(self):
+        if getattr(self, "_s", None):
+            lib().stixels_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, camera: Stixels, disparity) -> Optional[int]:
+        """Admit one frame (CUDA tensor or float32 numpy array); the ticket, or None if rejected."""
+        if hasattr(disparity, "data_ptr"):
+            assert disparity.dtype.is_floating_point and disparity.element_size() == 4 and disparity.is_contiguous()
+            ptr, (H, W) = disparity.data_ptr(), disparity.shape
+        else:
+            assert isinstance(disparity, np.ndarray) and disparity.dtype == np.float32 and \
+                disparity.flags.c_contiguous
+            ptr, (H, W) = disparity.ctypes.data, disparity.shape
+        t = C.c_uint64()
+        rc = _check(lib().stixels_submit(self._s, camera.handle, ptr, H, W, C.byref(t)), "stixels_submit",
+                    (OK, E_REJECTED))
+        if rc != OK:
+            return None
+        self._shape[t.value] = camera.output_shape(H, W)
+        return t.value
+
+    def poll(self, ticket: int, out, timeout_us: int = 0) -> int:
+        """Wait up to timeout_us for the ticket; fills `out` and returns OK / E_CAPACITY, or
+        E_NOT_READY / E_TIMEOUT while the frame is not done.  `out` is a
+        (stixels, counts, cost) host tuple as Stixels.alloc_host_output, or a device dict
+        as Stixels.alloc_output."""
+        ncols, cap = self._shape.get(int(ticket), (0, 0))
+        if isinstance(out, dict):
+            o = Stixels._out_struct(out)
+        else:
+            st, counts, cost = out
+            o = Output(st.ctypes.data, counts.ctypes.data, cost.ctypes.data, 0, ncols, cap)
+        rc = _check(lib().stixels_poll(self._s, int(ticket), C.byref(o), int(timeout_us)), "stixels_poll",
+                    (OK, E_CAPACITY, E_NOT_READY, E_TIMEOUT))
+        if rc in (OK, E_CAPACITY):
+            self._shape.pop(int(ticket), None)
+        return rc
+
+    def stats(self) -> Dict[str, int]:
+        st = ServerStats()
+        _check(lib().stixels_server_stats(self._s, C.byref(st)), "stixels_server_stats")
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_}

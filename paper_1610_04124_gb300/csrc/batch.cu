@@ -1,7 +1,7 @@
 // batch.cu -- batched mode: a fixed set of frames (each with its own camera
 // handle and size) processed by one graph-captured launch sequence, with a
 // persistent DP kernel over a longest-first column work list, and an autotuner
-// for the DP launch shape.
+// for the DP launch shape.  The table planning here is shared with the server.
 #include <stdio.h>
 #include <string.h>
 
@@ -12,24 +12,131 @@
 
 #include "internal.h"
 
+namespace stx {
+
+namespace {
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+}  // namespace
+
+size_t frame_work_bytes(const FrameGeom& g, int dmax)
+{
+    const size_t C = (size_t)g.ncols, P = (size_t)g.P, F = (size_t)dmax + 1;
+    return up256(sizeof(int16_t) * C * g.H) + 3 * up256(sizeof(int32_t) * C * P) + up256(sizeof(int32_t) * C * F * P);
+}
+
+void frame_work_carve(FrameJob* job, char* base)
+{
+    const FrameGeom& g = job->g;
+    const size_t C = (size_t)g.ncols, P = (size_t)g.P;
+    size_t off = 0;
+    job->q = (int16_t*)(base + off);  off += up256(sizeof(int16_t) * C * g.H);
+    job->pd = (int32_t*)(base + off); off += up256(sizeof(int32_t) * C * P);
+    job->pg = (int32_t*)(base + off); off += up256(sizeof(int32_t) * C * P);
+    job->ps = (int32_t*)(base + off); off += up256(sizeof(int32_t) * C * P);
+    job->po = (int32_t*)(base + off);
+}
+
+void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
+{
+    const int n = (int)jobs.size();
+    std::vector<ReduceArgs> ra(n);
+    std::vector<LutArgs> la(n);
+    std::vector<DpArgs> da(n);
+    std::vector<int2> lut_items, dp_items;
+    std::vector<std::vector<int4>> group_tiles;
+    t->groups.clear();
+    t->maxH = t->max_groups = 0;
+    t->lut_smem = 0;
+    t->std_trans = true;
+    for (int i = 0; i < n; ++i) {
+        const FrameJob& f = jobs[i];
+        const ModelDev& m = f.view.model;
+        ra[i].disp = f.in;
+        ra[i].H = f.g.H; ra[i].W = f.g.W; ra[i].ncols = f.g.ncols; ra[i].dmax = m.dmax;
+        ra[i].q = f.q;
+        la[i].q = f.q;
+        la[i].H = f.g.H; la[i].P = f.g.P; la[i].F = m.dmax + 1; la[i].m = m; la[i].rows = f.view.rows;
+        la[i].pd = f.pd; la[i].pg = f.pg; la[i].ps = f.ps; la[i].po = f.po;
+        dp_frame_args(f.pd, f.pg, f.ps, f.po, f.g, m, f.view.rows, f.out, f.view.err, &da[i]);
+        if (f.g.ncols == 0) continue;
+        t->maxH = std::max(t->maxH, f.g.H);
+        t->max_groups = std::max(t->max_groups, lut_row_groups(m.dmax + 1));
+        t->lut_smem = std::max(t->lut_smem, lut_shared_bytes(f.g.H, m));
+        t->std_trans = t->std_trans && m.trans[1][1] >= kBig && m.trans[1][2] >= kBig && m.trans[2][2] >= kBig;
+        for (int c = 0; c < f.g.ncols; ++c) {
+            lut_items.push_back(make_int2(i, c));
+            dp_items.push_back(make_int2(i, c));
+        }
+        int gi = -1;
+        for (size_t k = 0; k < t->groups.size(); ++k)
+            if (t->groups[k].s == f.g.s && t->groups[k].mode == f.view.reduce_mode) gi = (int)k;
+        if (gi < 0) {
+            t->groups.push_back(ReduceGroup{f.g.s, f.view.reduce_mode, 0, 0});
+            group_tiles.emplace_back();
+            gi = (int)t->groups.size() - 1;
+        }
+        for (int c0 = 0; c0 < f.g.ncols; c0 += 32)
+            for (int r0 = 0; r0 < f.g.H; r0 += 16) group_tiles[gi].push_back(make_int4(i, c0, r0, 0));
+    }
+    // DP work list: longest columns first (work grows as H^2), stable otherwise
+    std::stable_sort(dp_items.begin(), dp_items.end(),
+                     [&](const int2& x, const int2& y) { return jobs[x.x].g.H > jobs[y.x].g.H; });
+    t->nitems = (int)dp_items.size();
+
+    size_t o = 0;
+    t->o_red = o; o += up256(sizeof(ReduceArgs) * n);
+    t->o_lut = o; o += up256(sizeof(LutArgs) * n);
+    t->o_dp = o;  o += up256(sizeof(DpArgs) * n);
+    t->o_li = o;  o += up256(sizeof(int2) * lut_items.size());
+    t->o_di = o;  o += up256(sizeof(int2) * dp_items.size());
+    t->o_cnt = o; o += 256;
+    for (size_t k = 0; k < t->groups.size(); ++k) {
+        t->groups[k].tiles_off = o;
+        t->groups[k].ntiles = (int)group_tiles[k].size();
+        o += up256(sizeof(int4) * group_tiles[k].size());
+    }
+    t->host.assign(o, 0);
+    char* h = t->host.data();
+    memcpy(h + t->o_red, ra.data(), sizeof(ReduceArgs) * n);
+    memcpy(h + t->o_lut, la.data(), sizeof(LutArgs) * n);
+    memcpy(h + t->o_dp, da.data(), sizeof(DpArgs) * n);
+    if (!lut_items.empty()) memcpy(h + t->o_li, lut_items.data(), sizeof(int2) * lut_items.size());
+    if (!dp_items.empty()) memcpy(h + t->o_di, dp_items.data(), sizeof(int2) * dp_items.size());
+    for (size_t k = 0; k < t->groups.size(); ++k)
+        memcpy(h + t->groups[k].tiles_off, group_tiles[k].data(), sizeof(int4) * group_tiles[k].size());
+}
+
+cudaError_t enqueue_tables(const BatchTables& t, char* d_tab, int dp_warps, int dp_ctas_per_sm, cudaStream_t st)
+{
+    int* counter = (int*)(d_tab + t.o_cnt);
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    for (const ReduceGroup& gr : t.groups) {
+        if (e != cudaSuccess) return e;
+        e = launch_reduce_batch((const ReduceArgs*)(d_tab + t.o_red), (const int4*)(d_tab + gr.tiles_off), gr.ntiles,
+                                gr.s, gr.mode, st);
+    }
+    if (e == cudaSuccess)
+        e = launch_luts_batch((const LutArgs*)(d_tab + t.o_lut), (const int2*)(d_tab + t.o_li), t.nitems, t.max_groups,
+                              t.lut_smem, st);
+    if (e == cudaSuccess) {
+        const int grid = std::max(1, std::min(t.nitems, sm_count() * dp_ctas_per_sm));
+        e = launch_dp_batch((const DpArgs*)(d_tab + t.o_dp), (const int2*)(d_tab + t.o_di), t.nitems, counter, t.maxH,
+                            dp_warps, t.std_trans, grid, st);
+    }
+    return e;
+}
+
+}  // namespace stx
+
 using namespace stx;
 
 namespace {
 
-size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+size_t up256b(size_t x) { return (x + 255) / 256 * 256; }
 
 struct FramePlan {
-    stixels_t cam;
-    HandleView view;
-    FrameGeom g;
-    size_t in_off, q_off, pd_off, pg_off, ps_off, po_off;
-    size_t st_off, cnt_off, cost_off, fix_off;
-};
-
-struct ReduceGroup {            // frames sharing stixel width and reduction mode
-    int s, mode;
-    size_t tiles_off;           // offset of its int4 tiles in the table block
-    int ntiles;
+    FrameJob job;
+    size_t in_off, work_off, st_off, cnt_off, cost_off, fix_off;
 };
 
 }  // namespace
@@ -37,19 +144,10 @@ struct ReduceGroup {            // frames sharing stixel width and reduction mod
 struct stixels_batch_s {
     int device = 0;
     std::vector<FramePlan> frames;
-    std::vector<ReduceGroup> groups;
+    BatchTables tables;
     void* d_mem = nullptr;                 // inputs, intermediates, outputs
     void* d_tab = nullptr;                 // argument tables and work lists
-    size_t mem_bytes = 0, tab_bytes = 0;
-    ReduceArgs* d_reduce = nullptr;
-    LutArgs* d_lut = nullptr;
-    DpArgs* d_dp = nullptr;
-    int2* d_lut_items = nullptr;
-    int2* d_dp_items = nullptr;
-    int* d_counter = nullptr;
-    int nitems = 0, max_groups = 0, maxH = 0;
-    size_t lut_smem = 0;
-    bool std_trans = true;
+    size_t mem_bytes = 0;
     stixels_batch_config_t cfg{8, 2};
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
@@ -58,40 +156,19 @@ struct stixels_batch_s {
 
 namespace {
 
-int status_of(cudaError_t e) { return status_from_cuda(e); }
-
-cudaError_t enqueue(stixels_batch_t b, cudaStream_t st)
-{
-    cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st);
-    for (const ReduceGroup& gr : b->groups) {
-        if (e != cudaSuccess) return e;
-        e = launch_reduce_batch(b->d_reduce, reinterpret_cast<const int4*>((char*)b->d_tab + gr.tiles_off), gr.ntiles,
-                                gr.s, gr.mode, st);
-    }
-    if (e == cudaSuccess)
-        e = launch_luts_batch(b->d_lut, b->d_lut_items, b->nitems, b->max_groups, b->lut_smem, st);
-    if (e == cudaSuccess) {
-        const int grid = std::max(1, std::min(b->nitems, sm_count() * b->cfg.dp_ctas_per_sm));
-        e = launch_dp_batch(b->d_dp, b->d_dp_items, b->nitems, b->d_counter, b->maxH, b->cfg.dp_warps, b->std_trans,
-                            grid, st);
-    }
-    return e;
-}
-
 int capture(stixels_batch_t b)
 {
     cudaError_t pe = prepare_dp_kernels();
-    if (pe != cudaSuccess) return status_of(pe);
+    if (pe != cudaSuccess) return status_from_cuda(pe);
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
     cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return status_of(e);
-    cudaError_t e2 = enqueue(b, b->cap_stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    cudaError_t e2 = enqueue_tables(b->tables, (char*)b->d_tab, b->cfg.dp_warps, b->cfg.dp_ctas_per_sm, b->cap_stream);
     e = cudaStreamEndCapture(b->cap_stream, &b->graph);
-    if (e2 != cudaSuccess) return status_of(e2);
-    if (e != cudaSuccess) return status_of(e);
-    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
-    return status_of(e);
+    if (e2 != cudaSuccess) return status_from_cuda(e2);
+    if (e != cudaSuccess) return status_from_cuda(e);
+    return status_from_cuda(cudaGraphInstantiate(&b->exec, b->graph, 0));
 }
 
 bool config_ok(const stixels_batch_config_t& c)
@@ -105,7 +182,7 @@ std::string batch_signature(stixels_batch_t b)
     std::vector<std::string> parts;
     for (const FramePlan& f : b->frames) {
         char buf[96];
-        snprintf(buf, sizeof(buf), "%dx%d/s%d/d%d", f.g.W, f.g.H, f.g.s, f.view.model.dmax);
+        snprintf(buf, sizeof(buf), "%dx%d/s%d/d%d", f.job.g.W, f.job.g.H, f.job.g.s, f.job.view.model.dmax);
         parts.push_back(buf);
     }
     std::sort(parts.begin(), parts.end());
@@ -134,116 +211,47 @@ int stixels_batch_create(const stixels_frame_desc_t* frames, int nframes, stixel
     size_t off = 0;
     for (int i = 0; i < nframes; ++i) {
         const stixels_frame_desc_t& d = frames[i];
-        FramePlan f;
-        f.cam = d.camera;
         if (!d.camera || d.H < 1 || d.H > STIXELS_MAX_HEIGHT || d.W < 1 || d.W > (1 << 24)) {
             delete b;
             return STIXELS_E_INVALID_ARG;
         }
-        int rc = handle_prepare(d.camera, d.H, &f.view);
+        FramePlan f;
+        int rc = handle_prepare(d.camera, d.H, &f.job.view);
         if (rc != STIXELS_OK) { delete b; return rc; }
-        if (f.view.device != b->device) { delete b; return STIXELS_E_INVALID_ARG; }
-        f.g.H = d.H; f.g.W = d.W; f.g.s = f.view.stixel_width; f.g.ncols = d.W / f.g.s; f.g.P = lut_pitch(d.H);
-        const size_t C = (size_t)f.g.ncols, P = (size_t)f.g.P, F = (size_t)f.view.model.dmax + 1;
-        f.in_off = off;   off += up256(sizeof(float) * (size_t)d.H * d.W);
-        f.q_off = off;    off += up256(sizeof(int16_t) * C * d.H);
-        f.pd_off = off;   off += up256(sizeof(int32_t) * C * P);
-        f.pg_off = off;   off += up256(sizeof(int32_t) * C * P);
-        f.ps_off = off;   off += up256(sizeof(int32_t) * C * P);
-        f.po_off = off;   off += up256(sizeof(int32_t) * C * F * P);
-        f.st_off = off;   off += up256(sizeof(stixel_t) * C * f.view.capacity);
-        f.cnt_off = off;  off += up256(sizeof(int32_t) * C);
-        f.cost_off = off; off += up256(sizeof(float) * C);
-        f.fix_off = off;  off += up256(sizeof(int32_t) * C);
+        if (f.job.view.device != b->device) { delete b; return STIXELS_E_INVALID_ARG; }
+        FrameGeom& g = f.job.g;
+        g.H = d.H; g.W = d.W; g.s = f.job.view.stixel_width; g.ncols = d.W / g.s; g.P = lut_pitch(d.H);
+        const size_t C = (size_t)g.ncols;
+        f.in_off = off;   off += up256b(sizeof(float) * (size_t)d.H * d.W);
+        f.work_off = off; off += frame_work_bytes(g, f.job.view.model.dmax);
+        f.st_off = off;   off += up256b(sizeof(stixel_t) * C * f.job.view.capacity);
+        f.cnt_off = off;  off += up256b(sizeof(int32_t) * C);
+        f.cost_off = off; off += up256b(sizeof(float) * C);
+        f.fix_off = off;  off += up256b(sizeof(int32_t) * C);
         b->frames.push_back(f);
     }
     b->mem_bytes = std::max<size_t>(off, 256);
     cudaError_t e = cudaMalloc(&b->d_mem, b->mem_bytes);
-    if (e != cudaSuccess) { stixels_batch_destroy(b); return status_of(e); }
+    if (e != cudaSuccess) { stixels_batch_destroy(b); return status_from_cuda(e); }
     char* mem = (char*)b->d_mem;
-
-    // host-side tables
-    const int n = nframes;
-    std::vector<ReduceArgs> ra(n);
-    std::vector<LutArgs> la(n);
-    std::vector<DpArgs> da(n);
-    std::vector<int2> lut_items, dp_items;
-    std::vector<std::vector<int4>> group_tiles;
-    for (int i = 0; i < n; ++i) {
-        FramePlan& f = b->frames[i];
-        const ModelDev& m = f.view.model;
-        ra[i].disp = (const float*)(mem + f.in_off);
-        ra[i].H = f.g.H; ra[i].W = f.g.W; ra[i].ncols = f.g.ncols; ra[i].dmax = m.dmax;
-        ra[i].q = (int16_t*)(mem + f.q_off);
-        la[i].q = (const int16_t*)(mem + f.q_off);
-        la[i].H = f.g.H; la[i].P = f.g.P; la[i].F = m.dmax + 1; la[i].m = m; la[i].rows = f.view.rows;
-        la[i].pd = (int32_t*)(mem + f.pd_off); la[i].pg = (int32_t*)(mem + f.pg_off);
-        la[i].ps = (int32_t*)(mem + f.ps_off); la[i].po = (int32_t*)(mem + f.po_off);
-        stixels_output_t o;
-        o.stixels = (stixel_t*)(mem + f.st_off); o.counts = (int32_t*)(mem + f.cnt_off);
-        o.column_cost = (float*)(mem + f.cost_off); o.column_cost_fixed = (int32_t*)(mem + f.fix_off);
-        o.ncols = f.g.ncols; o.capacity = f.view.capacity;
-        dp_frame_args(la[i].pd, la[i].pg, la[i].ps, la[i].po, f.g, m, f.view.rows, o, f.view.err, &da[i]);
-        b->maxH = std::max(b->maxH, f.g.H);
-        b->max_groups = std::max(b->max_groups, lut_row_groups(m.dmax + 1));
-        b->lut_smem = std::max(b->lut_smem, lut_shared_bytes(f.g.H, m));
-        b->std_trans = b->std_trans && m.trans[1][1] >= kBig && m.trans[1][2] >= kBig && m.trans[2][2] >= kBig;
-        for (int c = 0; c < f.g.ncols; ++c) {
-            lut_items.push_back(make_int2(i, c));
-            dp_items.push_back(make_int2(i, c));
-        }
-        // reduction tiles, grouped by (stixel width, mode)
-        int gi = -1;
-        for (size_t k = 0; k < b->groups.size(); ++k)
-            if (b->groups[k].s == f.g.s && b->groups[k].mode == f.view.reduce_mode) gi = (int)k;
-        if (gi < 0) {
-            b->groups.push_back(ReduceGroup{f.g.s, f.view.reduce_mode, 0, 0});
-            group_tiles.emplace_back();
-            gi = (int)b->groups.size() - 1;
-        }
-        for (int c0 = 0; c0 < f.g.ncols; c0 += 32)
-            for (int r0 = 0; r0 < f.g.H; r0 += 16) group_tiles[gi].push_back(make_int4(i, c0, r0, 0));
+    std::vector<FrameJob> jobs;
+    for (FramePlan& f : b->frames) {
+        f.job.in = (const float*)(mem + f.in_off);
+        frame_work_carve(&f.job, mem + f.work_off);
+        f.job.out.stixels = (stixel_t*)(mem + f.st_off);
+        f.job.out.counts = (int32_t*)(mem + f.cnt_off);
+        f.job.out.column_cost = (float*)(mem + f.cost_off);
+        f.job.out.column_cost_fixed = (int32_t*)(mem + f.fix_off);
+        f.job.out.ncols = f.job.g.ncols;
+        f.job.out.capacity = f.job.view.capacity;
+        jobs.push_back(f.job);
     }
-    // DP work list: longest columns first (work grows as H^2), stable otherwise
-    std::stable_sort(dp_items.begin(), dp_items.end(), [&](const int2& x, const int2& y) {
-        return b->frames[x.x].g.H > b->frames[y.x].g.H;
-    });
-    b->nitems = (int)dp_items.size();
-
-    // device tables in one block
-    size_t t = 0;
-    const size_t o_red = t;  t += up256(sizeof(ReduceArgs) * n);
-    const size_t o_lut = t;  t += up256(sizeof(LutArgs) * n);
-    const size_t o_dp = t;   t += up256(sizeof(DpArgs) * n);
-    const size_t o_li = t;   t += up256(sizeof(int2) * lut_items.size());
-    const size_t o_di = t;   t += up256(sizeof(int2) * dp_items.size());
-    const size_t o_cnt = t;  t += 256;
-    for (size_t k = 0; k < b->groups.size(); ++k) {
-        b->groups[k].tiles_off = t;
-        b->groups[k].ntiles = (int)group_tiles[k].size();
-        t += up256(sizeof(int4) * group_tiles[k].size());
-    }
-    b->tab_bytes = t;
-    std::vector<char> host(t, 0);
-    memcpy(host.data() + o_red, ra.data(), sizeof(ReduceArgs) * n);
-    memcpy(host.data() + o_lut, la.data(), sizeof(LutArgs) * n);
-    memcpy(host.data() + o_dp, da.data(), sizeof(DpArgs) * n);
-    memcpy(host.data() + o_li, lut_items.data(), sizeof(int2) * lut_items.size());
-    memcpy(host.data() + o_di, dp_items.data(), sizeof(int2) * dp_items.size());
-    for (size_t k = 0; k < b->groups.size(); ++k)
-        memcpy(host.data() + b->groups[k].tiles_off, group_tiles[k].data(), sizeof(int4) * group_tiles[k].size());
-    e = cudaMalloc(&b->d_tab, t);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_tab, host.data(), t, cudaMemcpyHostToDevice);
+    plan_tables(jobs, &b->tables);
+    e = cudaMalloc(&b->d_tab, b->tables.host.size());
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_tab, b->tables.host.data(), b->tables.host.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->d_mem, 0, b->mem_bytes);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) { stixels_batch_destroy(b); return status_of(e); }
-    char* tab = (char*)b->d_tab;
-    b->d_reduce = (ReduceArgs*)(tab + o_red);
-    b->d_lut = (LutArgs*)(tab + o_lut);
-    b->d_dp = (DpArgs*)(tab + o_dp);
-    b->d_lut_items = (int2*)(tab + o_li);
-    b->d_dp_items = (int2*)(tab + o_di);
-    b->d_counter = (int*)(tab + o_cnt);
+    if (e != cudaSuccess) { stixels_batch_destroy(b); return status_from_cuda(e); }
     int rc = capture(b);
     if (rc != STIXELS_OK) { stixels_batch_destroy(b); return rc; }
     *out = b;
@@ -260,14 +268,7 @@ int stixels_batch_input(stixels_batch_t b, int i, float** d_frame)
 int stixels_batch_output(stixels_batch_t b, int i, stixels_output_t* out)
 {
     if (!b || !out || i < 0 || i >= (int)b->frames.size()) return STIXELS_E_INVALID_ARG;
-    const FramePlan& f = b->frames[i];
-    char* mem = (char*)b->d_mem;
-    out->stixels = (stixel_t*)(mem + f.st_off);
-    out->counts = (int32_t*)(mem + f.cnt_off);
-    out->column_cost = (float*)(mem + f.cost_off);
-    out->column_cost_fixed = (int32_t*)(mem + f.fix_off);
-    out->ncols = f.g.ncols;
-    out->capacity = f.view.capacity;
+    *out = b->frames[i].job.out;
     return STIXELS_OK;
 }
 
@@ -275,38 +276,38 @@ int stixels_batch_set_input(stixels_batch_t b, int i, const float* src, void* st
 {
     if (!b || !src || i < 0 || i >= (int)b->frames.size()) return STIXELS_E_INVALID_ARG;
     const FramePlan& f = b->frames[i];
-    return status_of(cudaMemcpyAsync((char*)b->d_mem + f.in_off, src, sizeof(float) * (size_t)f.g.H * f.g.W,
-                                     cudaMemcpyDefault, (cudaStream_t)stream));
+    return status_from_cuda(cudaMemcpyAsync((char*)b->d_mem + f.in_off, src,
+                                            sizeof(float) * (size_t)f.job.g.H * f.job.g.W, cudaMemcpyDefault,
+                                            (cudaStream_t)stream));
 }
 
 int stixels_batch_get_output(stixels_batch_t b, int i, stixel_t* stixels, int32_t* counts, float* cost,
                              int32_t* cost_fixed, void* stream)
 {
     if (!b || i < 0 || i >= (int)b->frames.size()) return STIXELS_E_INVALID_ARG;
-    const FramePlan& f = b->frames[i];
-    const char* mem = (const char*)b->d_mem;
-    const size_t C = (size_t)f.g.ncols;
+    const stixels_output_t& o = b->frames[i].job.out;
+    const size_t C = (size_t)o.ncols;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
-    if (stixels) e = cudaMemcpyAsync(stixels, mem + f.st_off, sizeof(stixel_t) * C * f.view.capacity, cudaMemcpyDefault, st);
-    if (e == cudaSuccess && counts) e = cudaMemcpyAsync(counts, mem + f.cnt_off, sizeof(int32_t) * C, cudaMemcpyDefault, st);
-    if (e == cudaSuccess && cost) e = cudaMemcpyAsync(cost, mem + f.cost_off, sizeof(float) * C, cudaMemcpyDefault, st);
+    if (stixels) e = cudaMemcpyAsync(stixels, o.stixels, sizeof(stixel_t) * C * o.capacity, cudaMemcpyDefault, st);
+    if (e == cudaSuccess && counts) e = cudaMemcpyAsync(counts, o.counts, sizeof(int32_t) * C, cudaMemcpyDefault, st);
+    if (e == cudaSuccess && cost) e = cudaMemcpyAsync(cost, o.column_cost, sizeof(float) * C, cudaMemcpyDefault, st);
     if (e == cudaSuccess && cost_fixed)
-        e = cudaMemcpyAsync(cost_fixed, mem + f.fix_off, sizeof(int32_t) * C, cudaMemcpyDefault, st);
-    return status_of(e);
+        e = cudaMemcpyAsync(cost_fixed, o.column_cost_fixed, sizeof(int32_t) * C, cudaMemcpyDefault, st);
+    return status_from_cuda(e);
 }
 
 int stixels_batch_launch(stixels_batch_t b, void* stream)
 {
     if (!b || !b->exec) return STIXELS_E_INVALID_ARG;
-    return status_of(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    return status_from_cuda(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
 }
 
 int stixels_batch_set_config(stixels_batch_t b, const stixels_batch_config_t* cfg)
 {
     if (!b || !cfg || !config_ok(*cfg)) return STIXELS_E_INVALID_ARG;
     cudaError_t e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return status_of(e);
+    if (e != cudaSuccess) return status_from_cuda(e);
     b->cfg = *cfg;
     return capture(b);
 }
@@ -348,7 +349,8 @@ int stixels_batch_tune(stixels_batch_t b, void* stream, const char* cache_path, 
     const stixels_batch_config_t cands[] = {{8, 2}, {16, 1}, {8, 1}, {8, 3}};
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return STIXELS_E_CUDA;
+    if (cudaEventCreate(&e0) != cudaSuccess) return STIXELS_E_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return STIXELS_E_CUDA; }
     float best_ms = 0.0f;
     stixels_batch_config_t best = b->cfg;
     int rc = STIXELS_OK;
@@ -362,7 +364,7 @@ int stixels_batch_tune(stixels_batch_t b, void* stream, const char* cache_path, 
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.0f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) { rc = status_of(e); break; }
+        if (e != cudaSuccess) { rc = status_from_cuda(e); break; }
         if (best_ms == 0.0f || ms < best_ms) { best_ms = ms; best = c; }
     }
     cudaEventDestroy(e0);

@@ -3,6 +3,8 @@
 
 #include <stdint.h>
 
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "stixels.h"
@@ -120,6 +122,38 @@ cudaError_t launch_dp(const int32_t* pd, const int32_t* pg, const int32_t* ps, c
 void dp_frame_args(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po, const FrameGeom& g,
                    const ModelDev& m, const RowsDev& r, const stixels_output_t& out, uint32_t* err, DpArgs* a);
 size_t dp_shared_bytes(int H);
+// ---- batch planning shared by the batched mode and the server (batch.cu) ----
+// One frame's device buffers for a pipeline run.
+struct FrameJob {
+    HandleView view;
+    FrameGeom g;
+    const float* in;
+    int16_t* q;
+    int32_t *pd, *pg, *ps, *po;
+    stixels_output_t out;
+};
+// Bytes of intermediates (q, PD, PG, PS, PO) a frame needs, and their carving
+// from one 256-byte-aligned block.
+size_t frame_work_bytes(const FrameGeom& g, int dmax);
+void frame_work_carve(FrameJob* job, char* base);
+struct ReduceGroup {            // frames sharing stixel width and reduction mode
+    int s, mode;
+    size_t tiles_off;           // offset of its int4 tiles in the table block
+    int ntiles;
+};
+// Host image of the argument tables and work lists of a set of frames.
+struct BatchTables {
+    std::vector<char> host;
+    size_t o_red = 0, o_lut = 0, o_dp = 0, o_li = 0, o_di = 0, o_cnt = 0;
+    std::vector<ReduceGroup> groups;
+    int nitems = 0, max_groups = 0, maxH = 0;
+    size_t lut_smem = 0;
+    bool std_trans = true;
+};
+void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t);
+// Launches all stages for tables already copied to d_tab (counter reset included).
+cudaError_t enqueue_tables(const BatchTables& t, char* d_tab, int dp_warps, int dp_ctas_per_sm, cudaStream_t st);
+
 // Sets the DP kernels' shared-memory attributes (call outside stream capture).
 cudaError_t prepare_dp_kernels();
 // Persistent DP over a work list of (frame, column) items; *d_counter must be 0.

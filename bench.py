@@ -37,7 +37,11 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by the sha1 of the kernel's source file at the time of the capture.  A
 # kernel whose source changed since reports null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    "kernels_dp.cu": ("a060475ddc0b", 15461632),
+    "kernels_luts.cu": ("e944a4b7d3b9", 210688),
+    "kernels_reduce.cu": ("fc07f6c2866c", 1808512),
+}
 
 
 def _sha(path):
@@ -62,6 +66,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-seconds", type=float, default=2.0, help="length of the Poisson arrival trace")
     return ap.parse_args()
 
 
@@ -148,6 +155,188 @@ def oracle_rate(cam, scene_fn, seconds, max_frames=64):
         el = time.perf_counter() - t0
         if el >= seconds or frames >= max_frames:
             return frames / el, frames, el
+
+
+# ----------------------------------------------------------------------------- batched / served
+
+def _cells(cam):
+    return (cam.width // cam.stixel_width) * cam.height * (cam.height + 1) // 2
+
+
+def bench_batched(S, scenes, torch, dev, cams, seed0, launches, label):
+    """One graph-captured batch over `cams` (one frame each), autotuned; frames/s over `launches`
+    back-to-back launches (inputs and LUTs far exceed L2, so no flush is needed)."""
+    hs = [S.Stixels(S.default_params(c)) for c in cams]
+    b = S.Batch([(h, c.height, c.width) for h, c in zip(hs, cams)])
+    for i, c in enumerate(cams):
+        sc = scenes.make_scene(c, seed0 + i, n_obstacles=(8, 20))
+        b.set_input(i, torch.from_numpy(sc.disparity).to(dev))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    chosen = b.tune(None, stream)
+    for _ in range(3):
+        b.launch(stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(launches):
+        b.launch(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / launches
+    cells = sum(_cells(c) for c in cams)
+    b.close()
+    for h in hs:
+        h.close()
+    return {"workload": label, "frames": len(cams), "launches_timed": launches, "ms_per_launch": ms,
+            "frames_per_s": len(cams) / (ms / 1000.0), "dp_cells_per_s": cells / (ms / 1000.0),
+            "tuned_config": {"dp_warps": chosen[0], "dp_ctas_per_sm": chosen[1]},
+            "kernels_per_launch": "reduce (one per stixel-width/mode group) + LUT + persistent DP, one CUDA graph"}
+
+
+def bench_served(S, scenes, torch, seconds, rate=2000.0, budget=20 << 30, seed=5000):
+    """8 cameras, Poisson arrivals at `rate` frames/s in aggregate, host frames in pinned memory,
+    submitted by one client thread at their arrival times and polled by another; latency =
+    completion of poll (results in host memory) - scheduled arrival."""
+    import queue
+    import threading
+
+    import numpy as np
+
+    cams = scenes.serving_cameras(seed)
+    hs = [S.Stixels(S.default_params(c)) for c in cams]
+    per_cam = 3
+    frames = []
+    for k, c in enumerate(cams):
+        fr = []
+        for j in range(per_cam):
+            d = scenes.make_scene(c, seed + 100 * k + j, n_obstacles=(8, 20)).disparity
+            fr.append(torch.from_numpy(d).pin_memory().numpy())
+        frames.append(fr)
+    outs = [hs[k].alloc_host_output(c.height, c.width, pinned=True) for k, c in enumerate(cams)]
+    srv = S.Server(budget, max_slots=1024)
+    # warm-up: one frame per camera
+    for k in range(8):
+        t = srv.submit(hs[k], frames[k][0])
+        srv.poll(t, outs[k], timeout_us=10_000_000)
+
+    rng = np.random.default_rng(seed)
+    n = int(rate * seconds)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    which = rng.integers(0, 8, size=n)
+    pending = queue.Queue()
+    lat = np.zeros(n)
+    done_at = np.zeros(n)
+    retries = [0]
+    t0 = time.perf_counter() + 0.05
+
+    def client():
+        for i in range(n):
+            k = int(which[i])
+            wait = t0 + arrivals[i] - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            while True:
+                t = srv.submit(hs[k], frames[k][i % per_cam])
+                if t is not None:
+                    break
+                retries[0] += 1
+                time.sleep(50e-6)
+            pending.put((i, k, t))
+        pending.put(None)
+
+    def poller():
+        live = []
+        finished = False
+        while not finished or live:
+            try:
+                while True:
+                    item = pending.get_nowait()
+                    if item is None:
+                        finished = True
+                        break
+                    live.append(item)
+            except queue.Empty:
+                pass
+            progressed = False
+            keep = []
+            for (i, k, t) in live:
+                rc = srv.poll(t, outs[k], timeout_us=0)
+                if rc == S.E_NOT_READY:
+                    keep.append((i, k, t))
+                    continue
+                now = time.perf_counter()
+                done_at[i] = now
+                lat[i] = now - (t0 + arrivals[i])
+                progressed = True
+            live = keep
+            if not progressed:
+                time.sleep(20e-6)
+
+    th = [threading.Thread(target=client), threading.Thread(target=poller)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    st = srv.stats()
+    srv.close()
+    for h in hs:
+        h.close()
+    span = float(done_at.max() - t0)
+    lat_ms = np.sort(lat) * 1000.0
+    return {"workload": "8 cameras (3x 640x240 dmax 64, 3x 1024x440, 2x 2048x880 dmax 128; s=5), Poisson "
+                        f"arrivals {rate:.0f} frames/s aggregate, {budget >> 30} GB arena budget, host frames "
+                        "(pinned) in, results in host memory out",
+            "offered_fps": rate, "frames": n, "achieved_fps": n / span,
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "max_ms": float(lat_ms[-1]), "mean_batch": st["frames_in_iterations"] / max(st["iterations"], 1),
+            "iterations": st["iterations"], "rejected_retries": retries[0],
+            "latency": "scheduled arrival -> poll returned with results in host memory"}
+
+
+def bench_served_saturated(S, scenes, torch, frames_total=2000, budget=20 << 30, seed=5000):
+    """Serving capacity: all frames submitted as fast as admission allows (no arrival pacing)."""
+    import threading
+
+    cams = scenes.serving_cameras(seed)
+    hs = [S.Stixels(S.default_params(c)) for c in cams]
+    frames = [torch.from_numpy(scenes.make_scene(c, seed + 100 * k, n_obstacles=(8, 20)).disparity)
+              .pin_memory().numpy() for k, c in enumerate(cams)]
+    outs = [hs[k].alloc_host_output(c.height, c.width, pinned=True) for k, c in enumerate(cams)]
+    srv = S.Server(budget, max_slots=1024)
+    for k in range(8):
+        srv.poll(srv.submit(hs[k], frames[k]), outs[k], timeout_us=10_000_000)
+    import queue
+    pending = queue.Queue()
+
+    def client():
+        for i in range(frames_total):
+            k = i % 8
+            while True:
+                t = srv.submit(hs[k], frames[k])
+                if t is not None:
+                    break
+                time.sleep(50e-6)
+            pending.put((k, t))
+        pending.put(None)
+
+    t0 = time.perf_counter()
+    th = threading.Thread(target=client)
+    th.start()
+    while True:
+        item = pending.get()
+        if item is None:
+            break
+        k, t = item
+        srv.poll(t, outs[k], timeout_us=60_000_000)
+    el = time.perf_counter() - t0
+    th.join()
+    st = srv.stats()
+    srv.close()
+    for h in hs:
+        h.close()
+    return {"frames": frames_total, "fps": frames_total / el,
+            "mean_batch": st["frames_in_iterations"] / max(st["iterations"], 1)}
 
 
 # ----------------------------------------------------------------------------- ours
@@ -252,6 +441,18 @@ def bench_ours(args, world, rank, local):
         e2e = {"value": n_e2e * world / el, "unit": "frames/s", "h2d_bytes_per_step": H * W * 4,
                "d2h_bytes_per_step": ncols * cap * 12 + ncols * 4 + ncols * 4, "steps": n_e2e}
 
+    batched = served = None
+    if rank == 0 and not args.no_batched:
+        batched = {
+            "mixed64": bench_batched(S, scenes, torch, dev, scenes.CONFIG4, 4000, 10,
+                                     "64 frames: 24x 640x240, 32x 1024x440, 8x 2048x880; s in {5,7}; dmax {64,128}"),
+            "paper32": bench_batched(S, scenes, torch, dev, [cam] * 32, 4100, 20,
+                                     "32 frames of 1024x440 s=5 dmax=128 in one launch"),
+        }
+    if rank == 0 and not args.no_served:
+        served = bench_served(S, scenes, torch, args.served_seconds)
+        served["saturated"] = bench_served_saturated(S, scenes, torch)
+
     if rank != 0:
         h.close()
         return None
@@ -300,7 +501,8 @@ def bench_ours(args, world, rank, local):
                           "peak_source": f"hbm_gbs ({peak_src})", "bytes": lut_bytes},
         "roofline_reduce": {"kernel": "reduce_transpose_kernel", "bound": "hbm",
                             "achieved": red_bytes / (red_ms / 1000.0) / 1e9, "peak": hbm, "unit": "GB/s",
-                            "frac": red_bytes / (red_ms / 1000.0) / 1e9 / hbm, "bytes": red_bytes},
+                            "frac": red_bytes / (red_ms / 1000.0) / 1e9 / hbm, "bytes": red_bytes,
+                            "traffic": _traffic(os.path.join(kdir, "kernels_reduce.cu"))},
         "stages_ms": {"reduce": red_ms, "luts": lut_ms, "dp": dp_ms,
                       "step_median": statistics.median(t_step), "step_p99": sorted(t_step)[int(0.99 * (K - 1))]},
         "dp_cells_per_s": cells / (dp_ms / 1000.0),
@@ -309,6 +511,8 @@ def bench_ours(args, world, rank, local):
         "device_error_word": err,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "batched": batched,
+        "served": served,
     }
     h.close()
     return rec

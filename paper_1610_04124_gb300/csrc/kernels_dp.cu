@@ -18,26 +18,25 @@
 // is a running minimum: O(1) per row.  Objects are the O(H^2) part.
 //
 // Parallel scheme (a redesign of the paper's one-thread-per-row CTA with a
-// barrier per row), one 256-thread CTA per column, rows cut into blocks of 32:
-//   - the chain warp finalises the blocks in order.  For block j it applies the
-//     32 starts of block j-1 to block j's end rows, then solves the block's
-//     triangle: 32 sequential starts, lane l owning end row 32 j + l; after each
-//     start the owner's running minimum is broadcast with a shuffle and every
-//     lane derives the next start's context in registers.  Lane l keeps row
-//     32 j + l's results in registers (predicated selects, no per-row stores)
-//     and the warp writes the block's back-pointers and start contexts with one
-//     coalesced store each at the end of the block.  The chain's data terms
-//     (with the input-only gravity / diving penalties already added) were
-//     gathered into shared memory beforehand, so the sequential chain never
-//     waits on global memory.
-//   - the 7 bulk warps apply the starts of every finalised block t to the end
-//     rows of blocks t+2, t+3, ... (independent 32 x 32 tiles).  End-row block c
-//     receives c - 1 tiles; blocks are dealt to the bulk warps largest first
-//     to the least-loaded warp, and a block always stays with its warp, so a
-//     cell's updates happen in start order.  Right after block t is final they
-//     first do what the chain needs next -- the tile (t, t+2) and, shared among
-//     all of them, the chain's data gathers for block t+2 -- and only then the
-//     tiles of later blocks.
+// barrier per row), one CTA per column, rows cut into blocks of 32:
+//   - the chain warp finalises the rows in order, lane l owning row 32 j + l of
+//     block j.  At step i (start b = 32 j + i) every lane applies start b to its
+//     row of block j and to its row of block j + 1 (a second running minimum,
+//     so the starts of block j reach block j + 1 while block j is solved);
+//     row b is then complete and its value is broadcast from lane i.  Lane 0
+//     records the row's raw results in a small buffer, and at the end of the
+//     block all lanes pack them into back-pointers and start contexts.  The
+//     data terms of the cells (with the input-only gravity / diving penalties
+//     already added) were gathered into shared memory up to three blocks
+//     ahead, so the sequential chain never waits on global memory.
+//   - the other warps (bulk) apply the starts of every finalised block t to the
+//     end rows of blocks t+2, t+3, ... (independent 32 x 32 tiles).  End-row
+//     block c receives c - 1 tiles; blocks are dealt to the bulk warps largest
+//     first in snake order, and a block always stays with its warp, so a cell's
+//     updates happen in start order.  Each bulk warp runs its pending
+//     work earliest deadline first: the tile of the lowest end-row block (the
+//     chain needs it soonest) or its share of the chain's data for a block,
+//     whichever the chain reaches first.
 // The two sides synchronise through progress counters in shared memory
 // instead of CTA barriers, so neither waits for the other's non-critical work.
 // Every wait is a bounded spin: on expiry the CTA records STIXELS_ERR_TIMEOUT,
@@ -57,7 +56,8 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxBlocks = (STIXELS_MAX_HEIGHT + 31) / 32;
-constexpr int kSpinLimit = 1 << 24;  // polls (~20 ns apart) before a wait gives up
+constexpr int kRing = 3;              // chain data buffers (blocks gathered ahead)
+constexpr int kSpinLimit = 1 << 22;   // polls before a wait gives up (well over 0.1 s)
 
 // Context of one start row b, shared by every end row k >= b: the three
 // previous-class terms V_p[b-1] + T(object | p) + code(p) and the ordering
@@ -66,33 +66,30 @@ struct __align__(16) StartCtx {
     int32_t bo, bg, bs, ford;
 };
 
-// Input-only data of row v: pd8 = PD[v] + 8 v (so that S + 8 n of a stixel
-// [b, k] is pd8[k + 1] - pd8[b]) and the gravity / diving thresholds at row v
-// (penalty iff f > fhi, iff f < flo).
-struct __align__(16) RowInfo {
-    int32_t pd8, fhi, flo, pad;
-};
+// Input-only data of row v, in two arrays: pd8[v] = PD[v] + 8 v (so that
+// S + 8 n of a stixel [b, k] is pd8[k + 1] - pd8[b]) and thr[v], the gravity /
+// diving thresholds at row v (penalty iff f > fhi, iff f < flo) as two int16
+// halves (fhi low, flo high), clamped to [-1, 256] where that keeps every
+// comparison with f in [0, 255] unchanged.
+__device__ __forceinline__ int thr_hi(int32_t w) { return (int32_t)(int16_t)(w & 0xffff); }
+__device__ __forceinline__ int thr_lo(int32_t w) { return w >> 16; }
 
-// Ground and sky prefix entries of rows v and v + 1, read by the chain in one load.
-struct __align__(16) GS4 {
-    int32_t pg0, ps0, pg1, ps1;
-};
-
-// Chain data of one block: for each (start i, end row l) slot e = 32 i + l,
+// Chain data of one block j (rows B = 32 j ..): for start i and end lane l,
 // {d, e_g} = the object data cost and the same plus the ground-below
-// penalties, and f = the rounded mean; part 0 = starts of the previous block,
-// part 1 = the block's own triangle.
+// penalties, and f = the rounded mean, of the cells (B + i, B + l) (tri, valid
+// for i <= l) and (B + i, B + 32 + l) (nxt).  Invalid cells hold zeros.
 struct ChainBuf {
-    int2 de[2][1024];
-    uint8_t f[2][1024];
+    int2 tri[1024];
+    int2 nxt[1024];
+    uint8_t ftri[1024];
+    uint8_t fnxt[1024];
 };
 
 struct SyncState {
     int final_blocks;            // blocks the chain warp has finalised
     int abort;                   // set when a wait gave up
     int ready[kMaxBlocks];       // ready[c]: bulk tiles applied to end-row block c
-    int gathered[kMaxBlocks];    // gathered[j]: bulk warps done gathering block j's chain data
-    int owner[kMaxBlocks];       // bulk warp that owns end-row block c
+    int gathered[kMaxBlocks];    // gathered[j]: bulk warps done with block j's chain data
 };
 
 __device__ __forceinline__ int32_t min3(int32_t a, int32_t b, int32_t c) { return min(min(a, b), c); }
@@ -117,9 +114,15 @@ __device__ __forceinline__ int mean_f(int32_t x, int n, const uint2* s_div, int 
     return (int)min(__umulhi((uint32_t)x, dm.x) >> dm.y, (uint32_t)dmax);
 }
 
+// Gravity / diving penalties of an object with rounded mean f directly above
+// ground, base row thresholds r (input-only).
+__device__ __forceinline__ int32_t ground_pen(int32_t thr, int f, const ModelDev& m)
+{
+    return (f > thr_hi(thr) ? m.pen_grav : 0) + (f < thr_lo(thr) ? m.pen_div : 0);
+}
+
 // Minimum of N candidates (cost, start << 8 | f) listed in ascending start
-// order, ties to the earlier start, by a pairwise tree (depth log2 N instead of
-// a serial chain of N compare-selects).  Result in v[0], bf[0].
+// order, ties to the earlier start, by a pairwise tree.  Result in v[0], bf[0].
 template <int N>
 __device__ __forceinline__ void tree_min(int32_t (&v)[N], int32_t (&bf)[N])
 {
@@ -133,24 +136,19 @@ __device__ __forceinline__ void tree_min(int32_t (&v)[N], int32_t (&bf)[N])
         }
 }
 
-// Gravity / diving penalties of an object with rounded mean f directly above
-// ground, base row thresholds r (input-only).
-__device__ __forceinline__ int32_t ground_pen(const RowInfo& r, int f, const ModelDev& m)
-{
-    return (f > r.fhi ? m.pen_grav : 0) + (f < r.flo ? m.pen_div : 0);
-}
-
-// Warp-wide bounded wait until *p >= target (lane 0 polls).  Returns false if
-// the wait gave up or another warp did; the caller then stops.
-__device__ __forceinline__ bool wait_geq(volatile int* p, int target, volatile int* abort_flag)
+// Warp-wide bounded wait until *p >= target (lane 0 polls, sleeping between
+// polls with a back-off up to max_ns).  Returns false if the wait gave up or
+// another warp did; the caller then stops.
+__device__ __forceinline__ bool wait_geq(volatile int* p, int target, volatile int* abort_flag, int max_ns)
 {
     int ok = 1;
     if ((threadIdx.x & 31) == 0) {
-        int it = 0;
+        int it = 0, ns = 8;
         while (*p < target) {
             if (*abort_flag) { ok = 0; break; }
             if (++it > kSpinLimit) { *abort_flag = 1; ok = 0; break; }
-            __nanosleep(20);
+            __nanosleep(ns);
+            ns = min(2 * ns, max_ns);
         }
     }
     ok = __shfl_sync(kFull, ok, 0);
@@ -161,8 +159,8 @@ __device__ __forceinline__ bool wait_geq(volatile int* p, int target, volatile i
 size_t dp_smem_bytes(int H)
 {
     const size_t HP = (size_t)((H + 3) & ~3);
-    return sizeof(StartCtx) * HP + sizeof(RowInfo) * (HP + 4) + sizeof(GS4) * HP + sizeof(uint2) * (HP + 4) +
-           sizeof(int32_t) * 5 * HP + sizeof(ChainBuf) * 2 + sizeof(SyncState);
+    return sizeof(StartCtx) * HP + sizeof(int4) * HP + sizeof(int32_t) * 2 * (HP + 4) + sizeof(int2) * (HP + 4) +
+           sizeof(uint2) * (HP + 4) + sizeof(int32_t) * 2 * HP + sizeof(ChainBuf) * kRing + sizeof(SyncState);
 }
 
 // Solves column `col` of frame `a` with all NW warps of the CTA (one chain
@@ -185,15 +183,16 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
     const int chain = col & 3;
     const int bulk_id = (warp - chain - 1 + kWarps) % kWarps;
 
-    StartCtx* s_ctx = reinterpret_cast<StartCtx*>(sm);                // [HP]
-    RowInfo* s_row = reinterpret_cast<RowInfo*>(s_ctx + HP);          // [HP + 4], row H holds pd8[H]
-    GS4* s_gs = reinterpret_cast<GS4*>(s_row + HP + 4);               // [HP]
-    uint2* s_div = reinterpret_cast<uint2*>(s_gs + HP);               // [HP + 4], index n = 1..H
-    int32_t* s_bp = reinterpret_cast<int32_t*>(s_div + HP + 4);        // [3][HP] back-pointers b << 2 | p
-    int32_t* s_runv = s_bp + 3 * HP;                                   // [HP] object running minimum
-    int32_t* s_runbf = s_runv + HP;                                    // [HP] its start << 8 | f
-    ChainBuf* s_cb = reinterpret_cast<ChainBuf*>(s_runbf + HP);        // [2]
-    SyncState* sync = reinterpret_cast<SyncState*>(s_cb + 2);
+    StartCtx* s_ctx = reinterpret_cast<StartCtx*>(sm);                 // [HP]
+    int4* s_bp = reinterpret_cast<int4*>(s_ctx + HP);                  // [HP] back-pointers b << 2 | p per class
+    int32_t* s_pd8 = reinterpret_cast<int32_t*>(s_bp + HP);            // [HP + 4], v = 0..H
+    int32_t* s_thr = s_pd8 + HP + 4;                                   // [HP + 4]
+    int2* s_gs = reinterpret_cast<int2*>(s_thr + HP + 4);              // [HP + 4] {PG[v], PS[v]}, v = 0..H
+    uint2* s_div = reinterpret_cast<uint2*>(s_gs + HP + 4);            // [HP + 4], index n = 1..H
+    int32_t* s_runv = reinterpret_cast<int32_t*>(s_div + HP + 4);       // [HP] object running minimum
+    int32_t* s_runbf = s_runv + HP;                                     // [HP] its start << 8 | f
+    ChainBuf* s_cb = reinterpret_cast<ChainBuf*>(s_runbf + HP);        // [kRing]
+    SyncState* sync = reinterpret_cast<SyncState*>(s_cb + kRing);
     volatile int* v_final = &sync->final_blocks;
     volatile int* v_abort = &sync->abort;
     const int NB = (H + 31) >> 5;
@@ -202,20 +201,19 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
     const int32_t* pg_col = a.pg + (size_t)col * P;
     const int32_t* ps_col = a.ps + (size_t)col * P;
     for (int v = threadIdx.x; v <= H; v += kThreads) {
-        RowInfo r;
-        r.pd8 = a.pd[(size_t)col * P + v] + 8 * v;
-        r.fhi = r.flo = r.pad = 0;
+        int32_t thr = 0;
         if (v < H) {
             const int32_t g = a.rows.fgq[v];
-            r.fhi = (g + m.eps_g) >> 4;             // 16 f > g + eps  <=>  f > floor((g + eps) / 16)
-            r.flo = -((m.eps_d - g) >> 4);          // 16 f < g - eps  <=>  f < ceil((g - eps) / 16)
-            GS4 q;
-            q.pg0 = pg_col[v]; q.ps0 = ps_col[v]; q.pg1 = pg_col[v + 1]; q.ps1 = ps_col[v + 1];
-            s_gs[v] = q;
+            // 16 f > g + eps  <=>  f > floor((g + eps) / 16);  16 f < g - eps  <=>  f < ceil((g - eps) / 16)
+            const int fhi = max(-1, min((g + m.eps_g) >> 4, 256));
+            const int flo = max(-1, min(-((m.eps_d - g) >> 4), 256));
+            thr = (fhi & 0xffff) | (flo << 16);
             s_runv[v] = INT_MAX;
             s_runbf[v] = 0;
         }
-        s_row[v] = r;
+        s_gs[v] = make_int2(pg_col[v], ps_col[v]);
+        s_pd8[v] = a.pd[(size_t)col * P + v] + 8 * v;
+        s_thr[v] = thr;
     }
     for (int n = 1 + threadIdx.x; n <= H; n += kThreads) s_div[n] = div_magic(n);
     if (threadIdx.x < kMaxBlocks) {
@@ -225,41 +223,29 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
     if (threadIdx.x == 0) {
         sync->final_blocks = 0;
         sync->abort = 0;
-        // end-row block c receives c - 1 bulk tiles; hand the blocks, largest
-        // first, to the least-loaded bulk warp (balanced per-warp work)
-        int load[kBulk];
-        for (int w = 0; w < kBulk; ++w) load[w] = 0;
-        for (int c = NB - 1; c >= 2; --c) {
-            int best = 0;
-            for (int w = 1; w < kBulk; ++w)
-                if (load[w] < load[best]) best = w;
-            sync->owner[c] = best;
-            load[best] += c - 1;
-        }
         // start 0 carries the first-stixel prior (code 3 = no previous stixel)
         s_ctx[0] = StartCtx{m.first[0] + kNoneCode, kBig, kBig, INT_MAX};
     }
     __syncthreads();
 
-    // Gather the data terms the chain warp needs for block jn into chain buffer
-    // jn & 1: part 0 = starts of block jn-1 x end rows of block jn, part 1 =
-    // starts and end rows of block jn (start <= end row).  All loads of a pass
-    // are issued before any store.
+    // Gather the chain data of block jn into ring buffer jn % kRing: the cells
+    // (start B + i, end B + l) and (start B + i, end B + 32 + l) of all 32
+    // starts i.  All loads of a pass are issued before any store.
     auto gather_chain = [&](int jn, int tid, int nthreads) {
-        ChainBuf* cb = s_cb + (jn & 1);
-        for (int base = tid; base < 2048; base += 5 * nthreads) {
-            int32_t lo[5], hi[5], fv[5];
-            bool ok[5];
+        ChainBuf* cb = s_cb + (jn % kRing);
+        const int B = 32 * jn;
+        for (int base = tid; base < 2048; base += 4 * nthreads) {
+            int32_t lo[4], hi[4], fv[4];
+            bool ok[4];
 #pragma unroll
-            for (int r = 0; r < 5; ++r) {
+            for (int r = 0; r < 4; ++r) {
                 const int idx = base + r * nthreads;
                 const int part = idx >> 10, e = idx & 1023, i = e >> 5, l = e & 31;
-                const int k = 32 * jn + l;
-                const int b = part == 0 ? 32 * (jn - 1) + i : 32 * jn + i;
-                ok[r] = idx < 2048 && k < H && (part == 0 ? jn >= 1 : i <= l);
+                const int b = B + i, k = B + 32 * part + l;
+                ok[r] = idx < 2048 && k < H && (part == 1 || i <= l);
                 lo[r] = hi[r] = fv[r] = 0;
                 if (ok[r]) {
-                    const int f = mean_f(s_row[k + 1].pd8 - s_row[b].pd8, k - b + 1, s_div, m.dmax);
+                    const int f = mean_f(s_pd8[k + 1] - s_pd8[b], k - b + 1, s_div, m.dmax);
                     const int32_t* row = po_col + (size_t)f * P;
                     lo[r] = __ldg(row + b);
                     hi[r] = __ldg(row + k + 1);
@@ -267,80 +253,119 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
                 }
             }
 #pragma unroll
-            for (int r = 0; r < 5; ++r) {
+            for (int r = 0; r < 4; ++r) {
                 const int idx = base + r * nthreads;
-                if (ok[r]) {
+                if (idx < 2048) {
                     const int part = idx >> 10, e = idx & 1023;
-                    const int b = part == 0 ? 32 * (jn - 1) + (e >> 5) : 32 * jn + (e >> 5);
+                    const int b = B + (e >> 5);
                     const int32_t d = hi[r] - lo[r];
-                    cb->de[part][e] = make_int2(d, d + ground_pen(s_row[b], fv[r], m));
-                    cb->f[part][e] = (uint8_t)fv[r];
+                    const int2 v = ok[r] ? make_int2(d, d + ground_pen(s_thr[b], fv[r], m)) : make_int2(0, 0);
+                    if (part == 0) { cb->tri[e] = v; cb->ftri[e] = (uint8_t)fv[r]; }
+                    else { cb->nxt[e] = v; cb->fnxt[e] = (uint8_t)fv[r]; }
                 }
             }
         }
     };
 
-    // Apply the 32 starts of finalised block t to end-row block jc (a bulk tile).
+    // Apply the 32 starts of finalised block t to end-row block jc (a bulk tile):
+    // lane l owns end row k = 32 jc + l; the starts go in four groups of 8
+    // (16 gathers in flight), each merged by a pairwise tree, then folded into
+    // the running minimum in start order.
     auto bulk_tile = [&](int t, int jc) {
         const int k = 32 * jc + lane;
         const bool kv = k < H;
         const int kk = kv ? k : H - 1;
         int32_t run = INT_MAX, runbf = 0;
         if (kv) { run = s_runv[k]; runbf = s_runbf[k]; }
-        const int32_t x1 = s_row[kk + 1].pd8;
+        const int32_t x1 = s_pd8[kk + 1];
+        const uint2* divp = s_div + (kk + 1 - 32 * t);     // s_div[k + 1 - b] = divp[-i], b = 32 t + i
+        const int32_t* lo_base = po_col + 32 * t;           // PO[f][b] = lo_base[f P + i]
+        const int32_t* hi_base = po_col + kk + 1;           // PO[f][k + 1] = hi_base[f P]
+        const int4* pd4 = reinterpret_cast<const int4*>(s_pd8 + 32 * t);
+        const int4* th4 = reinterpret_cast<const int4*>(s_thr + 32 * t);
+        const int32_t pen_g = m.pen_grav, pen_d = m.pen_div, pen_o = m.pen_ord;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {          // two groups of 16 starts: 32 gathers in flight
-            int32_t lo[16], hi[16], fv[16];
+        for (int g = 0; g < 4; ++g) {
+            int32_t lo[8], hi[8], fv[8];
+            const int4 pa = pd4[2 * g], pb = pd4[2 * g + 1];
+            const int32_t pdv[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int b = 32 * t + 16 * h + i;
-                const int f = mean_f(x1 - s_row[b].pd8, kk + 1 - b, s_div, m.dmax);
-                const int32_t* row = po_col + (size_t)f * P;
-                lo[i] = __ldg(row + b);
-                hi[i] = __ldg(row + kk + 1);
+            for (int i = 0; i < 8; ++i) {
+                const int ii = 8 * g + i;
+                const uint2 dm = divp[-ii];
+                const int f = (int)min(__umulhi((uint32_t)(x1 - pdv[i]), dm.x) >> dm.y, (uint32_t)m.dmax);
+                lo[i] = __ldg(lo_base + (size_t)f * P + ii);
+                hi[i] = __ldg(hi_base + (size_t)f * P);
                 fv[i] = f;
             }
+            const int4 ta = th4[2 * g], tb = th4[2 * g + 1];
+            const int32_t thv[8] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z, tb.w};
+            int32_t cv[8], cbf[8];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int b = 32 * t + 16 * h + i;
+            for (int i = 0; i < 8; ++i) {
+                const int b = 32 * t + 8 * g + i;
                 const StartCtx c = s_ctx[b];
                 const int32_t d = hi[i] - lo[i];
                 const int f = fv[i];
-                const int32_t cand = min3(c.bo + d + (f > c.ford ? m.pen_ord : 0),
-                                          c.bg + d + ground_pen(s_row[b], f, m), c.bs + d);
-                if (cand < run) { run = cand; runbf = (b << 8) | f; }
+                cv[i] = min3(c.bo + d + (f > c.ford ? pen_o : 0),
+                             c.bg + d + (f > thr_hi(thv[i]) ? pen_g : 0) + (f < thr_lo(thv[i]) ? pen_d : 0), c.bs + d);
+                cbf[i] = (b << 8) | f;
             }
+            tree_min<8>(cv, cbf);
+            if (cv[0] < run) { run = cv[0]; runbf = cbf[0]; }
         }
         if (kv) { s_runv[k] = run; s_runbf[k] = runbf; }
     };
 
-    // chain data of blocks 0 and 1 depend on the input only
+    // the chain data of block 0 (input only); the bulk warps gather the rest
     gather_chain(0, threadIdx.x, kThreads);
-    if (NB > 1) gather_chain(1, threadIdx.x, kThreads);
     __syncthreads();
 
     if (warp != chain) {
         // ---------------------------------------------------------------- bulk warps
-        for (int t = 0; t + 2 < NB; ++t) {
-            if (!wait_geq(v_final, t + 1, v_abort)) break;          // block t is final
-            const int jn = t + 2;
-            if (sync->owner[jn] == bulk_id) {                         // the tile the chain needs next
-                bulk_tile(t, jn);
+        // End-row block c receives c - 1 tiles.  The blocks are dealt, largest
+        // first, to the bulk warps in snake order (rounds of kBulk blocks,
+        // alternating direction), which keeps the per-warp work balanced; lane l
+        // of a bulk warp holds the block it owns in round l and the number of
+        // start blocks already applied to it.
+        const int snake = (lane & 1) ? kBulk - 1 - bulk_id : bulk_id;
+        const int my_c = NB - 1 - (lane * kBulk + snake);
+        const bool mine = my_c >= 2;
+        int my_r = 0;
+        // pending work, earliest deadline first: the tile (my_r, my_c) of the
+        // lowest owned end-row block whose next start block is final, or this
+        // warp's share of the chain data of block next_g (its ring slot is free
+        // once block next_g - kRing is final)
+        int next_g = 1;
+        for (;;) {
+            const int vf = __shfl_sync(kFull, lane == 0 ? *v_final : 0, 0);     // final blocks
+            if (*v_abort) break;
+            const bool pending = mine && my_r < my_c - 1;
+            const unsigned work = __ballot_sync(kFull, pending && my_r < vf);
+            const bool all_done = __ballot_sync(kFull, pending) == 0;
+            // owned blocks decrease with the lane: the lowest block is the highest lane
+            const int wl = work ? 31 - __clz(work) : -1;
+            const int jc_work = wl >= 0 ? __shfl_sync(kFull, my_c, wl) : -1;
+            const bool g_open = next_g < NB && vf >= next_g - kRing + 1;
+            if (g_open && (jc_work < 0 || next_g <= jc_work)) {
+                gather_chain(next_g, bulk_id * 32 + lane, kBulk * 32);
                 __threadfence_block();
                 __syncwarp();
-                if (lane == 0) sync->ready[jn] = t + 1;
+                if (lane == 0) atomicAdd(&sync->gathered[next_g], 1);
+                ++next_g;
+                continue;
             }
-            gather_chain(jn, bulk_id * 32 + lane, kBulk * 32);        // the chain's data for block t+2
-            __threadfence_block();
-            __syncwarp();
-            if (lane == 0) atomicAdd(&sync->gathered[jn], 1);
-            for (int jc = jn + 1; jc < NB; ++jc) {                    // tiles of later blocks
-                if (sync->owner[jc] != bulk_id) continue;
-                bulk_tile(t, jc);
+            if (jc_work >= 0) {
+                const int t = __shfl_sync(kFull, my_r, wl);
+                bulk_tile(t, jc_work);
                 __threadfence_block();
                 __syncwarp();
-                if (lane == 0) sync->ready[jc] = t + 1;
+                if (lane == 0) sync->ready[jc_work] = t + 1;
+                if (lane == wl) my_r = t + 1;
+                continue;
             }
+            if (all_done && next_g >= NB) break;
+            if (!wait_geq(v_final, vf + 1, v_abort, 32)) break;
         }
         return;
     }
@@ -351,106 +376,121 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
     const int32_t T_go = m.trans[1][0], T_gg = m.trans[1][1] + 1, T_gs = m.trans[1][2] + 2;
     const int32_t T_so = m.trans[2][0], T_sg = m.trans[2][1] + 1, T_ss = m.trans[2][2] + 2;
     const int ord_off = m.eps_o >> 4;               // 16 f > 16 f' + eps  <=>  f > f' + floor(eps / 16)
+    const int32_t pen_ord = m.pen_ord;
+    // per-row results of the current block, written by lane 0 at each step and
+    // packed into back-pointers / start contexts by all lanes at the block's end
+    // (a separate array, so these stores do not hold back the next steps' loads)
+    __shared__ int4 s_raw[32];                      // {object value, start << 8 | f, ground, sky}
+    __shared__ int2 s_raw2[32];                     // {ground start, sky start}
     // carried state (uniform across lanes): V of the last finalised row, f of
     // its best object stixel, and the ground / sky running minima
     int32_t vo_p = 0, vg_p = 0, vs_p = 0, fo_p = 0;
     int32_t rg = INT_MAX, rgb = 0, rs = INT_MAX, rsb = 0;
+    // lane l's running minimum for row 32 (j + 1) + l over the starts of block j
+    int32_t run2 = INT_MAX, run2bf = 0;
     bool aborted = false;
 
     for (int j = 0; j < NB; ++j) {
         const int B = 32 * j;
-        if (j >= 2) {
-            if (!wait_geq(&sync->ready[j], j - 1, v_abort) || !wait_geq(&sync->gathered[j], kBulk, v_abort)) {
-                aborted = true;
-                break;
-            }
-        }
-        const ChainBuf* cb = s_cb + (j & 1);
+        if (j >= 1 && !wait_geq(&sync->gathered[j], kBulk, v_abort, 16)) { aborted = true; break; }
+        if (j >= 2 && !wait_geq(&sync->ready[j], j - 1, v_abort, 16)) { aborted = true; break; }
+        const ChainBuf* cb = s_cb + (j % kRing);
         const int nb = min(32, H - B);
         const int k = B + lane;
-        const bool kv = lane < nb;
-        int32_t run = kv ? s_runv[k] : INT_MAX;
-        int32_t runbf = kv ? s_runbf[k] : 0;
-        if (j > 0) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                int32_t cv[16], cbf[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int e = (16 * h + i) * 32 + lane;
-                    const int b = B - 32 + 16 * h + i;
-                    const StartCtx c = s_ctx[b];
-                    const int2 de = cb->de[0][e];
-                    const int f = cb->f[0][e];
-                    cv[i] = min3(c.bo + de.x + (f > c.ford ? m.pen_ord : 0), c.bg + de.y, c.bs + de.x);
-                    cbf[i] = (b << 8) | f;
-                }
-                tree_min<16>(cv, cbf);
-                if (cv[0] < run) { run = cv[0]; runbf = cbf[0]; }
-            }
-        }
-        // lane l's copy of row B + l's results
-        int32_t my_r = 0, my_bf = 0, my_gr = 0, my_rgb = 0, my_sk = 0, my_rsb = 0;
-        // one start of the triangle, start row b = B + i; `first` is set only for
+        // starts of blocks <= j-2 (bulk tiles), then those of block j-1 (run2):
+        // ascending starts with strict "<" keep the earliest start on ties
+        int32_t run = INT_MAX, runbf = 0;
+        if (lane < nb) { run = s_runv[k]; runbf = s_runbf[k]; }
+        if (run2 < run) { run = run2; runbf = run2bf; }
+        run2 = INT_MAX; run2bf = 0;
+        // inputs of one step, loaded a step ahead so that shared-memory latency
+        // overlaps the previous step
+        struct StepIn {
+            int2 gs0, gs1, de, de2;
+            int ff, ff2;
+        };
+        auto load_in = [&](int i) {
+            StepIn x;
+            x.gs0 = s_gs[B + i];
+            x.gs1 = s_gs[B + i + 1];
+            x.de = cb->tri[i * 32 + lane];
+            x.ff = cb->ftri[i * 32 + lane];
+            x.de2 = cb->nxt[i * 32 + lane];
+            x.ff2 = cb->fnxt[i * 32 + lane];
+            return x;
+        };
+        // one start of the block, start row b = B + i; `first` is set only for
         // b = 0, whose candidates carry the first-stixel prior
-        auto step = [&](int i, bool first) {
+        auto step = [&](int i, const StepIn& x, bool first) {
             const int b = B + i;
-            const GS4 gs = s_gs[b];
-            const int2 de = cb->de[1][i * 32 + lane];
-            const int ff = cb->f[1][i * 32 + lane];
             int32_t bo, bg, bs, ford, ag, as;
             if (first) {
                 bo = m.first[0] + kNoneCode; bg = kBig; bs = kBig; ford = INT_MAX;
-                ag = m.first[1] + kNoneCode - gs.pg0;
-                as = m.first[2] + kNoneCode - gs.ps0;
+                ag = m.first[1] + kNoneCode - x.gs0.x;
+                as = m.first[2] + kNoneCode - x.gs0.y;
             } else {
                 bo = vo_p + T_oo; bg = vg_p + T_og; bs = vs_p + T_os; ford = fo_p + ord_off;
                 if (kStdTrans) {
-                    ag = vo_p + T_go - gs.pg0;
-                    as = min(vo_p + T_so, vg_p + T_sg) - gs.ps0;
+                    ag = vo_p + T_go - x.gs0.x;
+                    as = min(vo_p + T_so, vg_p + T_sg) - x.gs0.y;
                 } else {
-                    ag = min3(vo_p + T_go, vg_p + T_gg, vs_p + T_gs) - gs.pg0;
-                    as = min3(vo_p + T_so, vg_p + T_sg, vs_p + T_ss) - gs.ps0;
+                    ag = min3(vo_p + T_go, vg_p + T_gg, vs_p + T_gs) - x.gs0.x;
+                    as = min3(vo_p + T_so, vg_p + T_sg, vs_p + T_ss) - x.gs0.y;
                 }
             }
+            // every lane: start b applied to its rows of blocks j and j + 1
+            const int32_t cand = min3(bo + x.de.x + (x.ff > ford ? pen_ord : 0), bg + x.de.y, bs + x.de.x);
+            if (cand < run) { run = cand; runbf = (b << 8) | x.ff; }
+            const int32_t cand2 = min3(bo + x.de2.x + (x.ff2 > ford ? pen_ord : 0), bg + x.de2.y, bs + x.de2.x);
+            if (cand2 < run2) { run2 = cand2; run2bf = (b << 8) | x.ff2; }
             if (ag < rg) { rg = ag; rgb = b; }
             if (as < rs) { rs = as; rsb = b; }
-            const int32_t cand = min3(bo + de.x + (ff > ford ? m.pen_ord : 0), bg + de.y, bs + de.x);
-            if (cand < run) { run = cand; runbf = (b << 8) | ff; }
-            // row b is complete: every lane derives its values, lane i keeps them
+            // row b is complete (lane i has applied every start <= b)
             const int32_t r = __shfl_sync(kFull, run, i);
             const int32_t bf = __shfl_sync(kFull, runbf, i);
-            const int32_t gr = gs.pg1 + rg;
-            const int32_t sk = gs.ps1 + rs;
+            const int32_t gr = x.gs1.x + rg;
+            const int32_t sk = x.gs1.y + rs;
             vo_p = min(r & ~3, kBig);
             vg_p = min(gr & ~3, kBig);
             vs_p = min(sk & ~3, kBig);
             fo_p = bf & 255;
-            const bool mine = lane == i;
-            my_r = mine ? r : my_r;
-            my_bf = mine ? bf : my_bf;
-            my_gr = mine ? gr : my_gr;
-            my_rgb = mine ? rgb : my_rgb;
-            my_sk = mine ? sk : my_sk;
-            my_rsb = mine ? rsb : my_rsb;
+            if (lane == 0) {
+                s_raw[i] = make_int4(r, bf, gr, sk);
+                s_raw2[i] = make_int2(rgb, rsb);
+            }
         };
+        StepIn cur = load_in(0);
         int i0 = 0;
-        if (j == 0) { step(0, true); i0 = 1; }
+        if (j == 0) {
+            const StepIn nx = load_in(nb > 1 ? 1 : 0);
+            step(0, cur, true);
+            cur = nx;
+            i0 = 1;
+        }
         if (nb == 32) {
 #pragma unroll 8
-            for (int i = i0; i < 32; ++i) step(i, false);
+            for (int i = i0; i < 32; ++i) {
+                const StepIn nx = load_in(i < 31 ? i + 1 : 31);
+                step(i, cur, false);
+                cur = nx;
+            }
         } else {
 #pragma unroll 1
-            for (int i = i0; i < nb; ++i) step(i, false);
+            for (int i = i0; i < nb; ++i) {
+                const StepIn nx = load_in(i + 1 < nb ? i + 1 : i);
+                step(i, cur, false);
+                cur = nx;
+            }
         }
+        __syncwarp();
         // the block's back-pointers and the contexts of the starts that follow its rows
-        if (kv) {
-            s_bp[k] = ((my_bf >> 8) << 2) | (my_r & 3);
-            s_bp[HP + k] = (my_rgb << 2) | (my_gr & 3);
-            s_bp[2 * HP + k] = (my_rsb << 2) | (my_sk & 3);
+        if (lane < nb) {
+            const int4 w = s_raw[lane];
+            const int2 w2 = s_raw2[lane];
+            s_bp[k] = make_int4(((w.y >> 8) << 2) | (w.x & 3), (w2.x << 2) | (w.z & 3), (w2.y << 2) | (w.w & 3), 0);
             if (k + 1 < H)
-                s_ctx[k + 1] = StartCtx{min(my_r & ~3, kBig) + T_oo, min(my_gr & ~3, kBig) + T_og,
-                                        min(my_sk & ~3, kBig) + T_os, (my_bf & 255) + ord_off};
+                s_ctx[k + 1] = StartCtx{min(w.x & ~3, kBig) + T_oo, min(w.z & ~3, kBig) + T_og,
+                                        min(w.w & ~3, kBig) + T_os, (w.y & 255) + ord_off};
         }
         __threadfence_block();
         __syncwarp();
@@ -477,21 +517,23 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
             atomicOr(a.err, STIXELS_ERR_INFEASIBLE);
             return;
         }
+        const int32_t* bp_all = reinterpret_cast<const int32_t*>(s_bp);
         int n = 0;
         for (int k = H - 1, cc = c; k >= 0 && cc < 3;) {
-            const int32_t bp = s_bp[cc * HP + k];
+            const int32_t bp = bp_all[4 * k + cc];
             ++n;
+            if ((bp >> 2) > k) break;                 // never for a solved column; keeps the walk finite
             k = (bp >> 2) - 1;
             cc = bp & 3;
         }
         int idx = n - 1;
         stixel_t* out = a.stixels + (size_t)col * a.cap;
-        for (int k = H - 1, cc = c; k >= 0 && cc < 3; --idx) {
-            const int32_t bp = s_bp[cc * HP + k];
+        for (int k = H - 1, cc = c; k >= 0 && cc < 3 && idx >= 0; --idx) {
+            const int32_t bp = bp_all[4 * k + cc];
             const int b = bp >> 2;
             if (idx < a.cap) {
                 const int nrows = k - b + 1;
-                const int32_t S = s_row[k + 1].pd8 - s_row[b].pd8 - 8 * nrows;
+                const int32_t S = s_pd8[k + 1] - s_pd8[b] - 8 * nrows;
                 stixel_t st;
                 st.row_top = (int16_t)(H - 1 - k);
                 st.row_bottom = (int16_t)(H - 1 - b);

@@ -257,7 +257,7 @@ typedef struct stixels_frame_desc {
     int32_t H, W;              /* frame size, 1 <= H <= STIXELS_MAX_HEIGHT */
 } stixels_frame_desc_t;
 typedef struct stixels_batch_config {
-    int32_t dp_warps;          /* warps per DP CTA: 8 (two CTAs per SM) or 16 (one) */
+    int32_t dp_warps;          /* warps per DP CTA: 8 (two CTAs fit an SM) or 16 (one) */
     int32_t dp_ctas_per_sm;    /* persistent DP grid = SMs x this, 1..4 */
 } stixels_batch_config_t;
 

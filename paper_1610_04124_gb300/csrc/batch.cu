@@ -121,7 +121,7 @@ cudaError_t enqueue_tables(const BatchTables& t, char* d_tab, int dp_warps, int 
     if (e == cudaSuccess) {
         const int grid = std::max(1, std::min(t.nitems, sm_count() * dp_ctas_per_sm));
         e = launch_dp_batch((const DpArgs*)(d_tab + t.o_dp), (const int2*)(d_tab + t.o_di), t.nitems, counter, t.maxH,
-                            dp_warps, t.std_trans, grid, st);
+                            dp_warps, dp_ctas_per_sm, t.std_trans, grid, st);
     }
     return e;
 }

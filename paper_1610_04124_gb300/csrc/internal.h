@@ -158,6 +158,6 @@ cudaError_t enqueue_tables(const BatchTables& t, char* d_tab, int dp_warps, int 
 cudaError_t prepare_dp_kernels();
 // Persistent DP over a work list of (frame, column) items; *d_counter must be 0.
 cudaError_t launch_dp_batch(const DpArgs* d_frames, const int2* d_items, int nitems, int* d_counter, int maxH,
-                            int warps, bool std_trans, int grid, cudaStream_t st);
+                            int warps, int ctas_per_sm, bool std_trans, int grid, cudaStream_t st);
 
 }  // namespace stx

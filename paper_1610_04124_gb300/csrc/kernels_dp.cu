@@ -27,16 +27,20 @@
 //     records the row's raw results in a small buffer, and at the end of the
 //     block all lanes pack them into back-pointers and start contexts.  The
 //     data terms of the cells (with the input-only gravity / diving penalties
-//     already added) were gathered into shared memory up to three blocks
-//     ahead, so the sequential chain never waits on global memory.
+//     already added) were gathered into shared memory ahead of the chain (a
+//     ring of three blocks), so the sequential chain never waits on global
+//     memory.
 //   - the other warps (bulk) apply the starts of every finalised block t to the
 //     end rows of blocks t+2, t+3, ... (independent 32 x 32 tiles).  End-row
-//     block c receives c - 1 tiles; blocks are dealt to the bulk warps largest
-//     first in snake order, and a block always stays with its warp, so a cell's
-//     updates happen in start order.  Each bulk warp runs its pending
-//     work earliest deadline first: the tile of the lowest end-row block (the
-//     chain needs it soonest) or its share of the chain's data for a block,
-//     whichever the chain reaches first.
+//     block c receives c - 1 tiles; they are split by start block between two
+//     partial minima, the (block, partial) pairs are dealt to the bulk warps
+//     largest first in snake order, and a pair always stays with its warp, so
+//     each partial's updates happen in start order; the chain merges the
+//     partials by (cost, start) when it reaches the block, so two warps keep
+//     up with one block's growing list of tiles.  Each bulk warp runs its
+//     pending work earliest deadline first: the tile of the lowest end-row
+//     block (the chain needs it soonest) or its share of the chain's data for
+//     a block, whichever the chain reaches first.
 // The two sides synchronise through progress counters in shared memory
 // instead of CTA barriers, so neither waits for the other's non-critical work.
 // Every wait is a bounded spin: on expiry the CTA records STIXELS_ERR_TIMEOUT,
@@ -57,6 +61,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxBlocks = (STIXELS_MAX_HEIGHT + 31) / 32;
 constexpr int kRing = 3;              // chain data buffers (blocks gathered ahead)
+constexpr int kSlots = 2;             // partial running minima per end row (start blocks t mod kSlots)
 constexpr int kSpinLimit = 1 << 22;   // polls before a wait gives up (well over 0.1 s)
 
 // Context of one start row b, shared by every end row k >= b: the three
@@ -88,7 +93,7 @@ struct ChainBuf {
 struct SyncState {
     int final_blocks;            // blocks the chain warp has finalised
     int abort;                   // set when a wait gave up
-    int ready[kMaxBlocks];       // ready[c]: bulk tiles applied to end-row block c
+    int ready[kMaxBlocks];       // ready[c]: bulk tiles applied to end-row block c (of c - 1)
     int gathered[kMaxBlocks];    // gathered[j]: bulk warps done with block j's chain data
 };
 
@@ -160,7 +165,50 @@ size_t dp_smem_bytes(int H)
 {
     const size_t HP = (size_t)((H + 3) & ~3);
     return sizeof(StartCtx) * HP + sizeof(int4) * HP + sizeof(int32_t) * 2 * (HP + 4) + sizeof(int2) * (HP + 4) +
-           sizeof(uint2) * (HP + 4) + sizeof(int32_t) * 2 * HP + sizeof(ChainBuf) * kRing + sizeof(SyncState);
+           sizeof(uint2) * (HP + 4) + sizeof(int32_t) * 2 * kSlots * HP + sizeof(ChainBuf) * kRing +
+           sizeof(SyncState);
+}
+
+// Gathers the chain data of the block starting at row B into cb: the cells
+// (start B + i, end B + l) and (start B + i, end B + 32 + l) of all 32 starts
+// i, with the cells split over nthreads threads (this one is tid).  All loads
+// of a pass are issued before any store.  Kept out of line: it runs from two
+// places and its code is shared.
+__device__ __noinline__ void gather_chain(ChainBuf* cb, int B, int H, int P, const int32_t* __restrict__ po_col,
+                                          const int32_t* s_pd8, const int32_t* s_thr, const uint2* s_div,
+                                          const ModelDev& m, int tid, int nthreads)
+{
+    for (int base = tid; base < 2048; base += 4 * nthreads) {
+        int32_t lo[4], hi[4], fv[4];
+        bool ok[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int idx = base + r * nthreads;
+            const int part = idx >> 10, e = idx & 1023, i = e >> 5, l = e & 31;
+            const int b = B + i, k = B + 32 * part + l;
+            ok[r] = idx < 2048 && k < H && (part == 1 || i <= l);
+            lo[r] = hi[r] = fv[r] = 0;
+            if (ok[r]) {
+                const int f = mean_f(s_pd8[k + 1] - s_pd8[b], k - b + 1, s_div, m.dmax);
+                const int32_t* row = po_col + (size_t)f * P;
+                lo[r] = __ldg(row + b);
+                hi[r] = __ldg(row + k + 1);
+                fv[r] = f;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int idx = base + r * nthreads;
+            if (idx < 2048) {
+                const int part = idx >> 10, e = idx & 1023;
+                const int b = B + (e >> 5);
+                const int32_t d = hi[r] - lo[r];
+                const int2 v = ok[r] ? make_int2(d, d + ground_pen(s_thr[b], fv[r], m)) : make_int2(0, 0);
+                if (part == 0) { cb->tri[e] = v; cb->ftri[e] = (uint8_t)fv[r]; }
+                else { cb->nxt[e] = v; cb->fnxt[e] = (uint8_t)fv[r]; }
+            }
+        }
+    }
 }
 
 // Solves column `col` of frame `a` with all NW warps of the CTA (one chain
@@ -189,9 +237,10 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
     int32_t* s_thr = s_pd8 + HP + 4;                                   // [HP + 4]
     int2* s_gs = reinterpret_cast<int2*>(s_thr + HP + 4);              // [HP + 4] {PG[v], PS[v]}, v = 0..H
     uint2* s_div = reinterpret_cast<uint2*>(s_gs + HP + 4);            // [HP + 4], index n = 1..H
-    int32_t* s_runv = reinterpret_cast<int32_t*>(s_div + HP + 4);       // [HP] object running minimum
-    int32_t* s_runbf = s_runv + HP;                                     // [HP] its start << 8 | f
-    ChainBuf* s_cb = reinterpret_cast<ChainBuf*>(s_runbf + HP);        // [kRing]
+    // [kSlots][HP] object running minima over the start blocks t = s (mod kSlots)
+    int32_t* s_runv = reinterpret_cast<int32_t*>(s_div + HP + 4);
+    int32_t* s_runbf = s_runv + kSlots * HP;                           // [kSlots][HP] start << 8 | f
+    ChainBuf* s_cb = reinterpret_cast<ChainBuf*>(s_runbf + kSlots * HP);   // [kRing]
     SyncState* sync = reinterpret_cast<SyncState*>(s_cb + kRing);
     volatile int* v_final = &sync->final_blocks;
     volatile int* v_abort = &sync->abort;
@@ -208,8 +257,11 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
             const int fhi = max(-1, min((g + m.eps_g) >> 4, 256));
             const int flo = max(-1, min(-((m.eps_d - g) >> 4), 256));
             thr = (fhi & 0xffff) | (flo << 16);
-            s_runv[v] = INT_MAX;
-            s_runbf[v] = 0;
+#pragma unroll
+            for (int q = 0; q < kSlots; ++q) {
+                s_runv[q * HP + v] = INT_MAX;
+                s_runbf[q * HP + v] = 0;
+            }
         }
         s_gs[v] = make_int2(pg_col[v], ps_col[v]);
         s_pd8[v] = a.pd[(size_t)col * P + v] + 8 * v;
@@ -228,82 +280,46 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
     }
     __syncthreads();
 
-    // Gather the chain data of block jn into ring buffer jn % kRing: the cells
-    // (start B + i, end B + l) and (start B + i, end B + 32 + l) of all 32
-    // starts i.  All loads of a pass are issued before any store.
-    auto gather_chain = [&](int jn, int tid, int nthreads) {
-        ChainBuf* cb = s_cb + (jn % kRing);
-        const int B = 32 * jn;
-        for (int base = tid; base < 2048; base += 4 * nthreads) {
-            int32_t lo[4], hi[4], fv[4];
-            bool ok[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int idx = base + r * nthreads;
-                const int part = idx >> 10, e = idx & 1023, i = e >> 5, l = e & 31;
-                const int b = B + i, k = B + 32 * part + l;
-                ok[r] = idx < 2048 && k < H && (part == 1 || i <= l);
-                lo[r] = hi[r] = fv[r] = 0;
-                if (ok[r]) {
-                    const int f = mean_f(s_pd8[k + 1] - s_pd8[b], k - b + 1, s_div, m.dmax);
-                    const int32_t* row = po_col + (size_t)f * P;
-                    lo[r] = __ldg(row + b);
-                    hi[r] = __ldg(row + k + 1);
-                    fv[r] = f;
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int idx = base + r * nthreads;
-                if (idx < 2048) {
-                    const int part = idx >> 10, e = idx & 1023;
-                    const int b = B + (e >> 5);
-                    const int32_t d = hi[r] - lo[r];
-                    const int2 v = ok[r] ? make_int2(d, d + ground_pen(s_thr[b], fv[r], m)) : make_int2(0, 0);
-                    if (part == 0) { cb->tri[e] = v; cb->ftri[e] = (uint8_t)fv[r]; }
-                    else { cb->nxt[e] = v; cb->fnxt[e] = (uint8_t)fv[r]; }
-                }
-            }
-        }
-    };
-
     // Apply the 32 starts of finalised block t to end-row block jc (a bulk tile):
     // lane l owns end row k = 32 jc + l; the starts go in four groups of 8
     // (16 gathers in flight), each merged by a pairwise tree, then folded into
-    // the running minimum in start order.
+    // the running minimum in start order.  The group loop stays rolled to keep
+    // the kernel's code small.
     auto bulk_tile = [&](int t, int jc) {
         const int k = 32 * jc + lane;
         const bool kv = k < H;
         const int kk = kv ? k : H - 1;
+        int32_t* runv = s_runv + (t % kSlots) * HP;
+        int32_t* runbfv = s_runbf + (t % kSlots) * HP;
         int32_t run = INT_MAX, runbf = 0;
-        if (kv) { run = s_runv[k]; runbf = s_runbf[k]; }
+        if (kv) { run = runv[k]; runbf = runbfv[k]; }
         const int32_t x1 = s_pd8[kk + 1];
-        const uint2* divp = s_div + (kk + 1 - 32 * t);     // s_div[k + 1 - b] = divp[-i], b = 32 t + i
-        const int32_t* lo_base = po_col + 32 * t;           // PO[f][b] = lo_base[f P + i]
         const int32_t* hi_base = po_col + kk + 1;           // PO[f][k + 1] = hi_base[f P]
-        const int4* pd4 = reinterpret_cast<const int4*>(s_pd8 + 32 * t);
-        const int4* th4 = reinterpret_cast<const int4*>(s_thr + 32 * t);
         const int32_t pen_g = m.pen_grav, pen_d = m.pen_div, pen_o = m.pen_ord;
-#pragma unroll
+#pragma unroll 1
         for (int g = 0; g < 4; ++g) {
-            int32_t lo[8], hi[8], fv[8];
-            const int4 pa = pd4[2 * g], pb = pd4[2 * g + 1];
+            const int b0 = 32 * t + 8 * g;
+            const uint2* divp = s_div + (kk + 1 - b0);      // s_div[k + 1 - b] = divp[-i], b = b0 + i
+            const int32_t* lo_base = po_col + b0;           // PO[f][b] = lo_base[f P + i]
+            const int4 pa = *reinterpret_cast<const int4*>(s_pd8 + b0);
+            const int4 pb = *reinterpret_cast<const int4*>(s_pd8 + b0 + 4);
             const int32_t pdv[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+            int32_t lo[8], hi[8], fv[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const int ii = 8 * g + i;
-                const uint2 dm = divp[-ii];
+                const uint2 dm = divp[-i];
                 const int f = (int)min(__umulhi((uint32_t)(x1 - pdv[i]), dm.x) >> dm.y, (uint32_t)m.dmax);
-                lo[i] = __ldg(lo_base + (size_t)f * P + ii);
+                lo[i] = __ldg(lo_base + (size_t)f * P + i);
                 hi[i] = __ldg(hi_base + (size_t)f * P);
                 fv[i] = f;
             }
-            const int4 ta = th4[2 * g], tb = th4[2 * g + 1];
+            const int4 ta = *reinterpret_cast<const int4*>(s_thr + b0);
+            const int4 tb = *reinterpret_cast<const int4*>(s_thr + b0 + 4);
             const int32_t thv[8] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z, tb.w};
             int32_t cv[8], cbf[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const int b = 32 * t + 8 * g + i;
+                const int b = b0 + i;
                 const StartCtx c = s_ctx[b];
                 const int32_t d = hi[i] - lo[i];
                 const int f = fv[i];
@@ -314,41 +330,44 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
             tree_min<8>(cv, cbf);
             if (cv[0] < run) { run = cv[0]; runbf = cbf[0]; }
         }
-        if (kv) { s_runv[k] = run; s_runbf[k] = runbf; }
+        if (kv) { runv[k] = run; runbfv[k] = runbf; }
     };
 
     // the chain data of block 0 (input only); the bulk warps gather the rest
-    gather_chain(0, threadIdx.x, kThreads);
+    gather_chain(s_cb, 0, H, P, po_col, s_pd8, s_thr, s_div, m, threadIdx.x, kThreads);
     __syncthreads();
 
     if (warp != chain) {
         // ---------------------------------------------------------------- bulk warps
-        // End-row block c receives c - 1 tiles.  The blocks are dealt, largest
-        // first, to the bulk warps in snake order (rounds of kBulk blocks,
+        // End-row block c receives c - 1 tiles, split by start block into
+        // kSlots partial minima (t = s mod kSlots) so that two warps share a
+        // block's sequence of tiles.  The (block, slot) items are dealt, largest
+        // block first, to the bulk warps in snake order (rounds of kBulk items,
         // alternating direction), which keeps the per-warp work balanced; lane l
-        // of a bulk warp holds the block it owns in round l and the number of
-        // start blocks already applied to it.
+        // of a bulk warp holds its round-l item and the next start block due.
         const int snake = (lane & 1) ? kBulk - 1 - bulk_id : bulk_id;
-        const int my_c = NB - 1 - (lane * kBulk + snake);
+        const int item = lane * kBulk + snake;
+        const int my_c = NB - 1 - item / kSlots;
+        int my_t = item % kSlots;                             // next start block of the item
         const bool mine = my_c >= 2;
-        int my_r = 0;
-        // pending work, earliest deadline first: the tile (my_r, my_c) of the
-        // lowest owned end-row block whose next start block is final, or this
-        // warp's share of the chain data of block next_g (its ring slot is free
-        // once block next_g - kRing is final)
+        // pending work, earliest deadline first: the next tile of the lowest
+        // owned end-row block whose start block is final, or this warp's share
+        // of the chain data of block next_g (its ring slot is free once block
+        // next_g - kRing is final)
         int next_g = 1;
         for (;;) {
             const int vf = __shfl_sync(kFull, lane == 0 ? *v_final : 0, 0);     // final blocks
             if (*v_abort) break;
-            const bool pending = mine && my_r < my_c - 1;
-            const unsigned work = __ballot_sync(kFull, pending && my_r < vf);
+            const bool pending = mine && my_t <= my_c - 2;
+            const unsigned work = __ballot_sync(kFull, pending && my_t < vf);
             const bool all_done = __ballot_sync(kFull, pending) == 0;
             // owned blocks decrease with the lane: the lowest block is the highest lane
             const int wl = work ? 31 - __clz(work) : -1;
             const int jc_work = wl >= 0 ? __shfl_sync(kFull, my_c, wl) : -1;
             const bool g_open = next_g < NB && vf >= next_g - kRing + 1;
             if (g_open && (jc_work < 0 || next_g <= jc_work)) {
-                gather_chain(next_g, bulk_id * 32 + lane, kBulk * 32);
+                gather_chain(s_cb + next_g % kRing, 32 * next_g, H, P, po_col, s_pd8, s_thr, s_div, m,
+                             bulk_id * 32 + lane, kBulk * 32);
                 __threadfence_block();
                 __syncwarp();
                 if (lane == 0) atomicAdd(&sync->gathered[next_g], 1);
@@ -356,12 +375,12 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
                 continue;
             }
             if (jc_work >= 0) {
-                const int t = __shfl_sync(kFull, my_r, wl);
+                const int t = __shfl_sync(kFull, my_t, wl);
                 bulk_tile(t, jc_work);
                 __threadfence_block();
                 __syncwarp();
-                if (lane == 0) sync->ready[jc_work] = t + 1;
-                if (lane == wl) my_r = t + 1;
+                if (lane == 0) atomicAdd(&sync->ready[jc_work], 1);
+                if (lane == wl) my_t = t + kSlots;
                 continue;
             }
             if (all_done && next_g >= NB) break;
@@ -400,7 +419,17 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
         // starts of blocks <= j-2 (bulk tiles), then those of block j-1 (run2):
         // ascending starts with strict "<" keep the earliest start on ties
         int32_t run = INT_MAX, runbf = 0;
-        if (lane < nb) { run = s_runv[k]; runbf = s_runbf[k]; }
+        if (lane < nb) {
+            // merge the partial minima by (cost and class, start): the minimum
+            // over all their starts with ties to the earliest start
+            run = s_runv[k];
+            runbf = s_runbf[k];
+#pragma unroll
+            for (int q = 1; q < kSlots; ++q) {
+                const int32_t v = s_runv[q * HP + k], bf = s_runbf[q * HP + k];
+                if (v < run || (v == run && (bf >> 8) < (runbf >> 8))) { run = v; runbf = bf; }
+            }
+        }
         if (run2 < run) { run = run2; runbf = run2bf; }
         run2 = INT_MAX; run2bf = 0;
         // inputs of one step, loaded a step ahead so that shared-memory latency
@@ -460,27 +489,11 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
             }
         };
         StepIn cur = load_in(0);
-        int i0 = 0;
-        if (j == 0) {
-            const StepIn nx = load_in(nb > 1 ? 1 : 0);
-            step(0, cur, true);
+#pragma unroll 2
+        for (int i = 0; i < nb; ++i) {
+            const StepIn nx = load_in(i + 1 < nb ? i + 1 : i);
+            step(i, cur, j == 0 && i == 0);
             cur = nx;
-            i0 = 1;
-        }
-        if (nb == 32) {
-#pragma unroll 8
-            for (int i = i0; i < 32; ++i) {
-                const StepIn nx = load_in(i < 31 ? i + 1 : 31);
-                step(i, cur, false);
-                cur = nx;
-            }
-        } else {
-#pragma unroll 1
-            for (int i = i0; i < nb; ++i) {
-                const StepIn nx = load_in(i + 1 < nb ? i + 1 : i);
-                step(i, cur, false);
-                cur = nx;
-            }
         }
         __syncwarp();
         // the block's back-pointers and the contexts of the starts that follow its rows
@@ -553,8 +566,10 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
     }
 }
 
-template <int NW, bool kStd>
-__global__ void __launch_bounds__(NW * 32, 16 / NW) stixel_dp_kernel(DpArgs a)
+// MINB: CTAs per SM the register allocation is sized for (8 warps x 2 CTAs
+// and 16 warps x 1 CTA both leave 128 registers per thread).
+template <int NW, bool kStd, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) stixel_dp_kernel(DpArgs a)
 {
     extern __shared__ __align__(16) int32_t sm[];
     dp_column<NW, kStd>(a, blockIdx.x, sm);
@@ -563,8 +578,8 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) stixel_dp_kernel(DpArgs a)
 // Persistent form: each CTA takes columns from a work list (one shared atomic
 // counter, reset before the launch) until the list is empty.  The list is
 // ordered longest column first, so the last columns to start are the short ones.
-template <int NW, bool kStd>
-__global__ void __launch_bounds__(NW * 32, 16 / NW)
+template <int NW, bool kStd, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB)
     stixel_dp_batch_kernel(const DpArgs* __restrict__ frames, const int2* __restrict__ items, int nitems,
                            int* counter)
 {
@@ -622,33 +637,61 @@ cudaError_t allow_smem(K kernel, bool* done)
 }
 
 // per-instantiation "attribute set" flags, one per device
-template <int NW, bool kStd>
+template <int NW, bool kStd, int MINB>
 bool* frame_flags() { static bool f[64] = {false}; return f; }
-template <int NW, bool kStd>
+template <int NW, bool kStd, int MINB>
 bool* batch_flags() { static bool f[64] = {false}; return f; }
 
-template <int NW, bool kStd>
+template <int NW, bool kStd, int MINB>
 cudaError_t launch_frame(const DpArgs& a, int ncols, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = allow_smem(stixel_dp_kernel<NW, kStd>, frame_flags<NW, kStd>());
+    cudaError_t e = allow_smem(stixel_dp_kernel<NW, kStd, MINB>, frame_flags<NW, kStd, MINB>());
     if (e != cudaSuccess) return e;
-    stixel_dp_kernel<NW, kStd><<<ncols, NW * 32, smem, st>>>(a);
+    stixel_dp_kernel<NW, kStd, MINB><<<ncols, NW * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int NW, bool kStd>
+template <int NW, bool kStd, int MINB>
 cudaError_t launch_batch(const DpArgs* frames, const int2* items, int nitems, int* counter, int grid, size_t smem,
                          cudaStream_t st)
 {
-    cudaError_t e = allow_smem(stixel_dp_batch_kernel<NW, kStd>, batch_flags<NW, kStd>());
+    cudaError_t e = allow_smem(stixel_dp_batch_kernel<NW, kStd, MINB>, batch_flags<NW, kStd, MINB>());
     if (e != cudaSuccess) return e;
-    stixel_dp_batch_kernel<NW, kStd><<<grid, NW * 32, smem, st>>>(frames, items, nitems, counter);
+    stixel_dp_batch_kernel<NW, kStd, MINB><<<grid, NW * 32, smem, st>>>(frames, items, nitems, counter);
     return cudaGetLastError();
 }
 
 bool standard_transitions(const ModelDev& m)
 {
     return m.trans[1][1] >= kBig && m.trans[1][2] >= kBig && m.trans[2][2] >= kBig;
+}
+
+template <bool kStd>
+cudaError_t launch_frame_shape(const DpArgs& a, int ncols, size_t smem, cudaStream_t st)
+{
+    // with no more columns than SMs, each column gets a whole SM: 16 warps
+    // (15 bulk); otherwise two 8-warp CTAs share an SM
+    if (ncols <= sm_count()) return launch_frame<16, kStd, 1>(a, ncols, smem, st);
+    return launch_frame<8, kStd, 2>(a, ncols, smem, st);
+}
+
+template <bool kStd>
+cudaError_t prepare_std()
+{
+    cudaError_t e = allow_smem(stixel_dp_batch_kernel<8, kStd, 2>, batch_flags<8, kStd, 2>());
+    if (e == cudaSuccess) e = allow_smem(stixel_dp_batch_kernel<16, kStd, 1>, batch_flags<16, kStd, 1>());
+    if (e == cudaSuccess) e = allow_smem(stixel_dp_kernel<8, kStd, 2>, frame_flags<8, kStd, 2>());
+    if (e == cudaSuccess) e = allow_smem(stixel_dp_kernel<16, kStd, 1>, frame_flags<16, kStd, 1>());
+    return e;
+}
+
+template <bool kStd>
+cudaError_t launch_batch_shape(const DpArgs* f, const int2* it, int n, int* ctr, int warps, int grid, int ctas_per_sm,
+                               size_t smem, cudaStream_t st)
+{
+    (void)ctas_per_sm;        // only the grid depends on it
+    if (warps == 16) return launch_batch<16, kStd, 1>(f, it, n, ctr, grid, smem, st);
+    return launch_batch<8, kStd, 2>(f, it, n, ctr, grid, smem, st);
 }
 
 }  // namespace
@@ -675,40 +718,27 @@ cudaError_t launch_dp(const int32_t* pd, const int32_t* pg, const int32_t* ps, c
     DpArgs a;
     dp_frame_args(pd, pg, ps, po, g, m, r, out, err, &a);
     const size_t smem = dp_smem_bytes(g.H);
-    // with no more columns than SMs, each column gets a whole SM: 16 warps
-    // (15 bulk); otherwise two 8-warp CTAs share an SM
-    const bool wide = g.ncols <= sm_count();
-    if (standard_transitions(m))
-        return wide ? launch_frame<16, true>(a, g.ncols, smem, st) : launch_frame<8, true>(a, g.ncols, smem, st);
-    return wide ? launch_frame<16, false>(a, g.ncols, smem, st) : launch_frame<8, false>(a, g.ncols, smem, st);
+    return standard_transitions(m) ? launch_frame_shape<true>(a, g.ncols, smem, st)
+                                   : launch_frame_shape<false>(a, g.ncols, smem, st);
 }
 
 cudaError_t prepare_dp_kernels()
 {
     // attribute changes are not stream operations: do them before any capture
-    cudaError_t e = allow_smem(stixel_dp_batch_kernel<8, true>, batch_flags<8, true>());
-    if (e == cudaSuccess) e = allow_smem(stixel_dp_batch_kernel<8, false>, batch_flags<8, false>());
-    if (e == cudaSuccess) e = allow_smem(stixel_dp_batch_kernel<16, true>, batch_flags<16, true>());
-    if (e == cudaSuccess) e = allow_smem(stixel_dp_batch_kernel<16, false>, batch_flags<16, false>());
-    if (e == cudaSuccess) e = allow_smem(stixel_dp_kernel<8, true>, frame_flags<8, true>());
-    if (e == cudaSuccess) e = allow_smem(stixel_dp_kernel<8, false>, frame_flags<8, false>());
-    if (e == cudaSuccess) e = allow_smem(stixel_dp_kernel<16, true>, frame_flags<16, true>());
-    if (e == cudaSuccess) e = allow_smem(stixel_dp_kernel<16, false>, frame_flags<16, false>());
+    cudaError_t e = prepare_std<true>();
+    if (e == cudaSuccess) e = prepare_std<false>();
     if (e == cudaSuccess && sm_count() <= 0) e = cudaErrorInvalidDevice;
     return e;
 }
 
 cudaError_t launch_dp_batch(const DpArgs* d_frames, const int2* d_items, int nitems, int* d_counter, int maxH,
-                            int warps, bool std_trans, int grid, cudaStream_t st)
+                            int warps, int ctas_per_sm, bool std_trans, int grid, cudaStream_t st)
 {
     if (nitems <= 0) return cudaSuccess;
     if (maxH <= 0 || maxH > STIXELS_MAX_HEIGHT || grid <= 0) return cudaErrorInvalidValue;
     const size_t smem = dp_smem_bytes(maxH);
-    if (warps == 16)
-        return std_trans ? launch_batch<16, true>(d_frames, d_items, nitems, d_counter, grid, smem, st)
-                         : launch_batch<16, false>(d_frames, d_items, nitems, d_counter, grid, smem, st);
-    return std_trans ? launch_batch<8, true>(d_frames, d_items, nitems, d_counter, grid, smem, st)
-                     : launch_batch<8, false>(d_frames, d_items, nitems, d_counter, grid, smem, st);
+    return std_trans ? launch_batch_shape<true>(d_frames, d_items, nitems, d_counter, warps, grid, ctas_per_sm, smem, st)
+                     : launch_batch_shape<false>(d_frames, d_items, nitems, d_counter, warps, grid, ctas_per_sm, smem, st);
 }
 
 }  // namespace stx

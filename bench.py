@@ -69,6 +69,9 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--served-seconds", type=float, default=2.0, help="length of the Poisson arrival trace")
+    ap.add_argument("--only", choices=["all", "batched", "served"], default="all",
+                    help="run one secondary workload alone and print its record (for profiling); "
+                         "the default prints the full benchmark line")
     return ap.parse_args()
 
 
@@ -563,6 +566,23 @@ def bench_reference(args, world, rank):
 def main():
     args = parse_args()
     world, rank, local = dist_info()
+    if args.only != "all" and args.impl == "ours":
+        import torch
+        import paper_1610_04124_gb300 as S
+        import scenes
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        if args.only == "batched":
+            rec = {"batched": {
+                "mixed64": bench_batched(S, scenes, torch, dev, scenes.CONFIG4, 4000, max(1, args.steps),
+                                         "64 frames: 24x 640x240, 32x 1024x440, 8x 2048x880; s in {5,7}; dmax {64,128}"),
+                "paper32": bench_batched(S, scenes, torch, dev, [scenes.CONFIG2] * 32, 4100, max(1, args.steps),
+                                         "32 frames of 1024x440 s=5 dmax=128 in one launch")}}
+        else:
+            rec = {"served": bench_served(S, scenes, torch, args.served_seconds)}
+        if rank == 0:
+            print(json.dumps(rec), flush=True)
+        return
     if args.impl == "reference":
         rec = bench_reference(args, world, rank)
     else:

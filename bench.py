@@ -38,8 +38,8 @@ L2_FLUSH_BYTES = 256 << 20
 # keyed by the sha1 of the kernel's source file at the time of the capture.  A
 # kernel whose source changed since reports null.
 NCU_TRAFFIC = {
-    "kernels_dp.cu": ("a060475ddc0b", 15461632),
-    "kernels_luts.cu": ("e944a4b7d3b9", 210688),
+    "kernels_dp.cu": ("9e9f5bbe2cae", 15360256),
+    "kernels_luts.cu": ("e944a4b7d3b9", 201344),
     "kernels_reduce.cu": ("fc07f6c2866c", 1808512),
 }
 
@@ -80,6 +80,22 @@ def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(x, world, device):
+    """The largest of every rank's x (the job's time is its slowest replica's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
 
 
 def host_cores():
@@ -412,14 +428,8 @@ def bench_ours(args, world, rank, local):
     t_red = [ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]
     t_lut = [ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]
     t_dp = [ev[i][2].elapsed_time(ev[i][3]) for i in range(K)]
-    total_ms = sum(t_step)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    frames = K * world
-    value = frames / (total_ms / 1000.0)
+    total_ms = max_over_ranks(sum(t_step), world, dev)
+    value = job_rate(K, world, total_ms / 1000.0)
     err = h.get_error(stream)
 
     # end to end through the C ABI, host buffers (pinned), copies inside the timed region
@@ -435,13 +445,8 @@ def bench_ours(args, world, rank, local):
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             h.compute_host(host_in, host_out)
-        el = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([el], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            el = float(tt.item())
-        e2e = {"value": n_e2e * world / el, "unit": "frames/s", "h2d_bytes_per_step": H * W * 4,
+        el = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": job_rate(n_e2e, world, el), "unit": "frames/s", "h2d_bytes_per_step": H * W * 4,
                "d2h_bytes_per_step": ncols * cap * 12 + ncols * 4 + ncols * 4, "steps": n_e2e}
 
     batched = served = None

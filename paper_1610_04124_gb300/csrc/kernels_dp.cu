@@ -60,7 +60,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxBlocks = (STIXELS_MAX_HEIGHT + 31) / 32;
-constexpr int kRing = 3;              // chain data buffers (blocks gathered ahead)
+constexpr int kRingMax = 3;           // chain data buffers (blocks gathered ahead): 2 or 3
 constexpr int kSlots = 2;             // partial running minima per end row (start blocks t mod kSlots)
 constexpr int kSpinLimit = 1 << 22;   // polls before a wait gives up (well over 0.1 s)
 
@@ -161,11 +161,11 @@ __device__ __forceinline__ bool wait_geq(volatile int* p, int target, volatile i
     return ok != 0;
 }
 
-size_t dp_smem_bytes(int H)
+size_t dp_smem_bytes(int H, int ring)
 {
     const size_t HP = (size_t)((H + 3) & ~3);
     return sizeof(StartCtx) * HP + sizeof(int4) * HP + sizeof(int32_t) * 2 * (HP + 4) + sizeof(int2) * (HP + 4) +
-           sizeof(uint2) * (HP + 4) + sizeof(int32_t) * 2 * kSlots * HP + sizeof(ChainBuf) * kRing +
+           sizeof(uint2) * (HP + 4) + sizeof(int32_t) * 2 * kSlots * HP + sizeof(ChainBuf) * ring +
            sizeof(SyncState);
 }
 
@@ -213,10 +213,11 @@ __device__ __noinline__ void gather_chain(ChainBuf* cb, int B, int H, int P, con
 
 // Solves column `col` of frame `a` with all NW warps of the CTA (one chain
 // warp, NW - 1 bulk warps); `sm` is the CTA's dynamic shared memory
-// (dp_smem_bytes).  Every warp returns from here; the caller synchronises
+// (dp_smem_bytes with the same ring, 2 or 3 chain buffers).  Every warp
+// returns from here; the caller synchronises
 // before reusing `sm`.
 template <int NW, bool kStdTrans>
-__device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_t* sm)
+__device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const int ring, int32_t* sm)
 {
     constexpr int kWarps = NW;
     constexpr int kThreads = NW * 32;
@@ -240,8 +241,8 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
     // [kSlots][HP] object running minima over the start blocks t = s (mod kSlots)
     int32_t* s_runv = reinterpret_cast<int32_t*>(s_div + HP + 4);
     int32_t* s_runbf = s_runv + kSlots * HP;                           // [kSlots][HP] start << 8 | f
-    ChainBuf* s_cb = reinterpret_cast<ChainBuf*>(s_runbf + kSlots * HP);   // [kRing]
-    SyncState* sync = reinterpret_cast<SyncState*>(s_cb + kRing);
+    ChainBuf* s_cb = reinterpret_cast<ChainBuf*>(s_runbf + kSlots * HP);   // [ring]
+    SyncState* sync = reinterpret_cast<SyncState*>(s_cb + ring);
     volatile int* v_final = &sync->final_blocks;
     volatile int* v_abort = &sync->abort;
     const int NB = (H + 31) >> 5;
@@ -353,7 +354,7 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
         // pending work, earliest deadline first: the next tile of the lowest
         // owned end-row block whose start block is final, or this warp's share
         // of the chain data of block next_g (its ring slot is free once block
-        // next_g - kRing is final)
+        // next_g - ring is final)
         int next_g = 1;
         for (;;) {
             const int vf = __shfl_sync(kFull, lane == 0 ? *v_final : 0, 0);     // final blocks
@@ -364,9 +365,9 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
             // owned blocks decrease with the lane: the lowest block is the highest lane
             const int wl = work ? 31 - __clz(work) : -1;
             const int jc_work = wl >= 0 ? __shfl_sync(kFull, my_c, wl) : -1;
-            const bool g_open = next_g < NB && vf >= next_g - kRing + 1;
+            const bool g_open = next_g < NB && vf >= next_g - ring + 1;
             if (g_open && (jc_work < 0 || next_g <= jc_work)) {
-                gather_chain(s_cb + next_g % kRing, 32 * next_g, H, P, po_col, s_pd8, s_thr, s_div, m,
+                gather_chain(s_cb + next_g % ring, 32 * next_g, H, P, po_col, s_pd8, s_thr, s_div, m,
                              bulk_id * 32 + lane, kBulk * 32);
                 __threadfence_block();
                 __syncwarp();
@@ -413,7 +414,7 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
         const int B = 32 * j;
         if (j >= 1 && !wait_geq(&sync->gathered[j], kBulk, v_abort, 16)) { aborted = true; break; }
         if (j >= 2 && !wait_geq(&sync->ready[j], j - 1, v_abort, 16)) { aborted = true; break; }
-        const ChainBuf* cb = s_cb + (j % kRing);
+        const ChainBuf* cb = s_cb + (j % ring);
         const int nb = min(32, H - B);
         const int k = B + lane;
         // starts of blocks <= j-2 (bulk tiles), then those of block j-1 (run2):
@@ -567,12 +568,12 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, int32_
 }
 
 // MINB: CTAs per SM the register allocation is sized for (8 warps x 2 CTAs
-// and 16 warps x 1 CTA both leave 128 registers per thread).
+// and 16 warps x 1 CTA both leave 128 registers per thread, 8 x 3 leaves 85).
 template <int NW, bool kStd, int MINB>
-__global__ void __launch_bounds__(NW * 32, MINB) stixel_dp_kernel(DpArgs a)
+__global__ void __launch_bounds__(NW * 32, MINB) stixel_dp_kernel(DpArgs a, int ring)
 {
     extern __shared__ __align__(16) int32_t sm[];
-    dp_column<NW, kStd>(a, blockIdx.x, sm);
+    dp_column<NW, kStd>(a, blockIdx.x, ring, sm);
 }
 
 // Persistent form: each CTA takes columns from a work list (one shared atomic
@@ -581,7 +582,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) stixel_dp_kernel(DpArgs a)
 template <int NW, bool kStd, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB)
     stixel_dp_batch_kernel(const DpArgs* __restrict__ frames, const int2* __restrict__ items, int nitems,
-                           int* counter)
+                           int* counter, int ring)
 {
     extern __shared__ __align__(16) int32_t sm[];
     __shared__ DpArgs s_args;
@@ -597,7 +598,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
         int* dst = reinterpret_cast<int*>(&s_args);
         for (int i = threadIdx.x; i < (int)(sizeof(DpArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
         __syncthreads();
-        dp_column<NW, kStd>(s_args, w.y, sm);
+        dp_column<NW, kStd>(s_args, w.y, ring, sm);
         __syncthreads();
     }
 }
@@ -647,17 +648,17 @@ cudaError_t launch_frame(const DpArgs& a, int ncols, size_t smem, cudaStream_t s
 {
     cudaError_t e = allow_smem(stixel_dp_kernel<NW, kStd, MINB>, frame_flags<NW, kStd, MINB>());
     if (e != cudaSuccess) return e;
-    stixel_dp_kernel<NW, kStd, MINB><<<ncols, NW * 32, smem, st>>>(a);
+    stixel_dp_kernel<NW, kStd, MINB><<<ncols, NW * 32, smem, st>>>(a, kRingMax);
     return cudaGetLastError();
 }
 
 template <int NW, bool kStd, int MINB>
 cudaError_t launch_batch(const DpArgs* frames, const int2* items, int nitems, int* counter, int grid, size_t smem,
-                         cudaStream_t st)
+                         int ring, cudaStream_t st)
 {
     cudaError_t e = allow_smem(stixel_dp_batch_kernel<NW, kStd, MINB>, batch_flags<NW, kStd, MINB>());
     if (e != cudaSuccess) return e;
-    stixel_dp_batch_kernel<NW, kStd, MINB><<<grid, NW * 32, smem, st>>>(frames, items, nitems, counter);
+    stixel_dp_batch_kernel<NW, kStd, MINB><<<grid, NW * 32, smem, st>>>(frames, items, nitems, counter, ring);
     return cudaGetLastError();
 }
 
@@ -680,6 +681,7 @@ cudaError_t prepare_std()
 {
     cudaError_t e = allow_smem(stixel_dp_batch_kernel<8, kStd, 2>, batch_flags<8, kStd, 2>());
     if (e == cudaSuccess) e = allow_smem(stixel_dp_batch_kernel<16, kStd, 1>, batch_flags<16, kStd, 1>());
+    if (e == cudaSuccess) e = allow_smem(stixel_dp_batch_kernel<8, kStd, 3>, batch_flags<8, kStd, 3>());
     if (e == cudaSuccess) e = allow_smem(stixel_dp_kernel<8, kStd, 2>, frame_flags<8, kStd, 2>());
     if (e == cudaSuccess) e = allow_smem(stixel_dp_kernel<16, kStd, 1>, frame_flags<16, kStd, 1>());
     return e;
@@ -689,14 +691,16 @@ template <bool kStd>
 cudaError_t launch_batch_shape(const DpArgs* f, const int2* it, int n, int* ctr, int warps, int grid, int ctas_per_sm,
                                size_t smem, cudaStream_t st)
 {
-    (void)ctas_per_sm;        // only the grid depends on it
-    if (warps == 16) return launch_batch<16, kStd, 1>(f, it, n, ctr, grid, smem, st);
-    return launch_batch<8, kStd, 2>(f, it, n, ctr, grid, smem, st);
+    // three 8-warp CTAs per SM fit the registers; a ring of two chain buffers
+    // lets them fit the shared memory too (for heights up to about 450)
+    if (warps == 16) return launch_batch<16, kStd, 1>(f, it, n, ctr, grid, smem, kRingMax, st);
+    if (ctas_per_sm >= 3) return launch_batch<8, kStd, 3>(f, it, n, ctr, grid, smem, 2, st);
+    return launch_batch<8, kStd, 2>(f, it, n, ctr, grid, smem, kRingMax, st);
 }
 
 }  // namespace
 
-size_t dp_shared_bytes(int H) { return dp_smem_bytes(H); }
+size_t dp_shared_bytes(int H) { return dp_smem_bytes(H, kRingMax); }
 
 void dp_frame_args(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po, const FrameGeom& g,
                    const ModelDev& m, const RowsDev& r, const stixels_output_t& out, uint32_t* err, DpArgs* a)
@@ -717,7 +721,7 @@ cudaError_t launch_dp(const int32_t* pd, const int32_t* pg, const int32_t* ps, c
     if (g.H > STIXELS_MAX_HEIGHT) return cudaErrorInvalidValue;
     DpArgs a;
     dp_frame_args(pd, pg, ps, po, g, m, r, out, err, &a);
-    const size_t smem = dp_smem_bytes(g.H);
+    const size_t smem = dp_smem_bytes(g.H, kRingMax);
     return standard_transitions(m) ? launch_frame_shape<true>(a, g.ncols, smem, st)
                                    : launch_frame_shape<false>(a, g.ncols, smem, st);
 }
@@ -736,7 +740,7 @@ cudaError_t launch_dp_batch(const DpArgs* d_frames, const int2* d_items, int nit
 {
     if (nitems <= 0) return cudaSuccess;
     if (maxH <= 0 || maxH > STIXELS_MAX_HEIGHT || grid <= 0) return cudaErrorInvalidValue;
-    const size_t smem = dp_smem_bytes(maxH);
+    const size_t smem = dp_smem_bytes(maxH, warps == 8 && ctas_per_sm >= 3 ? 2 : kRingMax);
     return std_trans ? launch_batch_shape<true>(d_frames, d_items, nitems, d_counter, warps, grid, ctas_per_sm, smem, st)
                      : launch_batch_shape<false>(d_frames, d_items, nitems, d_counter, warps, grid, ctas_per_sm, smem, st);
 }

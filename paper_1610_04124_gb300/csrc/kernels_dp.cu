@@ -64,11 +64,17 @@ constexpr int kRingMax = 3;           // chain data buffers (blocks gathered ahe
 constexpr int kSlots = 2;             // partial running minima per end row (start blocks t mod kSlots)
 constexpr int kSpinLimit = 1 << 22;   // polls before a wait gives up (well over 0.1 s)
 
-// Context of one start row b, shared by every end row k >= b: the three
-// previous-class terms V_p[b-1] + T(object | p) + code(p) and the ordering
-// threshold (penalty iff f > ford).
-struct __align__(16) StartCtx {
-    int32_t bo, bg, bs, ford;
+// What the bulk tiles need of one start row b, shared by every end row k >= b
+// (cost terms include the previous class's code in their low bits):
+//   o0 = min(V_o[b-1] + T(obj|obj), V_s[b-1] + T(obj|sky)),  o1 = the same with
+//        the ordering penalty on the object term (applies iff f > ford),
+//   g0 / gg / gd = V_g[b-1] + T(obj|ground) plus no penalty / the gravity
+//        penalty (iff f > fhi) / the diving penalty (iff f < flo),
+// so that a candidate is d + min(f > ford ? o1 : o0, f > fhi ? gg : f < flo ? gd : g0).
+// (fhi >= flo - 1 holds for non-negative tolerances, so the two ground tests
+// never both hold.)
+struct __align__(16) BulkCtx {
+    int32_t o0, o1, g0, gg, gd, ford, fhi, flo;
 };
 
 // Input-only data of row v, in two arrays: pd8[v] = PD[v] + 8 v (so that
@@ -126,6 +132,16 @@ __device__ __forceinline__ int32_t ground_pen(int32_t thr, int f, const ModelDev
     return (f > thr_hi(thr) ? m.pen_grav : 0) + (f < thr_lo(thr) ? m.pen_div : 0);
 }
 
+// The bulk context of a start from its three previous-class terms (bo, bg, bs,
+// each V_p[b-1] + T(obj|p) + code(p)), its ordering threshold and the start
+// row's gravity / diving thresholds.
+__device__ __forceinline__ BulkCtx make_bulk_ctx(int32_t bo, int32_t bg, int32_t bs, int32_t ford, int32_t thr,
+                                                 const ModelDev& m)
+{
+    return BulkCtx{min(bo, bs), min(bo + m.pen_ord, bs), bg, bg + m.pen_grav, bg + m.pen_div, ford,
+                   thr_hi(thr), thr_lo(thr)};
+}
+
 // Minimum of N candidates (cost, start << 8 | f) listed in ascending start
 // order, ties to the earlier start, by a pairwise tree.  Result in v[0], bf[0].
 template <int N>
@@ -164,7 +180,7 @@ __device__ __forceinline__ bool wait_geq(volatile int* p, int target, volatile i
 size_t dp_smem_bytes(int H, int ring)
 {
     const size_t HP = (size_t)((H + 3) & ~3);
-    return sizeof(StartCtx) * HP + sizeof(int4) * HP + sizeof(int32_t) * 2 * (HP + 4) + sizeof(int2) * (HP + 4) +
+    return sizeof(BulkCtx) * HP + sizeof(int4) * HP + sizeof(int32_t) * 2 * (HP + 4) + sizeof(int2) * (HP + 4) +
            sizeof(uint2) * (HP + 4) + sizeof(int32_t) * 2 * kSlots * HP + sizeof(ChainBuf) * ring +
            sizeof(SyncState);
 }
@@ -232,7 +248,7 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
     const int chain = col & 3;
     const int bulk_id = (warp - chain - 1 + kWarps) % kWarps;
 
-    StartCtx* s_ctx = reinterpret_cast<StartCtx*>(sm);                 // [HP]
+    BulkCtx* s_ctx = reinterpret_cast<BulkCtx*>(sm);                   // [HP]
     int4* s_bp = reinterpret_cast<int4*>(s_ctx + HP);                  // [HP] back-pointers b << 2 | p per class
     int32_t* s_pd8 = reinterpret_cast<int32_t*>(s_bp + HP);            // [HP + 4], v = 0..H
     int32_t* s_thr = s_pd8 + HP + 4;                                   // [HP + 4]
@@ -277,7 +293,7 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
         sync->final_blocks = 0;
         sync->abort = 0;
         // start 0 carries the first-stixel prior (code 3 = no previous stixel)
-        s_ctx[0] = StartCtx{m.first[0] + kNoneCode, kBig, kBig, INT_MAX};
+        s_ctx[0] = make_bulk_ctx(m.first[0] + kNoneCode, kBig, kBig, INT_MAX, s_thr[0], m);
     }
     __syncthreads();
 
@@ -296,7 +312,6 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
         if (kv) { run = runv[k]; runbf = runbfv[k]; }
         const int32_t x1 = s_pd8[kk + 1];
         const int32_t* hi_base = po_col + kk + 1;           // PO[f][k + 1] = hi_base[f P]
-        const int32_t pen_g = m.pen_grav, pen_d = m.pen_div, pen_o = m.pen_ord;
 #pragma unroll 1
         for (int g = 0; g < 4; ++g) {
             const int b0 = 32 * t + 8 * g;
@@ -314,18 +329,15 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
                 hi[i] = __ldg(hi_base + (size_t)f * P);
                 fv[i] = f;
             }
-            const int4 ta = *reinterpret_cast<const int4*>(s_thr + b0);
-            const int4 tb = *reinterpret_cast<const int4*>(s_thr + b0 + 4);
-            const int32_t thv[8] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z, tb.w};
             int32_t cv[8], cbf[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int b = b0 + i;
-                const StartCtx c = s_ctx[b];
-                const int32_t d = hi[i] - lo[i];
+                const BulkCtx c = s_ctx[b];
                 const int f = fv[i];
-                cv[i] = min3(c.bo + d + (f > c.ford ? pen_o : 0),
-                             c.bg + d + (f > thr_hi(thv[i]) ? pen_g : 0) + (f < thr_lo(thv[i]) ? pen_d : 0), c.bs + d);
+                const int32_t o = f > c.ford ? c.o1 : c.o0;
+                const int32_t gr = f > c.fhi ? c.gg : (f < c.flo ? c.gd : c.g0);
+                cv[i] = min(o, gr) + (hi[i] - lo[i]);
                 cbf[i] = (b << 8) | f;
             }
             tree_min<8>(cv, cbf);
@@ -503,8 +515,8 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
             const int2 w2 = s_raw2[lane];
             s_bp[k] = make_int4(((w.y >> 8) << 2) | (w.x & 3), (w2.x << 2) | (w.z & 3), (w2.y << 2) | (w.w & 3), 0);
             if (k + 1 < H)
-                s_ctx[k + 1] = StartCtx{min(w.x & ~3, kBig) + T_oo, min(w.z & ~3, kBig) + T_og,
-                                        min(w.w & ~3, kBig) + T_os, (w.y & 255) + ord_off};
+                s_ctx[k + 1] = make_bulk_ctx(min(w.x & ~3, kBig) + T_oo, min(w.z & ~3, kBig) + T_og,
+                                             min(w.w & ~3, kBig) + T_os, (w.y & 255) + ord_off, s_thr[k + 1], m);
         }
         __threadfence_block();
         __syncwarp();

@@ -68,6 +68,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the LUT_cost-variant timing")
     ap.add_argument("--served-seconds", type=float, default=2.0, help="length of the Poisson arrival trace")
     ap.add_argument("--only", choices=["all", "batched", "served"], default="all",
                     help="run one secondary workload alone and print its record (for profiling); "
@@ -360,6 +361,48 @@ def bench_served_saturated(S, scenes, torch, frames_total=2000, budget=20 << 30,
 
 # ----------------------------------------------------------------------------- ours
 
+def time_stages(S, torch, h, disp, flush, stream, warmup, steps):
+    """The per-frame pipeline (reduce -> LUTs -> DP) for `steps` steps after
+    `warmup`, each stage between CUDA events on the launching stream and the L2
+    flushed (untimed) before every step.  Returns per-step times (ms): step,
+    reduce, LUTs, DP, and the last output."""
+    H, W = disp.shape
+    h.reserve(H, W)
+    ncols, cap = h.output_shape(H, W)
+    P, F = S.lut_pitch(H), h.params.dmax + 1
+    dev = disp.device
+    q = torch.zeros((ncols, H), dtype=torch.int16, device=dev)
+    pd = torch.zeros((ncols, P), dtype=torch.int32, device=dev)
+    pg, ps = torch.zeros_like(pd), torch.zeros_like(pd)
+    po = torch.zeros((ncols, F, P), dtype=torch.int32, device=dev)
+    out = h.alloc_output(H, W, dev)
+
+    def luts():
+        S._check(S.lib().stixels_build_luts(h.handle, S._ptr(q), H, ncols, S._stream_ptr(stream), S._ptr(pd),
+                                            S._ptr(pg), S._ptr(ps), S._ptr(po)), "build_luts")
+
+    for i in range(warmup):
+        flush.fill_(float(i))
+        h.reduce(disp, q, stream)
+        luts()
+        h.solve(pd, pg, ps, po, H, ncols, out, stream)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))                   # L2 flush between steps (not timed)
+        e = ev[i]
+        e[0].record(stream)
+        h.reduce(disp, q, stream)
+        e[1].record(stream)
+        luts()
+        e[2].record(stream)
+        h.solve(pd, pg, ps, po, H, ncols, out, stream)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    return ([e[0].elapsed_time(e[3]) for e in ev], [e[0].elapsed_time(e[1]) for e in ev],
+            [e[1].elapsed_time(e[2]) for e in ev], [e[2].elapsed_time(e[3]) for e in ev], out)
+
+
 def bench_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -376,58 +419,24 @@ def bench_ours(args, world, rank, local):
     cam = scenes.CONFIG2
     H, W, s, dmax = cam.height, cam.width, cam.stixel_width, cam.dmax
     sc = scenes.make_scene(cam, 2000 + rank, n_obstacles=(8, 20))
-    params = S.default_params(cam)
-    h = S.Stixels(params)
-    h.reserve(H, W)
-    ncols, cap = h.output_shape(H, W)
-    P, F = S.lut_pitch(H), dmax + 1
     disp = torch.from_numpy(sc.disparity).to(dev)
-    q = torch.zeros((ncols, H), dtype=torch.int16, device=dev)
-    pd = torch.zeros((ncols, P), dtype=torch.int32, device=dev)
-    pg, ps = torch.zeros_like(pd), torch.zeros_like(pd)
-    po = torch.zeros((ncols, F, P), dtype=torch.int32, device=dev)
-    out = h.alloc_output(H, W, dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    h = S.Stixels(S.default_params(cam))
+    ncols, cap = h.output_shape(H, W)
+    P, F = S.lut_pitch(H), dmax + 1
 
-    def step():
-        h.reduce(disp, q, stream)
-        S._check(S.lib().stixels_build_luts(h.handle, S._ptr(q), H, ncols, S._stream_ptr(stream), S._ptr(pd),
-                                            S._ptr(pg), S._ptr(ps), S._ptr(po)), "build_luts")
-        h.solve(pd, pg, ps, po, H, ncols, out, stream)
-
-    for i in range(args.warmup):
-        flush.fill_(float(i))
-        step()
-    torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    torch.cuda.synchronize()
-
-    K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
     clocks = ClockSampler(local)
     clocks.start()
-    for i in range(K):
-        flush.fill_(float(i))                   # L2 flush between steps (not timed)
-        e = ev[i]
-        e[0].record(stream)
-        h.reduce(disp, q, stream)
-        e[1].record(stream)
-        S._check(S.lib().stixels_build_luts(h.handle, S._ptr(q), H, ncols, S._stream_ptr(stream), S._ptr(pd),
-                                            S._ptr(pg), S._ptr(ps), S._ptr(po)), "build_luts")
-        e[2].record(stream)
-        h.solve(pd, pg, ps, po, H, ncols, out, stream)
-        e[3].record(stream)
+    t_step, t_red, t_lut, t_dp, out = time_stages(S, torch, h, disp, flush, stream, args.warmup, args.steps)
+    K = args.steps
     torch.cuda.synchronize()
     clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    t_step = [ev[i][0].elapsed_time(ev[i][3]) for i in range(K)]
-    t_red = [ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]
-    t_lut = [ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]
-    t_dp = [ev[i][2].elapsed_time(ev[i][3]) for i in range(K)]
     total_ms = max_over_ranks(sum(t_step), world, dev)
     value = job_rate(K, world, total_ms / 1000.0)
     err = h.get_error(stream)
@@ -448,6 +457,21 @@ def bench_ours(args, world, rank, local):
         el = max_over_ranks(time.perf_counter() - t0, world, dev)
         e2e = {"value": job_rate(n_e2e, world, el), "unit": "frames/s", "h2d_bytes_per_step": H * W * 4,
                "d2h_bytes_per_step": ncols * cap * 12 + ncols * 4 + ncols * 4, "steps": n_e2e}
+
+    # the paper's LUT_cost variant (Sec. 3.4): whole-pixel disparities, mean
+    # reduction, object pixel costs read from the off-line (f, d) table
+    lut_cost_variant = None
+    if rank == 0 and not args.no_variants:
+        hv = S.Stixels(S.default_params(cam, pixel_grid=1, reduce_mode=1))
+        vs, vr, vl, vd, _ = time_stages(S, torch, hv, disp, flush, stream, 5, min(K, 100))
+        lut_bytes_v = ncols * (F + 3) * P * 4 + ncols * H * 2
+        lut_cost_variant = {
+            "workload": "same 1024x440 frame; whole-pixel grid + mean reduction + off-line LUT_cost table",
+            "frames_per_s": len(vs) / (sum(vs) / 1000.0),
+            "stages_ms": {"reduce": statistics.mean(vr), "luts": statistics.mean(vl), "dp": statistics.mean(vd)},
+            "luts_gbs": lut_bytes_v / (statistics.mean(vl) / 1000.0) / 1e9,
+            "device_error_word": hv.get_error(stream)}
+        hv.close()
 
     batched = served = None
     if rank == 0 and not args.no_batched:
@@ -521,6 +545,7 @@ def bench_ours(args, world, rank, local):
         "e2e": e2e,
         "batched": batched,
         "served": served,
+        "lut_cost_variant": lut_cost_variant,
     }
     h.close()
     return rec

@@ -100,6 +100,10 @@ typedef struct stixels_params {
     float eps_order;           /*   tolerance (px) */
     int32_t reduce_mode;       /* 0 = median of the s pixels (default), 1 = mean (paper Sec. 5.1) */
     int32_t max_stixels_per_col; /* output capacity per column, >= 1 */
+    int32_t pixel_grid;        /* 0 = reduced disparities on the 1/16-px grid (default); 1 = whole
+                                  pixels, the paper's LUT_cost variant (Sec. 3.4): each reduced value
+                                  is rounded to the nearest integer (halves up) and the object pixel
+                                  costs are read from a (dmax+1) x (dmax+1) table built at create */
 } stixels_params_t;
 
 /* One output stixel: 12 bytes. */
@@ -198,7 +202,7 @@ int stixels_lut_pitch(int H);
 
 /* Stage 1 (Sec. 5.1): column reduction + transpose.  d_q: device, ncols x H
  * int16 Q4 codes, column c at d_q[c * H + v], v = H-1-r (v = 0 is the bottom
- * image row). */
+ * image row); with pixel_grid = 1 every code is a multiple of 16. */
 int stixels_reduce(stixels_t h, const float* d_disparity, int H, int W, void* stream, int16_t* d_q);
 
 /* Stage 2 (Sec. 3.4, Sec. 5.2): per-column prefix LUTs from Q4 codes d_q
@@ -208,7 +212,9 @@ int stixels_reduce(stixels_t h, const float* d_disparity, int H, int W, void* st
  *   d_po[(c * F + f) * P + j]   = sum of object pixel costs at integer
  *                                 disparity f over v < j
  * Costs in units of 2^-14 (every pixel cost is a multiple of 4).  Entries
- * j in (H, P) repeat the total. */
+ * j in (H, P) repeat the total.  With pixel_grid = 1 the codes are expected on
+ * the whole-pixel grid (multiples of 16, as stixels_reduce writes them); other
+ * codes read the table entry of floor(q / 16), clamped to [0, dmax]. */
 int stixels_build_luts(stixels_t h, const int16_t* d_q, int H, int ncols, void* stream,
                        int32_t* d_pd, int32_t* d_pg, int32_t* d_ps, int32_t* d_po);
 

@@ -44,7 +44,7 @@ class Params(C.Structure):
         ("cost_gravity", C.c_float), ("eps_gravity", C.c_float),
         ("cost_diving", C.c_float), ("eps_diving", C.c_float),
         ("cost_order", C.c_float), ("eps_order", C.c_float),
-        ("reduce_mode", C.c_int32), ("quantize", C.c_int32),
+        ("reduce_mode", C.c_int32), ("quantize", C.c_int32), ("pixel_grid", C.c_int32),
     ]
 
 
@@ -72,7 +72,7 @@ DEFAULTS: Dict[str, object] = dict(
     cost_new_stixel=3.0,
     cost_gravity=2.0, eps_gravity=1.0, cost_diving=10.0, eps_diving=1.0,
     cost_order=2.0, eps_order=0.0,
-    reduce_mode=0, quantize=1,
+    reduce_mode=0, quantize=1, pixel_grid=0,
 )
 
 
@@ -102,7 +102,7 @@ def lib():
     if _lib is None:
         L = C.CDLL(_build())
         P = C.POINTER
-        L.or_reduce.argtypes = [P(C.c_float), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P(C.c_int16)]
+        L.or_reduce.argtypes = [P(C.c_float), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P(C.c_int16)]
         L.or_pixel_cost.argtypes = [P(Params), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P(C.c_double)]
         L.or_gaussian_branch.argtypes = [P(Params), C.c_int, C.c_double, C.c_double, P(C.c_double)]
         L.or_model_constants.argtypes = [P(Params), C.c_int, P(C.c_double), P(C.c_double), P(C.c_double),
@@ -155,12 +155,13 @@ def _check(rc: int, what: str, allowed=(OK,)):
     return rc
 
 
-def reduce(disp: np.ndarray, s: int, dmax: int, mode: int = 0) -> np.ndarray:
-    """Column reduction + transpose (Sec. 5.1) -> (ncols, H) int16 Q4 codes, row 0 = bottom."""
+def reduce(disp: np.ndarray, s: int, dmax: int, mode: int = 0, pixel_grid: int = 0) -> np.ndarray:
+    """Column reduction + transpose (Sec. 5.1) -> (ncols, H) int16 Q4 codes, row 0 = bottom;
+    with pixel_grid the codes are rounded to whole pixels (multiples of 16, halves up)."""
     disp = np.ascontiguousarray(disp, dtype=np.float32)
     H, W = disp.shape
     q = np.zeros((W // s, H), dtype=np.int16)
-    _check(lib().or_reduce(_ptr(disp, C.c_float), H, W, s, dmax, mode, _ptr(q, C.c_int16)), "reduce")
+    _check(lib().or_reduce(_ptr(disp, C.c_float), H, W, s, dmax, mode, pixel_grid, _ptr(q, C.c_int16)), "reduce")
     return q
 
 

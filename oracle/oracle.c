@@ -11,7 +11,9 @@
  * Per stixel-width column it computes, in the paper's order:
  *   1. the column reduction of Sec. 5.1 (median of the s pixels of a row by
  *      default, or their mean as the paper states), after clamping each pixel
- *      to [0, dmax] and putting it on the 1/16-pixel grid ("Q4");
+ *      to [0, dmax] and putting it on the 1/16-pixel grid ("Q4"); with
+ *      pixel_grid set, the reduced value is then rounded to whole pixels, the
+ *      integer disparities of Sec. 3.4's LUT_cost variant;
  *   2. the per-pixel data cost of Eq. 4 for the object, ground and sky models
  *      of Sec. 3.1, with the sensor model of Eq. 3;
  *   3. prefix sums of those costs and of the disparities (Sec. 3.4);
@@ -92,6 +94,8 @@ typedef struct {
     float cost_gravity, eps_gravity, cost_diving, eps_diving, cost_order, eps_order;
     int32_t reduce_mode;        /* 0 = median, 1 = mean */
     int32_t quantize;           /* 1 = fixed grids (the library's arithmetic), 0 = plain reals */
+    int32_t pixel_grid;         /* 1 = reduced disparities rounded to whole pixels (Sec. 3.4's
+                                   integer LUT_cost variant), 0 = kept on the 1/16-px grid */
 } or_params_t;
 
 typedef struct {
@@ -279,7 +283,7 @@ static double pair_prior(const or_model_t* m, int c, int p, int b, int f, int f_
 
 /* Column reduction + transpose (Sec. 5.1).  disp: H x W row-major, row 0 = top.
  * q: ncols x H, column c at q[c*H + v] with v = H-1-r (bottom-up). */
-int or_reduce(const float* disp, int H, int W, int s, int dmax, int mode, int16_t* q)
+int or_reduce(const float* disp, int H, int W, int s, int dmax, int mode, int pixel_grid, int16_t* q)
 {
     if (H < 0 || W < 0 || s < 1 || s > 64 || dmax < 1 || dmax > 2047) return OR_E_ARG;
     const int C = W / s;
@@ -302,6 +306,12 @@ int or_reduce(const float* disp, int H, int W, int s, int dmax, int mode, int16_
                 int64_t sum = 0;
                 for (int i = 0; i < s; ++i) sum += vals[i];
                 out = (int32_t)((2 * sum + s) / (2 * (int64_t)s));
+            }
+            if (pixel_grid) {
+                /* whole pixels (Sec. 3.4 rounds to integer disparities): the nearest
+                 * integer to out / 16, halves up, back on the 1/16-px scale */
+                const int32_t px = (int32_t)floor((double)out / 16.0 + 0.5);
+                out = 16 * px;
             }
             q[(size_t)c * H + (size_t)(H - 1 - r)] = (int16_t)out;
         }
@@ -523,7 +533,7 @@ int or_frame(const or_params_t* p, const float* disp, int H, int W, int cap, or_
     const int C = W / s;
     int16_t* q = q_out ? q_out : (int16_t*)malloc(sizeof(int16_t) * (size_t)C * H + 1);
     if (!q) return OR_E_MEM;
-    int rc = or_reduce(disp, H, W, s, p->dmax, p->reduce_mode, q);
+    int rc = or_reduce(disp, H, W, s, p->dmax, p->reduce_mode, p->pixel_grid, q);
     if (rc) { if (!q_out) free(q); return rc; }
     or_model_t m;
     rc = model_build(p, H, &m);

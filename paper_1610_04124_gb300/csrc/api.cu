@@ -166,7 +166,7 @@ int handle_view(stixels_t h, int H, HandleView* v)
     v->rows.k_ground = it->second.d + H;
     v->err = h->d_err;
     v->stixel_width = h->hm.p.stixel_width;
-    v->reduce_mode = h->hm.p.reduce_mode;
+    v->reduce_mode = reduce_code(h->hm.p);
     v->capacity = h->hm.p.max_stixels_per_col;
     return STIXELS_OK;
 }
@@ -203,7 +203,7 @@ int stixels_create(const stixels_params_t* params, stixels_t* out_handle)
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) { delete h; return cuda_status(e); }
     const HostModel& m = h->hm;
-    const size_t n_tab = (size_t)(m.dmax + 1) + 3 * (size_t)(m.emax + 1);
+    const size_t n_tab = (size_t)(m.dmax + 1) + 3 * (size_t)(m.emax + 1) + m.lut_cost.size();
     e = cudaMalloc(&h->d_tables, sizeof(int32_t) * n_tab);
     if (e == cudaSuccess) {
         std::vector<int32_t> buf;
@@ -212,6 +212,7 @@ int stixels_create(const stixels_params_t* params, stixels_t* out_handle)
         buf.insert(buf.end(), m.g_obj.begin(), m.g_obj.end());
         buf.insert(buf.end(), m.g_ground.begin(), m.g_ground.end());
         buf.insert(buf.end(), m.g_sky.begin(), m.g_sky.end());
+        buf.insert(buf.end(), m.lut_cost.begin(), m.lut_cost.end());
         e = cudaMemcpy(h->d_tables, buf.data(), sizeof(int32_t) * n_tab, cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(uint32_t));
@@ -243,6 +244,8 @@ int stixels_create(const stixels_params_t* params, stixels_t* out_handle)
     d.g_obj = d.k_obj + (m.dmax + 1);
     d.g_ground = d.g_obj + (m.emax + 1);
     d.g_sky = d.g_ground + (m.emax + 1);
+    d.int_grid = m.p.pixel_grid;
+    d.lut_cost = m.p.pixel_grid ? d.g_sky + (m.emax + 1) : nullptr;
     *out_handle = h;
     return STIXELS_OK;
 }
@@ -296,7 +299,7 @@ int stixels_reduce(stixels_t h, const float* d_disparity, int H, int W, void* st
     const FrameGeom g = geom(h, H, W);
     if (g.H == 0 || g.ncols == 0) return STIXELS_OK;
     if (!d_disparity || !d_q) return STIXELS_E_INVALID_ARG;
-    return cuda_status(launch_reduce(d_disparity, g, h->hm.dmax, h->hm.p.reduce_mode, d_q, (cudaStream_t)stream));
+    return cuda_status(launch_reduce(d_disparity, g, h->hm.dmax, reduce_code(h->hm.p), d_q, (cudaStream_t)stream));
 }
 
 int stixels_build_luts(stixels_t h, const int16_t* d_q, int H, int ncols, void* stream, int32_t* d_pd,
@@ -352,7 +355,7 @@ int stixels_compute(stixels_t h, const float* d_disparity, int H, int W, void* s
     int32_t* ps = (int32_t*)(ws + L.ps);
     int32_t* po = (int32_t*)(ws + L.po);
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = launch_reduce(d_disparity, g, h->hm.dmax, h->hm.p.reduce_mode, q, st);
+    cudaError_t e = launch_reduce(d_disparity, g, h->hm.dmax, reduce_code(h->hm.p), q, st);
     if (e == cudaSuccess) e = launch_luts(q, g, h->md, r, pd, pg, ps, po, st);
     if (e == cudaSuccess) e = launch_dp(pd, pg, ps, po, g, h->md, r, *out, h->d_err, st);
     return cuda_status(e);

@@ -39,6 +39,8 @@ struct ModelDev {
     const int32_t* g_obj;    // [emax + 1]
     const int32_t* g_ground; // [emax + 1]
     const int32_t* g_sky;    // [emax + 1]
+    int32_t int_grid;        // 1: reduced disparities are whole pixels (multiples of 16 in Q4)
+    const int32_t* lut_cost; // int_grid only: [dmax + 1][dmax + 1], object cost of (f, d)
 };
 
 // Per-(handle, H) row tables.
@@ -96,11 +98,14 @@ struct HandleView {
     ModelDev model;
     RowsDev rows;
     uint32_t* err;
-    int stixel_width, reduce_mode, capacity;
+    int stixel_width, capacity;
+    int reduce_mode;            // reduce_code of the params: bit 0 mean, bit 1 whole-pixel grid
 };
 int handle_view(stixels_t h, int H, HandleView* v);
 // stixels status for a CUDA error, remembering its text for stixels_last_cuda_error()
 int status_from_cuda(cudaError_t e);
+// The reduction kernels' mode: bit 0 = mean (else median), bit 1 = round to whole pixels.
+inline int reduce_code(const stixels_params_t& p) { return (p.reduce_mode & 1) | ((p.pixel_grid & 1) << 1); }
 const char* t_last_cuda_error_string();
 int handle_prepare(stixels_t h, int H, HandleView* v);
 int sm_count();

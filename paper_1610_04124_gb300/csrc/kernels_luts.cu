@@ -7,7 +7,9 @@
 //   - the object per-pixel cost at every integer model disparity f in [0, dmax]
 //     (PO, the paper's LUT_object: (dmax+1) rows per column)
 // so that any stixel's data cost is the difference of two table entries.
-// Per-pixel cost: min(C_out, K + G[min(|q - 16 f|, esat)]), all int32 in
+// On the whole-pixel grid the object pixel cost is instead read from the
+// off-line (f, d) table (the paper's LUT_cost, Sec. 3.4), which holds the same
+// values.  Per-pixel cost: min(C_out, K + G[min(|q - 16 f|, esat)]), all int32 in
 // 2^-14 units (see stixels.h); G is the per-class residual table built at
 // create time and esat the residual from which every pixel of the class costs
 // C_out (so the clamp changes no cost and the staged table is small: ~64
@@ -31,8 +33,17 @@ constexpr int kChunk = 32 * kPerLane;          // outputs per warp iteration
 
 enum RowKind { kObject = 0, kDisp = 1, kGround = 2, kSky = 3 };
 
+// Half-width (whole pixels) of the window of the LUT_cost row of disparity f
+// outside which every pixel costs C_out: |d - f| >= ceil(esat / 16).
+__host__ __device__ inline int lc_radius(int esat_obj) { return (esat_obj + 15) >> 4; }
+
 // Rows [row0, row0 + kRowsPerCta) of column `col`'s LUTs (row f < F: object
 // at disparity f; F: disparities; F + 1: ground; F + 2: sky), by one CTA.
+// kIntGrid: codes are whole pixels and object costs come from the staged
+// window [f - r, f + r] of LUT_cost row f (d outside it is clamped to its
+// edge, where the cost is already C_out, so every saturated pixel of a warp
+// reads the same word).
+template <bool kIntGrid>
 __device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const int row0, int32_t* sm)
 {
     const int16_t* __restrict__ q = a.q;
@@ -48,12 +59,23 @@ __device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const 
     int32_t* s_go = s_q + QP;                    // [esat_obj + 1]   residual tables, clamped at saturation
     int32_t* s_gg = s_go + m.esat_obj + 1;       // [esat_ground + 1]
     int32_t* s_gs = s_gg + m.esat_ground + 1;    // [esat_sky + 1]
+    int32_t* s_lc = s_gs + m.esat_sky + 1;       // whole-pixel grid: [kRowsPerCta][2 r + 1] windows
     const int R = F + 3;
+    const int lr = lc_radius(m.esat_obj), lw = 2 * lr + 1;
 
     for (int j = threadIdx.x; j < QP; j += blockDim.x) s_q[j] = (j >= 1 && j <= H) ? q[(size_t)col * H + j - 1] : 0;
     for (int e = threadIdx.x; e <= m.esat_obj; e += blockDim.x) s_go[e] = __ldg(m.g_obj + e);
     for (int e = threadIdx.x; e <= m.esat_ground; e += blockDim.x) s_gg[e] = __ldg(m.g_ground + e);
     for (int e = threadIdx.x; e <= m.esat_sky; e += blockDim.x) s_gs[e] = __ldg(m.g_sky + e);
+    if (kIntGrid) {
+        // the windows of the LUT_cost rows of this CTA's object disparities
+        // (entries beyond [0, dmax] are never read: d is clamped to [0, dmax] first)
+        const int nf = min(kRowsPerCta, F - row0);
+        for (int i = threadIdx.x; i < nf * lw; i += blockDim.x) {
+            const int ff = row0 + i / lw, d = ff - lr + i % lw;
+            s_lc[i] = (d >= 0 && d < F) ? __ldg(m.lut_cost + (size_t)ff * F + d) : m.c_out;
+        }
+    }
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -89,7 +111,14 @@ __device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const 
                 if (v >= 0 && v < H) {
                     const int32_t qv = qs[i];
                     if (kind == kObject) {
-                        x = min(m.c_out, kf + s_go[min(abs(qv - f16), m.esat_obj)]);
+                        if (kIntGrid) {
+                            // one read of the off-line table (codes are 16 d; the
+                            // unsigned clamp keeps malformed caller codes in [0, dmax])
+                            const int d = (int)(min((uint32_t)qv, (uint32_t)m.emax) >> 4);
+                            x = s_lc[rr * lw + min(max(d - f, -lr), lr) + lr];
+                        } else {
+                            x = min(m.c_out, kf + s_go[min(abs(qv - f16), m.esat_obj)]);
+                        }
                     } else if (kind == kDisp) {
                         x = qv;
                     } else if (kind == kGround) {
@@ -122,10 +151,11 @@ __device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const 
     }
 }
 
+template <bool kIntGrid>
 __global__ void __launch_bounds__(256) prefix_lut_kernel(LutArgs a)
 {
     extern __shared__ __align__(16) int32_t sm[];
-    lut_rows(a, blockIdx.x, blockIdx.y * kRowsPerCta, sm);
+    lut_rows<kIntGrid>(a, blockIdx.x, blockIdx.y * kRowsPerCta, sm);
 }
 
 // Batch form: blockIdx.x indexes a list of (frame, column) items, blockIdx.y
@@ -141,7 +171,10 @@ __global__ void __launch_bounds__(256) prefix_lut_batch_kernel(const LutArgs* __
     for (int i = threadIdx.x; i < (int)(sizeof(LutArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
     __syncthreads();
     if ((int)blockIdx.y * kRowsPerCta >= s_args.F + 3) return;
-    lut_rows(s_args, w.y, blockIdx.y * kRowsPerCta, sm);
+    if (s_args.m.int_grid)
+        lut_rows<true>(s_args, w.y, blockIdx.y * kRowsPerCta, sm);
+    else
+        lut_rows<false>(s_args, w.y, blockIdx.y * kRowsPerCta, sm);
 }
 
 }  // namespace
@@ -150,7 +183,8 @@ size_t lut_shared_bytes(int H, const ModelDev& m)
 {
     const int P = lut_pitch(H);
     const int QP = (P + kChunk - 1) / kChunk * kChunk;
-    return sizeof(int32_t) * ((size_t)QP + m.esat_obj + m.esat_ground + m.esat_sky + 3);
+    const size_t lc = m.int_grid ? (size_t)kRowsPerCta * (2 * lc_radius(m.esat_obj) + 1) : 0;
+    return sizeof(int32_t) * ((size_t)QP + m.esat_obj + m.esat_ground + m.esat_sky + 3 + lc);
 }
 
 int lut_row_groups(int F) { return (F + 3 + kRowsPerCta - 1) / kRowsPerCta; }
@@ -163,7 +197,10 @@ cudaError_t launch_luts(const int16_t* q, const FrameGeom& g, const ModelDev& m,
     a.q = q; a.H = g.H; a.P = g.P; a.F = m.dmax + 1; a.m = m; a.rows = r;
     a.pd = pd; a.pg = pg; a.ps = ps; a.po = po;
     dim3 grid(g.ncols, lut_row_groups(a.F));
-    prefix_lut_kernel<<<grid, 256, lut_shared_bytes(g.H, m), st>>>(a);
+    if (m.int_grid)
+        prefix_lut_kernel<true><<<grid, 256, lut_shared_bytes(g.H, m), st>>>(a);
+    else
+        prefix_lut_kernel<false><<<grid, 256, lut_shared_bytes(g.H, m), st>>>(a);
     return cudaGetLastError();
 }
 

@@ -4,7 +4,9 @@
 // H Q4 codes: each pixel is clamped to [0, dmax] (NaN -> 0) and rounded to the
 // 1/16-px grid, then the s codes of a row are reduced to their lower median
 // (rank (s-1)/2; the median commutes with the monotone quantisation) or to
-// their mean rounded half up (the paper's average).  The output is stored
+// their mean rounded half up (the paper's average).  On the whole-pixel grid
+// (the paper's LUT_cost variant, Sec. 3.4) the reduced code is then rounded
+// to the nearest multiple of 16, halves up.  The output is stored
 // column-major and bottom-up (q[c * H + v], v = H-1-r) -- the layout the LUT
 // and DP stages read.
 //
@@ -27,7 +29,7 @@ __device__ __forceinline__ int q4_code(float d, int dmax)
 }
 
 template <int S, int MODE>
-__device__ __forceinline__ int reduce_group(const float* __restrict__ px, int dmax)
+__device__ __forceinline__ int reduce_q4(const float* __restrict__ px, int dmax)
 {
     int v[S];
 #pragma unroll
@@ -53,6 +55,14 @@ __device__ __forceinline__ int reduce_group(const float* __restrict__ px, int dm
         if (lt <= m && m < le) out = v[i];
     }
     return out;
+}
+
+// MODE bit 0: mean (else lower median); bit 1: round the result to whole pixels.
+template <int S, int MODE>
+__device__ __forceinline__ int reduce_group(const float* __restrict__ px, int dmax)
+{
+    const int r = reduce_q4<S, MODE & 1>(px, dmax);
+    return (MODE & 2) ? ((r + 8) >> 4) << 4 : r;
 }
 
 template <int S, int MODE>
@@ -98,10 +108,13 @@ template <int S>
 cudaError_t launch_batch_s(const ReduceArgs* frames, const int4* tiles, int ntiles, int mode, cudaStream_t st)
 {
     dim3 block(32, 16);
-    if (mode == 1)
-        reduce_transpose_batch_kernel<S, 1><<<ntiles, block, 0, st>>>(frames, tiles);
-    else
-        reduce_transpose_batch_kernel<S, 0><<<ntiles, block, 0, st>>>(frames, tiles);
+    switch (mode) {
+        case 0: reduce_transpose_batch_kernel<S, 0><<<ntiles, block, 0, st>>>(frames, tiles); break;
+        case 1: reduce_transpose_batch_kernel<S, 1><<<ntiles, block, 0, st>>>(frames, tiles); break;
+        case 2: reduce_transpose_batch_kernel<S, 2><<<ntiles, block, 0, st>>>(frames, tiles); break;
+        case 3: reduce_transpose_batch_kernel<S, 3><<<ntiles, block, 0, st>>>(frames, tiles); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -109,10 +122,13 @@ template <int S>
 cudaError_t launch_s(const float* disp, const FrameGeom& g, int dmax, int mode, int16_t* q, cudaStream_t st)
 {
     dim3 block(32, 16), grid((g.ncols + 31) / 32, (g.H + 15) / 16);
-    if (mode == 1)
-        reduce_transpose_kernel<S, 1><<<grid, block, 0, st>>>(disp, g.H, g.W, g.ncols, dmax, q);
-    else
-        reduce_transpose_kernel<S, 0><<<grid, block, 0, st>>>(disp, g.H, g.W, g.ncols, dmax, q);
+    switch (mode) {
+        case 0: reduce_transpose_kernel<S, 0><<<grid, block, 0, st>>>(disp, g.H, g.W, g.ncols, dmax, q); break;
+        case 1: reduce_transpose_kernel<S, 1><<<grid, block, 0, st>>>(disp, g.H, g.W, g.ncols, dmax, q); break;
+        case 2: reduce_transpose_kernel<S, 2><<<grid, block, 0, st>>>(disp, g.H, g.W, g.ncols, dmax, q); break;
+        case 3: reduce_transpose_kernel<S, 3><<<grid, block, 0, st>>>(disp, g.H, g.W, g.ncols, dmax, q); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

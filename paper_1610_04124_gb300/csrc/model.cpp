@@ -93,6 +93,7 @@ void default_params(stixels_params_t* p)
     p->cost_order = 2.0f; p->eps_order = 0.0f;
     p->reduce_mode = 0;
     p->max_stixels_per_col = 64;
+    p->pixel_grid = 0;
 }
 
 int build_model(const stixels_params_t* p, HostModel* m)
@@ -124,6 +125,7 @@ int build_model(const stixels_params_t* p, HostModel* m)
     // exclude each other
     if (p->eps_gravity < 0.0f || p->eps_diving < 0.0f) return STIXELS_E_INVALID_ARG;
     if (p->reduce_mode != 0 && p->reduce_mode != 1) return STIXELS_E_INVALID_ARG;
+    if (p->pixel_grid != 0 && p->pixel_grid != 1) return STIXELS_E_INVALID_ARG;
     if (p->max_stixels_per_col < 1 || p->max_stixels_per_col > STIXELS_MAX_HEIGHT) return STIXELS_E_INVALID_ARG;
 
     m->p = *p;
@@ -182,6 +184,19 @@ int build_model(const stixels_params_t* p, HostModel* m)
     m->eps_g = (int32_t)llround(16.0 * (double)p->eps_gravity);
     m->eps_d = (int32_t)llround(16.0 * (double)p->eps_diving);
     m->eps_o = (int32_t)llround(16.0 * (double)p->eps_order);
+    // whole-pixel grid: the object pixel cost of every (model disparity f,
+    // pixel disparity d) pair, the same value as the per-pixel formula at the
+    // Q4 residual 16 |d - f| (paper Sec. 3.4's LUT_cost, computed off-line)
+    m->lut_cost.clear();
+    if (p->pixel_grid) {
+        const int F = m->dmax + 1;
+        m->lut_cost.resize((size_t)F * F);
+        for (int f = 0; f < F; ++f)
+            for (int d = 0; d < F; ++d) {
+                const int e = std::min(16 * std::abs(d - f), m->esat[0]);
+                m->lut_cost[(size_t)f * F + d] = std::min(m->c_out, m->k_obj[f] + m->g_obj[e]);
+            }
+    }
     return STIXELS_OK;
 }
 

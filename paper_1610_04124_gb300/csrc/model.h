@@ -25,6 +25,9 @@ struct HostModel {
     int32_t eps_g = 0, eps_d = 0, eps_o = 0;
     int32_t max_finite_prior = 0;       // largest finite prior + penalty sum for one stixel
     int32_t esat[3] = {0, 0, 0};        // saturation residual (Q4) per class: object, ground, sky
+    // whole-pixel grid only: object pixel cost of pixel disparity d under model
+    // disparity f, cost[f * (dmax + 1) + d] (the paper's LUT_cost); empty otherwise
+    std::vector<int32_t> lut_cost;
 };
 
 // Validate params and build the model; returns a stixels_status.

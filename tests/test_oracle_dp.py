@@ -300,3 +300,32 @@ def test_fixed_grid_effect_is_small():
     fu = oracle.frame(oracle.make_params(cam, quantize=0), sc.disparity)
     rel = np.abs(fq.cost - fu.cost) / np.maximum(1.0, np.abs(fu.cost))
     assert rel.max() < 1e-3
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_pixel_grid_equals_q4_grid_on_whole_pixel_disparities(seed):
+    """Integer disparities are already on the whole-pixel grid, and the median of
+    whole pixels is a whole pixel, so the LUT_cost variant (Sec. 3.4) must give the
+    identical segmentation, cost and disparities."""
+    cam = scenes.CONFIG1
+    sc = scenes.make_scene(cam, 4300 + seed, n_obstacles=(3, 6), integer_disp=True, noise_sigma=0,
+                           p_outlier=0, p_invalid=0)
+    D = np.rint(sc.disparity).astype(np.float32)
+    a = oracle.frame(oracle.make_params(cam), D, cap=64)
+    b = oracle.frame(oracle.make_params(cam, pixel_grid=1), D, cap=64)
+    assert np.array_equal(a.q, b.q) and np.array_equal(a.counts, b.counts)
+    assert np.array_equal(a.cost, b.cost)
+    for c in range(len(a.counts)):
+        assert np.array_equal(a.stixels[c, :a.counts[c]], b.stixels[c, :b.counts[c]])
+
+
+def test_pixel_grid_frame_invariants():
+    """On noisy input the whole-pixel variant is a different model, but every
+    segmentation still tiles its column and its cost re-evaluates from per-pixel
+    sums."""
+    cam = scenes.CONFIG1
+    sc = scenes.make_scene(cam, 4310)
+    p = oracle.make_params(cam, pixel_grid=1, reduce_mode=1)
+    fr = oracle.frame(p, sc.disparity, cap=cam.height)
+    assert np.all(fr.q % 16 == 0)
+    _check_frame_invariants(p, fr, cam.height)

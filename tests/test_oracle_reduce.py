@@ -75,3 +75,41 @@ def test_layout_bottom_up_column_major():
     for c in range(W // s):
         for v in range(H):
             assert q[c, v] == 16 * ((H - 1 - v) + 10 * c)
+
+
+# ---- whole-pixel grid (the integer disparities of Sec. 3.4's LUT_cost variant)
+
+def test_pixel_grid_rounds_to_the_nearest_whole_pixel_halves_up():
+    # px value -> expected code, from the definition: the Q4 code first (16 x
+    # rounded, halves to even), then the nearest whole pixel of that code,
+    # halves up, times 16.  The two roundings compose: 3.49 px is Q4 56 = 3.5 px
+    # and so 4 px; 0.47 px is Q4 8 = 0.5 px and so 1 px; 2.46875 px is Q4 40.
+    cases = [(0.0, 0), (2.0, 32), (2.4375, 32), (2.46875, 48), (2.5, 48), (2.5625, 48), (3.49, 64),
+             (3.46, 48), (63.5, 1024), (64.0, 1024), (70.0, 1024), (-1.0, 0), (float("nan"), 0),
+             (0.5, 16), (0.47, 16), (0.4, 0)]
+    x = np.array([c[0] for c in cases], np.float32).reshape(1, -1)
+    q = oracle.reduce(x, 1, 64, mode=0, pixel_grid=1)[:, 0]
+    assert list(q) == [c[1] for c in cases]
+
+
+@pytest.mark.parametrize("s,mode", [(1, 0), (1, 1), (3, 0), (5, 0), (4, 0)])
+def test_pixel_grid_is_the_identity_on_whole_pixel_inputs(s, mode):
+    # integer disparities stay on the whole-pixel grid through clamping and the
+    # median (and through any reduction when s = 1)
+    rng = np.random.default_rng(40 + s)
+    D = rng.integers(-3, 70, size=(13, 6 * s)).astype(np.float32)
+    a = oracle.reduce(D, s, 64, mode=mode, pixel_grid=0)
+    b = oracle.reduce(D, s, 64, mode=mode, pixel_grid=1)
+    assert np.array_equal(a, b)
+    assert np.all(b % 16 == 0)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_pixel_grid_is_within_half_a_pixel_of_the_q4_reduction(mode):
+    rng = np.random.default_rng(50 + mode)
+    D = _nasty_image(rng, 19, 25, 96)
+    a = oracle.reduce(D, 5, 96, mode=mode, pixel_grid=0).astype(np.int64)
+    b = oracle.reduce(D, 5, 96, mode=mode, pixel_grid=1).astype(np.int64)
+    assert np.all(b % 16 == 0)
+    assert np.all((a - 8 < b) & (b <= a + 8))          # a - 1/2 px < b <= a + 1/2 px (halves up)
+    assert np.all((0 <= b) & (b <= 16 * 96))

@@ -68,7 +68,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
-    ap.add_argument("--no-variants", action="store_true", help="skip the LUT_cost-variant timing")
+    ap.add_argument("--no-variants", action="store_true", help="skip the model-variant timings")
     ap.add_argument("--served-seconds", type=float, default=2.0, help="length of the Poisson arrival trace")
     ap.add_argument("--only", choices=["all", "batched", "served"], default="all",
                     help="run one secondary workload alone and print its record (for profiling); "
@@ -458,20 +458,27 @@ def bench_ours(args, world, rank, local):
         e2e = {"value": job_rate(n_e2e, world, el), "unit": "frames/s", "h2d_bytes_per_step": H * W * 4,
                "d2h_bytes_per_step": ncols * cap * 12 + ncols * 4 + ncols * 4, "steps": n_e2e}
 
-    # the paper's LUT_cost variant (Sec. 3.4): whole-pixel disparities, mean
-    # reduction, object pixel costs read from the off-line (f, d) table
-    lut_cost_variant = None
+    # model variants on the same frame: the paper's LUT_cost variant (Sec. 3.4:
+    # whole-pixel disparities, mean reduction, object pixel costs from the
+    # off-line (f, d) table) and the disparity-dependent noise model (Eq. 3's
+    # sigma^c(f, v)), each through the same staged loop
+    variants = None
     if rank == 0 and not args.no_variants:
-        hv = S.Stixels(S.default_params(cam, pixel_grid=1, reduce_mode=1))
-        vs, vr, vl, vd, _ = time_stages(S, torch, hv, disp, flush, stream, 5, min(K, 100))
-        lut_bytes_v = ncols * (F + 3) * P * 4 + ncols * H * 2
-        lut_cost_variant = {
-            "workload": "same 1024x440 frame; whole-pixel grid + mean reduction + off-line LUT_cost table",
-            "frames_per_s": len(vs) / (sum(vs) / 1000.0),
-            "stages_ms": {"reduce": statistics.mean(vr), "luts": statistics.mean(vl), "dp": statistics.mean(vd)},
-            "luts_gbs": lut_bytes_v / (statistics.mean(vl) / 1000.0) / 1e9,
-            "device_error_word": hv.get_error(stream)}
-        hv.close()
+        variants = {}
+        for name, kw, label in [
+                ("lut_cost", dict(pixel_grid=1, reduce_mode=1),
+                 "same 1024x440 frame; whole-pixel grid + mean reduction + off-line LUT_cost table"),
+                ("variable_sigma", dict(sigma_gain=1.0, sigma_mid=40.0, sigma_width=10.0),
+                 "same 1024x440 frame; sigma(f) = sigma (1 + logistic((f - 40) / 10)), per-f / per-row tables")]:
+            hv = S.Stixels(S.default_params(cam, **kw))
+            vs, vr, vl, vd, _ = time_stages(S, torch, hv, disp, flush, stream, 5, min(K, 100))
+            lut_bytes_v = ncols * (F + 3) * P * 4 + ncols * H * 2
+            variants[name] = {
+                "workload": label, "frames_per_s": len(vs) / (sum(vs) / 1000.0),
+                "stages_ms": {"reduce": statistics.mean(vr), "luts": statistics.mean(vl), "dp": statistics.mean(vd)},
+                "luts_gbs": lut_bytes_v / (statistics.mean(vl) / 1000.0) / 1e9,
+                "device_error_word": hv.get_error(stream)}
+            hv.close()
 
     batched = served = None
     if rank == 0 and not args.no_batched:
@@ -545,7 +552,7 @@ def bench_ours(args, world, rank, local):
         "e2e": e2e,
         "batched": batched,
         "served": served,
-        "lut_cost_variant": lut_cost_variant,
+        "model_variants": variants,
     }
     h.close()
     return rec

@@ -104,6 +104,16 @@ typedef struct stixels_params {
                                   pixels, the paper's LUT_cost variant (Sec. 3.4): each reduced value
                                   is rounded to the nearest integer (halves up) and the object pixel
                                   costs are read from a (dmax+1) x (dmax+1) table built at create */
+    /* Disparity-dependent noise (Eq. 3's sigma^c(f, v), "a sigmoid function"; the
+     * paper defers its form to Pfeiffer's thesis, so this is a parameterised
+     * logistic): sigma^c(f) = sigma_c * (1 + sigma_gain / (1 + exp(-(f - sigma_mid) /
+     * sigma_width))), with f the model disparity (object: its f; ground: the ground
+     * line at the row; sky: 0).  sigma_gain = 0 (default) is the constant-sigma model;
+     * otherwise sigma_gain in (-1, 10] and sigma_width > 0 (px), and the library keeps
+     * one residual table per object disparity and per ground row. */
+    float sigma_gain;
+    float sigma_mid;
+    float sigma_width;
 } stixels_params_t;
 
 /* One output stixel: 12 bytes. */
@@ -226,8 +236,9 @@ int stixels_solve(stixels_t h, const int32_t* d_pd, const int32_t* d_pg, const i
 /* Build, on the host only (no CUDA call), the fixed-point model tables that
  * stixels_create would upload for `params`, plus the row tables for height H,
  * into caller-owned host arrays (for inspection and tests).  Returns
- * INVALID_ARG for parameters stixels_create would reject, or for H outside
- * [0, STIXELS_MAX_HEIGHT].  Cost values in 2^-14 units, forbidden /
+ * INVALID_ARG for parameters stixels_create would reject, for H outside
+ * [0, STIXELS_MAX_HEIGHT], and for sigma_gain != 0 (whose per-disparity and
+ * per-row residual tables are not exported).  Cost values in 2^-14 units, forbidden /
  * infinite entries = 2^29.  Sizes and meaning:
  *   k_obj[dmax+1]    normalisation constant K (Eq. 4) of the object model at integer f
  *   g_obj, g_ground, g_sky [16*dmax+1]   residual term (e/16)^2 / (2 sigma^2) of each

@@ -96,6 +96,11 @@ typedef struct {
     int32_t quantize;           /* 1 = fixed grids (the library's arithmetic), 0 = plain reals */
     int32_t pixel_grid;         /* 1 = reduced disparities rounded to whole pixels (Sec. 3.4's
                                    integer LUT_cost variant), 0 = kept on the 1/16-px grid */
+    /* disparity-dependent noise (Eq. 3's sigma^c(f, v), "a sigmoid function"):
+     * sigma^c(f) = sigma_c (1 + sigma_gain / (1 + exp(-(f - sigma_mid) / sigma_width))),
+     * f the model disparity (object: f; ground: the ground line at row v; sky: 0);
+     * sigma_gain = 0 is the constant-sigma model */
+    float sigma_gain, sigma_mid, sigma_width;
 } or_params_t;
 
 typedef struct {
@@ -114,7 +119,10 @@ typedef struct {
     double *fg;                /* [H]: ground-model disparity at bottom-up row v */
     double *k_ground;          /* [H] */
     double k_sky;
-    double sigma[3];
+    double sigma[3];           /* base sigma per class */
+    double *sig_obj;           /* [dmax+1]: object sigma at integer f */
+    double *sig_gnd;           /* [H]: ground sigma at row v */
+    double sig_sky;
     double first[3];           /* first-stixel prior + BIC (INFINITY = forbidden) */
     double trans[3][3];        /* transition prior + BIC, [above][below] */
     double pen_grav, pen_div, pen_ord;
@@ -170,13 +178,13 @@ static double pixel_cost(const or_model_t* m, int cls, int v, int32_t q, int f)
     double d = q / 16.0, K, r;
     if (cls == OR_OBJECT) {
         K = m->k_obj[f];
-        r = resid_term(d - (double)f, m->sigma[OR_OBJECT]);
+        r = resid_term(d - (double)f, m->sig_obj[f]);
     } else if (cls == OR_GROUND) {
         K = m->k_ground[v];
-        r = resid_term(d - m->fg[v], m->sigma[OR_GROUND]);
+        r = resid_term(d - m->fg[v], m->sig_gnd[v]);
     } else {
         K = m->k_sky;
-        r = resid_term(d, m->sigma[OR_SKY]);
+        r = resid_term(d, m->sig_sky);
     }
     double g = maybe_grid(m, K) + maybe_grid(m, r);
     double c = maybe_grid(m, m->c_out);
@@ -191,6 +199,7 @@ static int mean_f(int64_t S, int n) { return (int)((S + 8 * (int64_t)n) / (16 * 
 static void model_free(or_model_t* m)
 {
     free(m->k_obj); free(m->fg); free(m->k_ground); free(m->g_hi); free(m->g_lo);
+    free(m->sig_obj); free(m->sig_gnd);
     memset(m, 0, sizeof(*m));
 }
 
@@ -201,7 +210,17 @@ static int check_params(const or_params_t* p)
     if (!(p->sigma_ground > 0.0f && p->sigma_object > 0.0f && p->sigma_sky > 0.0f)) return OR_E_ARG;
     if (!(p->camera_height_m > 0.0f)) return OR_E_ARG;
     if (p->stixel_width < 1) return OR_E_ARG;
+    if (!(p->sigma_gain > -1.0f && p->sigma_gain <= 10.0f)) return OR_E_ARG;
+    if (p->sigma_gain != 0.0f && !(p->sigma_width > 0.0f && isfinite(p->sigma_mid))) return OR_E_ARG;
     return OR_OK;
+}
+
+/* sigma^c at model disparity f (base = the class's sigma) */
+static double sigma_at(const or_params_t* p, double base, double f)
+{
+    if (p->sigma_gain == 0.0f) return base;
+    double s = 1.0 / (1.0 + exp(-(f - (double)p->sigma_mid) / (double)p->sigma_width));
+    return base * (1.0 + (double)p->sigma_gain * s);
 }
 
 static int model_build(const or_params_t* p, int H, or_model_t* m)
@@ -225,11 +244,19 @@ static int model_build(const or_params_t* p, int H, or_model_t* m)
     m->k_ground = (double*)malloc(sizeof(double) * (size_t)H);
     m->g_hi = (double*)malloc(sizeof(double) * (size_t)H);
     m->g_lo = (double*)malloc(sizeof(double) * (size_t)H);
-    if (!m->k_obj || !m->fg || !m->k_ground || !m->g_hi || !m->g_lo) { model_free(m); return OR_E_MEM; }
+    m->sig_obj = (double*)malloc(sizeof(double) * (size_t)(p->dmax + 1));
+    m->sig_gnd = (double*)malloc(sizeof(double) * (size_t)H);
+    if (!m->k_obj || !m->fg || !m->k_ground || !m->g_hi || !m->g_lo || !m->sig_obj || !m->sig_gnd) {
+        model_free(m);
+        return OR_E_MEM;
+    }
 
-    for (int f = 0; f <= p->dmax; ++f)
-        m->k_obj[f] = k_const((double)f, m->sigma[OR_OBJECT], p_out, d_range);
-    m->k_sky = k_const(0.0, m->sigma[OR_SKY], p_out, d_range);
+    for (int f = 0; f <= p->dmax; ++f) {
+        m->sig_obj[f] = sigma_at(p, m->sigma[OR_OBJECT], (double)f);
+        m->k_obj[f] = k_const((double)f, m->sig_obj[f], p_out, d_range);
+    }
+    m->sig_sky = sigma_at(p, m->sigma[OR_SKY], 0.0);
+    m->k_sky = k_const(0.0, m->sig_sky, p_out, d_range);
 
     /* ground line: image row r = H-1-v; f = alpha (r - horizon) */
     const double alpha = (double)p->baseline_m * cos((double)p->pitch_rad) / (double)p->camera_height_m;
@@ -249,7 +276,8 @@ static int model_build(const or_params_t* p, int H, or_model_t* m)
             m->g_lo[v] = 16.0 * (fg - (double)p->eps_diving);
         }
         m->fg[v] = fg;
-        m->k_ground[v] = k_const(fg, m->sigma[OR_GROUND], p_out, d_range);
+        m->sig_gnd[v] = sigma_at(p, m->sigma[OR_GROUND], fg);
+        m->k_ground[v] = k_const(fg, m->sig_gnd[v], p_out, d_range);
     }
     m->ord_eps16 = m->quantize ? (double)llround(16.0 * (double)p->eps_order) : 16.0 * (double)p->eps_order;
 
@@ -343,7 +371,8 @@ int or_gaussian_branch(const or_params_t* p, int cls, double f, double d, double
 {
     int rc = check_params(p);
     if (rc) return rc;
-    double sigma = cls == OR_OBJECT ? p->sigma_object : (cls == OR_GROUND ? p->sigma_ground : p->sigma_sky);
+    double base = cls == OR_OBJECT ? p->sigma_object : (cls == OR_GROUND ? p->sigma_ground : p->sigma_sky);
+    double sigma = sigma_at(p, base, f);
     *out = k_const(f, sigma, (double)p->p_out, (double)p->dmax) + resid_term(d - f, sigma);
     return OR_OK;
 }

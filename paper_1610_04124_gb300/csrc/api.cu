@@ -16,7 +16,7 @@ namespace {
 
 // Per-height row tables resident on the device.
 struct RowsBuf {
-    int32_t* d = nullptr;   // fgq[H] followed by k_ground[H]
+    int32_t* d = nullptr;   // fgq[H], k_ground[H], then (variable sigma) g_ground[H][emax + 1]
     int H = 0;
 };
 
@@ -72,22 +72,25 @@ int ensure_rows(stixels_t h, int H, RowsDev* out)
 {
     auto it = h->rows.find(H);
     if (it == h->rows.end()) {
-        std::vector<int32_t> fgq, kg;
-        build_rows(h->hm, H, &fgq, &kg);
+        std::vector<int32_t> fgq, kg, gr;
+        if (!build_rows(h->hm, H, &fgq, &kg, &gr)) return STIXELS_E_INVALID_ARG;
         if (!budget_ok(h->hm, H, kg)) return STIXELS_E_INVALID_ARG;
         RowsBuf rb;
         rb.H = H;
-        cudaError_t e = cudaMalloc(&rb.d, sizeof(int32_t) * 2 * (size_t)H);
+        const size_t n = 2 * (size_t)H + gr.size();
+        cudaError_t e = cudaMalloc(&rb.d, sizeof(int32_t) * n);
         if (e != cudaSuccess) return cuda_status(e);
-        std::vector<int32_t> buf(2 * (size_t)H);
+        std::vector<int32_t> buf(n);
         memcpy(buf.data(), fgq.data(), sizeof(int32_t) * H);
         memcpy(buf.data() + H, kg.data(), sizeof(int32_t) * H);
-        e = cudaMemcpy(rb.d, buf.data(), sizeof(int32_t) * 2 * (size_t)H, cudaMemcpyHostToDevice);
+        if (!gr.empty()) memcpy(buf.data() + 2 * (size_t)H, gr.data(), sizeof(int32_t) * gr.size());
+        e = cudaMemcpy(rb.d, buf.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { cudaFree(rb.d); return cuda_status(e); }
         it = h->rows.emplace(H, rb).first;
     }
     out->fgq = it->second.d;
     out->k_ground = it->second.d + H;
+    out->g_ground = h->hm.var_sigma ? it->second.d + 2 * (size_t)H : nullptr;
     return STIXELS_OK;
 }
 
@@ -164,6 +167,7 @@ int handle_view(stixels_t h, int H, HandleView* v)
     v->model = h->md;
     v->rows.fgq = it->second.d;
     v->rows.k_ground = it->second.d + H;
+    v->rows.g_ground = h->hm.var_sigma ? it->second.d + 2 * (size_t)H : nullptr;
     v->err = h->d_err;
     v->stixel_width = h->hm.p.stixel_width;
     v->reduce_mode = reduce_code(h->hm.p);
@@ -203,7 +207,7 @@ int stixels_create(const stixels_params_t* params, stixels_t* out_handle)
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) { delete h; return cuda_status(e); }
     const HostModel& m = h->hm;
-    const size_t n_tab = (size_t)(m.dmax + 1) + 3 * (size_t)(m.emax + 1) + m.lut_cost.size();
+    const size_t n_tab = m.k_obj.size() + m.g_obj.size() + m.g_ground.size() + m.g_sky.size() + m.lut_cost.size();
     e = cudaMalloc(&h->d_tables, sizeof(int32_t) * n_tab);
     if (e == cudaSuccess) {
         std::vector<int32_t> buf;
@@ -241,11 +245,12 @@ int stixels_create(const stixels_params_t* params, stixels_t* out_handle)
     d.esat_ground = m.esat[1];
     d.esat_sky = m.esat[2];
     d.k_obj = h->d_tables;
-    d.g_obj = d.k_obj + (m.dmax + 1);
-    d.g_ground = d.g_obj + (m.emax + 1);
-    d.g_sky = d.g_ground + (m.emax + 1);
+    d.g_obj = d.k_obj + m.k_obj.size();
+    d.g_ground = d.g_obj + m.g_obj.size();
+    d.g_sky = d.g_ground + m.g_ground.size();
+    d.var_sigma = m.var_sigma ? 1 : 0;
     d.int_grid = m.p.pixel_grid;
-    d.lut_cost = m.p.pixel_grid ? d.g_sky + (m.emax + 1) : nullptr;
+    d.lut_cost = m.p.pixel_grid ? d.g_sky + m.g_sky.size() : nullptr;
     *out_handle = h;
     return STIXELS_OK;
 }
@@ -437,13 +442,14 @@ int stixels_model_tables(const stixels_params_t* params, int H, int32_t* k_obj, 
     HostModel m;
     int rc = build_model(params, &m);
     if (rc) return rc;
+    if (m.var_sigma) return STIXELS_E_INVALID_ARG;     // per-disparity / per-row tables are not exported
     if (k_obj) memcpy(k_obj, m.k_obj.data(), sizeof(int32_t) * m.k_obj.size());
     if (g_obj) memcpy(g_obj, m.g_obj.data(), sizeof(int32_t) * m.g_obj.size());
     if (g_ground) memcpy(g_ground, m.g_ground.data(), sizeof(int32_t) * m.g_ground.size());
     if (g_sky) memcpy(g_sky, m.g_sky.data(), sizeof(int32_t) * m.g_sky.size());
     if (fgq || k_ground) {
-        std::vector<int32_t> f, k;
-        build_rows(m, H, &f, &k);
+        std::vector<int32_t> f, k, g;
+        build_rows(m, H, &f, &k, &g);
         if (fgq) memcpy(fgq, f.data(), sizeof(int32_t) * H);
         if (k_ground) memcpy(k_ground, k.data(), sizeof(int32_t) * H);
     }

@@ -39,6 +39,8 @@ struct ModelDev {
     const int32_t* g_obj;    // [emax + 1]
     const int32_t* g_ground; // [emax + 1]
     const int32_t* g_sky;    // [emax + 1]
+    int32_t var_sigma;       // 1: g_obj is [dmax + 1][emax + 1] (one residual row per f) and the
+                             //    ground residuals come per row (RowsDev::g_ground)
     int32_t int_grid;        // 1: reduced disparities are whole pixels (multiples of 16 in Q4)
     const int32_t* lut_cost; // int_grid only: [dmax + 1][dmax + 1], object cost of (f, d)
 };
@@ -47,6 +49,7 @@ struct ModelDev {
 struct RowsDev {
     const int32_t* fgq;      // [H] ground-model Q4 disparity at bottom-up row v
     const int32_t* k_ground; // [H]
+    const int32_t* g_ground; // variable sigma only: [H][emax + 1] residual table of each row, else null
 };
 
 struct FrameGeom {

@@ -42,8 +42,10 @@ __host__ __device__ inline int lc_radius(int esat_obj) { return (esat_obj + 15) 
 // kIntGrid: codes are whole pixels and object costs come from the staged
 // window [f - r, f + r] of LUT_cost row f (d outside it is clamped to its
 // edge, where the cost is already C_out, so every saturated pixel of a warp
-// reads the same word).
-template <bool kIntGrid>
+// reads the same word).  kVarSigma: sigma depends on the model disparity, so
+// each object row f reads its own residual row (global, L1-resident) and each
+// ground pixel its row's table; the constant-sigma tables are not staged.
+template <bool kIntGrid, bool kVarSigma>
 __device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const int row0, int32_t* sm)
 {
     const int16_t* __restrict__ q = a.q;
@@ -56,16 +58,18 @@ __device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const 
     int32_t* __restrict__ po = a.po;
     const int QP = (P + kChunk - 1) / kChunk * kChunk;
     int32_t* s_q = sm;                           // [QP]: s_q[j] = q[j - 1] (j = 1..H), 0 elsewhere
-    int32_t* s_go = s_q + QP;                    // [esat_obj + 1]   residual tables, clamped at saturation
-    int32_t* s_gg = s_go + m.esat_obj + 1;       // [esat_ground + 1]
-    int32_t* s_gs = s_gg + m.esat_ground + 1;    // [esat_sky + 1]
+    const int ngo = kVarSigma ? 0 : m.esat_obj + 1, ngg = kVarSigma ? 0 : m.esat_ground + 1;
+    const int E = m.emax + 1;
+    int32_t* s_go = s_q + QP;                    // [ngo]   residual tables, clamped at saturation
+    int32_t* s_gg = s_go + ngo;                  // [ngg]
+    int32_t* s_gs = s_gg + ngg;                  // [esat_sky + 1]
     int32_t* s_lc = s_gs + m.esat_sky + 1;       // whole-pixel grid: [kRowsPerCta][2 r + 1] windows
     const int R = F + 3;
     const int lr = lc_radius(m.esat_obj), lw = 2 * lr + 1;
 
     for (int j = threadIdx.x; j < QP; j += blockDim.x) s_q[j] = (j >= 1 && j <= H) ? q[(size_t)col * H + j - 1] : 0;
-    for (int e = threadIdx.x; e <= m.esat_obj; e += blockDim.x) s_go[e] = __ldg(m.g_obj + e);
-    for (int e = threadIdx.x; e <= m.esat_ground; e += blockDim.x) s_gg[e] = __ldg(m.g_ground + e);
+    for (int e = threadIdx.x; e < ngo; e += blockDim.x) s_go[e] = __ldg(m.g_obj + e);
+    for (int e = threadIdx.x; e < ngg; e += blockDim.x) s_gg[e] = __ldg(m.g_ground + e);
     for (int e = threadIdx.x; e <= m.esat_sky; e += blockDim.x) s_gs[e] = __ldg(m.g_sky + e);
     if (kIntGrid) {
         // the windows of the LUT_cost rows of this CTA's object disparities
@@ -116,14 +120,21 @@ __device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const 
                             // unsigned clamp keeps malformed caller codes in [0, dmax])
                             const int d = (int)(min((uint32_t)qv, (uint32_t)m.emax) >> 4);
                             x = s_lc[rr * lw + min(max(d - f, -lr), lr) + lr];
+                        } else if (kVarSigma) {
+                            x = min(m.c_out, kf + __ldg(m.g_obj + (size_t)f * E + min(abs(qv - f16), m.emax)));
                         } else {
                             x = min(m.c_out, kf + s_go[min(abs(qv - f16), m.esat_obj)]);
                         }
                     } else if (kind == kDisp) {
                         x = qv;
                     } else if (kind == kGround) {
-                        const int e = min(abs(qv - __ldg(rows.fgq + v)), m.esat_ground);
-                        x = min(m.c_out, __ldg(rows.k_ground + v) + s_gg[e]);
+                        if (kVarSigma) {
+                            const int e = min(abs(qv - __ldg(rows.fgq + v)), m.emax);
+                            x = min(m.c_out, __ldg(rows.k_ground + v) + __ldg(rows.g_ground + (size_t)v * E + e));
+                        } else {
+                            const int e = min(abs(qv - __ldg(rows.fgq + v)), m.esat_ground);
+                            x = min(m.c_out, __ldg(rows.k_ground + v) + s_gg[e]);
+                        }
                     } else {
                         x = min(m.c_out, m.k_sky + s_gs[min(abs(qv), m.esat_sky)]);
                     }
@@ -151,11 +162,11 @@ __device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const 
     }
 }
 
-template <bool kIntGrid>
+template <bool kIntGrid, bool kVarSigma>
 __global__ void __launch_bounds__(256) prefix_lut_kernel(LutArgs a)
 {
     extern __shared__ __align__(16) int32_t sm[];
-    lut_rows<kIntGrid>(a, blockIdx.x, blockIdx.y * kRowsPerCta, sm);
+    lut_rows<kIntGrid, kVarSigma>(a, blockIdx.x, blockIdx.y * kRowsPerCta, sm);
 }
 
 // Batch form: blockIdx.x indexes a list of (frame, column) items, blockIdx.y
@@ -171,10 +182,14 @@ __global__ void __launch_bounds__(256) prefix_lut_batch_kernel(const LutArgs* __
     for (int i = threadIdx.x; i < (int)(sizeof(LutArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
     __syncthreads();
     if ((int)blockIdx.y * kRowsPerCta >= s_args.F + 3) return;
-    if (s_args.m.int_grid)
-        lut_rows<true>(s_args, w.y, blockIdx.y * kRowsPerCta, sm);
-    else
-        lut_rows<false>(s_args, w.y, blockIdx.y * kRowsPerCta, sm);
+    const int row0 = blockIdx.y * kRowsPerCta;
+    if (s_args.m.var_sigma) {
+        if (s_args.m.int_grid) lut_rows<true, true>(s_args, w.y, row0, sm);
+        else lut_rows<false, true>(s_args, w.y, row0, sm);
+    } else {
+        if (s_args.m.int_grid) lut_rows<true, false>(s_args, w.y, row0, sm);
+        else lut_rows<false, false>(s_args, w.y, row0, sm);
+    }
 }
 
 }  // namespace
@@ -184,7 +199,8 @@ size_t lut_shared_bytes(int H, const ModelDev& m)
     const int P = lut_pitch(H);
     const int QP = (P + kChunk - 1) / kChunk * kChunk;
     const size_t lc = m.int_grid ? (size_t)kRowsPerCta * (2 * lc_radius(m.esat_obj) + 1) : 0;
-    return sizeof(int32_t) * ((size_t)QP + m.esat_obj + m.esat_ground + m.esat_sky + 3 + lc);
+    const size_t tabs = m.var_sigma ? (size_t)m.esat_sky + 1 : (size_t)m.esat_obj + m.esat_ground + m.esat_sky + 3;
+    return sizeof(int32_t) * ((size_t)QP + tabs + lc);
 }
 
 int lut_row_groups(int F) { return (F + 3 + kRowsPerCta - 1) / kRowsPerCta; }
@@ -197,10 +213,14 @@ cudaError_t launch_luts(const int16_t* q, const FrameGeom& g, const ModelDev& m,
     a.q = q; a.H = g.H; a.P = g.P; a.F = m.dmax + 1; a.m = m; a.rows = r;
     a.pd = pd; a.pg = pg; a.ps = ps; a.po = po;
     dim3 grid(g.ncols, lut_row_groups(a.F));
-    if (m.int_grid)
-        prefix_lut_kernel<true><<<grid, 256, lut_shared_bytes(g.H, m), st>>>(a);
-    else
-        prefix_lut_kernel<false><<<grid, 256, lut_shared_bytes(g.H, m), st>>>(a);
+    const size_t smem = lut_shared_bytes(g.H, m);
+    if (m.var_sigma) {
+        if (m.int_grid) prefix_lut_kernel<true, true><<<grid, 256, smem, st>>>(a);
+        else prefix_lut_kernel<false, true><<<grid, 256, smem, st>>>(a);
+    } else {
+        if (m.int_grid) prefix_lut_kernel<true, false><<<grid, 256, smem, st>>>(a);
+        else prefix_lut_kernel<false, false><<<grid, 256, smem, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -94,6 +94,16 @@ void default_params(stixels_params_t* p)
     p->reduce_mode = 0;
     p->max_stixels_per_col = 64;
     p->pixel_grid = 0;
+    p->sigma_gain = 0.0f;
+    p->sigma_mid = 32.0f;
+    p->sigma_width = 8.0f;
+}
+
+double sigma_at(const stixels_params_t& p, double base, double f)
+{
+    if (p.sigma_gain == 0.0f) return base;
+    const double s = 1.0 / (1.0 + exp(-(f - (double)p.sigma_mid) / (double)p.sigma_width));
+    return base * (1.0 + (double)p.sigma_gain * s);
 }
 
 int build_model(const stixels_params_t* p, HostModel* m)
@@ -126,6 +136,10 @@ int build_model(const stixels_params_t* p, HostModel* m)
     if (p->eps_gravity < 0.0f || p->eps_diving < 0.0f) return STIXELS_E_INVALID_ARG;
     if (p->reduce_mode != 0 && p->reduce_mode != 1) return STIXELS_E_INVALID_ARG;
     if (p->pixel_grid != 0 && p->pixel_grid != 1) return STIXELS_E_INVALID_ARG;
+    if (!(p->sigma_gain > -1.0f && p->sigma_gain <= 10.0f)) return STIXELS_E_INVALID_ARG;
+    if (p->sigma_gain != 0.0f && !(p->sigma_width > 0.0f && std::isfinite(p->sigma_width) &&
+                                   std::isfinite(p->sigma_mid)))
+        return STIXELS_E_INVALID_ARG;
     if (p->max_stixels_per_col < 1 || p->max_stixels_per_col > STIXELS_MAX_HEIGHT) return STIXELS_E_INVALID_ARG;
 
     m->p = *p;
@@ -136,33 +150,64 @@ int build_model(const stixels_params_t* p, HostModel* m)
     const double s_obj = (double)p->sigma_object, s_gnd = (double)p->sigma_ground, s_sky = (double)p->sigma_sky;
 
     m->c_out = to_fixed(log(d_range) - log(p_out));
-    m->k_obj.resize(m->dmax + 1);
-    for (int f = 0; f <= m->dmax; ++f) m->k_obj[f] = to_fixed(gauss_const((double)f, s_obj, p_out, d_range));
-    m->k_sky = to_fixed(gauss_const(0.0, s_sky, p_out, d_range));
-    m->g_obj.resize(m->emax + 1);
-    m->g_ground.resize(m->emax + 1);
-    m->g_sky.resize(m->emax + 1);
-    for (int e = 0; e <= m->emax; ++e) {
-        const double dpx = e / 16.0;
-        m->g_obj[e] = to_fixed(resid_capped(dpx, s_obj));
-        m->g_ground[e] = to_fixed(resid_capped(dpx, s_gnd));
-        m->g_sky[e] = to_fixed(resid_capped(dpx, s_sky));
+    m->var_sigma = p->sigma_gain != 0.0f;
+    const int F = m->dmax + 1, E = m->emax + 1;
+    // sigma^c(f) (Eq. 3): per object disparity, and the sky's at f = 0; the
+    // ground's depends on the row (build_rows)
+    std::vector<double> so(F);
+    m->k_obj.resize(F);
+    for (int f = 0; f < F; ++f) {
+        so[f] = sigma_at(*p, s_obj, (double)f);
+        m->k_obj[f] = to_fixed(gauss_const((double)f, so[f], p_out, d_range));
     }
-    // the residual table must reach the outlier branch before it ends, for every
-    // class and every K (K is smallest at the clamped ends of [0, d_range])
-    const int32_t kmin[3] = {to_fixed(gauss_const(0.0, s_obj, p_out, d_range)),
-                             to_fixed(gauss_const(0.0, s_gnd, p_out, d_range)),
-                             to_fixed(gauss_const(0.0, s_sky, p_out, d_range))};
-    const int32_t glast[3] = {m->g_obj[m->emax], m->g_ground[m->emax], m->g_sky[m->emax]};
-    for (int c = 0; c < 3; ++c)
-        if ((int64_t)kmin[c] + glast[c] < m->c_out) return STIXELS_E_INVALID_ARG;
-    // first residual from which every pixel of the class costs C_out (the tables
-    // are non-decreasing in e, and K >= kmin)
-    const std::vector<int32_t>* gtab[3] = {&m->g_obj, &m->g_ground, &m->g_sky};
-    for (int c = 0; c < 3; ++c) {
+    const double s_sky_f = sigma_at(*p, s_sky, 0.0);
+    m->k_sky = to_fixed(gauss_const(0.0, s_sky_f, p_out, d_range));
+    m->g_obj.resize(m->var_sigma ? (size_t)F * E : (size_t)E);
+    m->g_ground.resize(E);
+    m->g_sky.resize(E);
+    for (int e = 0; e < E; ++e) {
+        const double dpx = e / 16.0;
+        if (!m->var_sigma) m->g_obj[e] = to_fixed(resid_capped(dpx, s_obj));
+        m->g_ground[e] = to_fixed(resid_capped(dpx, s_gnd));
+        m->g_sky[e] = to_fixed(resid_capped(dpx, s_sky_f));
+    }
+    if (m->var_sigma)
+        for (int f = 0; f < F; ++f)
+            for (int e = 0; e < E; ++e) m->g_obj[(size_t)f * E + e] = to_fixed(resid_capped(e / 16.0, so[f]));
+    if (!m->var_sigma) {
+        // the residual table must reach the outlier branch before it ends, for
+        // every class and every K (K is smallest at the clamped ends of [0, d_range])
+        const int32_t kmin[3] = {to_fixed(gauss_const(0.0, s_obj, p_out, d_range)),
+                                 to_fixed(gauss_const(0.0, s_gnd, p_out, d_range)),
+                                 to_fixed(gauss_const(0.0, s_sky, p_out, d_range))};
+        const int32_t glast[3] = {m->g_obj[m->emax], m->g_ground[m->emax], m->g_sky[m->emax]};
+        for (int c = 0; c < 3; ++c)
+            if ((int64_t)kmin[c] + glast[c] < m->c_out) return STIXELS_E_INVALID_ARG;
+        // first residual from which every pixel of the class costs C_out (the
+        // tables are non-decreasing in e, and K >= kmin)
+        const std::vector<int32_t>* gtab[3] = {&m->g_obj, &m->g_ground, &m->g_sky};
+        for (int c = 0; c < 3; ++c) {
+            int e = 0;
+            while (e < m->emax && (int64_t)kmin[c] + (*gtab[c])[e] < m->c_out) ++e;
+            m->esat[c] = e;
+        }
+    } else {
+        // per disparity: the row of every f must reach the outlier branch; esat
+        // of the objects is the largest first saturated residual over f
+        int es = 0;
+        for (int f = 0; f < F; ++f) {
+            const int32_t* g = m->g_obj.data() + (size_t)f * E;
+            if ((int64_t)m->k_obj[f] + g[m->emax] < m->c_out) return STIXELS_E_INVALID_ARG;
+            int e = 0;
+            while (e < m->emax && (int64_t)m->k_obj[f] + g[e] < m->c_out) ++e;
+            es = std::max(es, e);
+        }
+        m->esat[0] = es;
+        m->esat[1] = m->emax;                          // ground rows are checked per height
+        if ((int64_t)m->k_sky + m->g_sky[m->emax] < m->c_out) return STIXELS_E_INVALID_ARG;
         int e = 0;
-        while (e < m->emax && (int64_t)kmin[c] + (*gtab[c])[e] < m->c_out) ++e;
-        m->esat[c] = e;
+        while (e < m->emax && (int64_t)m->k_sky + m->g_sky[e] < m->c_out) ++e;
+        m->esat[2] = e;
     }
 
     m->alpha = (double)p->baseline_m * cos((double)p->pitch_rad) / (double)p->camera_height_m;
@@ -189,30 +234,43 @@ int build_model(const stixels_params_t* p, HostModel* m)
     // Q4 residual 16 |d - f| (paper Sec. 3.4's LUT_cost, computed off-line)
     m->lut_cost.clear();
     if (p->pixel_grid) {
-        const int F = m->dmax + 1;
         m->lut_cost.resize((size_t)F * F);
         for (int f = 0; f < F; ++f)
             for (int d = 0; d < F; ++d) {
-                const int e = std::min(16 * std::abs(d - f), m->esat[0]);
-                m->lut_cost[(size_t)f * F + d] = std::min(m->c_out, m->k_obj[f] + m->g_obj[e]);
+                const int e = std::min(16 * std::abs(d - f), m->var_sigma ? m->emax : m->esat[0]);
+                const int32_t g = m->var_sigma ? m->g_obj[(size_t)f * (m->emax + 1) + e] : m->g_obj[e];
+                m->lut_cost[(size_t)f * F + d] = std::min(m->c_out, m->k_obj[f] + g);
             }
     }
     return STIXELS_OK;
 }
 
-void build_rows(const HostModel& m, int H, std::vector<int32_t>* fgq, std::vector<int32_t>* k_ground)
+bool build_rows(const HostModel& m, int H, std::vector<int32_t>* fgq, std::vector<int32_t>* k_ground,
+                std::vector<int32_t>* g_rows)
 {
     fgq->resize(H);
     k_ground->resize(H);
+    g_rows->clear();
+    const int E = m.emax + 1;
+    if (m.var_sigma) g_rows->resize((size_t)H * E);
     const double d_range = (double)m.dmax;
     const double p_out = (double)m.p.p_out;
     const double s_gnd = (double)m.p.sigma_ground;
     for (int v = 0; v < H; ++v) {
         const int r = H - 1 - v;                       // image row of bottom-up row v
         const long long code = llround(16.0 * m.alpha * (double)(r - m.p.horizon_row));
+        const double fg = (double)code / 16.0;
+        const double sg = sigma_at(m.p, s_gnd, fg);
         (*fgq)[v] = (int32_t)code;
-        (*k_ground)[v] = to_fixed(gauss_const((double)code / 16.0, s_gnd, p_out, d_range));
+        (*k_ground)[v] = to_fixed(gauss_const(fg, sg, p_out, d_range));
+        if (m.var_sigma) {
+            int32_t* g = g_rows->data() + (size_t)v * E;
+            for (int e = 0; e < E; ++e) g[e] = to_fixed(resid_capped(e / 16.0, sg));
+            // residuals are clamped to the table's end: it must already be the outlier branch
+            if ((int64_t)(*k_ground)[v] + g[m.emax] < m.c_out) return false;
+        }
     }
+    return true;
 }
 
 // A feasible cell of the cost table is reached by some segmentation of at most

@@ -18,7 +18,9 @@ struct HostModel {
     double alpha = 0.0;                 // ground slope in px of disparity per image row
     int32_t c_out = 0, k_sky = 0;
     std::vector<int32_t> k_obj;         // [dmax + 1]
-    std::vector<int32_t> g_obj, g_ground, g_sky;   // [emax + 1]
+    std::vector<int32_t> g_obj;         // [emax + 1], or [dmax + 1][emax + 1] with variable sigma
+    std::vector<int32_t> g_ground, g_sky;          // [emax + 1] (g_ground: constant sigma only)
+    bool var_sigma = false;             // sigma_gain != 0: per-disparity / per-row residual tables
     int32_t first[3] = {0, 0, 0};
     int32_t trans[3][3] = {{0}};
     int32_t pen_grav = 0, pen_div = 0, pen_ord = 0;
@@ -34,8 +36,14 @@ struct HostModel {
 int build_model(const stixels_params_t* p, HostModel* m);
 
 // Per-height row tables: ground-line Q4 disparity and ground K for v = 0..H-1
-// (v = 0 is the bottom image row).
-void build_rows(const HostModel& m, int H, std::vector<int32_t>* fgq, std::vector<int32_t>* k_ground);
+// (v = 0 is the bottom image row); with variable sigma also the ground
+// residual table of every row, g_rows[v * (emax + 1) + e] (else left empty).
+// Returns false if a row's table would not reach the outlier branch.
+bool build_rows(const HostModel& m, int H, std::vector<int32_t>* fgq, std::vector<int32_t>* k_ground,
+                std::vector<int32_t>* g_rows);
+
+// sigma^c at model disparity f for a class whose base sigma is `base`.
+double sigma_at(const stixels_params_t& p, double base, double f);
 
 // True if every cost of an H-row column fits the int32 budget (see internal.h).
 bool budget_ok(const HostModel& m, int H, const std::vector<int32_t>& k_ground);

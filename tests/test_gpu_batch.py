@@ -24,6 +24,7 @@ def _mixed_frames():
         scenes.Camera(333, 97, stixel_width=4, dmax=48, horizon_row=30, baseline_m=0.4, camera_height_m=1.0),
         scenes.CONFIG1,
         scenes.Camera(640, 240, stixel_width=5, dmax=64, horizon_row=80),
+        scenes.Camera(640, 240, stixel_width=7, dmax=64, horizon_row=80),
     ]
     out = []
     for i, cam in enumerate(cams):
@@ -32,6 +33,8 @@ def _mixed_frames():
             kw = dict(prior_trans=((1.5, 1.0, 4.0), (1.5, 6.0, 9.0), (0.5, 0.5, 7.0)))
         if i == 6:   # the whole-pixel grid (LUT_cost variant), mean reduction
             kw = dict(pixel_grid=1, reduce_mode=1)
+        if i == 7:   # disparity-dependent sigma
+            kw = dict(sigma_gain=1.2, sigma_mid=30.0, sigma_width=8.0)
         h = S.Stixels(S.default_params(cam, **kw))
         sc = scenes.make_scene(cam, 4400 + i, n_obstacles=(3, 10))
         out.append((h, cam, sc.disparity))

@@ -81,9 +81,11 @@ def test_reduce_parity(s, mode, grid):
 
 @pytest.mark.parametrize("cam", [scenes.CONFIG1, scenes.Camera(160, 37, stixel_width=4, dmax=40, horizon_row=11)])
 @pytest.mark.parametrize("grid", [0, 1])
-def test_lut_parity(cam, grid):
+@pytest.mark.parametrize("gain", [0.0, 1.3, -0.4])
+def test_lut_parity(cam, grid, gain):
     sc = scenes.make_scene(cam, 77)
-    lp, op = both_params(cam, sigma_ground=0.8, sigma_sky=1.4, p_out=0.1, pixel_grid=grid)
+    lp, op = both_params(cam, sigma_ground=0.8, sigma_sky=1.4, p_out=0.1, pixel_grid=grid, sigma_gain=gain,
+                         sigma_mid=20.0, sigma_width=5.0)
     h = S.Stixels(lp)
     H, W = sc.disparity.shape
     q = h.reduce(cuda(sc.disparity))
@@ -157,6 +159,8 @@ def test_pipeline_ragged_heights(H):
     dict(pitch_rad=0.035, horizon_row=52, baseline_m=0.5, camera_height_m=1.5),
     dict(pixel_grid=1),
     dict(pixel_grid=1, reduce_mode=1, sigma_object=1.5),
+    dict(sigma_gain=1.5, sigma_mid=25.0, sigma_width=6.0),
+    dict(sigma_gain=-0.5, sigma_mid=10.0, sigma_width=3.0, pixel_grid=1),
 ])
 def test_pipeline_model_variants(variant):
     cam = scenes.CONFIG1

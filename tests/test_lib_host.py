@@ -111,6 +111,9 @@ def test_pixel_costs_from_tables_equal_oracle(i):
     dict(prior_first=(1.0, -0.5, 1.0)), dict(cost_diving=float("inf")), dict(cost_new_stixel=float("inf")),
     dict(eps_gravity=-1.0), dict(eps_order=200.0), dict(reduce_mode=2), dict(max_stixels_per_col=0),
     dict(sigma_sky=900.0),            # residual table would not reach the outlier branch
+    dict(pixel_grid=2), dict(sigma_gain=-1.0), dict(sigma_gain=11.0), dict(sigma_gain=float("nan")),
+    dict(sigma_gain=0.5, sigma_width=0.0), dict(sigma_gain=0.5, sigma_mid=float("inf")),
+    dict(sigma_gain=0.5),             # valid, but its per-disparity tables are not exported
 ])
 def test_invalid_params_rejected(bad):
     p = S.default_params(**bad)

@@ -329,3 +329,18 @@ def test_pixel_grid_frame_invariants():
     fr = oracle.frame(p, sc.disparity, cap=cam.height)
     assert np.all(fr.q % 16 == 0)
     _check_frame_invariants(p, fr, cam.height)
+
+
+@pytest.mark.parametrize("gain", [1.2, -0.5])
+def test_variable_sigma_dp_equals_exhaustive_minimum(gain):
+    """With disparity-dependent sigma the DP still returns the minimum over all
+    segmentations of short columns (ordering off, where the paper's DP is exact)."""
+    rng = np.random.default_rng(70 + int(10 * gain))
+    p = oracle.make_params(**SHORT, cost_order=0.0, quantize=1, sigma_gain=gain, sigma_mid=15.0,
+                           sigma_width=5.0)
+    for trial in range(60):
+        H = int(rng.integers(1, 11))
+        q = _random_column(rng, H, SHORT["dmax"], "piecewise" if trial % 2 else "uniform")
+        dp = oracle.column(p, q)
+        bf_cost, count, bf_st = oracle.brute_force(p, q)
+        assert dp.cost == bf_cost, (H, q.tolist())

@@ -10,6 +10,7 @@ import pytest
 from scipy import integrate
 
 import oracle
+import scenes
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sensor_closed_forms.txt")
 
@@ -106,3 +107,44 @@ def test_cost_grid_resolution():
             b = oracle.pixel_cost(pq, 4, cls, 0, q, f)
             assert abs(a - b) <= 2.0 ** -12 + 1e-15
             assert (b * 4096.0).is_integer()
+
+
+# ---- disparity-dependent noise (Eq. 3's sigma^c(f, v), a logistic in the model disparity)
+
+@pytest.mark.parametrize("cls", [oracle.OBJECT, oracle.GROUND])
+@pytest.mark.parametrize("gain", [0.8, -0.4])
+def test_variable_sigma_branch_still_carries_inlier_mass(cls, gain):
+    """With sigma depending on f, A_norm must be evaluated at that same sigma:
+    the Gaussian branch still integrates to 1 - p_out at every f."""
+    p = oracle.make_params(dmax=64, p_out=0.05, quantize=0, sigma_gain=gain, sigma_mid=20.0, sigma_width=6.0)
+    for f in [0.0, 7.0, 20.0, 41.5, 64.0]:
+        val, _ = integrate.quad(lambda d: math.exp(-oracle.gaussian_branch(p, cls, f, d)), 0.0, 64.0,
+                                points=[f], limit=400, epsabs=1e-13, epsrel=1e-12)
+        assert abs(val - (1.0 - float(np.float32(0.05)))) < 1e-9, (f, val)
+
+
+def test_variable_sigma_closed_form_at_the_midpoint_and_tails():
+    """At f = mid the logistic is 1/2: sigma = base (1 + gain / 2).  The branch's
+    curvature in d is 1 / sigma^2, read from three values; far below / above mid
+    the sigma tends to base and base (1 + gain)."""
+    base, gain, mid, width = 1.2, 1.5, 24.0, 4.0
+    p = oracle.make_params(dmax=64, quantize=0, sigma_object=base, sigma_gain=gain, sigma_mid=mid,
+                           sigma_width=width)
+
+    def curvature(f):
+        h = 0.25
+        g = [oracle.gaussian_branch(p, oracle.OBJECT, f, f + x) for x in (-h, 0.0, h)]
+        return (g[0] - 2 * g[1] + g[2]) / (h * h)
+
+    b32 = float(np.float32(base))                      # parameters are single precision
+    assert abs(curvature(mid) - 1.0 / (b32 * (1 + gain / 2)) ** 2) < 1e-9
+    assert abs(curvature(0.0) - 1.0 / (b32 * (1 + gain / (1 + math.exp(mid / width)))) ** 2) < 1e-9
+    assert abs(curvature(64.0) - 1.0 / (b32 * (1 + gain / (1 + math.exp(-(64 - mid) / width)))) ** 2) < 1e-9
+
+
+def test_zero_gain_is_the_constant_sigma_model():
+    cam = scenes.CONFIG1
+    sc = scenes.make_scene(cam, 4400)
+    a = oracle.frame(oracle.make_params(cam), sc.disparity, cap=64)
+    b = oracle.frame(oracle.make_params(cam, sigma_gain=0.0, sigma_mid=3.0, sigma_width=1.0), sc.disparity, cap=64)
+    assert np.array_equal(a.cost, b.cost) and np.array_equal(a.counts, b.counts)

@@ -185,24 +185,44 @@ size_t dp_smem_bytes(int H, int ring)
            sizeof(SyncState);
 }
 
-// Gathers the chain data of the block starting at row B into cb: the cells
-// (start B + i, end B + l) and (start B + i, end B + 32 + l) of all 32 starts
-// i, with the cells split over nthreads threads (this one is tid).  All loads
-// of a pass are issued before any store.  Kept out of line: it runs from two
-// places and its code is shared.
+constexpr int kTriCells = 528;          // cells (i, l) with i <= l of a 32-row block
+constexpr int kChainCells = kTriCells + 1024;
+
+// Gathers the chain data of the block starting at row B into cb: the 528
+// triangle cells (start B + i, end B + l, i <= l) and the 1024 cells (start
+// B + i, end B + 32 + l), with the cells split over nthreads threads (this one
+// is tid).  Slots of the triangle with i > l are never written here (they are
+// zeroed once per column).  All loads of a pass are issued before any store.
+// Kept out of line: it runs from two places and its code is shared.
 __device__ __noinline__ void gather_chain(ChainBuf* cb, int B, int H, int P, const int32_t* __restrict__ po_col,
                                           const int32_t* s_pd8, const int32_t* s_thr, const uint2* s_div,
                                           const ModelDev& m, int tid, int nthreads)
 {
-    for (int base = tid; base < 2048; base += 4 * nthreads) {
+    for (int base = tid; base < kChainCells; base += 4 * nthreads) {
         int32_t lo[4], hi[4], fv[4];
+        int slot[4];
         bool ok[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            const int idx = base + r * nthreads;
-            const int part = idx >> 10, e = idx & 1023, i = e >> 5, l = e & 31;
-            const int b = B + i, k = B + 32 * part + l;
-            ok[r] = idx < 2048 && k < H && (part == 1 || i <= l);
+            const int u = base + r * nthreads;
+            int i, l, k;
+            if (u < kTriCells) {
+                // u = l (l + 1) / 2 + i: l from the square root, then corrected exactly
+                l = (int)((sqrtf((float)(8 * u + 1)) - 1.0f) * 0.5f);
+                if ((l + 1) * (l + 2) / 2 <= u) ++l;
+                if (l * (l + 1) / 2 > u) --l;
+                i = u - l * (l + 1) / 2;
+                k = B + l;
+                slot[r] = i * 32 + l;
+            } else {
+                const int w = u - kTriCells;
+                i = w >> 5;
+                l = w & 31;
+                k = B + 32 + l;
+                slot[r] = 1024 + w;
+            }
+            const int b = B + i;
+            ok[r] = u < kChainCells && k < H;
             lo[r] = hi[r] = fv[r] = 0;
             if (ok[r]) {
                 const int f = mean_f(s_pd8[k + 1] - s_pd8[b], k - b + 1, s_div, m.dmax);
@@ -214,13 +234,13 @@ __device__ __noinline__ void gather_chain(ChainBuf* cb, int B, int H, int P, con
         }
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            const int idx = base + r * nthreads;
-            if (idx < 2048) {
-                const int part = idx >> 10, e = idx & 1023;
+            const int u = base + r * nthreads;
+            if (u < kChainCells) {
+                const int e = slot[r] & 1023;
                 const int b = B + (e >> 5);
                 const int32_t d = hi[r] - lo[r];
                 const int2 v = ok[r] ? make_int2(d, d + ground_pen(s_thr[b], fv[r], m)) : make_int2(0, 0);
-                if (part == 0) { cb->tri[e] = v; cb->ftri[e] = (uint8_t)fv[r]; }
+                if (slot[r] < 1024) { cb->tri[e] = v; cb->ftri[e] = (uint8_t)fv[r]; }
                 else { cb->nxt[e] = v; cb->fnxt[e] = (uint8_t)fv[r]; }
             }
         }
@@ -346,6 +366,14 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
         if (kv) { runv[k] = run; runbfv[k] = runbf; }
     };
 
+    // the triangle slots with start above end are never gathered: zero them once
+    for (int x = threadIdx.x; x < ring * 1024; x += kThreads) {
+        const int e = x & 1023;
+        if ((e >> 5) > (e & 31)) {
+            s_cb[x >> 10].tri[e] = make_int2(0, 0);
+            s_cb[x >> 10].ftri[e] = 0;
+        }
+    }
     // the chain data of block 0 (input only); the bulk warps gather the rest
     gather_chain(s_cb, 0, H, P, po_col, s_pd8, s_thr, s_div, m, threadIdx.x, kThreads);
     __syncthreads();

@@ -479,6 +479,31 @@ def bench_ours(args, world, rank, local):
                 "luts_gbs": lut_bytes_v / (statistics.mean(vl) / 1000.0) / 1e9,
                 "device_error_word": hv.get_error(stream)}
             hv.close()
+        # the per-frame ground estimate (v-disparity) runs inside stixels_compute
+        hg = S.Stixels(S.default_params(cam, ground_estimate=1))
+        outg = hg.alloc_output(H, W, dev)
+        for i in range(5):
+            flush.fill_(float(i))
+            hg.compute(disp, outg, stream)
+        nk = min(K, 100)
+        evg = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nk)]
+        for i in range(nk):
+            flush.fill_(float(i))
+            evg[i][0].record(stream)
+            hg.compute(disp, outg, stream)
+            evg[i][1].record(stream)
+        torch.cuda.synchronize()
+        tg = [a.elapsed_time(b) for a, b in evg]
+        q0 = hg.reduce(disp)
+        line = hg.estimate_ground(q0, H, ncols)
+        variants["ground_estimate"] = {
+            "workload": "same 1024x440 frame; ground line estimated per frame from its v-disparity "
+                        "(stixels_compute: reduce, estimate, LUTs, DP)",
+            "frames_per_s": nk / (sum(tg) / 1000.0), "ms_per_frame": statistics.mean(tg),
+            "line": {"slope_px_per_row": line[0] / 256.0, "horizon_row": line[1], "votes": line[2],
+                     "camera": {"slope_px_per_row": cam.alpha, "horizon_row": cam.horizon_row}},
+            "device_error_word": hg.get_error(stream)}
+        hg.close()
 
     batched = served = None
     if rank == 0 and not args.no_batched:

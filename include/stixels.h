@@ -114,6 +114,10 @@ typedef struct stixels_params {
     float sigma_gain;
     float sigma_mid;
     float sigma_width;
+    int32_t ground_estimate;   /* 0 = ground line from the camera parameters (default); 1 = estimated
+                                  for every frame from its v-disparity (stixels_estimate_ground),
+                                  per-frame path only (stixels_compute / _compute_host); needs
+                                  sigma_gain = 0 and ncols * H <= 7,000,000 */
 } stixels_params_t;
 
 /* One output stixel: 12 bytes. */
@@ -214,6 +218,20 @@ int stixels_lut_pitch(int H);
  * int16 Q4 codes, column c at d_q[c * H + v], v = H-1-r (v = 0 is the bottom
  * image row); with pixel_grid = 1 every code is a multiple of 16. */
 int stixels_reduce(stixels_t h, const float* d_disparity, int H, int W, void* stream, int16_t* d_q);
+
+/* The frame's ground line from its v-disparity (the paper assumes the ground
+ * slope and horizon known per image, Sec. 3; this is the step before the path),
+ * for a handle created with ground_estimate = 1, from the Q4 codes d_q of
+ * stixels_reduce.  On the 1/16-px grid: per image row r a histogram of the codes
+ * in [16, 16 dmax], smoothed with weights 17 - |t| over |t| <= 16; candidate lines
+ * have the code (k (r - h) + 8) >> 4 at rows r > h (slope k / 256 px per row,
+ * k = 1..256, horizon at image row h = 0..H-1); a line's votes are the smoothed
+ * counts at its codes on the rows where they lie in [16, 16 dmax]; the most
+ * votes win, ties to the smaller k, then the smaller h.  d_line (device, 3
+ * int32) receives {k, h, votes}; votes = 0 means no ground was seen, and
+ * stixels_compute then keeps the camera's line.  INVALID_ARG if the handle
+ * was created without ground_estimate, or if ncols * H > 7,000,000. */
+int stixels_estimate_ground(stixels_t h, const int16_t* d_q, int H, int ncols, void* stream, int32_t* d_line);
 
 /* Stage 2 (Sec. 3.4, Sec. 5.2): per-column prefix LUTs from Q4 codes d_q
  * (layout of stixels_reduce).  With P = stixels_lut_pitch(H) and F = dmax + 1:

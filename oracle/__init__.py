@@ -46,6 +46,7 @@ class Params(C.Structure):
         ("cost_order", C.c_float), ("eps_order", C.c_float),
         ("reduce_mode", C.c_int32), ("quantize", C.c_int32), ("pixel_grid", C.c_int32),
         ("sigma_gain", C.c_float), ("sigma_mid", C.c_float), ("sigma_width", C.c_float),
+        ("ground_estimate", C.c_int32),
     ]
 
 
@@ -74,7 +75,7 @@ DEFAULTS: Dict[str, object] = dict(
     cost_gravity=2.0, eps_gravity=1.0, cost_diving=10.0, eps_diving=1.0,
     cost_order=2.0, eps_order=0.0,
     reduce_mode=0, quantize=1, pixel_grid=0,
-    sigma_gain=0.0, sigma_mid=32.0, sigma_width=8.0,
+    sigma_gain=0.0, sigma_mid=32.0, sigma_width=8.0, ground_estimate=0,
 )
 
 
@@ -105,6 +106,7 @@ def lib():
         L = C.CDLL(_build())
         P = C.POINTER
         L.or_reduce.argtypes = [P(C.c_float), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P(C.c_int16)]
+        L.or_ground_estimate.argtypes = [P(C.c_int16), C.c_int, C.c_int, C.c_int, P(C.c_int32)]
         L.or_pixel_cost.argtypes = [P(Params), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P(C.c_double)]
         L.or_gaussian_branch.argtypes = [P(Params), C.c_int, C.c_double, C.c_double, P(C.c_double)]
         L.or_model_constants.argtypes = [P(Params), C.c_int, P(C.c_double), P(C.c_double), P(C.c_double),
@@ -165,6 +167,16 @@ def reduce(disp: np.ndarray, s: int, dmax: int, mode: int = 0, pixel_grid: int =
     q = np.zeros((W // s, H), dtype=np.int16)
     _check(lib().or_reduce(_ptr(disp, C.c_float), H, W, s, dmax, mode, pixel_grid, _ptr(q, C.c_int16)), "reduce")
     return q
+
+
+def ground_estimate(q: np.ndarray, dmax: int):
+    """v-disparity ground line of reduced codes q (ncols, H), bottom-up: (k, horizon row, votes),
+    slope k / 256 px of disparity per image row."""
+    q = np.ascontiguousarray(q, dtype=np.int16)
+    out = np.zeros(3, np.int32)
+    _check(lib().or_ground_estimate(_ptr(q, C.c_int16), q.shape[0], q.shape[1], dmax, _ptr(out, C.c_int32)),
+           "ground_estimate")
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def pixel_cost(params: Params, H: int, cls: int, v: int, q: int, f: int = 0) -> float:

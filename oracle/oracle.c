@@ -101,6 +101,9 @@ typedef struct {
      * f the model disparity (object: f; ground: the ground line at row v; sky: 0);
      * sigma_gain = 0 is the constant-sigma model */
     float sigma_gain, sigma_mid, sigma_width;
+    /* 1 = the ground line comes from the frame itself (or_ground_estimate on
+     * its reduced codes) instead of the camera parameters */
+    int32_t ground_estimate;
 } or_params_t;
 
 typedef struct {
@@ -223,7 +226,13 @@ static double sigma_at(const or_params_t* p, double base, double f)
     return base * (1.0 + (double)p->sigma_gain * s);
 }
 
-static int model_build(const or_params_t* p, int H, or_model_t* m)
+/* The model for height H; line_k > 0 replaces the camera's ground line by
+ * f(r) = (line_k / 256) (r - line_h) (an estimate from the frame). */
+static int model_build_line(const or_params_t* p, int H, int line_k, int line_h, or_model_t* m);
+
+static int model_build(const or_params_t* p, int H, or_model_t* m) { return model_build_line(p, H, 0, 0, m); }
+
+static int model_build_line(const or_params_t* p, int H, int line_k, int line_h, or_model_t* m)
 {
     memset(m, 0, sizeof(*m));
     int rc = check_params(p);
@@ -266,12 +275,13 @@ static int model_build(const or_params_t* p, int H, or_model_t* m)
         int r = H - 1 - v;
         double fg;
         if (m->quantize) {
-            long long fgq = llround(16.0 * alpha * (double)(r - p->horizon_row));
+            long long fgq = line_k > 0 ? llround((double)line_k * (double)(r - line_h) / 16.0)
+                                       : llround(16.0 * alpha * (double)(r - p->horizon_row));
             fg = (double)fgq / 16.0;
             m->g_hi[v] = (double)(fgq + eg);
             m->g_lo[v] = (double)(fgq - ed);
         } else {
-            fg = alpha * (double)(r - p->horizon_row);
+            fg = line_k > 0 ? (double)line_k * (double)(r - line_h) / 256.0 : alpha * (double)(r - p->horizon_row);
             m->g_hi[v] = 16.0 * (fg + (double)p->eps_gravity);
             m->g_lo[v] = 16.0 * (fg - (double)p->eps_diving);
         }
@@ -344,6 +354,64 @@ int or_reduce(const float* disp, int H, int W, int s, int dmax, int mode, int pi
             q[(size_t)c * H + (size_t)(H - 1 - r)] = (int16_t)out;
         }
     }
+    return OR_OK;
+}
+
+/* ------------------------------------------------- ground line from the frame (v-disparity) */
+
+/* The paper takes the ground slope and the horizon as known for every image
+ * (Sec. 3); this estimates them from the frame, the step before the path, on
+ * the 1/16-px grid the DP uses:
+ *   hist[r][e] = number of columns whose reduced code at image row r is e,
+ *                for codes e in [16, 16 dmax] (below 1 px: sky / invalid, left out);
+ *   S[r][e]    = sum over |t| <= 16 of (17 - |t|) hist[r][e + t]  (a triangular
+ *                kernel of half-width 1 px, so noisy ground still votes);
+ *   line (k, h): code (k (r - h) + 8) / 16 at image row r > h (the disparity
+ *                (k / 256) (r - h) px rounded half up on the 1/16 grid), for
+ *                k = 1..256 and every image row h;
+ *   votes(k, h) = sum of S[r][code] over the rows r > h whose code lies in
+ *                [16, 16 dmax];
+ * and returns the line with the most votes, ties to the smaller k, then the
+ * smaller h: out = {k, h, votes}.  Lines that are exact on a noise-free ground
+ * win strictly: an exact code scores 17 per pixel, a code off by 1/16 px 16. */
+int or_ground_estimate(const int16_t* q, int ncols, int H, int dmax, int32_t* out)
+{
+    if (ncols < 0 || H < 1 || dmax < 1 || !out) return OR_E_ARG;
+    const int E = 16 * dmax + 1;
+    int64_t* hist = (int64_t*)calloc((size_t)H * E, sizeof(int64_t));
+    int64_t* sm = (int64_t*)calloc((size_t)H * E, sizeof(int64_t));
+    if (!hist || !sm) { free(hist); free(sm); return OR_E_MEM; }
+    for (int c = 0; c < ncols; ++c)
+        for (int v = 0; v < H; ++v) {
+            const int code = q[(size_t)c * H + v];
+            if (code >= 16 && code < E) hist[(size_t)(H - 1 - v) * E + code] += 1;
+        }
+    for (int r = 0; r < H; ++r)
+        for (int e = 16; e < E; ++e) {
+            int64_t acc = 0;
+            for (int t = -16; t <= 16; ++t) {
+                const int x = e + t;
+                if (x >= 16 && x < E) acc += (17 - (t < 0 ? -t : t)) * hist[(size_t)r * E + x];
+            }
+            sm[(size_t)r * E + e] = acc;
+        }
+    int64_t best = -1;
+    int bk = 0, bh = 0;
+    for (int k = 1; k <= 256; ++k)
+        for (int h = 0; h < H; ++h) {
+            int64_t votes = 0;
+            for (int r = h + 1; r < H; ++r) {
+                const int code = (k * (r - h) + 8) / 16;
+                if (code >= E) break;
+                if (code >= 16) votes += sm[(size_t)r * E + code];
+            }
+            if (votes > best) { best = votes; bk = k; bh = h; }
+        }
+    free(hist);
+    free(sm);
+    out[0] = bk;
+    out[1] = bh;
+    out[2] = (int32_t)best;
     return OR_OK;
 }
 
@@ -564,8 +632,14 @@ int or_frame(const or_params_t* p, const float* disp, int H, int W, int cap, or_
     if (!q) return OR_E_MEM;
     int rc = or_reduce(disp, H, W, s, p->dmax, p->reduce_mode, p->pixel_grid, q);
     if (rc) { if (!q_out) free(q); return rc; }
+    int32_t line[3] = {0, 0, 0};
+    if (p->ground_estimate) {
+        rc = or_ground_estimate(q, C, H, p->dmax, line);
+        if (rc) { if (!q_out) free(q); return rc; }
+        if (line[2] == 0) line[0] = 0;          /* no ground seen: keep the camera's line */
+    }
     or_model_t m;
-    rc = model_build(p, H, &m);
+    rc = model_build_line(p, H, line[0], line[1], &m);
     if (rc) { if (!q_out) free(q); return rc; }
     int worst = OR_OK;
 #ifdef _OPENMP

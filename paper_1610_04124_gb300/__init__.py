@@ -46,6 +46,7 @@ class Params(C.Structure):
         ("cost_order", C.c_float), ("eps_order", C.c_float),
         ("reduce_mode", C.c_int32), ("max_stixels_per_col", C.c_int32), ("pixel_grid", C.c_int32),
         ("sigma_gain", C.c_float), ("sigma_mid", C.c_float), ("sigma_width", C.c_float),
+        ("ground_estimate", C.c_int32),
     ]
 
     def to_dict(self) -> Dict[str, object]:
@@ -112,6 +113,7 @@ def lib():
         L.stixels_lut_pitch.argtypes = [I]
         L.stixels_reduce.argtypes = [V, V, I, I, V, V]
         L.stixels_build_luts.argtypes = [V, V, I, I, V, V, V, V, V]
+        L.stixels_estimate_ground.argtypes = [V, V, I, I, V, V]
         L.stixels_solve.argtypes = [V, V, V, V, V, I, I, V, P(Output)]
         L.stixels_model_tables.argtypes = [P(Params), I, V, V, V, V, V, V, V]
         L.stixels_compute_noalloc.argtypes = [V, V, I, I, V, P(Output)]
@@ -302,6 +304,15 @@ class Stixels:
             q = torch.zeros((max(ncols, 1), max(H, 1)), dtype=torch.int16, device=disparity.device)
         _check(lib().stixels_reduce(self._h, _ptr(disparity), H, W, _stream_ptr(stream), _ptr(q)), "stixels_reduce")
         return q
+
+    def estimate_ground(self, q, H: int, ncols: int, stream=None):
+        """stixels_estimate_ground on reduced codes q: (k, horizon row, votes); slope k / 256 px per row."""
+        import torch
+        line = torch.zeros(3, dtype=torch.int32, device=q.device)
+        _check(lib().stixels_estimate_ground(self._h, _ptr(q), H, ncols, _stream_ptr(stream), _ptr(line)),
+               "stixels_estimate_ground")
+        k, h, votes = (int(x) for x in line.cpu())
+        return k, h, votes
 
     def build_luts(self, q, H: int, ncols: int, stream=None):
         import torch

@@ -118,6 +118,10 @@ int check_frame(stixels_t h, int H, int W)
     return STIXELS_OK;
 }
 
+// The ground estimate's int32 votes stay below 289 ncols H (the smoothing
+// kernel's weight times every column of every row).
+bool ground_size_ok(const FrameGeom& g) { return (int64_t)g.ncols * g.H <= 7000000; }
+
 FrameGeom geom(stixels_t h, int H, int W)
 {
     FrameGeom g;
@@ -171,6 +175,7 @@ int handle_view(stixels_t h, int H, HandleView* v)
     v->err = h->d_err;
     v->stixel_width = h->hm.p.stixel_width;
     v->reduce_mode = reduce_code(h->hm.p);
+    v->ground_estimate = h->hm.p.ground_estimate;
     v->capacity = h->hm.p.max_stixels_per_col;
     return STIXELS_OK;
 }
@@ -207,7 +212,8 @@ int stixels_create(const stixels_params_t* params, stixels_t* out_handle)
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) { delete h; return cuda_status(e); }
     const HostModel& m = h->hm;
-    const size_t n_tab = m.k_obj.size() + m.g_obj.size() + m.g_ground.size() + m.g_sky.size() + m.lut_cost.size();
+    const size_t n_tab = m.k_obj.size() + m.g_obj.size() + m.g_ground.size() + m.g_sky.size() + m.lut_cost.size() +
+                         m.kg_tab.size();
     e = cudaMalloc(&h->d_tables, sizeof(int32_t) * n_tab);
     if (e == cudaSuccess) {
         std::vector<int32_t> buf;
@@ -217,6 +223,7 @@ int stixels_create(const stixels_params_t* params, stixels_t* out_handle)
         buf.insert(buf.end(), m.g_ground.begin(), m.g_ground.end());
         buf.insert(buf.end(), m.g_sky.begin(), m.g_sky.end());
         buf.insert(buf.end(), m.lut_cost.begin(), m.lut_cost.end());
+        buf.insert(buf.end(), m.kg_tab.begin(), m.kg_tab.end());
         e = cudaMemcpy(h->d_tables, buf.data(), sizeof(int32_t) * n_tab, cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(uint32_t));
@@ -251,6 +258,7 @@ int stixels_create(const stixels_params_t* params, stixels_t* out_handle)
     d.var_sigma = m.var_sigma ? 1 : 0;
     d.int_grid = m.p.pixel_grid;
     d.lut_cost = m.p.pixel_grid ? d.g_sky + m.g_sky.size() : nullptr;
+    d.kg_tab = m.p.ground_estimate ? d.g_sky + m.g_sky.size() + m.lut_cost.size() : nullptr;
     *out_handle = h;
     return STIXELS_OK;
 }
@@ -307,6 +315,23 @@ int stixels_reduce(stixels_t h, const float* d_disparity, int H, int W, void* st
     return cuda_status(launch_reduce(d_disparity, g, h->hm.dmax, reduce_code(h->hm.p), d_q, (cudaStream_t)stream));
 }
 
+int stixels_estimate_ground(stixels_t h, const int16_t* d_q, int H, int ncols, void* stream, int32_t* d_line)
+{
+    if (!h || H < 0 || H > STIXELS_MAX_HEIGHT || ncols < 0) return STIXELS_E_INVALID_ARG;
+    if (H == 0 || ncols == 0) return STIXELS_OK;
+    if (!d_q || !d_line || !h->md.kg_tab) return STIXELS_E_INVALID_ARG;
+    FrameGeom g;
+    g.H = H; g.W = ncols * h->hm.p.stixel_width; g.s = h->hm.p.stixel_width; g.ncols = ncols; g.P = lut_pitch(H);
+    if (!ground_size_ok(g)) return STIXELS_E_INVALID_ARG;
+    RowsDev r;
+    int rc = ensure_rows(h, H, &r);
+    if (rc) return rc;
+    rc = ensure_workspace(h, ground_work_bytes(H, h->hm.dmax));
+    if (rc) return rc;
+    RowsDev fr;
+    return cuda_status(launch_ground(d_q, g, h->md, r, (char*)h->ws.base, &fr, d_line, (cudaStream_t)stream));
+}
+
 int stixels_build_luts(stixels_t h, const int16_t* d_q, int H, int ncols, void* stream, int32_t* d_pd,
                        int32_t* d_pg, int32_t* d_ps, int32_t* d_po)
 {
@@ -350,8 +375,10 @@ int stixels_compute(stixels_t h, const float* d_disparity, int H, int W, void* s
     RowsDev r;
     rc = ensure_rows(h, H, &r);
     if (rc) return rc;
+    const bool est = h->hm.p.ground_estimate != 0;
+    if (est && !ground_size_ok(g)) return STIXELS_E_INVALID_ARG;
     const FrameLayout L = frame_layout(H, g.ncols, h->hm.dmax + 1);
-    rc = ensure_workspace(h, L.total);
+    rc = ensure_workspace(h, L.total + (est ? ground_work_bytes(H, h->hm.dmax) : 0));
     if (rc) return rc;
     char* ws = (char*)h->ws.base;
     int16_t* q = (int16_t*)(ws + L.q);
@@ -361,6 +388,7 @@ int stixels_compute(stixels_t h, const float* d_disparity, int H, int W, void* s
     int32_t* po = (int32_t*)(ws + L.po);
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = launch_reduce(d_disparity, g, h->hm.dmax, reduce_code(h->hm.p), q, st);
+    if (e == cudaSuccess && est) e = launch_ground(q, g, h->md, r, ws + L.total, &r, nullptr, st);
     if (e == cudaSuccess) e = launch_luts(q, g, h->md, r, pd, pg, ps, po, st);
     if (e == cudaSuccess) e = launch_dp(pd, pg, ps, po, g, h->md, r, *out, h->d_err, st);
     return cuda_status(e);

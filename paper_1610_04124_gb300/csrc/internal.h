@@ -43,6 +43,7 @@ struct ModelDev {
                              //    ground residuals come per row (RowsDev::g_ground)
     int32_t int_grid;        // 1: reduced disparities are whole pixels (multiples of 16 in Q4)
     const int32_t* lut_cost; // int_grid only: [dmax + 1][dmax + 1], object cost of (f, d)
+    const int32_t* kg_tab;   // ground estimate only: [16 dmax + 1] ground K at a clamped ground code
 };
 
 // Per-(handle, H) row tables.
@@ -103,6 +104,7 @@ struct HandleView {
     uint32_t* err;
     int stixel_width, capacity;
     int reduce_mode;            // reduce_code of the params: bit 0 mean, bit 1 whole-pixel grid
+    int ground_estimate;        // the handle estimates its ground per frame (per-frame path only)
 };
 int handle_view(stixels_t h, int H, HandleView* v);
 // stixels status for a CUDA error, remembering its text for stixels_last_cuda_error()
@@ -161,6 +163,14 @@ struct BatchTables {
 void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t);
 // Launches all stages for tables already copied to d_tab (counter reset included).
 cudaError_t enqueue_tables(const BatchTables& t, char* d_tab, int dp_warps, int dp_ctas_per_sm, cudaStream_t st);
+
+// The frame's ground line from its v-disparity (kernels_ground.cu): work bytes
+// for height H, and the launch (cam = the camera's rows, kept when nothing
+// votes; frame_rows receives the frame's tables inside `work`; line, if not
+// null, receives {k, horizon row, votes} on the device).
+size_t ground_work_bytes(int H, int dmax);
+cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& m, RowsDev cam, char* work,
+                          RowsDev* frame_rows, int32_t* line, cudaStream_t st);
 
 // Sets the DP kernels' shared-memory attributes (call outside stream capture).
 cudaError_t prepare_dp_kernels();

@@ -97,6 +97,7 @@ void default_params(stixels_params_t* p)
     p->sigma_gain = 0.0f;
     p->sigma_mid = 32.0f;
     p->sigma_width = 8.0f;
+    p->ground_estimate = 0;
 }
 
 double sigma_at(const stixels_params_t& p, double base, double f)
@@ -140,6 +141,8 @@ int build_model(const stixels_params_t* p, HostModel* m)
     if (p->sigma_gain != 0.0f && !(p->sigma_width > 0.0f && std::isfinite(p->sigma_width) &&
                                    std::isfinite(p->sigma_mid)))
         return STIXELS_E_INVALID_ARG;
+    if (p->ground_estimate != 0 && p->ground_estimate != 1) return STIXELS_E_INVALID_ARG;
+    if (p->ground_estimate && p->sigma_gain != 0.0f) return STIXELS_E_INVALID_ARG;
     if (p->max_stixels_per_col < 1 || p->max_stixels_per_col > STIXELS_MAX_HEIGHT) return STIXELS_E_INVALID_ARG;
 
     m->p = *p;
@@ -229,6 +232,11 @@ int build_model(const stixels_params_t* p, HostModel* m)
     m->eps_g = (int32_t)llround(16.0 * (double)p->eps_gravity);
     m->eps_d = (int32_t)llround(16.0 * (double)p->eps_diving);
     m->eps_o = (int32_t)llround(16.0 * (double)p->eps_order);
+    m->kg_tab.clear();
+    if (p->ground_estimate) {
+        m->kg_tab.resize(m->emax + 1);
+        for (int c = 0; c <= m->emax; ++c) m->kg_tab[c] = to_fixed(gauss_const(c / 16.0, s_gnd, p_out, d_range));
+    }
     // whole-pixel grid: the object pixel cost of every (model disparity f,
     // pixel disparity d) pair, the same value as the per-pixel formula at the
     // Q4 residual 16 |d - f| (paper Sec. 3.4's LUT_cost, computed off-line)

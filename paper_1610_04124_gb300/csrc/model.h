@@ -30,6 +30,9 @@ struct HostModel {
     // whole-pixel grid only: object pixel cost of pixel disparity d under model
     // disparity f, cost[f * (dmax + 1) + d] (the paper's LUT_cost); empty otherwise
     std::vector<int32_t> lut_cost;
+    // ground estimate only: ground K for every ground code c in [0, 16 dmax]
+    // (K depends on the ground disparity only through its clamp to [0, d_range])
+    std::vector<int32_t> kg_tab;
 };
 
 // Validate params and build the model; returns a stixels_status.

@@ -1,0 +1,104 @@
+"""The frame's ground line from its v-disparity (the step before the path):
+the estimate (slope, horizon, votes) and whole frames computed with it must
+equal the oracle's exactly; the camera's line is kept when nothing votes; the
+paths that do not support the estimate refuse it."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1610_04124_gb300 as S
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from test_gpu_parity import assert_frame_equal, cuda  # noqa: E402
+
+WRONG = dict(horizon_row=10, baseline_m=0.2)       # camera parameters the estimate overrides
+
+
+def _scenes():
+    out = [(scenes.CONFIG1, scenes.make_scene(scenes.CONFIG1, 6000, n_obstacles=(3, 6))),
+           (scenes.CONFIG1, scenes.make_scene(scenes.CONFIG1, 6001, n_obstacles=(3, 6), integer_disp=True,
+                                              noise_sigma=0, p_outlier=0, p_invalid=0)),
+           (scenes.CONFIG2, scenes.make_scene(scenes.CONFIG2, 6002, n_obstacles=(8, 20))),
+           (scenes.Camera(83, 97, stixel_width=5, dmax=48, horizon_row=30, baseline_m=0.4, camera_height_m=1.0),
+            None)]
+    cam = out[-1][0]
+    out[-1] = (cam, scenes.make_scene(cam, 6003, n_obstacles=(1, 3), span_cols=(1, 6)))
+    return out
+
+
+@pytest.mark.parametrize("i", range(4))
+def test_estimate_equals_oracle(i):
+    cam, sc = _scenes()[i]
+    h = S.Stixels(S.default_params(cam, ground_estimate=1))
+    q = h.reduce(cuda(sc.disparity))
+    ncols = cam.width // cam.stixel_width
+    got = h.estimate_ground(q, cam.height, ncols)
+    ref = oracle.ground_estimate(oracle.reduce(sc.disparity, cam.stixel_width, cam.dmax), cam.dmax)
+    assert got == ref
+    h.close()
+
+
+def test_estimate_equals_oracle_2048x880():
+    cam = scenes.CONFIG3[-1]
+    sc = scenes.make_scene(cam, 6010, n_obstacles=(8, 20))
+    h = S.Stixels(S.default_params(cam, ground_estimate=1))
+    q = h.reduce(cuda(sc.disparity))
+    got = h.estimate_ground(q, cam.height, cam.width // cam.stixel_width)
+    ref = oracle.ground_estimate(oracle.reduce(sc.disparity, cam.stixel_width, cam.dmax), cam.dmax)
+    assert got == ref
+    h.close()
+
+
+@pytest.mark.parametrize("i", range(4))
+def test_frames_with_the_estimate_equal_oracle(i):
+    cam, sc = _scenes()[i]
+    lp = S.default_params(cam, ground_estimate=1, **WRONG)
+    op = oracle.make_params(cam, ground_estimate=1, **WRONG)
+    h = S.Stixels(lp)
+    out = h.compute(cuda(sc.disparity))
+    torch.cuda.synchronize()
+    res = S.Stixels.to_host(out)
+    err = h.get_error()
+    fr = oracle.frame(op, sc.disparity, cap=lp.max_stixels_per_col)
+    assert err == (S.ERR_CAPACITY if (fr.counts > lp.max_stixels_per_col).any() else 0)
+    assert_frame_equal(res, fr, cam.height, lp.max_stixels_per_col)
+    # and through host buffers
+    st, counts, cost, rc = h.compute_host(sc.disparity)
+    assert np.array_equal(counts, res[1]) and np.array_equal(cost, res[2])
+    h.close()
+
+
+def test_no_ground_keeps_the_camera_line():
+    cam = scenes.CONFIG1
+    D = np.zeros((cam.height, cam.width), np.float32)
+    a, b = S.Stixels(S.default_params(cam)), S.Stixels(S.default_params(cam, ground_estimate=1))
+    q = b.reduce(cuda(D))
+    assert b.estimate_ground(q, cam.height, cam.width // cam.stixel_width)[2] == 0
+    ra, rb = S.Stixels.to_host(a.compute(cuda(D))), S.Stixels.to_host(b.compute(cuda(D)))
+    torch.cuda.synchronize()
+    assert np.array_equal(ra[1], rb[1]) and np.array_equal(ra[3], rb[3])
+
+
+def test_unsupported_paths_refuse_the_estimate():
+    cam = scenes.CONFIG1
+    with pytest.raises(S.StixelsError):
+        S.Stixels(S.default_params(cam, ground_estimate=1, sigma_gain=0.5))
+    h = S.Stixels(S.default_params(cam, ground_estimate=1))
+    with pytest.raises(S.StixelsError):
+        S.Batch([(h, cam.height, cam.width)])
+    srv = S.Server(64 << 20, max_slots=2)
+    with pytest.raises(S.StixelsError):
+        srv.submit(h, np.zeros((cam.height, cam.width), np.float32))
+    srv.close()
+    h.reserve(cam.height, cam.width)
+    out = h.alloc_output(cam.height, cam.width)
+    with pytest.raises(S.StixelsError):
+        h.compute_noalloc(cuda(np.zeros((cam.height, cam.width), np.float32)), out)
+    plain = S.Stixels(S.default_params(cam))
+    q = plain.reduce(cuda(np.zeros((cam.height, cam.width), np.float32)))
+    with pytest.raises(S.StixelsError):
+        plain.estimate_ground(q, cam.height, cam.width // cam.stixel_width)

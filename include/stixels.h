@@ -118,6 +118,10 @@ typedef struct stixels_params {
                                   for every frame from its v-disparity (stixels_estimate_ground),
                                   per-frame path only (stixels_compute / _compute_host); needs
                                   sigma_gain = 0 and ncols * H <= 7,000,000 */
+    int32_t global_map;        /* 0 = the paper's DP (Eq. 6: one best stixel per row and class, so the
+                                  ordering prior is judged against that stixel only); 1 = the global MAP
+                                  with the ordering prior exact (object states carry their disparity;
+                                  per-frame path only, 24 H (dmax+1) bytes of workspace per column) */
 } stixels_params_t;
 
 /* One output stixel: 12 bytes. */

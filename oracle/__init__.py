@@ -46,7 +46,7 @@ class Params(C.Structure):
         ("cost_order", C.c_float), ("eps_order", C.c_float),
         ("reduce_mode", C.c_int32), ("quantize", C.c_int32), ("pixel_grid", C.c_int32),
         ("sigma_gain", C.c_float), ("sigma_mid", C.c_float), ("sigma_width", C.c_float),
-        ("ground_estimate", C.c_int32),
+        ("ground_estimate", C.c_int32), ("global_map", C.c_int32),
     ]
 
 
@@ -75,7 +75,7 @@ DEFAULTS: Dict[str, object] = dict(
     cost_gravity=2.0, eps_gravity=1.0, cost_diving=10.0, eps_diving=1.0,
     cost_order=2.0, eps_order=0.0,
     reduce_mode=0, quantize=1, pixel_grid=0,
-    sigma_gain=0.0, sigma_mid=32.0, sigma_width=8.0, ground_estimate=0,
+    sigma_gain=0.0, sigma_mid=32.0, sigma_width=8.0, ground_estimate=0, global_map=0,
 )
 
 

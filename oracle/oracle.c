@@ -104,6 +104,11 @@ typedef struct {
     /* 1 = the ground line comes from the frame itself (or_ground_estimate on
      * its reduced codes) instead of the camera parameters */
     int32_t ground_estimate;
+    /* 1 = the global MAP over all segmentations with the ordering prior exact:
+     * the object state carries the disparity of its stixel (Eq. 6 keeps only
+     * the best stixel per row and class, which makes the ordering prior an
+     * approximation); 0 = the paper's DP */
+    int32_t global_map;
 } or_params_t;
 
 typedef struct {
@@ -608,13 +613,115 @@ static int column_dp(const or_model_t* m, const int16_t* q, int cap, or_stixel_t
     return n > cap ? OR_E_CAPACITY : OR_OK;
 }
 
+/* Lexicographic order of candidates in the global-MAP DP: cost, then the
+ * previous class (object < ground < sky < none), start row, previous object f. */
+typedef struct { double cost; int p, b, fprev; } map_key_t;
+
+static int key_less(map_key_t a, map_key_t b)
+{
+    if (a.cost != b.cost) return a.cost < b.cost;
+    if (a.p != b.p) return a.p < b.p;
+    if (a.b != b.b) return a.b < b.b;
+    return a.fprev < b.fprev;
+}
+
+/* The global MAP (global_map = 1): states (row k, object, f) for every mean
+ * disparity f of the top stixel, and (row k, ground), (row k, sky); a stixel
+ * [b, k] of class c extends every state of row b - 1 with the exact prior of
+ * the pair (for object above object: the ordering penalty against that
+ * state's f).  Evaluated plainly: every end row, start row, previous class and
+ * previous object disparity.  gap_abs / gap_rel are not computed (0). */
+static int column_dp_map(const or_model_t* m, const int16_t* q, int cap, or_stixel_t* out, or_column_result_t* res)
+{
+    const int H = m->H, F = m->dmax + 1;
+    const size_t NO = (size_t)H * F;
+    int64_t* pd = (int64_t*)malloc(sizeof(int64_t) * (size_t)(H + 1));
+    double* pg = (double*)malloc(sizeof(double) * (size_t)(H + 1));
+    double* ps = (double*)malloc(sizeof(double) * (size_t)(H + 1));
+    double* po = (double*)malloc(sizeof(double) * (size_t)F * (H + 1));
+    map_key_t* KO = (map_key_t*)malloc(sizeof(map_key_t) * NO);          /* [k][f] object states */
+    map_key_t* KG = (map_key_t*)malloc(sizeof(map_key_t) * (size_t)H);    /* ground states */
+    map_key_t* KS = (map_key_t*)malloc(sizeof(map_key_t) * (size_t)H);    /* sky states */
+    or_stixel_t* path = (or_stixel_t*)malloc(sizeof(or_stixel_t) * (size_t)H);
+    if (!pd || !pg || !ps || !po || !KO || !KG || !KS || !path) {
+        free(pd); free(pg); free(ps); free(po); free(KO); free(KG); free(KS); free(path);
+        return OR_E_MEM;
+    }
+    build_prefix(m, q, pd, pg, ps, po);
+    const map_key_t none = {INFINITY, OR_NONE, 0, 0};
+
+    for (int k = 0; k < H; ++k) {
+        for (int f = 0; f < F; ++f) KO[(size_t)k * F + f] = none;
+        KG[k] = none;
+        KS[k] = none;
+        for (int b = 0; b <= k; ++b) {
+            const int n = k - b + 1;
+            const int64_t S = pd[k + 1] - pd[b];
+            const int fo = mean_f(S, n);
+            const double data[3] = {po[(size_t)fo * (H + 1) + k + 1] - po[(size_t)fo * (H + 1) + b],
+                                    pg[k + 1] - pg[b], ps[k + 1] - ps[b]};
+            map_key_t* dst[3] = {&KO[(size_t)k * F + fo], &KG[k], &KS[k]};
+            for (int c = 0; c < 3; ++c) {
+                if (b == 0) {
+                    map_key_t cand = {data[c] + m->first[c], OR_NONE, 0, 0};
+                    if (key_less(cand, *dst[c])) *dst[c] = cand;
+                    continue;
+                }
+                for (int fp = 0; fp < F; ++fp) {          /* previous state: object with f = fp */
+                    const double prev = KO[(size_t)(b - 1) * F + fp].cost;
+                    if (isinf(prev)) continue;
+                    map_key_t cand = {data[c] + pair_prior(m, c, OR_OBJECT, b, fo, fp) + prev, OR_OBJECT, b, fp};
+                    if (key_less(cand, *dst[c])) *dst[c] = cand;
+                }
+                map_key_t cg = {data[c] + pair_prior(m, c, OR_GROUND, b, fo, 0) + KG[b - 1].cost, OR_GROUND, b, 0};
+                if (key_less(cg, *dst[c])) *dst[c] = cg;
+                map_key_t cs = {data[c] + pair_prior(m, c, OR_SKY, b, fo, 0) + KS[b - 1].cost, OR_SKY, b, 0};
+                if (key_less(cs, *dst[c])) *dst[c] = cs;
+            }
+        }
+    }
+
+    /* top row: lexicographic (cost, class, f), classes object < ground < sky */
+    int c = -1, f = 0;
+    double best = INFINITY;
+    for (int ff = 0; ff < F; ++ff)
+        if (KO[(size_t)(H - 1) * F + ff].cost < best) { best = KO[(size_t)(H - 1) * F + ff].cost; c = OR_OBJECT; f = ff; }
+    if (KG[H - 1].cost < best) { best = KG[H - 1].cost; c = OR_GROUND; f = 0; }
+    if (KS[H - 1].cost < best) { best = KS[H - 1].cost; c = OR_SKY; f = 0; }
+    res->cost = best;
+    res->gap_abs = res->gap_rel = 0.0;
+    if (c < 0 || isinf(best)) {
+        res->n = 0;
+        free(pd); free(pg); free(ps); free(po); free(KO); free(KG); free(KS); free(path);
+        return OR_E_INFEASIBLE;
+    }
+    int n = 0, k = H - 1;
+    while (k >= 0 && c != OR_NONE) {
+        const map_key_t key = c == OR_OBJECT ? KO[(size_t)k * F + f] : (c == OR_GROUND ? KG[k] : KS[k]);
+        const int b = key.b;
+        or_stixel_t st;
+        st.v_bottom = b; st.v_top = k; st.cls = c;
+        st.sum_q = pd[k + 1] - pd[b];
+        st.f = mean_f(st.sum_q, k - b + 1);
+        st.disparity = (double)st.sum_q / (16.0 * (double)(k - b + 1));
+        path[n++] = st;
+        k = b - 1;
+        c = key.p;
+        f = key.fprev;
+    }
+    for (int i = 0; i < n && i < cap; ++i) out[i] = path[n - 1 - i];
+    res->n = n;
+    free(pd); free(pg); free(ps); free(po); free(KO); free(KG); free(KS); free(path);
+    return n > cap ? OR_E_CAPACITY : OR_OK;
+}
+
 /* One column: q[0..H-1] bottom-up Q4 codes.  Writes up to cap stixels. */
 int or_column(const or_params_t* p, const int16_t* q, int H, int cap, or_stixel_t* out, or_column_result_t* res)
 {
     or_model_t m;
     int rc = model_build(p, H, &m);
     if (rc) return rc;
-    rc = column_dp(&m, q, cap, out, res);
+    rc = p->global_map ? column_dp_map(&m, q, cap, out, res) : column_dp(&m, q, cap, out, res);
     model_free(&m);
     return rc;
 }
@@ -647,7 +754,8 @@ int or_frame(const or_params_t* p, const float* disp, int H, int W, int cap, or_
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
 #endif
     for (int c = 0; c < C; ++c) {
-        int r = column_dp(&m, q + (size_t)c * H, cap, out + (size_t)c * cap, res + c);
+        int r = p->global_map ? column_dp_map(&m, q + (size_t)c * H, cap, out + (size_t)c * cap, res + c)
+                              : column_dp(&m, q + (size_t)c * H, cap, out + (size_t)c * cap, res + c);
         if (r != OR_OK) {
 #ifdef _OPENMP
 #pragma omp critical

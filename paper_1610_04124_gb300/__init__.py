@@ -46,7 +46,7 @@ class Params(C.Structure):
         ("cost_order", C.c_float), ("eps_order", C.c_float),
         ("reduce_mode", C.c_int32), ("max_stixels_per_col", C.c_int32), ("pixel_grid", C.c_int32),
         ("sigma_gain", C.c_float), ("sigma_mid", C.c_float), ("sigma_width", C.c_float),
-        ("ground_estimate", C.c_int32),
+        ("ground_estimate", C.c_int32), ("global_map", C.c_int32),
     ]
 
     def to_dict(self) -> Dict[str, object]:

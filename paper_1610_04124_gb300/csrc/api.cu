@@ -176,6 +176,7 @@ int handle_view(stixels_t h, int H, HandleView* v)
     v->stixel_width = h->hm.p.stixel_width;
     v->reduce_mode = reduce_code(h->hm.p);
     v->ground_estimate = h->hm.p.ground_estimate;
+    v->global_map = h->hm.p.global_map;
     v->capacity = h->hm.p.max_stixels_per_col;
     return STIXELS_OK;
 }
@@ -360,6 +361,12 @@ int stixels_solve(stixels_t h, const int32_t* d_pd, const int32_t* d_pg, const i
     RowsDev r;
     rc = ensure_rows(h, H, &r);
     if (rc) return rc;
+    if (h->hm.p.global_map) {
+        rc = ensure_workspace(h, map_scratch_bytes(H, ncols, h->hm.dmax + 1));
+        if (rc) return rc;
+        return cuda_status(launch_dp_map(d_pd, d_pg, d_ps, d_po, g, h->md, r, *out, h->d_err, h->ws.base,
+                                         (cudaStream_t)stream));
+    }
     return cuda_status(launch_dp(d_pd, d_pg, d_ps, d_po, g, h->md, r, *out, h->d_err, (cudaStream_t)stream));
 }
 
@@ -378,7 +385,9 @@ int stixels_compute(stixels_t h, const float* d_disparity, int H, int W, void* s
     const bool est = h->hm.p.ground_estimate != 0;
     if (est && !ground_size_ok(g)) return STIXELS_E_INVALID_ARG;
     const FrameLayout L = frame_layout(H, g.ncols, h->hm.dmax + 1);
-    rc = ensure_workspace(h, L.total + (est ? ground_work_bytes(H, h->hm.dmax) : 0));
+    const size_t gw = est ? (ground_work_bytes(H, h->hm.dmax) + 255) / 256 * 256 : 0;
+    const bool gmap = h->hm.p.global_map != 0;
+    rc = ensure_workspace(h, L.total + gw + (gmap ? map_scratch_bytes(H, g.ncols, h->hm.dmax + 1) : 0));
     if (rc) return rc;
     char* ws = (char*)h->ws.base;
     int16_t* q = (int16_t*)(ws + L.q);
@@ -390,7 +399,9 @@ int stixels_compute(stixels_t h, const float* d_disparity, int H, int W, void* s
     cudaError_t e = launch_reduce(d_disparity, g, h->hm.dmax, reduce_code(h->hm.p), q, st);
     if (e == cudaSuccess && est) e = launch_ground(q, g, h->md, r, ws + L.total, &r, nullptr, st);
     if (e == cudaSuccess) e = launch_luts(q, g, h->md, r, pd, pg, ps, po, st);
-    if (e == cudaSuccess) e = launch_dp(pd, pg, ps, po, g, h->md, r, *out, h->d_err, st);
+    if (e == cudaSuccess)
+        e = gmap ? launch_dp_map(pd, pg, ps, po, g, h->md, r, *out, h->d_err, ws + L.total + gw, st)
+                 : launch_dp(pd, pg, ps, po, g, h->md, r, *out, h->d_err, st);
     return cuda_status(e);
 }
 

@@ -218,7 +218,7 @@ int stixels_batch_create(const stixels_frame_desc_t* frames, int nframes, stixel
         FramePlan f;
         int rc = handle_prepare(d.camera, d.H, &f.job.view);
         if (rc != STIXELS_OK) { delete b; return rc; }
-        if (f.job.view.ground_estimate) { delete b; return STIXELS_E_INVALID_ARG; }   // per-frame path only
+        if (f.job.view.ground_estimate || f.job.view.global_map) { delete b; return STIXELS_E_INVALID_ARG; }   // per-frame path only
         if (f.job.view.device != b->device) { delete b; return STIXELS_E_INVALID_ARG; }
         FrameGeom& g = f.job.g;
         g.H = d.H; g.W = d.W; g.s = f.job.view.stixel_width; g.ncols = d.W / g.s; g.P = lut_pitch(d.H);

@@ -105,6 +105,7 @@ struct HandleView {
     int stixel_width, capacity;
     int reduce_mode;            // reduce_code of the params: bit 0 mean, bit 1 whole-pixel grid
     int ground_estimate;        // the handle estimates its ground per frame (per-frame path only)
+    int global_map;             // the handle solves the global MAP (per-frame path only)
 };
 int handle_view(stixels_t h, int H, HandleView* v);
 // stixels status for a CUDA error, remembering its text for stixels_last_cuda_error()
@@ -171,6 +172,12 @@ cudaError_t enqueue_tables(const BatchTables& t, char* d_tab, int dp_warps, int 
 size_t ground_work_bytes(int H, int dmax);
 cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& m, RowsDev cam, char* work,
                           RowsDev* frame_rows, int32_t* line, cudaStream_t st);
+
+// The global-MAP DP (kernels_dp_map.cu): scratch bytes for a frame, and the launch.
+size_t map_scratch_bytes(int H, int ncols, int F);
+cudaError_t launch_dp_map(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po,
+                          const FrameGeom& g, const ModelDev& m, const RowsDev& r, const stixels_output_t& out,
+                          uint32_t* err, void* scratch, cudaStream_t st);
 
 // Sets the DP kernels' shared-memory attributes (call outside stream capture).
 cudaError_t prepare_dp_kernels();

@@ -98,6 +98,7 @@ void default_params(stixels_params_t* p)
     p->sigma_mid = 32.0f;
     p->sigma_width = 8.0f;
     p->ground_estimate = 0;
+    p->global_map = 0;
 }
 
 double sigma_at(const stixels_params_t& p, double base, double f)
@@ -143,6 +144,7 @@ int build_model(const stixels_params_t* p, HostModel* m)
         return STIXELS_E_INVALID_ARG;
     if (p->ground_estimate != 0 && p->ground_estimate != 1) return STIXELS_E_INVALID_ARG;
     if (p->ground_estimate && p->sigma_gain != 0.0f) return STIXELS_E_INVALID_ARG;
+    if (p->global_map != 0 && p->global_map != 1) return STIXELS_E_INVALID_ARG;
     if (p->max_stixels_per_col < 1 || p->max_stixels_per_col > STIXELS_MAX_HEIGHT) return STIXELS_E_INVALID_ARG;
 
     m->p = *p;

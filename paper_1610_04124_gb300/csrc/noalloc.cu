@@ -51,7 +51,7 @@ extern "C" int stixels_compute_noalloc(stixels_t h, const float* d_disparity, in
     HandleView v;
     int rc = handle_view(h, H, &v);            // no row tables for H yet -> INVALID_ARG (would allocate)
     if (rc != STIXELS_OK) return rc;
-    if (v.ground_estimate) return STIXELS_E_INVALID_ARG;   // the estimate's work does not fit the fixed array
+    if (v.ground_estimate || v.global_map) return STIXELS_E_INVALID_ARG;   // their work does not fit the fixed array
     FrameGeom g;
     g.H = H;
     g.W = W;

@@ -238,7 +238,7 @@ int stixels_submit(stixels_server_t s, stixels_t camera, const float* disparity,
         s->stats.submitted += 1;
         int rc = handle_prepare(camera, H, &r->job.view);
         if (rc != STIXELS_OK) return rc;
-        if (r->job.view.ground_estimate) return STIXELS_E_INVALID_ARG;   // per-frame path only
+        if (r->job.view.ground_estimate || r->job.view.global_map) return STIXELS_E_INVALID_ARG;   // per-frame path only
         if (r->job.view.device != s->device) return STIXELS_E_INVALID_ARG;
         FrameGeom& g = r->job.g;
         g.H = H; g.W = W; g.s = r->job.view.stixel_width; g.ncols = W / g.s; g.P = lut_pitch(H);

@@ -43,7 +43,9 @@
  *   - ground model f(v) = alpha (v_horizon - v) (Sec. 3.1) with
  *     alpha = baseline cos(pitch) / camera height, i.e. in image rows r
  *     (0 = top) f = alpha (r - horizon_row);
- *   - sigma^c is a per-class constant; A_norm is the mass of the Gaussian
+ *   - sigma^c is a per-class constant, or with sigma_gain set a logistic in
+ *     the model disparity (the paper names a sigmoid but not its form; see
+ *     or_params_t); A_norm is the mass of the Gaussian
  *     N(f, sigma^2) on [0, d_range] with f clamped to [0, d_range];
  *     d_range = dmax;
  *   - Eq. 4's min(., .) is used as printed;
@@ -57,7 +59,8 @@
  *     directly above an object whose disparity is lower by more than eps;
  *   - the DP keeps, per end row and class, only the best stixel (Eq. 6 links
  *     candidates to ob^{k-1}, gr^{k-1}, sk^{k-1}); with the ordering penalty
- *     on this is the paper's DP, not the global MAP;
+ *     on this is the paper's DP, not the global MAP (global_map = 1 computes
+ *     the global MAP instead);
  *   - ties within a cell are broken by (cost, previous class, start row) in
  *     lexicographic order, classes ordered object < ground < sky < none (the
  *     first stixel); the final class at the top row is chosen in the order

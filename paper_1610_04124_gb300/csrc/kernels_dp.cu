@@ -107,14 +107,31 @@ __device__ __forceinline__ int32_t min3(int32_t a, int32_t b, int32_t c) { retur
 
 // floor(x / (16 n)) for 0 <= x < 2^31 via a multiply-high: M = ceil(2^(32+s) / d),
 // s = floor(log2 d), d = 16 n (M = 2^31, s - 1 when d is a power of two).
-__device__ __forceinline__ uint2 div_magic(int n)
+// The constants for n = 1 .. STIXELS_MAX_HEIGHT are built at compile time;
+// each CTA copies the ones its column height needs into shared memory.
+struct alignas(8) DivMagic {
+    uint32_t m, s;
+};
+struct DivTable {
+    DivMagic v[STIXELS_MAX_HEIGHT + 1];
+};
+constexpr DivTable make_div_table()
 {
-    const uint32_t d = 16u * (uint32_t)n;
-    const int s = 31 - __clz(d);
-    if ((d & (d - 1)) == 0) return make_uint2(1u << 31, (uint32_t)(s - 1));
-    const unsigned long long num = 1ull << (32 + s);
-    return make_uint2((uint32_t)((num + d - 1) / d), (uint32_t)s);
+    DivTable t{};
+    for (int n = 1; n <= STIXELS_MAX_HEIGHT; ++n) {
+        const uint32_t d = 16u * (uint32_t)n;
+        int s = 0;
+        while ((d >> (s + 1)) != 0) ++s;
+        if ((d & (d - 1)) == 0) {
+            t.v[n] = DivMagic{1u << 31, (uint32_t)(s - 1)};
+        } else {
+            const unsigned long long num = 1ull << (32 + s);
+            t.v[n] = DivMagic{(uint32_t)((num + d - 1) / d), (uint32_t)s};
+        }
+    }
+    return t;
 }
+__device__ const DivTable kDivTable = make_div_table();
 
 // Rounded mean disparity of a stixel of n rows from x = S + 8 n, clamped to
 // the LUT's rows: valid Q4 input always gives f <= dmax; the clamp only keeps
@@ -123,13 +140,6 @@ __device__ __forceinline__ int mean_f(int32_t x, int n, const uint2* s_div, int 
 {
     const uint2 dm = s_div[n];
     return (int)min(__umulhi((uint32_t)x, dm.x) >> dm.y, (uint32_t)dmax);
-}
-
-// Gravity / diving penalties of an object with rounded mean f directly above
-// ground, base row thresholds r (input-only).
-__device__ __forceinline__ int32_t ground_pen(int32_t thr, int f, const ModelDev& m)
-{
-    return (f > thr_hi(thr) ? m.pen_grav : 0) + (f < thr_lo(thr) ? m.pen_div : 0);
 }
 
 // The bulk context of a start from its three previous-class terms (bo, bg, bs,
@@ -185,63 +195,64 @@ size_t dp_smem_bytes(int H, int ring)
            sizeof(SyncState);
 }
 
-constexpr int kTriCells = 528;          // cells (i, l) with i <= l of a 32-row block
-constexpr int kChainCells = kTriCells + 1024;
-
-// Gathers the chain data of the block starting at row B into cb: the 528
-// triangle cells (start B + i, end B + l, i <= l) and the 1024 cells (start
-// B + i, end B + 32 + l), with the cells split over nthreads threads (this one
-// is tid).  Slots of the triangle with i > l are never written here (they are
-// zeroed once per column).  All loads of a pass are issued before any store.
-// Kept out of line: it runs from two places and its code is shared.
-__device__ __noinline__ void gather_chain(ChainBuf* cb, int B, int H, int P, const int32_t* __restrict__ po_col,
-                                          const int32_t* s_pd8, const int32_t* s_thr, const uint2* s_div,
-                                          const ModelDev& m, int tid, int nthreads)
+// Gathers the chain data of the block starting at row B into cb.  Warp w of
+// nw takes the starts b = B + i for i = w, w + nw, ...; lane l computes the
+// cells (b, B + l) (triangle slot i 32 + l, written only for i <= l) and
+// (b, B + 32 + l) (next-block slot), two starts' loads in flight at a time.
+// Cells past the column's end hold zeros; starts past it are skipped (the
+// chain never reads them); triangle slots with i > l are zeroed once per
+// column and never written here.
+__device__ __forceinline__ void gather_chain(ChainBuf* cb, int B, int H, int P, const int32_t* __restrict__ po_col,
+                                             const int32_t* s_pd8, const int32_t* s_thr, const uint2* s_div,
+                                             int dmax, int32_t pen_grav, int32_t pen_div, int w, int nw, int lane)
 {
-    for (int base = tid; base < kChainCells; base += 4 * nthreads) {
-        int32_t lo[4], hi[4], fv[4];
-        int slot[4];
-        bool ok[4];
+    const int k0 = B + lane, k1 = B + 32 + lane;
+    const bool in0 = k0 < H, in1 = k1 < H;
+    const int32_t x0 = s_pd8[(in0 ? k0 : 0) + 1], x1 = s_pd8[(in1 ? k1 : 0) + 1];
+#pragma unroll 1
+    for (int i0 = w; i0 < 32; i0 += 2 * nw) {
+        int32_t lo[4], hi[4];
+        int fv[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int u = base + r * nthreads;
-            int i, l, k;
-            if (u < kTriCells) {
-                // u = l (l + 1) / 2 + i: l from the square root, then corrected exactly
-                l = (int)((sqrtf((float)(8 * u + 1)) - 1.0f) * 0.5f);
-                if ((l + 1) * (l + 2) / 2 <= u) ++l;
-                if (l * (l + 1) / 2 > u) --l;
-                i = u - l * (l + 1) / 2;
-                k = B + l;
-                slot[r] = i * 32 + l;
-            } else {
-                const int w = u - kTriCells;
-                i = w >> 5;
-                l = w & 31;
-                k = B + 32 + l;
-                slot[r] = 1024 + w;
+        for (int r = 0; r < 2; ++r) {
+            const int i = i0 + r * nw, b = B + i;
+            const bool sv = i < 32 && b < H;                      // uniform across the warp
+            const int32_t pb = sv ? s_pd8[b] : 0;
+            const bool ok0 = sv && i <= lane && in0, ok1 = sv && in1;
+            lo[2 * r] = hi[2 * r] = fv[2 * r] = 0;
+            lo[2 * r + 1] = hi[2 * r + 1] = fv[2 * r + 1] = 0;
+            if (ok0) {
+                const int f = mean_f(x0 - pb, k0 - b + 1, s_div, dmax);
+                const int32_t* row = po_col + f * P;
+                lo[2 * r] = __ldg(row + b);
+                hi[2 * r] = __ldg(row + k0 + 1);
+                fv[2 * r] = f;
             }
-            const int b = B + i;
-            ok[r] = u < kChainCells && k < H;
-            lo[r] = hi[r] = fv[r] = 0;
-            if (ok[r]) {
-                const int f = mean_f(s_pd8[k + 1] - s_pd8[b], k - b + 1, s_div, m.dmax);
-                const int32_t* row = po_col + (size_t)f * P;
-                lo[r] = __ldg(row + b);
-                hi[r] = __ldg(row + k + 1);
-                fv[r] = f;
+            if (ok1) {
+                const int f = mean_f(x1 - pb, k1 - b + 1, s_div, dmax);
+                const int32_t* row = po_col + f * P;
+                lo[2 * r + 1] = __ldg(row + b);
+                hi[2 * r + 1] = __ldg(row + k1 + 1);
+                fv[2 * r + 1] = f;
             }
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int u = base + r * nthreads;
-            if (u < kChainCells) {
-                const int e = slot[r] & 1023;
-                const int b = B + (e >> 5);
-                const int32_t d = hi[r] - lo[r];
-                const int2 v = ok[r] ? make_int2(d, d + ground_pen(s_thr[b], fv[r], m)) : make_int2(0, 0);
-                if (slot[r] < 1024) { cb->tri[e] = v; cb->ftri[e] = (uint8_t)fv[r]; }
-                else { cb->nxt[e] = v; cb->fnxt[e] = (uint8_t)fv[r]; }
+        for (int r = 0; r < 2; ++r) {
+            const int i = i0 + r * nw, b = B + i;
+            if (i < 32 && b < H) {
+                const int32_t thr = s_thr[b];
+                const int fhi = thr_hi(thr), flo = thr_lo(thr);
+                const int32_t d0 = hi[2 * r] - lo[2 * r], d1 = hi[2 * r + 1] - lo[2 * r + 1];
+                const int f0 = fv[2 * r], f1 = fv[2 * r + 1];
+                const int32_t g0 = (f0 > fhi ? pen_grav : 0) + (f0 < flo ? pen_div : 0);
+                const int32_t g1 = (f1 > fhi ? pen_grav : 0) + (f1 < flo ? pen_div : 0);
+                const bool ok0 = i <= lane && in0;
+                if (i <= lane) {
+                    cb->tri[i * 32 + lane] = ok0 ? make_int2(d0, d0 + g0) : make_int2(0, 0);
+                    cb->ftri[i * 32 + lane] = (uint8_t)f0;
+                }
+                cb->nxt[i * 32 + lane] = in1 ? make_int2(d1, d1 + g1) : make_int2(0, 0);
+                cb->fnxt[i * 32 + lane] = (uint8_t)f1;
             }
         }
     }
@@ -304,7 +315,10 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
         s_pd8[v] = a.pd[(size_t)col * P + v] + 8 * v;
         s_thr[v] = thr;
     }
-    for (int n = 1 + threadIdx.x; n <= H; n += kThreads) s_div[n] = div_magic(n);
+    for (int n = 1 + threadIdx.x; n <= H; n += kThreads) {
+        const DivMagic dm = kDivTable.v[n];
+        s_div[n] = make_uint2(dm.m, dm.s);
+    }
     if (threadIdx.x < kMaxBlocks) {
         sync->ready[threadIdx.x] = 0;
         sync->gathered[threadIdx.x] = 0;
@@ -374,8 +388,6 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
             s_cb[x >> 10].ftri[e] = 0;
         }
     }
-    // the chain data of block 0 (input only); the bulk warps gather the rest
-    gather_chain(s_cb, 0, H, P, po_col, s_pd8, s_thr, s_div, m, threadIdx.x, kThreads);
     __syncthreads();
 
     if (warp != chain) {
@@ -395,7 +407,7 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
         // owned end-row block whose start block is final, or this warp's share
         // of the chain data of block next_g (its ring slot is free once block
         // next_g - ring is final)
-        int next_g = 1;
+        int next_g = 0;
         for (;;) {
             const int vf = __shfl_sync(kFull, lane == 0 ? *v_final : 0, 0);     // final blocks
             if (*v_abort) break;
@@ -407,8 +419,8 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
             const int jc_work = wl >= 0 ? __shfl_sync(kFull, my_c, wl) : -1;
             const bool g_open = next_g < NB && vf >= next_g - ring + 1;
             if (g_open && (jc_work < 0 || next_g <= jc_work)) {
-                gather_chain(s_cb + next_g % ring, 32 * next_g, H, P, po_col, s_pd8, s_thr, s_div, m,
-                             bulk_id * 32 + lane, kBulk * 32);
+                gather_chain(s_cb + next_g % ring, 32 * next_g, H, P, po_col, s_pd8, s_thr, s_div, m.dmax,
+                             m.pen_grav, m.pen_div, bulk_id, kBulk, lane);
                 __threadfence_block();
                 __syncwarp();
                 if (lane == 0) atomicAdd(&sync->gathered[next_g], 1);
@@ -452,7 +464,7 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
 
     for (int j = 0; j < NB; ++j) {
         const int B = 32 * j;
-        if (j >= 1 && !wait_geq(&sync->gathered[j], kBulk, v_abort, 16)) { aborted = true; break; }
+        if (!wait_geq(&sync->gathered[j], kBulk, v_abort, 16)) { aborted = true; break; }
         if (j >= 2 && !wait_geq(&sync->ready[j], j - 1, v_abort, 16)) { aborted = true; break; }
         const ChainBuf* cb = s_cb + (j % ring);
         const int nb = min(32, H - B);

@@ -199,59 +199,56 @@ size_t dp_smem_bytes(int H, int ring)
 // nw takes the starts b = B + i for i = w, w + nw, ...; lane l computes the
 // cells (b, B + l) (triangle slot i 32 + l, written only for i <= l) and
 // (b, B + 32 + l) (next-block slot), two starts' loads in flight at a time.
-// Cells past the column's end hold zeros; starts past it are skipped (the
-// chain never reads them); triangle slots with i > l are zeroed once per
-// column and never written here.
+// Every lane runs the same instructions: an invalid cell (end row above the
+// column or below the start) is evaluated at a clamped end row, so that its
+// loads stay inside the column, and stored as zeros.  Starts past the block
+// or the column are skipped (the chain never reads them); triangle slots with
+// i > l are zeroed once per column and never written here.
 __device__ __forceinline__ void gather_chain(ChainBuf* cb, int B, int H, int P, const int32_t* __restrict__ po_col,
                                              const int32_t* s_pd8, const int32_t* s_thr, const uint2* s_div,
                                              int dmax, int32_t pen_grav, int32_t pen_div, int w, int nw, int lane)
 {
     const int k0 = B + lane, k1 = B + 32 + lane;
     const bool in0 = k0 < H, in1 = k1 < H;
-    const int32_t x0 = s_pd8[(in0 ? k0 : 0) + 1], x1 = s_pd8[(in1 ? k1 : 0) + 1];
+    const int kh0 = min(k0, H - 1), kh1 = min(k1, H - 1);
+    const int32_t x0 = s_pd8[kh0 + 1], x1 = s_pd8[kh1 + 1];
 #pragma unroll 1
     for (int i0 = w; i0 < 32; i0 += 2 * nw) {
         int32_t lo[4], hi[4];
         int fv[4];
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            const int i = i0 + r * nw, b = B + i;
-            const bool sv = i < 32 && b < H;                      // uniform across the warp
-            const int32_t pb = sv ? s_pd8[b] : 0;
-            const bool ok0 = sv && i <= lane && in0, ok1 = sv && in1;
-            lo[2 * r] = hi[2 * r] = fv[2 * r] = 0;
-            lo[2 * r + 1] = hi[2 * r + 1] = fv[2 * r + 1] = 0;
-            if (ok0) {
-                const int f = mean_f(x0 - pb, k0 - b + 1, s_div, dmax);
-                const int32_t* row = po_col + f * P;
-                lo[2 * r] = __ldg(row + b);
-                hi[2 * r] = __ldg(row + k0 + 1);
-                fv[2 * r] = f;
-            }
-            if (ok1) {
-                const int f = mean_f(x1 - pb, k1 - b + 1, s_div, dmax);
-                const int32_t* row = po_col + f * P;
-                lo[2 * r + 1] = __ldg(row + b);
-                hi[2 * r + 1] = __ldg(row + k1 + 1);
-                fv[2 * r + 1] = f;
-            }
+            // a start past the block or the column repeats a valid one (not stored)
+            const int b = min(B + min(i0 + r * nw, 31), H - 1);
+            const int32_t pb = s_pd8[b];
+            const int f0 = mean_f(x0 - pb, max(kh0 - b + 1, 1), s_div, dmax);
+            const int f1 = mean_f(x1 - pb, kh1 - b + 1, s_div, dmax);     // kh1 >= b always
+            const int32_t* row0 = po_col + f0 * P;
+            const int32_t* row1 = po_col + f1 * P;
+            lo[2 * r] = __ldg(row0 + b);
+            hi[2 * r] = __ldg(row0 + kh0 + 1);
+            lo[2 * r + 1] = __ldg(row1 + b);
+            hi[2 * r + 1] = __ldg(row1 + kh1 + 1);
+            fv[2 * r] = f0;
+            fv[2 * r + 1] = f1;
         }
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const int i = i0 + r * nw, b = B + i;
-            if (i < 32 && b < H) {
+            if (i < 32 && b < H) {                                       // uniform across the warp
                 const int32_t thr = s_thr[b];
                 const int fhi = thr_hi(thr), flo = thr_lo(thr);
-                const int32_t d0 = hi[2 * r] - lo[2 * r], d1 = hi[2 * r + 1] - lo[2 * r + 1];
-                const int f0 = fv[2 * r], f1 = fv[2 * r + 1];
-                const int32_t g0 = (f0 > fhi ? pen_grav : 0) + (f0 < flo ? pen_div : 0);
-                const int32_t g1 = (f1 > fhi ? pen_grav : 0) + (f1 < flo ? pen_div : 0);
                 const bool ok0 = i <= lane && in0;
+                const int f0 = ok0 ? fv[2 * r] : 0, f1 = in1 ? fv[2 * r + 1] : 0;
+                const int32_t d0 = ok0 ? hi[2 * r] - lo[2 * r] : 0;
+                const int32_t d1 = in1 ? hi[2 * r + 1] - lo[2 * r + 1] : 0;
+                const int32_t g0 = ok0 ? (f0 > fhi ? pen_grav : 0) + (f0 < flo ? pen_div : 0) : 0;
+                const int32_t g1 = in1 ? (f1 > fhi ? pen_grav : 0) + (f1 < flo ? pen_div : 0) : 0;
                 if (i <= lane) {
-                    cb->tri[i * 32 + lane] = ok0 ? make_int2(d0, d0 + g0) : make_int2(0, 0);
+                    cb->tri[i * 32 + lane] = make_int2(d0, d0 + g0);
                     cb->ftri[i * 32 + lane] = (uint8_t)f0;
                 }
-                cb->nxt[i * 32 + lane] = in1 ? make_int2(d1, d1 + g1) : make_int2(0, 0);
+                cb->nxt[i * 32 + lane] = make_int2(d1, d1 + g1);
                 cb->fnxt[i * 32 + lane] = (uint8_t)f1;
             }
         }

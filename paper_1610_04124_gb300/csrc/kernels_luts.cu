@@ -31,11 +31,52 @@ constexpr int kRowsPerCta = 32;
 constexpr int kPerLane = 8;                    // consecutive outputs per lane
 constexpr int kChunk = 32 * kPerLane;          // outputs per warp iteration
 
-enum RowKind { kObject = 0, kDisp = 1, kGround = 2, kSky = 3 };
-
 // Half-width (whole pixels) of the window of the LUT_cost row of disparity f
 // outside which every pixel costs C_out: |d - f| >= ceil(esat / 16).
 __host__ __device__ inline int lc_radius(int esat_obj) { return (esat_obj + 15) >> 4; }
+
+// One LUT row: out[j] = sum over pixels v < j of cost(q[v], v), j = 0 .. P-1,
+// by one warp; s_q[j] = q[j - 1].  A lane owns kPerLane consecutive outputs
+// of each 256-entry chunk: in-register adds, a shuffle scan of the lane
+// totals, two 16-byte stores.  Pixels outside [0, H) contribute nothing
+// (cost is evaluated for them and discarded, so the loop has no branch).
+template <class Cost>
+__device__ __forceinline__ void scan_row(int32_t* __restrict__ out, const int32_t* s_q, int P, int H, int lane,
+                                         Cost cost)
+{
+    int32_t carry = 0;
+    for (int base = 0; base < P; base += kChunk) {
+        const int j0 = base + kPerLane * lane;
+        // the lane's 8 codes in two 16-byte reads (conflict-free)
+        const int4 qa = *reinterpret_cast<const int4*>(s_q + j0);
+        const int4 qb = *reinterpret_cast<const int4*>(s_q + j0 + 4);
+        const int32_t qs[kPerLane] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+        int32_t c[kPerLane];
+#pragma unroll
+        for (int i = 0; i < kPerLane; ++i) {
+            const int v = j0 + i - 1;                     // pixel that enters at output j
+            const int32_t x = cost(qs[i], min(max(v, 0), H - 1));
+            c[i] = (unsigned)v < (unsigned)H ? x : 0;
+        }
+#pragma unroll
+        for (int i = 1; i < kPerLane; ++i) c[i] += c[i - 1];
+        int32_t tot = c[kPerLane - 1];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t t = __shfl_up_sync(0xffffffffu, tot, o);
+            if (lane >= o) tot += t;
+        }
+        const int32_t add = carry + tot - c[kPerLane - 1];   // exclusive prefix of this lane
+#pragma unroll
+        for (int h = 0; h < kPerLane; h += 4) {
+            if (j0 + h < P) {
+                int4 w = make_int4(c[h] + add, c[h + 1] + add, c[h + 2] + add, c[h + 3] + add);
+                *reinterpret_cast<int4*>(out + j0 + h) = w;
+            }
+        }
+        carry += __shfl_sync(0xffffffffu, tot, 31);
+    }
+}
 
 // Rows [row0, row0 + kRowsPerCta) of column `col`'s LUTs (row f < F: object
 // at disparity f; F: disparities; F + 1: ground; F + 2: sky), by one CTA.
@@ -86,84 +127,52 @@ __device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const 
     for (int rr = warp; rr < kRowsPerCta; rr += 8) {
         const int row = row0 + rr;
         if (row >= R) break;
-        int kind, f = 0;
-        int32_t kf = 0;
-        int32_t* out;
+        // one row kind per call, so the per-pixel cost below is branch-free
         if (row < F) {
-            kind = kObject; f = row; kf = __ldg(m.k_obj + f);
-            out = po + ((size_t)col * F + f) * P;
+            const int f = row, f16 = 16 * f;
+            const int32_t kf = __ldg(m.k_obj + f);
+            int32_t* out = po + ((size_t)col * F + f) * P;
+            if (kIntGrid) {
+                // one read of the off-line table (codes are 16 d; the unsigned
+                // clamp keeps malformed caller codes in [0, dmax])
+                const int32_t* lc = s_lc + rr * lw + lr;
+                scan_row(out, s_q, P, H, lane, [&](int32_t qv, int) {
+                    const int d = (int)(min((uint32_t)qv, (uint32_t)m.emax) >> 4);
+                    return lc[min(max(d - f, -lr), lr)];
+                });
+            } else if (kVarSigma) {
+                const int32_t* g = m.g_obj + (size_t)f * E;
+                scan_row(out, s_q, P, H, lane, [&](int32_t qv, int) {
+                    return min(m.c_out, kf + __ldg(g + min(abs(qv - f16), m.emax)));
+                });
+            } else {
+                const int es = m.esat_obj;
+                const int32_t co = m.c_out;
+                scan_row(out, s_q, P, H, lane, [&](int32_t qv, int) {
+                    return min(co, kf + s_go[min(abs(qv - f16), es)]);
+                });
+            }
         } else if (row == F) {
-            kind = kDisp; out = pd + (size_t)col * P;
+            scan_row(pd + (size_t)col * P, s_q, P, H, lane, [&](int32_t qv, int) { return qv; });
         } else if (row == F + 1) {
-            kind = kGround; out = pg + (size_t)col * P;
+            scan_row(pg + (size_t)col * P, s_q, P, H, lane, [&](int32_t qv, int v) {
+                if (kVarSigma) {
+                    const int e = min(abs(qv - __ldg(rows.fgq + v)), m.emax);
+                    return min(m.c_out, __ldg(rows.k_ground + v) + __ldg(rows.g_ground + (size_t)v * E + e));
+                }
+                const int e = min(abs(qv - __ldg(rows.fgq + v)), m.esat_ground);
+                return min(m.c_out, __ldg(rows.k_ground + v) + s_gg[e]);
+            });
         } else {
-            kind = kSky; out = ps + (size_t)col * P;
-        }
-        const int f16 = 16 * f;
-        int32_t carry = 0;
-        for (int base = 0; base < P; base += kChunk) {
-            const int j0 = base + kPerLane * lane;       // outputs j0 .. j0+7 hold sums over v < j
-            // the lane's 8 codes in two 16-byte reads (conflict-free)
-            const int4 qa = *reinterpret_cast<const int4*>(s_q + j0);
-            const int4 qb = *reinterpret_cast<const int4*>(s_q + j0 + 4);
-            const int32_t qs[kPerLane] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
-            int32_t c[kPerLane];
-#pragma unroll
-            for (int i = 0; i < kPerLane; ++i) {
-                const int v = j0 + i - 1;                 // pixel that enters at output j
-                int32_t x = 0;
-                if (v >= 0 && v < H) {
-                    const int32_t qv = qs[i];
-                    if (kind == kObject) {
-                        if (kIntGrid) {
-                            // one read of the off-line table (codes are 16 d; the
-                            // unsigned clamp keeps malformed caller codes in [0, dmax])
-                            const int d = (int)(min((uint32_t)qv, (uint32_t)m.emax) >> 4);
-                            x = s_lc[rr * lw + min(max(d - f, -lr), lr) + lr];
-                        } else if (kVarSigma) {
-                            x = min(m.c_out, kf + __ldg(m.g_obj + (size_t)f * E + min(abs(qv - f16), m.emax)));
-                        } else {
-                            x = min(m.c_out, kf + s_go[min(abs(qv - f16), m.esat_obj)]);
-                        }
-                    } else if (kind == kDisp) {
-                        x = qv;
-                    } else if (kind == kGround) {
-                        if (kVarSigma) {
-                            const int e = min(abs(qv - __ldg(rows.fgq + v)), m.emax);
-                            x = min(m.c_out, __ldg(rows.k_ground + v) + __ldg(rows.g_ground + (size_t)v * E + e));
-                        } else {
-                            const int e = min(abs(qv - __ldg(rows.fgq + v)), m.esat_ground);
-                            x = min(m.c_out, __ldg(rows.k_ground + v) + s_gg[e]);
-                        }
-                    } else {
-                        x = min(m.c_out, m.k_sky + s_gs[min(abs(qv), m.esat_sky)]);
-                    }
-                }
-                c[i] = x;
-            }
-#pragma unroll
-            for (int i = 1; i < kPerLane; ++i) c[i] += c[i - 1];
-            int32_t tot = c[kPerLane - 1];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int32_t t = __shfl_up_sync(0xffffffffu, tot, o);
-                if (lane >= o) tot += t;
-            }
-            const int32_t add = carry + tot - c[kPerLane - 1];   // exclusive prefix of this lane
-#pragma unroll
-            for (int h = 0; h < kPerLane; h += 4) {
-                if (j0 + h < P) {
-                    int4 w = make_int4(c[h] + add, c[h + 1] + add, c[h + 2] + add, c[h + 3] + add);
-                    *reinterpret_cast<int4*>(out + j0 + h) = w;
-                }
-            }
-            carry += __shfl_sync(0xffffffffu, tot, 31);
+            scan_row(ps + (size_t)col * P, s_q, P, H, lane, [&](int32_t qv, int) {
+                return min(m.c_out, m.k_sky + s_gs[min(abs(qv), m.esat_sky)]);
+            });
         }
     }
 }
 
 template <bool kIntGrid, bool kVarSigma>
-__global__ void __launch_bounds__(256) prefix_lut_kernel(LutArgs a)
+__global__ void __launch_bounds__(256, kVarSigma ? 6 : 8) prefix_lut_kernel(LutArgs a)
 {
     extern __shared__ __align__(16) int32_t sm[];
     lut_rows<kIntGrid, kVarSigma>(a, blockIdx.x, blockIdx.y * kRowsPerCta, sm);

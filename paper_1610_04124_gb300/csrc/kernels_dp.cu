@@ -87,14 +87,17 @@ __device__ __forceinline__ int thr_lo(int32_t w) { return w >> 16; }
 
 // Chain data of one block j (rows B = 32 j ..): for start i and end lane l,
 // {d, e_g} = the object data cost and the same plus the ground-below
-// penalties, and f = the rounded mean, of the cells (B + i, B + l) (tri, valid
-// for i <= l) and (B + i, B + 32 + l) (nxt).  Invalid cells hold zeros.
+// penalties, and f = the rounded mean, of the cells (B + i, B + l), i <= l
+// (tri, packed by start: slot tri_slot(i) + l - i) and (B + i, B + 32 + l)
+// (nxt, slot 32 i + l).  Cells past the column's end hold zeros.
 struct ChainBuf {
-    int2 tri[1024];
+    int2 tri[528];
     int2 nxt[1024];
-    uint8_t ftri[1024];
+    uint8_t ftri[528];
     uint8_t fnxt[1024];
 };
+// first triangle slot of start i: the starts before it own 32, 31, ... slots
+__device__ __forceinline__ int tri_slot(int i) { return (i * (65 - i)) >> 1; }
 
 struct SyncState {
     int final_blocks;            // blocks the chain warp has finalised
@@ -201,9 +204,9 @@ size_t dp_smem_bytes(int H, int ring)
 // (b, B + 32 + l) (next-block slot), two starts' loads in flight at a time.
 // Every lane runs the same instructions: an invalid cell (end row above the
 // column or below the start) is evaluated at a clamped end row, so that its
-// loads stay inside the column, and stored as zeros.  Starts past the block
-// or the column are skipped (the chain never reads them); triangle slots with
-// i > l are zeroed once per column and never written here.
+// loads stay inside the column, and stored as zeros (cells below the start
+// are not stored).  Starts past the block or the column are skipped (the
+// chain never reads them).
 __device__ __forceinline__ void gather_chain(ChainBuf* cb, int B, int H, int P, const int32_t* __restrict__ po_col,
                                              const int32_t* s_pd8, const int32_t* s_thr, const uint2* s_div,
                                              int dmax, int32_t pen_grav, int32_t pen_div, int w, int nw, int lane)
@@ -245,8 +248,9 @@ __device__ __forceinline__ void gather_chain(ChainBuf* cb, int B, int H, int P, 
                 const int32_t g0 = ok0 ? (f0 > fhi ? pen_grav : 0) + (f0 < flo ? pen_div : 0) : 0;
                 const int32_t g1 = in1 ? (f1 > fhi ? pen_grav : 0) + (f1 < flo ? pen_div : 0) : 0;
                 if (i <= lane) {
-                    cb->tri[i * 32 + lane] = make_int2(d0, d0 + g0);
-                    cb->ftri[i * 32 + lane] = (uint8_t)f0;
+                    const int e = tri_slot(i) + lane - i;
+                    cb->tri[e] = make_int2(d0, d0 + g0);
+                    cb->ftri[e] = (uint8_t)f0;
                 }
                 cb->nxt[i * 32 + lane] = make_int2(d1, d1 + g1);
                 cb->fnxt[i * 32 + lane] = (uint8_t)f1;
@@ -258,8 +262,7 @@ __device__ __forceinline__ void gather_chain(ChainBuf* cb, int B, int H, int P, 
 // Solves column `col` of frame `a` with all NW warps of the CTA (one chain
 // warp, NW - 1 bulk warps); `sm` is the CTA's dynamic shared memory
 // (dp_smem_bytes with the same ring, 2 or 3 chain buffers).  Every warp
-// returns from here; the caller synchronises
-// before reusing `sm`.
+// returns from here; the caller synchronises before reusing `sm`.
 template <int NW, bool kStdTrans>
 __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const int ring, int32_t* sm)
 {
@@ -377,29 +380,27 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
         if (kv) { runv[k] = run; runbfv[k] = runbf; }
     };
 
-    // the triangle slots with start above end are never gathered: zero them once
-    for (int x = threadIdx.x; x < ring * 1024; x += kThreads) {
-        const int e = x & 1023;
-        if ((e >> 5) > (e & 31)) {
-            s_cb[x >> 10].tri[e] = make_int2(0, 0);
-            s_cb[x >> 10].ftri[e] = 0;
-        }
-    }
-    __syncthreads();
-
     if (warp != chain) {
         // ---------------------------------------------------------------- bulk warps
         // End-row block c receives c - 1 tiles, split by start block into
         // kSlots partial minima (t = s mod kSlots) so that two warps share a
         // block's sequence of tiles.  The (block, slot) items are dealt, largest
-        // block first, to the bulk warps in snake order (rounds of kBulk items,
+        // block first, to the tile warps in snake order (rounds of kTile items,
         // alternating direction), which keeps the per-warp work balanced; lane l
-        // of a bulk warp holds its round-l item and the next start block due.
-        const int snake = (lane & 1) ? kBulk - 1 - bulk_id : bulk_id;
-        const int item = lane * kBulk + snake;
+        // of a tile warp holds its round-l item and the next start block due.
+        // The bulk warps that share the chain warp's scheduler (warp index
+        // congruent to the chain's mod 4: bulk ids 3, 7, 11) take no tiles, only
+        // their share of the gathers, so the chain's dependent steps are not
+        // starved of issue slots there.
+        constexpr int kTile = kBulk - (NW / 4 - 1);
+        static_assert(32 * kTile >= kSlots * (kMaxBlocks - 2), "every (block, slot) item has a tile warp");
+        const bool quiet = ((bulk_id + 1) & 3) == 0;
+        const int tile_id = bulk_id - ((bulk_id + 1) >> 2);
+        const int snake = (lane & 1) ? kTile - 1 - tile_id : tile_id;
+        const int item = lane * kTile + snake;
         const int my_c = NB - 1 - item / kSlots;
         int my_t = item % kSlots;                             // next start block of the item
-        const bool mine = my_c >= 2;
+        const bool mine = !quiet && my_c >= 2;
         // pending work, earliest deadline first: the next tile of the lowest
         // owned end-row block whose start block is final, or this warp's share
         // of the chain data of block next_g (its ring slot is free once block
@@ -492,8 +493,11 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
             StepIn x;
             x.gs0 = s_gs[B + i];
             x.gs1 = s_gs[B + i + 1];
-            x.de = cb->tri[i * 32 + lane];
-            x.ff = cb->ftri[i * 32 + lane];
+            // a lane below the start reads the cell (i, i): its rows are final,
+            // so what it then computes is never used
+            const int e = tri_slot(i) + max(lane - i, 0);
+            x.de = cb->tri[e];
+            x.ff = cb->ftri[e];
             x.de2 = cb->nxt[i * 32 + lane];
             x.ff2 = cb->fnxt[i * 32 + lane];
             return x;

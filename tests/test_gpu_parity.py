@@ -150,6 +150,21 @@ def test_pipeline_ragged_heights(H):
     assert_frame_equal(out, fr, H, lp.max_stixels_per_col)
 
 
+@pytest.mark.parametrize("ncols,H", [(153, 1), (153, 97), (200, 33), (257, 440), (304, 450), (304, 500)])
+def test_pipeline_column_counts_between_one_and_two_per_sm(ncols, H):
+    """Frames with more columns than SMs (up to twice as many on a 152-SM
+    part) run each column on a two-CTA cluster; every column must still equal
+    the oracle, at ragged heights and at the tallest height that form takes."""
+    cam = scenes.Camera(ncols * 5, H, stixel_width=5, dmax=64, horizon_row=H // 3, baseline_m=0.4,
+                        camera_height_m=1.2)
+    sc = scenes.make_scene(cam, 900 + ncols + H, n_obstacles=(3, 12), span_cols=(1, 12))
+    lp, op = both_params(cam, cost_order=2.0)
+    out, err = run_frame(lp, sc.disparity)
+    fr = oracle.frame(op, sc.disparity, cap=lp.max_stixels_per_col)
+    assert err == (S.ERR_CAPACITY if (fr.counts > lp.max_stixels_per_col).any() else 0)
+    assert_frame_equal(out, fr, H, lp.max_stixels_per_col)
+
+
 @pytest.mark.parametrize("variant", [
     dict(reduce_mode=1),
     dict(cost_order=0.0),

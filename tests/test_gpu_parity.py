@@ -150,6 +150,29 @@ def test_pipeline_ragged_heights(H):
     assert_frame_equal(out, fr, H, lp.max_stixels_per_col)
 
 
+@pytest.mark.parametrize("s", [3, 5, 7])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_compute_equals_the_staged_pipeline(s, mode):
+    """On hostile pixels (NaN, inf, negatives, beyond dmax, on and off the
+    1/16 grid) stixels_compute must equal the staged reduce -> LUT -> solve
+    entry points, and both the oracle."""
+    rng = np.random.default_rng(40 + 10 * s + mode)
+    H, ncols, dmax = 97, 61, 64
+    D = nasty_image(rng, H, ncols * s, dmax)
+    cam = scenes.Camera(ncols * s, H, stixel_width=s, dmax=dmax, horizon_row=30, baseline_m=0.4, camera_height_m=1.0)
+    h = S.Stixels(S.default_params(cam, reduce_mode=mode))
+    d = cuda(D)
+    fused = S.Stixels.to_host(h.compute(d))
+    q = h.reduce(d)
+    staged = S.Stixels.to_host(h.solve(*h.build_luts(q, H, ncols), H, ncols))
+    torch.cuda.synchronize()
+    for a, b in zip(fused, staged):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
+    fr = oracle.frame(oracle.make_params(cam, reduce_mode=mode), D, cap=h.params.max_stixels_per_col)
+    assert_frame_equal(fused, fr, H, h.params.max_stixels_per_col)
+    h.close()
+
+
 @pytest.mark.parametrize("ncols,H", [(153, 1), (153, 97), (200, 33), (257, 440), (304, 450), (304, 500)])
 def test_pipeline_column_counts_between_one_and_two_per_sm(ncols, H):
     """Frames with more columns than SMs (up to twice as many on a 152-SM

@@ -21,6 +21,34 @@ constexpr int32_t kBig = 1 << 29;                // infeasible / forbidden
 constexpr int32_t kFiniteBudget = 1 << 28;       // |finite cost| bound checked by the host
 constexpr int32_t kNoneCode = 3;
 
+// floor(x / (16 n)) for 0 <= x < 2^31 via a multiply-high: M = ceil(2^(32+s) / d),
+// s = floor(log2 d), d = 16 n (M = 2^31, s - 1 when d is a power of two).
+// The constants for n = 1 .. STIXELS_MAX_HEIGHT are built at compile time;
+// each DP kernel's translation unit holds one copy in device memory and every
+// CTA copies the ones its column height needs into shared memory.
+struct alignas(8) DivMagic {
+    uint32_t m, s;
+};
+struct DivTable {
+    DivMagic v[STIXELS_MAX_HEIGHT + 1];
+};
+constexpr DivTable make_div_table()
+{
+    DivTable t{};
+    for (int n = 1; n <= STIXELS_MAX_HEIGHT; ++n) {
+        const uint32_t d = 16u * (uint32_t)n;
+        int s = 0;
+        while ((d >> (s + 1)) != 0) ++s;
+        if ((d & (d - 1)) == 0) {
+            t.v[n] = DivMagic{1u << 31, (uint32_t)(s - 1)};
+        } else {
+            const unsigned long long num = 1ull << (32 + s);
+            t.v[n] = DivMagic{(uint32_t)((num + d - 1) / d), (uint32_t)s};
+        }
+    }
+    return t;
+}
+
 // Per-handle model, resident on the device (the "offline" LUTs of Sec. 3.4)
 // plus the scalars every kernel needs.  Passed to kernels by value.
 struct ModelDev {

@@ -108,32 +108,6 @@ struct SyncState {
 
 __device__ __forceinline__ int32_t min3(int32_t a, int32_t b, int32_t c) { return min(min(a, b), c); }
 
-// floor(x / (16 n)) for 0 <= x < 2^31 via a multiply-high: M = ceil(2^(32+s) / d),
-// s = floor(log2 d), d = 16 n (M = 2^31, s - 1 when d is a power of two).
-// The constants for n = 1 .. STIXELS_MAX_HEIGHT are built at compile time;
-// each CTA copies the ones its column height needs into shared memory.
-struct alignas(8) DivMagic {
-    uint32_t m, s;
-};
-struct DivTable {
-    DivMagic v[STIXELS_MAX_HEIGHT + 1];
-};
-constexpr DivTable make_div_table()
-{
-    DivTable t{};
-    for (int n = 1; n <= STIXELS_MAX_HEIGHT; ++n) {
-        const uint32_t d = 16u * (uint32_t)n;
-        int s = 0;
-        while ((d >> (s + 1)) != 0) ++s;
-        if ((d & (d - 1)) == 0) {
-            t.v[n] = DivMagic{1u << 31, (uint32_t)(s - 1)};
-        } else {
-            const unsigned long long num = 1ull << (32 + s);
-            t.v[n] = DivMagic{(uint32_t)((num + d - 1) / d), (uint32_t)s};
-        }
-    }
-    return t;
-}
 __device__ const DivTable kDivTable = make_div_table();
 
 // Rounded mean disparity of a stixel of n rows from x = S + 8 n, clamped to

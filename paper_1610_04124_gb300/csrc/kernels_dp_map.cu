@@ -15,11 +15,16 @@
 // library; a candidate is one 64-bit key (cost | code) << 32 | start << 8 | f,
 // so one integer minimum orders them (shared-memory atomicMin per object bin).
 //
-// Parallel scheme (correctness first): one 256-thread CTA per column, rows in
-// order; at row k the threads take the starts b <= k, the object candidates
-// go to their bin f' by atomic minimum, ground and sky by warp minima then one
-// atomic each; then the CTA turns row k's bins into prefix / suffix minima
-// (a block scan over f) in global scratch, which row k + 1 onwards reads.
+// Parallel scheme: one 256-thread CTA per column, rows in blocks of 32.  For
+// block j (rows K0 ..): phase A, every warp evaluates the starts b < K0 (their
+// rows are final) for the block's rows, lane = row, warps over the starts;
+// object candidates go to their bin (row, f') in shared memory by atomic
+// minimum (a lane merges consecutive candidates of the same f' first), ground
+// and sky stay in registers until one atomic per lane.  Phase B, one warp,
+// the block's rows in order: row k adds its starts inside the block (lane =
+// start), then the warp turns the row's bins into prefix / suffix minima over
+// f (one lane owns 8 consecutive f) in global scratch, which the rows above
+// read.  Three CTA barriers per block instead of several per row.
 #include <climits>
 
 #include "internal.h"
@@ -28,6 +33,7 @@ namespace stx {
 namespace {
 
 constexpr unsigned long long kNoKey = ~0ull;
+__device__ const DivTable kDivTable = make_div_table();
 
 __device__ __forceinline__ unsigned long long make_key(int32_t cost_code, int b, int f)
 {
@@ -53,167 +59,244 @@ __device__ __forceinline__ unsigned long long warp_min(unsigned long long x)
     return x;
 }
 
-struct MapScratch {
-    unsigned long long* keyo;   // [H][F] best key of each object state
-    unsigned long long* pre;    // [H][F] (min over f' <= x of value) << 32 | argmin f'
-    unsigned long long* suf;    // [H][F] (min over f' >= x) << 32 | argmin f'
+constexpr int kMapRows = 32;                 // rows per block
+constexpr int kMapWarps = 8;
+
+// What one column's candidate evaluation needs (shared memory and the LUT).
+struct MapCol {
+    const int32_t* s_pd8;        // [H + 1] PD[v] + 8 v
+    const int32_t* s_pg;         // [H + 1]
+    const int32_t* s_ps;         // [H + 1]
+    const int32_t* s_fhi;        // [H] gravity iff f > fhi
+    const int32_t* s_flo;        // [H] diving iff f < flo
+    const uint2* s_div;          // [H + 1] rounded-mean constants
+    const unsigned long long* s_kg;   // [H] ground state keys
+    const unsigned long long* s_ks;   // [H] sky state keys
+    const unsigned long long* s_bo;   // [H] best object state of each row, value << 32 | f
+    const unsigned long long* pre;    // [H][F] (min over f' <= x of value) << 32 | argmin f'
+    const unsigned long long* suf;    // [H][F] (min over f' >= x) << 32 | argmin f'
+    const int32_t* po;           // the column's object LUT, [F][P]
+    int P, F, dmax, ord_off;
+    int32_t T_oo, T_og, T_os, T_go, T_gg, T_gs, T_so, T_sg, T_ss;
 };
 
-__global__ void __launch_bounds__(256) stixel_map_kernel(DpArgs a, unsigned long long* scratch)
+// The candidate keys of the stixel [b, k]: object (for the state (k, fo)),
+// ground and sky; every key is (cost | previous class code) << 32 | b << 8 |
+// previous object f, so one integer minimum is the tie order.
+__device__ __forceinline__ void map_cands(const MapCol& c, const ModelDev& m, int b, int k, int& fo,
+                                          unsigned long long& ko, unsigned long long& kg, unsigned long long& ks)
+{
+    const int n = k - b + 1;
+    const uint2 dm = c.s_div[n];
+    fo = (int)min(__umulhi((uint32_t)(c.s_pd8[k + 1] - c.s_pd8[b]), dm.x) >> dm.y, (uint32_t)c.dmax);
+    const int32_t* row = c.po + (size_t)fo * c.P;
+    const int32_t d_o = __ldg(row + k + 1) - __ldg(row + b);
+    const int32_t d_g = c.s_pg[k + 1] - c.s_pg[b], d_s = c.s_ps[k + 1] - c.s_ps[b];
+    if (b == 0) {
+        ko = make_key(d_o + m.first[0] + kNoneCode, 0, 0);
+        kg = make_key(d_g + m.first[1] + kNoneCode, 0, 0);
+        ks = make_key(d_s + m.first[2] + kNoneCode, 0, 0);
+        return;
+    }
+    const size_t rw = (size_t)(b - 1) * c.F;
+    // object above object: free for previous f >= fo - ord_off, penalised below
+    const int x = fo - c.ord_off;
+    ko = kNoKey;
+    if (x <= c.F - 1) {
+        const unsigned long long su = c.suf[rw + max(x, 0)];
+        const int32_t v = min((int32_t)(su >> 32), kBig);
+        const unsigned long long t = make_key(d_o + v + c.T_oo, b, (int)(su & 255));
+        ko = t < ko ? t : ko;
+    }
+    if (x - 1 >= 0) {
+        const unsigned long long pr = c.pre[rw + min(x - 1, c.F - 1)];
+        const int32_t v = min((int32_t)(pr >> 32), kBig);
+        const unsigned long long t = make_key(d_o + v + c.T_oo + m.pen_ord, b, (int)(pr & 255));
+        ko = t < ko ? t : ko;
+    }
+    const int32_t vg = state_value(c.s_kg[b - 1]), vs = state_value(c.s_ks[b - 1]);
+    const int32_t gpen = (fo > c.s_fhi[b] ? m.pen_grav : 0) + (fo < c.s_flo[b] ? m.pen_div : 0);
+    const unsigned long long cg = make_key(d_o + vg + c.T_og + gpen, b, 0);
+    const unsigned long long cs = make_key(d_o + vs + c.T_os, b, 0);
+    ko = cg < ko ? cg : ko;
+    ko = cs < ko ? cs : ko;
+    // ground / sky above: the best object of row b-1 (any f), ground, sky
+    const unsigned long long mo = c.s_bo[b - 1];
+    const int32_t vo = min((int32_t)(mo >> 32), kBig);
+    const int fm = (int)(mo & 255);
+    kg = make_key(d_g + vo + c.T_go, b, fm);
+    const unsigned long long g2 = make_key(d_g + vg + c.T_gg, b, 0), g3 = make_key(d_g + vs + c.T_gs, b, 0);
+    kg = g2 < kg ? g2 : kg;
+    kg = g3 < kg ? g3 : kg;
+    ks = make_key(d_s + vo + c.T_so, b, fm);
+    const unsigned long long s2 = make_key(d_s + vg + c.T_sg, b, 0), s3 = make_key(d_s + vs + c.T_ss, b, 0);
+    ks = s2 < ks ? s2 : ks;
+    ks = s3 < ks ? s3 : ks;
+}
+
+__global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, unsigned long long* scratch)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int H = a.H, P = a.P, F = a.F;
     const int col = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const ModelDev& m = a.m;
     const size_t HF = (size_t)H * F;
-    MapScratch sc;
-    sc.keyo = scratch + (size_t)col * 3 * HF;
-    sc.pre = sc.keyo + HF;
-    sc.suf = sc.pre + HF;
+    unsigned long long* keyo = scratch + (size_t)col * 3 * HF;   // [H][F] best key of each object state
+    unsigned long long* pre = keyo + HF;
+    unsigned long long* suf = pre + HF;
 
-    int32_t* s_pd = reinterpret_cast<int32_t*>(smem);                 // [H + 1]
-    int32_t* s_pg = s_pd + (H + 1);                                   // [H + 1]
-    int32_t* s_ps = s_pg + (H + 1);                                   // [H + 1]
-    int32_t* s_fhi = s_ps + (H + 1);                                  // [H]
-    int32_t* s_flo = s_fhi + H;                                       // [H]
-    unsigned long long* s_kg = reinterpret_cast<unsigned long long*>(s_flo + H + ((2 * H + 3 * (H + 1)) & 1));  // [H]
-    unsigned long long* s_ks = s_kg + H;                              // [H]
-    unsigned long long* s_bin = s_ks + H;                             // [F]
-    unsigned long long* s_red = s_bin + F;                            // [8] warp partials
-    __shared__ unsigned long long s_rowg, s_rows;
+    unsigned long long* s_kg = reinterpret_cast<unsigned long long*>(smem);      // [H]
+    unsigned long long* s_ks = s_kg + H;                                         // [H]
+    unsigned long long* s_bo = s_ks + H;                                         // [H]
+    unsigned long long* s_bin = s_bo + H;                                        // [kMapRows][F]
+    unsigned long long* s_gbin = s_bin + (size_t)kMapRows * F;                   // [kMapRows]
+    unsigned long long* s_sbin = s_gbin + kMapRows;                              // [kMapRows]
+    uint2* s_div = reinterpret_cast<uint2*>(s_sbin + kMapRows);                  // [H + 1]
+    int32_t* s_pd8 = reinterpret_cast<int32_t*>(s_div + H + 1);                  // [H + 1]
+    int32_t* s_pg = s_pd8 + (H + 1);                                             // [H + 1]
+    int32_t* s_ps = s_pg + (H + 1);                                              // [H + 1]
+    int32_t* s_fhi = s_ps + (H + 1);                                             // [H]
+    int32_t* s_flo = s_fhi + H;                                                  // [H]
 
-    const int32_t* po_col = a.po + (size_t)col * F * P;
     for (int v = tid; v <= H; v += blockDim.x) {
-        s_pd[v] = a.pd[(size_t)col * P + v];
+        s_pd8[v] = a.pd[(size_t)col * P + v] + 8 * v;
         s_pg[v] = a.pg[(size_t)col * P + v];
         s_ps[v] = a.ps[(size_t)col * P + v];
+        if (v >= 1) {
+            const DivMagic dm = kDivTable.v[v];
+            s_div[v] = make_uint2(dm.m, dm.s);
+        }
         if (v < H) {
             const int32_t g = a.rows.fgq[v];
             s_fhi[v] = (g + m.eps_g) >> 4;            // gravity iff f > fhi
             s_flo[v] = -((m.eps_d - g) >> 4);         // diving iff f < flo
         }
     }
-    __syncthreads();
-    const int ord_off = m.eps_o >> 4;               // ordering iff f' > f + ord_off
-    const int32_t T_oo = m.trans[0][0], T_og = m.trans[0][1] + 1, T_os = m.trans[0][2] + 2;
-    const int32_t T_go = m.trans[1][0], T_gg = m.trans[1][1] + 1, T_gs = m.trans[1][2] + 2;
-    const int32_t T_so = m.trans[2][0], T_sg = m.trans[2][1] + 1, T_ss = m.trans[2][2] + 2;
+    MapCol c;
+    c.s_pd8 = s_pd8; c.s_pg = s_pg; c.s_ps = s_ps; c.s_fhi = s_fhi; c.s_flo = s_flo; c.s_div = s_div;
+    c.s_kg = s_kg; c.s_ks = s_ks; c.s_bo = s_bo; c.pre = pre; c.suf = suf;
+    c.po = a.po + (size_t)col * F * P;
+    c.P = P; c.F = F; c.dmax = m.dmax; c.ord_off = m.eps_o >> 4;    // ordering iff f' > f + ord_off
+    c.T_oo = m.trans[0][0]; c.T_og = m.trans[0][1] + 1; c.T_os = m.trans[0][2] + 2;
+    c.T_go = m.trans[1][0]; c.T_gg = m.trans[1][1] + 1; c.T_gs = m.trans[1][2] + 2;
+    c.T_so = m.trans[2][0]; c.T_sg = m.trans[2][1] + 1; c.T_ss = m.trans[2][2] + 2;
 
-    for (int k = 0; k < H; ++k) {
-        for (int f = tid; f < F; f += blockDim.x) s_bin[f] = kNoKey;
-        if (tid == 0) { s_rowg = kNoKey; s_rows = kNoKey; }
-        __syncthreads();
-        unsigned long long bg = kNoKey, bs = kNoKey;   // this thread's best ground / sky candidates
-        for (int b = tid; b <= k; b += blockDim.x) {
-            const int n = k - b + 1;
-            const int32_t S = s_pd[k + 1] - s_pd[b];
-            const int fo = min((S + 8 * n) / (16 * n), m.dmax);
-            const int32_t d_o = __ldg(po_col + (size_t)fo * P + k + 1) - __ldg(po_col + (size_t)fo * P + b);
-            const int32_t d_g = s_pg[k + 1] - s_pg[b], d_s = s_ps[k + 1] - s_ps[b];
-            unsigned long long ko, kg, ks;
-            if (b == 0) {
-                ko = make_key(d_o + m.first[0] + kNoneCode, 0, 0);
-                kg = make_key(d_g + m.first[1] + kNoneCode, 0, 0);
-                ks = make_key(d_s + m.first[2] + kNoneCode, 0, 0);
-            } else {
-                const size_t row = (size_t)(b - 1) * F;
-                // object above object: free for previous f >= fo - ord_off, penalised below
-                const int x = fo - ord_off;
-                ko = kNoKey;
-                if (x <= F - 1) {
-                    const unsigned long long su = sc.suf[row + max(x, 0)];
-                    const int32_t v = min((int32_t)(su >> 32), kBig);
-                    const unsigned long long c = make_key(d_o + v + T_oo, b, (int)(su & 255));
-                    ko = c < ko ? c : ko;
+    const int NB = (H + kMapRows - 1) / kMapRows;
+    constexpr int kPer = 8;                       // object states per lane in the row scan (F <= 256)
+    for (int j = 0; j < NB; ++j) {
+        const int K0 = kMapRows * j, nb = min(kMapRows, H - K0);
+        for (int i = tid; i < kMapRows * F; i += blockDim.x) s_bin[i] = kNoKey;
+        if (tid < kMapRows) { s_gbin[tid] = kNoKey; s_sbin[tid] = kNoKey; }
+        __syncthreads();                          // also: the rows of block j-1 are visible
+
+        // Phase A, every warp: the starts of earlier blocks (their rows are
+        // final) for the rows of this block, lane = row K0 + lane, warps over
+        // the starts.  A lane keeps its object candidates for one bin until f
+        // changes (consecutive starts mostly share f), its ground / sky minima
+        // in registers.
+        if (lane < nb) {
+            const int k = K0 + lane;
+            unsigned long long rg = kNoKey, rs = kNoKey, ck = kNoKey;
+            int cf = -1;
+            for (int b = warp; b < K0; b += kMapWarps) {
+                int fo;
+                unsigned long long ko, kg, ks;
+                map_cands(c, m, b, k, fo, ko, kg, ks);
+                rg = kg < rg ? kg : rg;
+                rs = ks < rs ? ks : rs;
+                if (fo != cf) {
+                    if (cf >= 0) atomicMin(&s_bin[lane * F + cf], ck);
+                    cf = fo;
+                    ck = ko;
+                } else {
+                    ck = ko < ck ? ko : ck;
                 }
-                if (x - 1 >= 0) {
-                    const unsigned long long pr = sc.pre[row + min(x - 1, F - 1)];
-                    const int32_t v = min((int32_t)(pr >> 32), kBig);
-                    const unsigned long long c = make_key(d_o + v + T_oo + m.pen_ord, b, (int)(pr & 255));
-                    ko = c < ko ? c : ko;
-                }
-                const int32_t vg = state_value(s_kg[b - 1]), vs = state_value(s_ks[b - 1]);
-                const int32_t gpen = (fo > s_fhi[b] ? m.pen_grav : 0) + (fo < s_flo[b] ? m.pen_div : 0);
-                const unsigned long long cg = make_key(d_o + vg + T_og + gpen, b, 0);
-                const unsigned long long cs = make_key(d_o + vs + T_os, b, 0);
-                ko = cg < ko ? cg : ko;
-                ko = cs < ko ? cs : ko;
-                // ground / sky above: the best object of row b-1 (any f), ground, sky
-                const unsigned long long mo = sc.pre[row + F - 1];
-                const int32_t vo = min((int32_t)(mo >> 32), kBig);
-                const int fm = (int)(mo & 255);
-                kg = make_key(d_g + vo + T_go, b, fm);
-                const unsigned long long g2 = make_key(d_g + vg + T_gg, b, 0), g3 = make_key(d_g + vs + T_gs, b, 0);
-                kg = g2 < kg ? g2 : kg;
-                kg = g3 < kg ? g3 : kg;
-                ks = make_key(d_s + vo + T_so, b, fm);
-                const unsigned long long s2 = make_key(d_s + vg + T_sg, b, 0), s3 = make_key(d_s + vs + T_ss, b, 0);
-                ks = s2 < ks ? s2 : ks;
-                ks = s3 < ks ? s3 : ks;
             }
-            atomicMin(&s_bin[fo], ko);
-            bg = kg < bg ? kg : bg;
-            bs = ks < bs ? ks : bs;
-        }
-        bg = warp_min(bg);
-        bs = warp_min(bs);
-        if (lane == 0) {
-            atomicMin(&s_rowg, bg);
-            atomicMin(&s_rows, bs);
+            if (cf >= 0) atomicMin(&s_bin[lane * F + cf], ck);
+            if (K0 > 0) {
+                atomicMin(&s_gbin[lane], rg);
+                atomicMin(&s_sbin[lane], rs);
+            }
         }
         __syncthreads();
-        // row k: object keys, and their prefix / suffix minima over f (value << 32 | f)
-        const size_t row = (size_t)k * F;
-        for (int base = 0; base < F; base += blockDim.x) {
-            const int f = base + tid;
-            if (f < F) sc.keyo[row + f] = s_bin[f];
-        }
-        if (tid == 0) {
-            s_kg[k] = s_rowg;
-            s_ks[k] = s_rows;
-        }
-        // F <= 256 = blockDim: one value per thread, block-wide inclusive scans
-        const int f = tid;
-        const unsigned long long mine = f < F ? ((unsigned long long)(uint32_t)state_value(s_bin[f]) << 32) | f : kNoKey;
-        unsigned long long pmin = mine, smin = mine;
+
+        // Phase B, warp 0: the block's rows in order; row k adds its starts
+        // within the block (lane = start K0 + lane <= k), then its object
+        // states become prefix / suffix minima over f for the rows above.
+        if (warp == 0) {
+            for (int r = 0; r < nb; ++r) {
+                const int k = K0 + r;
+                unsigned long long kg = kNoKey, ks = kNoKey;
+                if (lane <= r) {
+                    int fo;
+                    unsigned long long ko;
+                    map_cands(c, m, K0 + lane, k, fo, ko, kg, ks);
+                    atomicMin(&s_bin[r * F + fo], ko);
+                }
+                kg = warp_min(kg);
+                ks = warp_min(ks);
+                __syncwarp();
+                const unsigned long long* bin = s_bin + (size_t)r * F;
+                // lane l owns f = kPer l .. kPer l + kPer - 1: local prefix / suffix, then warp scans
+                unsigned long long pv[kPer], sv[kPer];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long up = __shfl_up_sync(0xffffffffu, pmin, o);
-            const unsigned long long dn = __shfl_down_sync(0xffffffffu, smin, o);
-            if (lane >= o) pmin = up < pmin ? up : pmin;
-            if (lane + o < 32) smin = dn < smin ? dn : smin;
+                for (int i = 0; i < kPer; ++i) {
+                    const int f = kPer * lane + i;
+                    pv[i] = f < F ? ((unsigned long long)(uint32_t)state_value(bin[f]) << 32) | (unsigned)f : kNoKey;
+                    sv[i] = pv[i];
+                }
+#pragma unroll
+                for (int i = 1; i < kPer; ++i) pv[i] = pv[i - 1] < pv[i] ? pv[i - 1] : pv[i];
+#pragma unroll
+                for (int i = kPer - 2; i >= 0; --i) sv[i] = sv[i + 1] < sv[i] ? sv[i + 1] : sv[i];
+                unsigned long long pt = pv[kPer - 1], st = sv[0];       // lane totals
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned long long up = __shfl_up_sync(0xffffffffu, pt, o);
+                    const unsigned long long dn = __shfl_down_sync(0xffffffffu, st, o);
+                    if (lane >= o) pt = up < pt ? up : pt;
+                    if (lane + o < 32) st = dn < st ? dn : st;
+                }
+                // exclusive carries from the lanes below / above
+                unsigned long long pc = __shfl_up_sync(0xffffffffu, pt, 1);
+                unsigned long long sc = __shfl_down_sync(0xffffffffu, st, 1);
+                if (lane == 0) pc = kNoKey;
+                if (lane == 31) sc = kNoKey;
+                const size_t rw = (size_t)k * F;
+#pragma unroll
+                for (int i = 0; i < kPer; ++i) {
+                    const int f = kPer * lane + i;
+                    if (f < F) {
+                        keyo[rw + f] = bin[f];
+                        pre[rw + f] = pc < pv[i] ? pc : pv[i];
+                        suf[rw + f] = sc < sv[i] ? sc : sv[i];
+                    }
+                }
+                if (lane == 0) {
+                    s_kg[k] = kg < s_gbin[r] ? kg : s_gbin[r];
+                    s_ks[k] = ks < s_sbin[r] ? ks : s_sbin[r];
+                }
+                // the row's best object state (over every f): the last prefix
+                const unsigned long long best = __shfl_sync(0xffffffffu, pt, 31);
+                if (lane == 0) s_bo[k] = best;
+                __threadfence_block();
+                __syncwarp();
+            }
         }
-        __syncthreads();                              // s_bin no longer read below: reuse s_red
-        if (lane == 31) s_red[warp] = pmin;           // warp totals for the prefix
-        __syncthreads();
-        unsigned long long pcarry = kNoKey;
-        for (int w = 0; w < warp; ++w) pcarry = s_red[w] < pcarry ? s_red[w] : pcarry;
-        __syncthreads();
-        if (lane == 0) s_red[warp] = smin;            // warp totals for the suffix
-        __syncthreads();
-        unsigned long long scarry = kNoKey;
-        for (int w = warp + 1; w < 8; ++w) scarry = s_red[w] < scarry ? s_red[w] : scarry;
-        pmin = pcarry < pmin ? pcarry : pmin;
-        smin = scarry < smin ? scarry : smin;
-        if (f < F) {
-            sc.pre[row + f] = pmin;
-            sc.suf[row + f] = smin;
-        }
-        __threadfence_block();
-        __syncthreads();
+        __syncthreads();                          // warp 0 is done with the bins before they are reset
     }
 
     // top row (lexicographic cost, class, f) and backtracking
     if (tid == 0) {
-        int c = -1, fb = 0;
+        int cc0 = -1, fb = 0;
         int32_t best = kBig;
         for (int f = 0; f < F; ++f) {
-            const int32_t v = state_value(sc.keyo[(size_t)(H - 1) * F + f]);
-            if (v < best) { best = v; c = 0; fb = f; }
+            const int32_t v = state_value(keyo[(size_t)(H - 1) * F + f]);
+            if (v < best) { best = v; cc0 = 0; fb = f; }
         }
-        if (state_value(s_kg[H - 1]) < best) { best = state_value(s_kg[H - 1]); c = 1; fb = 0; }
-        if (state_value(s_ks[H - 1]) < best) { best = state_value(s_ks[H - 1]); c = 2; fb = 0; }
-        if (c < 0 || best >= kBig) {
+        if (state_value(s_kg[H - 1]) < best) { best = state_value(s_kg[H - 1]); cc0 = 1; fb = 0; }
+        if (state_value(s_ks[H - 1]) < best) { best = state_value(s_ks[H - 1]); cc0 = 2; fb = 0; }
+        if (cc0 < 0 || best >= kBig) {
             a.counts[col] = 0;
             if (a.cost) a.cost[col] = __int_as_float(0x7f800000);
             if (a.cost_fixed) a.cost_fixed[col] = kBig;
@@ -222,8 +305,8 @@ __global__ void __launch_bounds__(256) stixel_map_kernel(DpArgs a, unsigned long
         }
         // count, then write bottom -> top
         int n = 0;
-        for (int k = H - 1, cc = c, ff = fb; k >= 0 && cc < 3 && n <= H;) {
-            const unsigned long long key = cc == 0 ? sc.keyo[(size_t)k * F + ff] : (cc == 1 ? s_kg[k] : s_ks[k]);
+        for (int k = H - 1, cc = cc0, ff = fb; k >= 0 && cc < 3 && n <= H;) {
+            const unsigned long long key = cc == 0 ? keyo[(size_t)k * F + ff] : (cc == 1 ? s_kg[k] : s_ks[k]);
             ++n;
             const int b = key_start(key);
             if (b > k) break;
@@ -233,12 +316,12 @@ __global__ void __launch_bounds__(256) stixel_map_kernel(DpArgs a, unsigned long
         }
         int idx = n - 1;
         stixel_t* out = a.stixels + (size_t)col * a.cap;
-        for (int k = H - 1, cc = c, ff = fb; k >= 0 && cc < 3 && idx >= 0; --idx) {
-            const unsigned long long key = cc == 0 ? sc.keyo[(size_t)k * F + ff] : (cc == 1 ? s_kg[k] : s_ks[k]);
+        for (int k = H - 1, cc = cc0, ff = fb; k >= 0 && cc < 3 && idx >= 0; --idx) {
+            const unsigned long long key = cc == 0 ? keyo[(size_t)k * F + ff] : (cc == 1 ? s_kg[k] : s_ks[k]);
             const int b = key_start(key);
             if (idx < a.cap) {
                 const int nrows = k - b + 1;
-                const int32_t S = s_pd[k + 1] - s_pd[b];
+                const int32_t S = s_pd8[k + 1] - s_pd8[b] - 8 * nrows;
                 stixel_t st;
                 st.row_top = (int16_t)(H - 1 - k);
                 st.row_bottom = (int16_t)(H - 1 - b);
@@ -262,8 +345,8 @@ __global__ void __launch_bounds__(256) stixel_map_kernel(DpArgs a, unsigned long
 
 size_t map_smem_bytes(int H, int F)
 {
-    const size_t ints = 3 * (size_t)(H + 1) + 2 * (size_t)H;
-    return sizeof(int32_t) * (ints + (ints & 1)) + sizeof(unsigned long long) * (2 * (size_t)H + F + 8);
+    return sizeof(unsigned long long) * (3 * (size_t)H + (size_t)kMapRows * F + 2 * kMapRows) +
+           sizeof(uint2) * (size_t)(H + 1) + sizeof(int32_t) * (3 * (size_t)(H + 1) + 2 * (size_t)H);
 }
 
 }  // namespace

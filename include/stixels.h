@@ -121,7 +121,9 @@ typedef struct stixels_params {
     int32_t global_map;        /* 0 = the paper's DP (Eq. 6: one best stixel per row and class, so the
                                   ordering prior is judged against that stixel only); 1 = the global MAP
                                   with the ordering prior exact (object states carry their disparity;
-                                  per-frame path only, 24 H (dmax+1) bytes of workspace per column) */
+                                  per-frame path only, 24 H (dmax+1) bytes of workspace per column;
+                                  compute / solve return INVALID_ARG when a column's shared-memory
+                                  state, about 52 H + 512 (dmax+1) bytes, exceeds 227 KB) */
 } stixels_params_t;
 
 /* One output stixel: 12 bytes. */

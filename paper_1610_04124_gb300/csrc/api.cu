@@ -362,6 +362,7 @@ int stixels_solve(stixels_t h, const int32_t* d_pd, const int32_t* d_pg, const i
     rc = ensure_rows(h, H, &r);
     if (rc) return rc;
     if (h->hm.p.global_map) {
+        if (!map_fits(H, h->hm.dmax + 1)) return STIXELS_E_INVALID_ARG;
         rc = ensure_workspace(h, map_scratch_bytes(H, ncols, h->hm.dmax + 1));
         if (rc) return rc;
         return cuda_status(launch_dp_map(d_pd, d_pg, d_ps, d_po, g, h->md, r, *out, h->d_err, h->ws.base,
@@ -387,6 +388,7 @@ int stixels_compute(stixels_t h, const float* d_disparity, int H, int W, void* s
     const FrameLayout L = frame_layout(H, g.ncols, h->hm.dmax + 1);
     const size_t gw = est ? (ground_work_bytes(H, h->hm.dmax) + 255) / 256 * 256 : 0;
     const bool gmap = h->hm.p.global_map != 0;
+    if (gmap && !map_fits(H, h->hm.dmax + 1)) return STIXELS_E_INVALID_ARG;
     rc = ensure_workspace(h, L.total + gw + (gmap ? map_scratch_bytes(H, g.ncols, h->hm.dmax + 1) : 0));
     if (rc) return rc;
     char* ws = (char*)h->ws.base;

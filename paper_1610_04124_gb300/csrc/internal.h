@@ -203,6 +203,10 @@ cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& 
 
 // The global-MAP DP (kernels_dp_map.cu): scratch bytes for a frame, and the launch.
 size_t map_scratch_bytes(int H, int ncols, int F);
+// Whether a column of height H with F object disparities fits the global-MAP
+// kernel's shared memory (227 KB per CTA; false only for tall columns with a
+// large dmax, e.g. H > 1900 at dmax 255).
+bool map_fits(int H, int F);
 cudaError_t launch_dp_map(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po,
                           const FrameGeom& g, const ModelDev& m, const RowsDev& r, const stixels_output_t& out,
                           uint32_t* err, void* scratch, cudaStream_t st);

@@ -60,6 +60,7 @@ __device__ __forceinline__ unsigned long long warp_min(unsigned long long x)
 }
 
 constexpr int kMapRows = 32;                 // rows per block
+constexpr size_t kMapSmemMax = 227 * 1024;   // dynamic shared memory one CTA may use
 constexpr int kMapWarps = 8;
 
 // What one column's candidate evaluation needs (shared memory and the LUT).
@@ -73,8 +74,6 @@ struct MapCol {
     const unsigned long long* s_kg;   // [H] ground state keys
     const unsigned long long* s_ks;   // [H] sky state keys
     const unsigned long long* s_bo;   // [H] best object state of each row, value << 32 | f
-    const unsigned long long* pre;    // [H][F] (min over f' <= x of value) << 32 | argmin f'
-    const unsigned long long* suf;    // [H][F] (min over f' >= x) << 32 | argmin f'
     const int32_t* po;           // the column's object LUT, [F][P]
     int P, F, dmax, ord_off;
     int32_t T_oo, T_og, T_os, T_go, T_gg, T_gs, T_so, T_sg, T_ss;
@@ -83,7 +82,9 @@ struct MapCol {
 // The candidate keys of the stixel [b, k]: object (for the state (k, fo)),
 // ground and sky; every key is (cost | previous class code) << 32 | b << 8 |
 // previous object f, so one integer minimum is the tie order.
-__device__ __forceinline__ void map_cands(const MapCol& c, const ModelDev& m, int b, int k, int& fo,
+// prer / sufr: the prefix / suffix minima of row b - 1 (unused for b = 0).
+__device__ __forceinline__ void map_cands(const MapCol& c, const ModelDev& m, int b, int k,
+                                          const unsigned long long* prer, const unsigned long long* sufr, int& fo,
                                           unsigned long long& ko, unsigned long long& kg, unsigned long long& ks)
 {
     const int n = k - b + 1;
@@ -98,18 +99,17 @@ __device__ __forceinline__ void map_cands(const MapCol& c, const ModelDev& m, in
         ks = make_key(d_s + m.first[2] + kNoneCode, 0, 0);
         return;
     }
-    const size_t rw = (size_t)(b - 1) * c.F;
     // object above object: free for previous f >= fo - ord_off, penalised below
     const int x = fo - c.ord_off;
     ko = kNoKey;
     if (x <= c.F - 1) {
-        const unsigned long long su = c.suf[rw + max(x, 0)];
+        const unsigned long long su = sufr[max(x, 0)];
         const int32_t v = min((int32_t)(su >> 32), kBig);
         const unsigned long long t = make_key(d_o + v + c.T_oo, b, (int)(su & 255));
         ko = t < ko ? t : ko;
     }
     if (x - 1 >= 0) {
-        const unsigned long long pr = c.pre[rw + min(x - 1, c.F - 1)];
+        const unsigned long long pr = prer[min(x - 1, c.F - 1)];
         const int32_t v = min((int32_t)(pr >> 32), kBig);
         const unsigned long long t = make_key(d_o + v + c.T_oo + m.pen_ord, b, (int)(pr & 255));
         ko = t < ko ? t : ko;
@@ -148,10 +148,10 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, un
     unsigned long long* s_kg = reinterpret_cast<unsigned long long*>(smem);      // [H]
     unsigned long long* s_ks = s_kg + H;                                         // [H]
     unsigned long long* s_bo = s_ks + H;                                         // [H]
-    unsigned long long* s_bin = s_bo + H;                                        // [kMapRows][F]
-    unsigned long long* s_gbin = s_bin + (size_t)kMapRows * F;                   // [kMapRows]
-    unsigned long long* s_sbin = s_gbin + kMapRows;                              // [kMapRows]
-    uint2* s_div = reinterpret_cast<uint2*>(s_sbin + kMapRows);                  // [H + 1]
+    unsigned long long* s_bin = s_bo + H;                                        // [2][kMapRows][F]
+    unsigned long long* s_gbin = s_bin + 2 * (size_t)kMapRows * F;               // [2][kMapRows]
+    unsigned long long* s_sbin = s_gbin + 2 * kMapRows;                          // [2][kMapRows]
+    uint2* s_div = reinterpret_cast<uint2*>(s_sbin + 2 * kMapRows);              // [H + 1]
     int32_t* s_pd8 = reinterpret_cast<int32_t*>(s_div + H + 1);                  // [H + 1]
     int32_t* s_pg = s_pd8 + (H + 1);                                             // [H + 1]
     int32_t* s_ps = s_pg + (H + 1);                                              // [H + 1]
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, un
     }
     MapCol c;
     c.s_pd8 = s_pd8; c.s_pg = s_pg; c.s_ps = s_ps; c.s_fhi = s_fhi; c.s_flo = s_flo; c.s_div = s_div;
-    c.s_kg = s_kg; c.s_ks = s_ks; c.s_bo = s_bo; c.pre = pre; c.suf = suf;
+    c.s_kg = s_kg; c.s_ks = s_ks; c.s_bo = s_bo;
     c.po = a.po + (size_t)col * F * P;
     c.P = P; c.F = F; c.dmax = m.dmax; c.ord_off = m.eps_o >> 4;    // ordering iff f' > f + ord_off
     c.T_oo = m.trans[0][0]; c.T_og = m.trans[0][1] + 1; c.T_os = m.trans[0][2] + 2;
@@ -183,60 +183,83 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, un
 
     const int NB = (H + kMapRows - 1) / kMapRows;
     constexpr int kPer = 8;                       // object states per lane in the row scan (F <= 256)
+    const size_t BF = (size_t)kMapRows * F;
+
+    // Phase A for the rows K + lane (lane < nr) and the starts b = b0, b0 + step,
+    // ... < b1 (rows of earlier blocks, all final), into one block's bins.  Two
+    // starts are evaluated together so that their loads overlap; a lane keeps
+    // its object candidates for one bin until f changes (consecutive starts
+    // mostly share f), its ground / sky minima in registers.
+    auto phase_a = [&](unsigned long long* bins, unsigned long long* gbin, unsigned long long* sbin, int K, int nr,
+                       int b0, int b1, int step) {
+        if (lane >= nr || b0 >= b1) return;
+        const int k = K + lane;
+        unsigned long long rg = kNoKey, rs = kNoKey, ck = kNoKey;
+        int cf = -1;
+        auto merge = [&](int fo, unsigned long long ko, unsigned long long kg, unsigned long long ks) {
+            rg = kg < rg ? kg : rg;
+            rs = ks < rs ? ks : rs;
+            if (fo != cf) {
+                if (cf >= 0) atomicMin(&bins[lane * F + cf], ck);
+                cf = fo;
+                ck = ko;
+            } else {
+                ck = ko < ck ? ko : ck;
+            }
+        };
+        int b = b0;
+        for (; b + step < b1; b += 2 * step) {
+            int f0, f1;
+            unsigned long long o0, g0, s0, o1, g1, s1;
+            map_cands(c, m, b, k, pre + (size_t)(b - 1) * F, suf + (size_t)(b - 1) * F, f0, o0, g0, s0);
+            map_cands(c, m, b + step, k, pre + (size_t)(b + step - 1) * F, suf + (size_t)(b + step - 1) * F, f1, o1,
+                      g1, s1);
+            merge(f0, o0, g0, s0);
+            merge(f1, o1, g1, s1);
+        }
+        if (b < b1) {
+            int f0;
+            unsigned long long o0, g0, s0;
+            map_cands(c, m, b, k, pre + (size_t)(b - 1) * F, suf + (size_t)(b - 1) * F, f0, o0, g0, s0);
+            merge(f0, o0, g0, s0);
+        }
+        if (cf >= 0) atomicMin(&bins[lane * F + cf], ck);
+        atomicMin(&gbin[lane], rg);
+        atomicMin(&sbin[lane], rs);
+    };
+
+    // bins of blocks 0 and 1 (the bins are double-buffered by block parity)
+    for (int i = tid; i < 2 * (int)BF; i += blockDim.x) s_bin[i] = kNoKey;
+    if (tid < 2 * kMapRows) { s_gbin[tid] = kNoKey; s_sbin[tid] = kNoKey; }
+    __syncthreads();
     for (int j = 0; j < NB; ++j) {
         const int K0 = kMapRows * j, nb = min(kMapRows, H - K0);
-        for (int i = tid; i < kMapRows * F; i += blockDim.x) s_bin[i] = kNoKey;
-        if (tid < kMapRows) { s_gbin[tid] = kNoKey; s_sbin[tid] = kNoKey; }
-        __syncthreads();                          // also: the rows of block j-1 are visible
+        const int K1 = K0 + kMapRows, nb1 = j + 1 < NB ? min(kMapRows, H - K1) : 0;
+        unsigned long long* bin_j = s_bin + (j & 1) * BF;
+        unsigned long long* gbin_j = s_gbin + (j & 1) * kMapRows;
+        unsigned long long* sbin_j = s_sbin + (j & 1) * kMapRows;
+        unsigned long long* bin_n = s_bin + ((j + 1) & 1) * BF;
+        unsigned long long* gbin_n = s_gbin + ((j + 1) & 1) * kMapRows;
+        unsigned long long* sbin_n = s_sbin + ((j + 1) & 1) * kMapRows;
 
-        // Phase A, every warp: the starts of earlier blocks (their rows are
-        // final) for the rows of this block, lane = row K0 + lane, warps over
-        // the starts.  A lane keeps its object candidates for one bin until f
-        // changes (consecutive starts mostly share f), its ground / sky minima
-        // in registers.
-        if (lane < nb) {
-            const int k = K0 + lane;
-            unsigned long long rg = kNoKey, rs = kNoKey, ck = kNoKey;
-            int cf = -1;
-            for (int b = warp; b < K0; b += kMapWarps) {
-                int fo;
-                unsigned long long ko, kg, ks;
-                map_cands(c, m, b, k, fo, ko, kg, ks);
-                rg = kg < rg ? kg : rg;
-                rs = ks < rs ? ks : rs;
-                if (fo != cf) {
-                    if (cf >= 0) atomicMin(&s_bin[lane * F + cf], ck);
-                    cf = fo;
-                    ck = ko;
-                } else {
-                    ck = ko < ck ? ko : ck;
-                }
-            }
-            if (cf >= 0) atomicMin(&s_bin[lane * F + cf], ck);
-            if (K0 > 0) {
-                atomicMin(&s_gbin[lane], rg);
-                atomicMin(&s_sbin[lane], rs);
-            }
-        }
-        __syncthreads();
-
-        // Phase B, warp 0: the block's rows in order; row k adds its starts
-        // within the block (lane = start K0 + lane <= k), then its object
-        // states become prefix / suffix minima over f for the rows above.
         if (warp == 0) {
+            // Phase B: the block's rows in order; row k adds its starts within
+            // the block (lane = start K0 + lane <= k), then its object states
+            // become prefix / suffix minima over f for the rows above.
             for (int r = 0; r < nb; ++r) {
                 const int k = K0 + r;
                 unsigned long long kg = kNoKey, ks = kNoKey;
                 if (lane <= r) {
+                    const int b = K0 + lane;
                     int fo;
                     unsigned long long ko;
-                    map_cands(c, m, K0 + lane, k, fo, ko, kg, ks);
-                    atomicMin(&s_bin[r * F + fo], ko);
+                    map_cands(c, m, b, k, pre + (size_t)(b - 1) * F, suf + (size_t)(b - 1) * F, fo, ko, kg, ks);
+                    atomicMin(&bin_j[r * F + fo], ko);
                 }
                 kg = warp_min(kg);
                 ks = warp_min(ks);
                 __syncwarp();
-                const unsigned long long* bin = s_bin + (size_t)r * F;
+                const unsigned long long* bin = bin_j + (size_t)r * F;
                 // lane l owns f = kPer l .. kPer l + kPer - 1: local prefix / suffix, then warp scans
                 unsigned long long pv[kPer], sv[kPer];
 #pragma unroll
@@ -273,8 +296,8 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, un
                     }
                 }
                 if (lane == 0) {
-                    s_kg[k] = kg < s_gbin[r] ? kg : s_gbin[r];
-                    s_ks[k] = ks < s_sbin[r] ? ks : s_sbin[r];
+                    s_kg[k] = kg < gbin_j[r] ? kg : gbin_j[r];
+                    s_ks[k] = ks < sbin_j[r] ? ks : sbin_j[r];
                 }
                 // the row's best object state (over every f): the last prefix
                 const unsigned long long best = __shfl_sync(0xffffffffu, pt, 31);
@@ -282,8 +305,18 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, un
                 __threadfence_block();
                 __syncwarp();
             }
+        } else {
+            // meanwhile: the next block's candidates whose starts lie in the
+            // blocks before this one (their rows are final)
+            phase_a(bin_n, gbin_n, sbin_n, K1, nb1, warp - 1, K0, kMapWarps - 1);
         }
-        __syncthreads();                          // warp 0 is done with the bins before they are reset
+        __syncthreads();                          // block j's rows are final and visible
+        // the next block's starts inside this block, then the bins of this
+        // block are reset for block j + 2
+        phase_a(bin_n, gbin_n, sbin_n, K1, nb1, K0 + warp, K0 + nb, kMapWarps);
+        for (int i = tid; i < (int)BF; i += blockDim.x) bin_j[i] = kNoKey;
+        if (tid < kMapRows) { gbin_j[tid] = kNoKey; sbin_j[tid] = kNoKey; }
+        __syncthreads();
     }
 
     // top row (lexicographic cost, class, f) and backtracking
@@ -345,7 +378,7 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, un
 
 size_t map_smem_bytes(int H, int F)
 {
-    return sizeof(unsigned long long) * (3 * (size_t)H + (size_t)kMapRows * F + 2 * kMapRows) +
+    return sizeof(unsigned long long) * (3 * (size_t)H + 2 * (size_t)kMapRows * F + 4 * kMapRows) +
            sizeof(uint2) * (size_t)(H + 1) + sizeof(int32_t) * (3 * (size_t)(H + 1) + 2 * (size_t)H);
 }
 
@@ -353,12 +386,14 @@ size_t map_smem_bytes(int H, int F)
 
 size_t map_scratch_bytes(int H, int ncols, int F) { return sizeof(unsigned long long) * 3 * (size_t)H * F * ncols; }
 
+bool map_fits(int H, int F) { return map_smem_bytes(H, F) <= kMapSmemMax; }
+
 cudaError_t launch_dp_map(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po,
                           const FrameGeom& g, const ModelDev& m, const RowsDev& r, const stixels_output_t& out,
                           uint32_t* err, void* scratch, cudaStream_t st)
 {
     if (g.H <= 0 || g.ncols <= 0) return cudaSuccess;
-    if (g.H > STIXELS_MAX_HEIGHT || m.dmax + 1 > 256) return cudaErrorInvalidValue;
+    if (g.H > STIXELS_MAX_HEIGHT || m.dmax + 1 > 256 || !map_fits(g.H, m.dmax + 1)) return cudaErrorInvalidValue;
     DpArgs a;
     dp_frame_args(pd, pg, ps, po, g, m, r, out, err, &a);
     const size_t smem = map_smem_bytes(g.H, m.dmax + 1);
@@ -367,7 +402,7 @@ cudaError_t launch_dp_map(const int32_t* pd, const int32_t* pg, const int32_t* p
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        e = cudaFuncSetAttribute(stixel_map_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        e = cudaFuncSetAttribute(stixel_map_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMapSmemMax);
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }

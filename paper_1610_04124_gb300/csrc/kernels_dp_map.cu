@@ -49,14 +49,14 @@ __device__ __forceinline__ int32_t state_value(unsigned long long k)
     return k == kNoKey ? kBig : min(key_cost(k) & ~3, kBig);
 }
 
+// Minimum of a 64-bit key over the warp: the high words' minimum, then the
+// low words' minimum among the lanes that hold it (two warp reductions).
 __device__ __forceinline__ unsigned long long warp_min(unsigned long long x)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
-        x = y < x ? y : x;
-    }
-    return x;
+    const unsigned hi = (unsigned)(x >> 32), lo = (unsigned)x;
+    const unsigned mh = __reduce_min_sync(0xffffffffu, hi);
+    const unsigned ml = __reduce_min_sync(0xffffffffu, hi == mh ? lo : 0xffffffffu);
+    return ((unsigned long long)mh << 32) | ml;
 }
 
 constexpr int kMapRows = 32;                 // rows per block
@@ -305,10 +305,12 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, un
                 __threadfence_block();
                 __syncwarp();
             }
-        } else {
+        } else if (warp != 4) {
             // meanwhile: the next block's candidates whose starts lie in the
-            // blocks before this one (their rows are final)
-            phase_a(bin_n, gbin_n, sbin_n, K1, nb1, warp - 1, K0, kMapWarps - 1);
+            // blocks before this one (their rows are final), on the warps that
+            // do not share warp 0's scheduler (warp 4 does), so that the
+            // sequential rows keep its issue slots
+            phase_a(bin_n, gbin_n, sbin_n, K1, nb1, warp - 1 - (warp > 4), K0, kMapWarps - 2);
         }
         __syncthreads();                          // block j's rows are final and visible
         // the next block's starts inside this block, then the bins of this

@@ -58,6 +58,7 @@ struct stixels_s {
     std::map<int, RowsBuf> rows;       // per height
     Workspace ws;
     uint32_t* d_err = nullptr;
+    uint32_t* h_err = nullptr;         // pinned copy of the error word (compute_host)
     cudaStream_t stream = nullptr;     // own stream for compute_host
     // device buffers for compute_host
     float* d_in = nullptr;
@@ -229,6 +230,7 @@ int stixels_create(const stixels_params_t* params, stixels_t* out_handle)
     }
     if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_err, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         stixels_destroy(h);
@@ -275,6 +277,7 @@ int stixels_destroy(stixels_t h)
     cudaFree(h->ws.base);
     cudaFree(h->d_tables);
     cudaFree(h->d_err);
+    if (h->h_err) cudaFreeHost(h->h_err);
     cudaFree(h->d_in);
     cudaFree(h->d_out);
     if (h->stream) cudaStreamDestroy(h->stream);
@@ -467,11 +470,13 @@ int stixels_compute_host(stixels_t h, const float* h_disparity, int H, int W, st
                             h->stream);
     if (e == cudaSuccess && h_cost)
         e = cudaMemcpyAsync(h_cost, out.column_cost, sizeof(float) * g.ncols, cudaMemcpyDeviceToHost, h->stream);
+    // the error word rides the same stream (read, then cleared): one wait in all
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_err, h->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_status(e);
-    uint32_t flags = 0;
-    rc = stixels_get_error(h, h->stream, &flags);
-    if (rc) return rc;
-    if (flags & STIXELS_ERR_INFEASIBLE) return STIXELS_E_DEVICE_FAULT;
+    const uint32_t flags = *h->h_err;
+    if (flags & (STIXELS_ERR_INFEASIBLE | STIXELS_ERR_TIMEOUT)) return STIXELS_E_DEVICE_FAULT;
     if (flags & STIXELS_ERR_CAPACITY) return STIXELS_E_CAPACITY;
     return STIXELS_OK;
 }

@@ -243,6 +243,9 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
     constexpr int kWarps = NW;
     constexpr int kThreads = NW * 32;
     constexpr int kBulk = NW - 1;                   // warps besides the chain warp
+    // the tile dealing below leaves out the bulk warps on the chain warp's
+    // scheduler (warp index congruent mod 4): NW / 4 - 1 of them
+    static_assert(NW % 4 == 0 && NW >= 8, "whole schedulers of warps");
     const int H = a.H, P = a.P, F = a.F;
     const int HP = (H + 3) & ~3;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

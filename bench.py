@@ -403,6 +403,15 @@ def time_stages(S, torch, h, disp, flush, stream, warmup, steps):
             [e[1].elapsed_time(e[2]) for e in ev], [e[2].elapsed_time(e[3]) for e in ev], out)
 
 
+def workload_config(cam, world):
+    """The workload both arms name in `config` (the same dict)."""
+    return {"workload": f"{cam.width}x{cam.height} s={cam.stixel_width} dmax={cam.dmax}, one frame per step "
+                        f"(paper-sized frame)",
+            "H": cam.height, "W": cam.width, "stixel_width": cam.stixel_width, "dmax": cam.dmax,
+            "frames_per_step": 1, "l2": "flushed between steps (256 MB write, untimed) on the GPU arm",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
 def time_compute(torch, h, disp, flush, stream, warmup, steps):
     """The per-frame entry point (stixels_compute: the whole hot path in one
     call) for `steps` steps after `warmup`, each between CUDA events on the
@@ -598,10 +607,7 @@ def bench_ours(args, world, rank, local):
         "vs_baseline": value / PAPER_FPS,
         "vs_baseline_ref": "paper: 413 fps on a Titan X (Maxwell) at 1024x440, s=5 (other hardware; context)",
         "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "1024x440 s=5 dmax=128, one frame per stixels_compute call (paper-sized frame)",
-                   "H": H, "W": W, "stixel_width": s, "dmax": dmax, "frames_per_step": 1,
-                   "l2": "flushed between steps (256 MB write, untimed)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": workload_config(cam, world),
         "roofline": {"kernel": "stixel_dp_kernel", "bound": "alu", "achieved": dp_tops, "peak": alu_peak,
                      "unit": "Tops/s", "frac": dp_tops / alu_peak,
                      "traffic": _traffic(os.path.join(kdir, "kernels_dp.cu")),
@@ -668,8 +674,7 @@ def bench_reference(args, world, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_FPS, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "1024x440 s=5 dmax=128, one frame per step (paper-sized frame)",
-                       "H": cam.height, "W": cam.width, "stixel_width": cam.stixel_width, "dmax": cam.dmax},
+            "config": workload_config(cam, world),
             "cpu_baseline": {"value": value, "unit": "frames/s", "cores": host_cores(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

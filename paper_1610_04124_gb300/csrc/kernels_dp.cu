@@ -28,8 +28,9 @@
 //     block all lanes pack them into back-pointers and start contexts.  The
 //     data terms of the cells (with the input-only gravity / diving penalties
 //     already added) were gathered into shared memory ahead of the chain (a
-//     ring of three blocks), so the sequential chain never waits on global
-//     memory.
+//     ring of three blocks, two in the three-CTA batch shape), so the
+//     sequential chain never waits on global memory.  The chain is bound by
+//     its instruction issue: the bulk warps on its scheduler take no tiles.
 //   - the other warps (bulk) apply the starts of every finalised block t to the
 //     end rows of blocks t+2, t+3, ... (independent 32 x 32 tiles).  End-row
 //     block c receives c - 1 tiles; they are split by start block between two

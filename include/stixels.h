@@ -214,6 +214,16 @@ int stixels_compute_host(stixels_t h, const float* h_disparity, int H, int W,
  * synchronising `stream`. */
 int stixels_get_error(stixels_t h, void* stream, uint32_t* flags);
 
+/* Diagnostic for the kernels' failure path (no counterpart in the paper):
+ * launches one CTA on `stream` that waits, with the bounded wait every DP
+ * kernel uses between its warps, on a flag that nothing sets.  After `polls`
+ * polls (1 .. 2^22; each sleeps at most 32 ns) the wait gives up, the kernel
+ * records STIXELS_ERR_TIMEOUT in the handle's error word and returns; the
+ * call then synchronises `stream` and returns the word in *flags (cleared, as
+ * stixels_get_error does).  The context stays usable.  INVALID_ARG for a bad
+ * handle, pointer or count. */
+int stixels_selftest_wait(stixels_t h, int polls, void* stream, uint32_t* flags);
+
 /* ---- individual stages (the same kernels stixels_compute launches) ---- */
 
 /* Row pitch (in int32 elements) of the prefix LUTs for height H:

@@ -110,6 +110,7 @@ def lib():
         L.stixels_compute.argtypes = [V, V, I, I, V, P(Output)]
         L.stixels_compute_host.argtypes = [V, V, I, I, V, V, V]
         L.stixels_get_error.argtypes = [V, V, P(C.c_uint32)]
+        L.stixels_selftest_wait.argtypes = [V, I, V, P(C.c_uint32)]
         L.stixels_lut_pitch.argtypes = [I]
         L.stixels_reduce.argtypes = [V, V, I, I, V, V]
         L.stixels_build_luts.argtypes = [V, V, I, I, V, V, V, V, V]
@@ -293,6 +294,14 @@ class Stixels:
     def get_error(self, stream=None) -> int:
         v = C.c_uint32()
         _check(lib().stixels_get_error(self._h, _stream_ptr(stream), C.byref(v)), "get_error")
+        return v.value
+
+    def selftest_wait(self, polls: int = 1000, stream=None) -> int:
+        """Run the kernels' bounded wait on a flag nothing sets; returns the
+        error word (ERR_TIMEOUT when the wait gave up as it should)."""
+        v = C.c_uint32()
+        _check(lib().stixels_selftest_wait(self._h, int(polls), _stream_ptr(stream), C.byref(v)),
+               "stixels_selftest_wait")
         return v.value
 
     # ---- stages ----

@@ -410,6 +410,14 @@ int stixels_compute(stixels_t h, const float* d_disparity, int H, int W, void* s
     return cuda_status(e);
 }
 
+int stixels_selftest_wait(stixels_t h, int polls, void* stream, uint32_t* flags)
+{
+    if (!h || !flags || polls < 1 || polls > (1 << 22)) return STIXELS_E_INVALID_ARG;
+    const int rc = cuda_status(launch_wait_selftest(h->d_err, polls, (cudaStream_t)stream));
+    if (rc) return rc;
+    return stixels_get_error(h, stream, flags);
+}
+
 int stixels_get_error(stixels_t h, void* stream, uint32_t* flags)
 {
     if (!h || !flags) return STIXELS_E_INVALID_ARG;

@@ -203,6 +203,8 @@ cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& 
 
 // The global-MAP DP (kernels_dp_map.cu): scratch bytes for a frame, and the launch.
 size_t map_scratch_bytes(int H, int ncols, int F);
+// One CTA whose bounded wait (the DP kernels' own) runs out after `limit` polls.
+cudaError_t launch_wait_selftest(uint32_t* err, int limit, cudaStream_t st);
 // Whether a column of height H with F object disparities fits the global-MAP
 // kernel's shared memory (227 KB per CTA; false only for tall columns with a
 // large dmax, e.g. H > 1900 at dmax 255).

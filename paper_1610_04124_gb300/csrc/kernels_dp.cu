@@ -146,16 +146,17 @@ __device__ __forceinline__ void tree_min(int32_t (&v)[N], int32_t (&bf)[N])
 }
 
 // Warp-wide bounded wait until *p >= target (lane 0 polls, sleeping between
-// polls with a back-off up to max_ns).  Returns false if the wait gave up or
-// another warp did; the caller then stops.
-__device__ __forceinline__ bool wait_geq(volatile int* p, int target, volatile int* abort_flag, int max_ns)
+// polls with a back-off up to max_ns, at most `limit` polls).  Returns false
+// if the wait gave up or another warp did; the caller then stops.
+__device__ __forceinline__ bool wait_geq(volatile int* p, int target, volatile int* abort_flag, int max_ns,
+                                         int limit = kSpinLimit)
 {
     int ok = 1;
     if ((threadIdx.x & 31) == 0) {
         int it = 0, ns = 8;
         while (*p < target) {
             if (*abort_flag) { ok = 0; break; }
-            if (++it > kSpinLimit) { *abort_flag = 1; ok = 0; break; }
+            if (++it > limit) { *abort_flag = 1; ok = 0; break; }
             __nanosleep(ns);
             ns = min(2 * ns, max_ns);
         }
@@ -634,7 +635,29 @@ __global__ void __launch_bounds__(NW * 32, MINB)
     }
 }
 
+// The bounded wait on a flag that nothing sets: it runs out after `limit`
+// polls, records STIXELS_ERR_TIMEOUT and returns (how every DP wait ends when
+// its partner stops), so the host sees a status and the context stays usable.
+__global__ void __launch_bounds__(64) wait_selftest_kernel(uint32_t* err, int limit)
+{
+    __shared__ int flag, abort_flag;
+    if (threadIdx.x == 0) {
+        flag = 0;
+        abort_flag = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && !wait_geq(&flag, 1, &abort_flag, 32, limit) && threadIdx.x == 0)
+        atomicOr(err, STIXELS_ERR_TIMEOUT);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(uint32_t* err, int limit, cudaStream_t st)
+{
+    if (limit < 1) return cudaErrorInvalidValue;
+    wait_selftest_kernel<<<1, 64, 0, st>>>(err, limit);
+    return cudaGetLastError();
+}
 
 int sm_count()
 {

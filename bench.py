@@ -31,7 +31,10 @@ if ROOT not in sys.path:
 
 METRIC = "frames/s @1024x440 w=5"
 PAPER_FPS = 413.0          # Titan X (Maxwell), 1024x440, s = 5 (paper Sec. 6): context only
-OPS_PER_CELL = 20          # algorithmic integer ops per object DP candidate
+# algorithmic integer ops per object DP candidate: S (1), rounded mean by a
+# multiply-high (3), two LUT reads and their difference (3), three prior
+# candidates (6), their minimum (2), plus the data term (1), running argmin (3)
+OPS_PER_CELL = 20
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),

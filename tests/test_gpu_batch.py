@@ -75,6 +75,31 @@ def test_batch_equals_per_frame_for_every_launch_shape():
     b.close()
 
 
+def test_batch_with_a_maximum_height_frame():
+    """A 2048-row frame (the most shared memory a column takes) batched with
+    small frames: every launch shape still equals the per-frame path."""
+    cams = [scenes.Camera(20, 2048, stixel_width=5, dmax=128, horizon_row=680, camera_height_m=1.2),
+            scenes.CONFIG1,
+            scenes.Camera(640, 240, stixel_width=7, dmax=64, horizon_row=80)]
+    frames = []
+    for i, cam in enumerate(cams):
+        h = S.Stixels(S.default_params(cam))
+        frames.append((h, cam, scenes.make_scene(cam, 4600 + i, n_obstacles=(1, 4), span_cols=(1, 4)).disparity))
+    refs = [_reference(h, d) for h, _, d in frames]
+    b = S.Batch([(h, cam.height, cam.width) for h, cam, _ in frames])
+    for i, (_, _, d) in enumerate(frames):
+        b.set_input(i, d)
+    for shape in [(8, 2), (16, 1), (8, 1), (8, 3)]:
+        b.set_config(*shape)
+        b.launch()
+        torch.cuda.synchronize()
+        for i, (h, cam, _) in enumerate(frames):
+            _assert_same(b.output(i), refs[i], h.params.max_stixels_per_col)
+    for h, _, _ in frames:
+        assert h.get_error() == 0
+    b.close()
+
+
 def test_batch_relaunch_with_new_inputs_and_host_sources():
     frames = _mixed_frames()[:3]
     b = S.Batch([(h, cam.height, cam.width) for h, cam, _ in frames])

@@ -188,6 +188,20 @@ def test_pipeline_column_counts_between_one_and_two_per_sm(ncols, H):
     assert_frame_equal(out, fr, H, lp.max_stixels_per_col)
 
 
+@pytest.mark.parametrize("H,dmax", [(2048, 128), (1800, 255)])
+def test_pipeline_maximum_height(H, dmax):
+    """The tallest column the library takes (64 row blocks), and the largest
+    dmax at a height its cost budget admits, against the oracle."""
+    cam = scenes.Camera(4 * 5, H, stixel_width=5, dmax=dmax, horizon_row=H // 3, baseline_m=0.3,
+                        camera_height_m=1.2)
+    sc = scenes.make_scene(cam, 950 + dmax, n_obstacles=(1, 3), span_cols=(1, 3))
+    lp, op = both_params(cam)
+    out, err = run_frame(lp, sc.disparity)
+    fr = oracle.frame(op, sc.disparity, cap=lp.max_stixels_per_col)
+    assert err == (S.ERR_CAPACITY if (fr.counts > lp.max_stixels_per_col).any() else 0)
+    assert_frame_equal(out, fr, H, lp.max_stixels_per_col)
+
+
 @pytest.mark.parametrize("variant", [
     dict(reduce_mode=1),
     dict(cost_order=0.0),

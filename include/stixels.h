@@ -378,7 +378,8 @@ int stixels_submit(stixels_server_t s, stixels_t camera, const float* disparity,
  * stixels_output_shape; column_cost, column_cost_fixed optional), frees the
  * frame's slot and retires the ticket.  STIXELS_E_NOT_READY if timeout_us == 0
  * and the frame is not done, STIXELS_E_TIMEOUT if a positive wait ran out,
- * INVALID_ARG for an unknown ticket or mismatched buffers. */
+ * INVALID_ARG for an unknown ticket, a ticket another poll is already
+ * copying out, or mismatched buffers. */
 int stixels_poll(stixels_server_t s, uint64_t ticket, const stixels_output_t* out, int timeout_us);
 int stixels_server_stats(stixels_server_t s, stixels_server_stats_t* stats);
 /* Stop the scheduler, wait for frames on the GPU, release everything.  Tickets

@@ -97,6 +97,7 @@ struct Request {
     size_t off = 0, bytes = 0;
     uint32_t* d_err = nullptr;          // the frame's own device error word
     State state = State::Queued;
+    bool claimed = false;               // a poll is copying its results out
     int status = STIXELS_OK;            // launch failure of its iteration
     std::shared_ptr<Iteration> iter;
 };
@@ -316,6 +317,13 @@ int stixels_poll(stixels_server_t s, uint64_t ticket, const stixels_output_t* ou
             return timeout_us == 0 ? STIXELS_E_NOT_READY : STIXELS_E_TIMEOUT;
         std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+    {
+        // one poll copies a frame out and frees it; a concurrent poll of the
+        // same ticket finds it claimed
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (r->claimed || !s->requests.count(ticket)) return STIXELS_E_INVALID_ARG;
+        r->claimed = true;
+    }
     const stixels_output_t& src = r->job.out;
     const size_t C = (size_t)src.ncols;
     uint32_t flags = 0;
@@ -333,7 +341,7 @@ int stixels_poll(stixels_server_t s, uint64_t ticket, const stixels_output_t* ou
     s->stats.completed += 1;
     if (r->status != STIXELS_OK) return r->status;
     if (e != cudaSuccess) return status_of(e);
-    if (flags & STIXELS_ERR_INFEASIBLE) return STIXELS_E_DEVICE_FAULT;
+    if (flags & (STIXELS_ERR_INFEASIBLE | STIXELS_ERR_TIMEOUT)) return STIXELS_E_DEVICE_FAULT;
     if (flags & STIXELS_ERR_CAPACITY) return STIXELS_E_CAPACITY;
     return STIXELS_OK;
 }

@@ -172,6 +172,37 @@ def test_poll_statuses():
     srv.close()
 
 
+def test_one_ticket_polled_from_many_threads_is_delivered_once():
+    """Threads racing to poll the same ticket: exactly one gets the frame (its
+    slot is freed once), the others are refused; the arena balances."""
+    import threading
+    cams, hs = _cameras()
+    srv = S.Server(2 << 30, max_slots=8)
+    cam, h = cams[2], hs[2]
+    frame = scenes.make_scene(cam, 7600).disparity
+    for rep in range(5):
+        t = srv.submit(h, frame)
+        assert t is not None
+        outs = [h.alloc_host_output(cam.height, cam.width) for _ in range(4)]
+        results = [None] * 4
+
+        def worker(i):
+            try:
+                results[i] = srv.poll(t, outs[i], timeout_us=2_000_000)
+            except S.StixelsError:
+                results[i] = "refused"
+
+        th = [threading.Thread(target=worker, args=(i,)) for i in range(4)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        assert results.count(S.OK) == 1 and results.count("refused") == 3, results
+    st = srv.stats()
+    assert st["slots_in_use"] == 0 and st["bytes_in_use"] == 0
+    srv.close()
+
+
 def test_concurrent_submitters():
     cams, hs = _cameras()
     frames = [scenes.make_scene(cams[i % 6], 7500 + i, n_obstacles=(3, 12)).disparity for i in range(36)]

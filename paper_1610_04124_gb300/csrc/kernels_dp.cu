@@ -240,7 +240,8 @@ __device__ __forceinline__ void gather_chain(ChainBuf* cb, int B, int H, int P, 
 // (dp_smem_bytes with the same ring, 2 or 3 chain buffers).  Every warp
 // returns from here; the caller synchronises before reusing `sm`.
 template <int NW, bool kStdTrans>
-__device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const int ring, int32_t* sm)
+__device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const int ring, int32_t* sm,
+                                          const int chain)
 {
     constexpr int kWarps = NW;
     constexpr int kThreads = NW * 32;
@@ -255,10 +256,11 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
     const int HP = (H + 3) & ~3;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const ModelDev& m = a.m;
-    // rotate the chain warp between CTAs so that two CTAs sharing an SM are
-    // less likely to put their chain warps on the same scheduler; the other
-    // warps are bulk warps 0 .. kBulk-1
-    const int chain = col & 3;
+    // `chain` is the chain warp (0 .. 3); the other warps are bulk warps
+    // 0 .. kBulk-1.  The per-frame kernel puts it on warp 0 in every CTA (two
+    // CTAs sharing an SM then have both chains on one scheduler, next to warps
+    // that take no tiles: 90.0 vs 91.2 us at two columns per SM); the batch
+    // kernel, up to three CTAs per SM, rotates it with the column.
     const int bulk_id = (warp - chain - 1 + kWarps) % kWarps;
 
     BulkCtx* s_ctx = reinterpret_cast<BulkCtx*>(sm);                   // [HP]
@@ -611,7 +613,7 @@ template <int NW, bool kStd, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) stixel_dp_kernel(DpArgs a, int ring)
 {
     extern __shared__ __align__(16) int32_t sm[];
-    dp_column<NW, kStd>(a, blockIdx.x, ring, sm);
+    dp_column<NW, kStd>(a, blockIdx.x, ring, sm, 0);
 }
 
 // Persistent form: each CTA takes columns from a work list (one shared atomic
@@ -636,7 +638,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
         int* dst = reinterpret_cast<int*>(&s_args);
         for (int i = threadIdx.x; i < (int)(sizeof(DpArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
         __syncthreads();
-        dp_column<NW, kStd>(s_args, w.y, ring, sm);
+        dp_column<NW, kStd>(s_args, w.y, ring, sm, w.y & 3);
         __syncthreads();
     }
 }

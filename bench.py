@@ -515,7 +515,9 @@ def bench_ours(args, world, rank, local):
                  "same 1024x440 frame; whole-pixel grid + mean reduction + off-line LUT_cost table"),
                 ("variable_sigma", dict(sigma_gain=1.0, sigma_mid=40.0, sigma_width=10.0),
                  "same 1024x440 frame; sigma(f) = sigma (1 + logistic((f - 40) / 10)), per-f / per-row tables")]:
-            hv = S.Stixels(S.default_params(cam, **kw))
+            # capacity H: no column's output is cut short (the whole-pixel grid
+            # over-segments some columns of this scene past the default 64)
+            hv = S.Stixels(S.default_params(cam, max_stixels_per_col=H, **kw))
             vs, vr, vl, vd, _ = time_stages(S, torch, hv, disp, flush, stream, 5, min(K, 100))
             lut_bytes_v = ncols * (F + 3) * P * 4 + ncols * H * 2
             variants[name] = {

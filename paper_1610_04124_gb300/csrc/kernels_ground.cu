@@ -16,81 +16,119 @@
 // a table over the clamped code built at create time.  With no vote at all
 // the camera's line is kept.
 //
-// Kernels: one CTA per image row builds and smooths its histogram in shared
-// memory; one thread per (k, h) sums its votes, 16 rows' loads at a time (the
-// smoothed rows are read from L1 / L2 -- neighbouring k read neighbouring
-// codes) and a 64-bit
-// atomic max over (votes, 256 - k, 65535 - h) picks the winner whatever the
-// order; one CTA then writes the frame's row tables.
+// Kernels: one CTA per four image rows builds their histograms in shared
+// memory, smooths them (the triangle as a box of 17 codes applied twice) and
+// stores S code-major (S[e][r], rows padded to a multiple of four), so that
+// for a fixed slope k and row offset j = r - h the code is the same for every
+// horizon h and a warp over 32 consecutive h reads 32 consecutive words.  A
+// vote CTA takes one k and 128 horizons (four per lane, so that one address
+// serves four loads); its 8 warps split the offsets, 32 loads in flight
+// each, and a 64-bit atomic max over (votes, 256 - k,
+// 65535 - h) picks the winner whatever the order; the last vote CTA to
+// finish writes the frame's row tables.
 #include "internal.h"
 
 namespace stx {
 namespace {
 
-// per image row: histogram of the codes, smoothed
-__global__ void __launch_bounds__(256) vdisp_kernel(const int16_t* __restrict__ q, int H, int ncols, int dmax,
-                                                    int32_t* __restrict__ smooth)
-{
-    extern __shared__ int32_t s_h[];               // [E]
-    const int E = 16 * dmax + 1;
-    const int r = blockIdx.x, v = H - 1 - r;
-    for (int e = threadIdx.x; e < E; e += blockDim.x) s_h[e] = 0;
-    __syncthreads();
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
-        const int code = q[(size_t)c * H + v];
-        if (code >= 16 && code < E) atomicAdd(&s_h[code], 1);
-    }
-    __syncthreads();
-    int32_t* out = smooth + (size_t)r * E;
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-        int32_t acc = 0;
-        if (e >= 16)
-            for (int t = -16; t <= 16; ++t) {
-                const int x = e + t;
-                if (x >= 16 && x < E) acc += (17 - abs(t)) * s_h[x];
-            }
-        out[e] = acc;
-    }
-}
+constexpr int kVdispRows = 4;   // image rows per histogram CTA
+constexpr int kVoteM = 4;              // horizons per lane, 32 apart
+constexpr int kVoteH = 32 * kVoteM;    // horizons per vote CTA
+constexpr int kVoteWarps = 8;          // warps per vote CTA, each over every eighth run of 8 offsets
 
-// one thread per candidate: k = threadIdx.x + 1, h = blockIdx.x
-__global__ void __launch_bounds__(256) vote_kernel(const int32_t* __restrict__ smooth, int H, int dmax,
-                                                   unsigned long long* __restrict__ best)
+// rows of the code-major table: the image height rounded up to kVdispRows
+__host__ __device__ inline int ground_pitch(int H) { return (H + kVdispRows - 1) / kVdispRows * kVdispRows; }
+// words per histogram row in shared memory: the E codes, then zeros far
+// enough for the last run of 8 codes to read 24 words past its end, in whole
+// 16-byte words
+__host__ __device__ inline int vdisp_pitch(int E) { return (E + 23 + 3) / 4 * 4; }
+
+// per four image rows: histograms of the codes, smoothed, stored code-major
+__global__ void __launch_bounds__(256) vdisp_kernel(const int16_t* __restrict__ q, int H, int ncols, int dmax,
+                                                    int32_t* __restrict__ smooth, unsigned long long* __restrict__ best)
 {
-    const int E = 16 * dmax + 1;
-    const int k = threadIdx.x + 1, h = blockIdx.x;
-    int32_t votes = 0;
-    // rows in chunks of 16 independent loads (the codes grow with r, so the
-    // first chunk that starts beyond the table ends the line)
-    for (int r0 = h + 1; r0 < H; r0 += 16) {
-        if (((k * (r0 - h) + 8) >> 4) >= E) break;
-        int32_t part[16];
+    // the vote kernel that follows on the stream starts from no winner and no
+    // finished block
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        best[0] = 0ull;
+        best[1] = 0ull;
+    }
+    // s_h[i][x]: codes below 16 are never counted and the words from E on stay
+    // zero, so every window below reads zeros outside [16, E)
+    extern __shared__ __align__(16) int32_t s_h[];
+    const int E = 16 * dmax + 1, P = vdisp_pitch(E), Hp = ground_pitch(H);
+    const int r0 = blockIdx.x * kVdispRows;
+    for (int x = threadIdx.x; x < kVdispRows * P; x += blockDim.x) s_h[x] = 0;
+    __syncthreads();
+    // four codes' loads in flight per thread, then their counts
+    for (int x0 = threadIdx.x; x0 < kVdispRows * ncols; x0 += 4 * blockDim.x) {
+        int code[4];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int r = r0 + i;
-            const int code = (k * (r - h) + 8) >> 4;
-            part[i] = (r < H && code >= 16 && code < E) ? __ldg(smooth + (size_t)r * E + code) : 0;
+        for (int u = 0; u < 4; ++u) {
+            const int x = x0 + u * blockDim.x;
+            const int c = x / kVdispRows, i = x % kVdispRows, r = r0 + i;
+            code[u] = (x < kVdispRows * ncols && r < H) ? q[(size_t)c * H + (H - 1 - r)] : 0;
         }
 #pragma unroll
-        for (int i = 0; i < 16; ++i) votes += part[i];
+        for (int u = 0; u < 4; ++u)
+            if (code[u] >= 16 && code[u] < E) atomicAdd(&s_h[((x0 + u * blockDim.x) % kVdispRows) * P + code[u]], 1);
     }
-    unsigned long long key = ((unsigned long long)(uint32_t)votes << 32) |
-                             ((unsigned long long)(256 - k) << 16) | (unsigned long long)(65535 - h);
+    __syncthreads();
+    // The triangle 17 - |t| (|t| <= 16) is a box of 17 codes convolved with
+    // itself: B[y] = sum of hist over [y - 8, y + 8], S[e] = sum of B over
+    // [e - 8, e + 8].  A thread takes 8 consecutive codes e0..e0+7 and slides
+    // both boxes over the 40 words hist[e0 - 16 .. e0 + 23].
+    const int G = (E - 16 + 7) / 8;
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        const int e0 = 16 + 8 * g;
+        int32_t out[kVdispRows][8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
-        key = other > key ? other : key;
+        for (int i = 0; i < kVdispRows; ++i) {
+            const int32_t* hp = s_h + i * P + 8 * g;   // code e0 - 16, 16-byte aligned
+            int32_t hv[40];
+#pragma unroll
+            for (int m = 0; m < 40; m += 4) {
+                const int4 x = *reinterpret_cast<const int4*>(hp + m);
+                hv[m] = x.x;
+                hv[m + 1] = x.y;
+                hv[m + 2] = x.z;
+                hv[m + 3] = x.w;
+            }
+            int32_t bx[24];   // bx[x] = B[e0 - 8 + x]
+            int32_t acc = 0;
+#pragma unroll
+            for (int m = 0; m <= 16; ++m) acc += hv[m];
+            bx[0] = acc;
+#pragma unroll
+            for (int x = 0; x < 23; ++x) {
+                acc += hv[x + 17] - hv[x];
+                bx[x + 1] = acc;
+            }
+            acc = 0;
+#pragma unroll
+            for (int m = 0; m <= 16; ++m) acc += bx[m];
+            out[i][0] = acc;
+#pragma unroll
+            for (int o = 0; o < 7; ++o) {
+                acc += bx[o + 17] - bx[o];
+                out[i][o + 1] = acc;
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < 8; ++o)
+            if (e0 + o < E)
+                *reinterpret_cast<int4*>(smooth + (size_t)(e0 + o) * Hp + r0) =
+                    make_int4(out[0][o], out[1][o], out[2][o], out[3][o]);
     }
-    if ((threadIdx.x & 31) == 0) atomicMax(best, key);
+    // codes below 16 carry no ground
+    for (int e = threadIdx.x; e < 16; e += blockDim.x)
+        *reinterpret_cast<int4*>(smooth + (size_t)e * Hp + r0) = make_int4(0, 0, 0, 0);
 }
 
 // the frame's row tables from the winning line (or the camera's when nothing voted)
-__global__ void __launch_bounds__(256) ground_rows_kernel(const unsigned long long* __restrict__ best, int H,
-                                                          int dmax, const int32_t* __restrict__ kg_tab,
-                                                          RowsDev cam, int32_t* __restrict__ rows,
-                                                          int32_t* __restrict__ line)
+__device__ void write_ground_rows(unsigned long long key, int H, int dmax, const int32_t* __restrict__ kg_tab,
+                                  const RowsDev& cam, int32_t* __restrict__ rows, int32_t* __restrict__ line)
 {
-    const unsigned long long key = *best;
     const int votes = (int)(key >> 32);
     const int k = 256 - (int)((key >> 16) & 0xffff);
     const int h = 65535 - (int)(key & 0xffff);
@@ -115,12 +153,106 @@ __global__ void __launch_bounds__(256) ground_rows_kernel(const unsigned long lo
     }
 }
 
+// one thread per four candidates and run of offsets: k = blockIdx.y + 1,
+// h = blockIdx.x * kVoteH + lane + 32 m (m < kVoteM); warp w sums the offsets
+// j in runs of 8 starting at j_lo + 8 w, every 8 kVoteWarps, and the block
+// adds the warps' sums.  One address per offset serves the four horizons.
+// best[0] is the running winner, best[1] counts finished blocks: the last
+// block to finish writes the frame's row tables.
+__global__ void __launch_bounds__(32 * kVoteWarps) vote_kernel(const int32_t* __restrict__ smooth, int H,
+                                                               int dmax, unsigned long long* __restrict__ best,
+                                                               const int32_t* __restrict__ kg_tab, RowsDev cam,
+                                                               int32_t* __restrict__ rows,
+                                                               int32_t* __restrict__ line)
+{
+    __shared__ bool s_last;
+    __shared__ int32_t s_v[kVoteWarps][kVoteH];
+    const int E = 16 * dmax + 1, Hp = ground_pitch(H);
+    const int k = blockIdx.y + 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int hb = blockIdx.x * kVoteH, hl = hb + lane;
+    // offsets j = r - h with code (k j + 8) >> 4 in [16, E): up to j_hi some
+    // horizon of the block has its row r < H, up to j_all every one has
+    const int j_lo = (248 + k - 1) / k;
+    const int j_top = (16 * E - 9) / k;
+    const int j_hi = min(j_top, H - 1 - hb);
+    const int j_all = min(j_top, H - kVoteH - hb);
+    const int32_t* __restrict__ base = smooth + hl;
+    int32_t votes[kVoteM];
+#pragma unroll
+    for (int m = 0; m < kVoteM; ++m) votes[m] = 0;
+    int j0 = j_lo + 8 * w;
+    for (; j0 + 7 <= j_all; j0 += 8 * kVoteWarps) {
+        int32_t part[8][kVoteM];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int j = j0 + i;
+            const int32_t* p = base + ((k * j + 8) >> 4) * Hp + j;
+#pragma unroll
+            for (int m = 0; m < kVoteM; ++m) part[i][m] = __ldg(p + 32 * m);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int m = 0; m < kVoteM; ++m) votes[m] += part[i][m];
+    }
+    for (; j0 <= j_hi; j0 += 8 * kVoteWarps) {
+        int32_t part[8][kVoteM];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int j = j0 + i;
+            const int32_t* p = base + ((k * j + 8) >> 4) * Hp + j;
+#pragma unroll
+            for (int m = 0; m < kVoteM; ++m)
+                part[i][m] = (j <= j_hi && hl + 32 * m + j < H) ? __ldg(p + 32 * m) : 0;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int m = 0; m < kVoteM; ++m) votes[m] += part[i][m];
+    }
+#pragma unroll
+    for (int m = 0; m < kVoteM; ++m) s_v[w][lane + 32 * m] = votes[m];
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long key = 0ull;
+#pragma unroll
+        for (int m = 0; m < kVoteM; ++m) {
+            const int h = hl + 32 * m;
+            int32_t v = 0;
+#pragma unroll
+            for (int i = 0; i < kVoteWarps; ++i) v += s_v[i][lane + 32 * m];
+            const unsigned long long km = h < H ? ((unsigned long long)(uint32_t)v << 32) |
+                                                      ((unsigned long long)(256 - k) << 16) |
+                                                      (unsigned long long)(65535 - h)
+                                                : 0ull;
+            key = km > key ? km : key;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
+            key = other > key ? other : key;
+        }
+        if (lane == 0) {
+            atomicMax(best, key);
+            // the winner is visible before this block counts as finished
+            __threadfence();
+            const unsigned long long done = atomicAdd(best + 1, 1ull);
+            s_last = done + 1 == (unsigned long long)gridDim.x * gridDim.y;
+        }
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    write_ground_rows(atomicAdd(best, 0ull), H, dmax, kg_tab, cam, rows, line);
+}
+
 }  // namespace
 
 size_t ground_work_bytes(int H, int dmax)
 {
     const size_t E = 16 * (size_t)dmax + 1;
-    return ((sizeof(int32_t) * H * E + 255) / 256 * 256) + 256 + ((sizeof(int32_t) * (2 * (size_t)H + 3) + 255) / 256 * 256);
+    return ((sizeof(int32_t) * ground_pitch(H) * E + 255) / 256 * 256) + 256 + ((sizeof(int32_t) * (2 * (size_t)H + 3) + 255) / 256 * 256);
 }
 
 cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& m, RowsDev cam, char* work,
@@ -129,20 +261,28 @@ cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& 
     // cam is a copy: frame_rows may be the caller's camera rows themselves
     const size_t E = 16 * (size_t)m.dmax + 1;
     int32_t* smooth = (int32_t*)work;
-    unsigned long long* best = (unsigned long long*)(work + (sizeof(int32_t) * g.H * E + 255) / 256 * 256);
+    unsigned long long* best = (unsigned long long*)(work + (sizeof(int32_t) * ground_pitch(g.H) * E + 255) / 256 * 256);
     int32_t* rows = (int32_t*)((char*)best + 256);
     frame_rows->fgq = rows;
     frame_rows->k_ground = rows + g.H;
     frame_rows->g_ground = nullptr;
-    cudaError_t e = cudaMemsetAsync(best, 0, sizeof(unsigned long long), st);
+    const size_t smem = sizeof(int32_t) * kVdispRows * vdisp_pitch((int)E);
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    vdisp_kernel<<<g.H, 256, sizeof(int32_t) * E, st>>>(q, g.H, g.ncols, m.dmax, smooth);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        // dmax 255: 65.7 KB
+        e = cudaFuncSetAttribute(vdisp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(int32_t) * kVdispRows * vdisp_pitch(16 * STIXELS_MAX_DMAX + 1)));
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    vdisp_kernel<<<(g.H + kVdispRows - 1) / kVdispRows, 256, smem, st>>>(q, g.H, g.ncols, m.dmax, smooth, best);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    vote_kernel<<<g.H, 256, 0, st>>>(smooth, g.H, m.dmax, best);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    ground_rows_kernel<<<1, 256, 0, st>>>(best, g.H, m.dmax, m.kg_tab, cam, rows, line ? line : rows + 2 * g.H);
+    vote_kernel<<<dim3((g.H + kVoteH - 1) / kVoteH, 256), 32 * kVoteWarps, 0, st>>>(
+        smooth, g.H, m.dmax, best, m.kg_tab, cam, rows, line ? line : rows + 2 * g.H);
     return cudaGetLastError();
 }
 

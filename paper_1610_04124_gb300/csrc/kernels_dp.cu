@@ -90,12 +90,15 @@ __device__ __forceinline__ int thr_lo(int32_t w) { return w >> 16; }
 // {d, e_g} = the object data cost and the same plus the ground-below
 // penalties, and f = the rounded mean, of the cells (B + i, B + l), i <= l
 // (tri, packed by start: slot tri_slot(i) + l - i) and (B + i, B + 32 + l)
-// (nxt, slot 32 i + l).  Cells past the column's end hold zeros.
+// (nxt, slot 32 i + l).  Cells past the column's end hold zeros.  One more
+// start's worth of slots (tri_slot(32) = 528, nxt 1024 + l) is never written:
+// the chain's look-ahead load after a block's last step reads there, so it
+// needs no clamp, and never uses what it read.
 struct ChainBuf {
-    int2 tri[528];
-    int2 nxt[1024];
-    uint8_t ftri[528];
-    uint8_t fnxt[1024];
+    int2 tri[528 + 1];
+    int2 nxt[1024 + 32];
+    uint8_t ftri[528 + 1];
+    uint8_t fnxt[1024 + 32];
 };
 // first triangle slot of start i: the starts before it own 32, 31, ... slots
 __device__ __forceinline__ int tri_slot(int i) { return (i * (65 - i)) >> 1; }
@@ -239,7 +242,7 @@ __device__ __forceinline__ void gather_chain(ChainBuf* cb, int B, int H, int P, 
 // warp, NW - 1 bulk warps); `sm` is the CTA's dynamic shared memory
 // (dp_smem_bytes with the same ring, 2 or 3 chain buffers).  Every warp
 // returns from here; the caller synchronises before reusing `sm`.
-template <int NW, bool kStdTrans>
+template <int NW, bool kStdTrans, bool kPeelFirst>
 __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const int ring, int32_t* sm,
                                           const int chain)
 {
@@ -471,18 +474,19 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
         if (run2 < run) { run = run2; runbf = run2bf; }
         run2 = INT_MAX; run2bf = 0;
         // inputs of one step, loaded a step ahead so that shared-memory latency
-        // overlaps the previous step
+        // overlaps the previous step (the ground / sky prefix at b comes from
+        // the step before, which loaded it as its b + 1)
         struct StepIn {
-            int2 gs0, gs1, de, de2;
+            int2 gs1, de, de2;
             int ff, ff2;
         };
-        auto load_in = [&](int i) {
+        // ts = tri_slot(i), carried from step to step
+        auto load_in = [&](int i, int ts) {
             StepIn x;
-            x.gs0 = s_gs[B + i];
             x.gs1 = s_gs[B + i + 1];
             // a lane below the start reads the cell (i, i): its rows are final,
             // so what it then computes is never used
-            const int e = tri_slot(i) + max(lane - i, 0);
+            const int e = ts + max(lane - i, 0);
             x.de = cb->tri[e];
             x.ff = cb->ftri[e];
             x.de2 = cb->nxt[i * 32 + lane];
@@ -491,27 +495,30 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
         };
         // one start of the block, start row b = B + i; `first` is set only for
         // b = 0, whose candidates carry the first-stixel prior
-        auto step = [&](int i, const StepIn& x, bool first) {
+        auto step = [&](int i, int2 gs0, const StepIn& x, bool first) {
             const int b = B + i;
             int32_t bo, bg, bs, ford, ag, as;
             if (first) {
                 bo = m.first[0] + kNoneCode; bg = kBig; bs = kBig; ford = INT_MAX;
-                ag = m.first[1] + kNoneCode - x.gs0.x;
-                as = m.first[2] + kNoneCode - x.gs0.y;
+                ag = m.first[1] + kNoneCode - gs0.x;
+                as = m.first[2] + kNoneCode - gs0.y;
             } else {
                 bo = vo_p + T_oo; bg = vg_p + T_og; bs = vs_p + T_os; ford = fo_p + ord_off;
                 if (kStdTrans) {
-                    ag = vo_p + T_go - x.gs0.x;
-                    as = min(vo_p + T_so, vg_p + T_sg) - x.gs0.y;
+                    ag = vo_p + T_go - gs0.x;
+                    as = min(vo_p + T_so, vg_p + T_sg) - gs0.y;
                 } else {
-                    ag = min3(vo_p + T_go, vg_p + T_gg, vs_p + T_gs) - x.gs0.x;
-                    as = min3(vo_p + T_so, vg_p + T_sg, vs_p + T_ss) - x.gs0.y;
+                    ag = min3(vo_p + T_go, vg_p + T_gg, vs_p + T_gs) - gs0.x;
+                    as = min3(vo_p + T_so, vg_p + T_sg, vs_p + T_ss) - gs0.y;
                 }
             }
-            // every lane: start b applied to its rows of blocks j and j + 1
-            const int32_t cand = min3(bo + x.de.x + (x.ff > ford ? pen_ord : 0), bg + x.de.y, bs + x.de.x);
+            // every lane: start b applied to its rows of blocks j and j + 1; the
+            // object and sky terms add the same data cost, so
+            // min(bo [+ ordering] + d, bs + d) = min(bo [+ ordering], bs) + d
+            const int32_t o_lo = min(bo, bs), o_hi = min(bo + pen_ord, bs);
+            const int32_t cand = min((x.ff > ford ? o_hi : o_lo) + x.de.x, bg + x.de.y);
             if (cand < run) { run = cand; runbf = (b << 8) | x.ff; }
-            const int32_t cand2 = min3(bo + x.de2.x + (x.ff2 > ford ? pen_ord : 0), bg + x.de2.y, bs + x.de2.x);
+            const int32_t cand2 = min((x.ff2 > ford ? o_hi : o_lo) + x.de2.x, bg + x.de2.y);
             if (cand2 < run2) { run2 = cand2; run2bf = (b << 8) | x.ff2; }
             if (ag < rg) { rg = ag; rgb = b; }
             if (as < rs) { rs = as; rsb = b; }
@@ -529,12 +536,27 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
                 s_raw2[i] = make_int2(rgb, rsb);
             }
         };
-        StepIn cur = load_in(0);
-#pragma unroll 2
-        for (int i = 0; i < nb; ++i) {
-            const StepIn nx = load_in(i + 1 < nb ? i + 1 : i);
-            step(i, cur, j == 0 && i == 0);
+        int2 gs0 = s_gs[B];
+        int ts = 0;
+        StepIn cur = load_in(0, 0);
+        int i = 0;
+        if (kPeelFirst && j == 0) {
+            // start 0, with the first-stixel prior, outside the loop
+            const StepIn nx = load_in(1, 32);            // 1 = nb: read, never used
+            step(0, gs0, cur, true);
+            gs0 = cur.gs1;
             cur = nx;
+            ts = 32;
+            i = 1;
+        }
+#pragma unroll 2
+        for (; i < nb; ++i) {
+            const int tsn = ts + 32 - i;                 // tri_slot(i + 1)
+            const StepIn nx = load_in(i + 1, tsn);       // i + 1 = nb: read, never used
+            step(i, gs0, cur, !kPeelFirst && j == 0 && i == 0);
+            gs0 = cur.gs1;
+            cur = nx;
+            ts = tsn;
         }
         __syncwarp();
         // the block's back-pointers and the contexts of the starts that follow its rows
@@ -613,7 +635,7 @@ template <int NW, bool kStd, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) stixel_dp_kernel(DpArgs a, int ring)
 {
     extern __shared__ __align__(16) int32_t sm[];
-    dp_column<NW, kStd>(a, blockIdx.x, ring, sm, 0);
+    dp_column<NW, kStd, false>(a, blockIdx.x, ring, sm, 0);
 }
 
 // Persistent form: each CTA takes columns from a work list (one shared atomic
@@ -638,7 +660,10 @@ __global__ void __launch_bounds__(NW * 32, MINB)
         int* dst = reinterpret_cast<int*>(&s_args);
         for (int i = threadIdx.x; i < (int)(sizeof(DpArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
         __syncthreads();
-        dp_column<NW, kStd>(s_args, w.y, ring, sm, w.y & 3);
+        // start 0 peeled out of the step loop: measured faster in this
+        // kernel's shapes (32 1024x440 frames 12.86 -> 13.07 K frames/s),
+        // slower in the per-frame kernel
+        dp_column<NW, kStd, true>(s_args, w.y, ring, sm, w.y & 3);
         __syncthreads();
     }
 }

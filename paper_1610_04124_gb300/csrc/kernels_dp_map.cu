@@ -24,7 +24,9 @@
 // the block's rows in order: row k adds its starts inside the block (lane =
 // start), then the warp turns the row's bins into prefix / suffix minima over
 // f (one lane owns 8 consecutive f) in global scratch, which the rows above
-// read.  Three CTA barriers per block instead of several per row.
+// read; at the block's end all warps copy its bins (the object state keys,
+// for the backtracking) to global memory.  Three CTA barriers per block
+// instead of several per row.
 #include <climits>
 
 #include "internal.h"
@@ -290,7 +292,6 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, un
                 for (int i = 0; i < kPer; ++i) {
                     const int f = kPer * lane + i;
                     if (f < F) {
-                        keyo[rw + f] = bin[f];
                         pre[rw + f] = pc < pv[i] ? pc : pv[i];
                         suf[rw + f] = sc < sv[i] ? sc : sv[i];
                     }
@@ -302,7 +303,8 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, un
                 // the row's best object state (over every f): the last prefix
                 const unsigned long long best = __shfl_sync(0xffffffffu, pt, 31);
                 if (lane == 0) s_bo[k] = best;
-                __threadfence_block();
+                // the rows above in this block are read by this warp only:
+                // the warp barrier orders its lanes' stores and loads
                 __syncwarp();
             }
         } else if (warp != 4) {
@@ -313,10 +315,14 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, un
             phase_a(bin_n, gbin_n, sbin_n, K1, nb1, warp - 1 - (warp > 4), K0, kMapWarps - 2);
         }
         __syncthreads();                          // block j's rows are final and visible
-        // the next block's starts inside this block, then the bins of this
-        // block are reset for block j + 2
+        // the next block's starts inside this block; then this block's bins
+        // (its object state keys) go to global memory for the backtracking,
+        // coalesced, and are reset for block j + 2
         phase_a(bin_n, gbin_n, sbin_n, K1, nb1, K0 + warp, K0 + nb, kMapWarps);
-        for (int i = tid; i < (int)BF; i += blockDim.x) bin_j[i] = kNoKey;
+        for (int i = tid; i < (int)BF; i += blockDim.x) {
+            if (i < nb * F) keyo[(size_t)K0 * F + i] = bin_j[i];
+            bin_j[i] = kNoKey;
+        }
         if (tid < kMapRows) { gbin_j[tid] = kNoKey; sbin_j[tid] = kNoKey; }
         __syncthreads();
     }

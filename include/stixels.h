@@ -200,12 +200,17 @@ int stixels_compute(stixels_t h, const float* d_disparity, int H, int W, void* s
                     const stixels_output_t* out);
 
 /*
- * Same pipeline from HOST memory to HOST memory, synchronous: copies the frame
- * to the device, runs stixels_compute on the handle's own stream, copies the
- * results back and waits.  h_stixels: ncols * capacity records; h_counts:
- * ncols; h_cost (optional): ncols floats.  Pinned (page-locked) host buffers
- * give full copy bandwidth; pageable ones work but are slower.  Returns the
- * compute status, or CAPACITY / DEVICE_FAULT if the error word was set.
+ * Same pipeline from HOST memory to HOST memory, synchronous: runs
+ * stixels_compute on the handle's own stream and waits.  h_stixels: ncols *
+ * capacity records; h_counts: ncols; h_cost (optional): ncols floats.
+ * Page-locked (pinned) host buffers are used in place over the host link: the
+ * reduction kernel reads a pinned frame directly, and when h_stixels, h_counts
+ * and h_cost (if given) are all pinned the DP writes its results into them.
+ * Pageable buffers go through device staging buffers and copies (slower).
+ * The buffers must not be freed or written by the caller during the call.
+ * Returns the compute status, or CAPACITY / DEVICE_FAULT if this frame set a
+ * status flag (the flags of this call only; the handle's error word that
+ * stixels_get_error reads is not touched).
  */
 int stixels_compute_host(stixels_t h, const float* h_disparity, int H, int W,
                          stixel_t* h_stixels, int32_t* h_counts, float* h_cost);

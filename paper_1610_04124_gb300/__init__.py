@@ -221,9 +221,14 @@ class Stixels:
         return self._h
 
     def output_shape(self, H: int, W: int):
-        n, c = C.c_int(), C.c_int()
-        _check(lib().stixels_output_shape(self._h, H, W, C.byref(n), C.byref(c)), "output_shape")
-        return n.value, c.value
+        # fixed for a handle and frame size: asked of the library once
+        cache = self.__dict__.setdefault("_shapes", {})
+        shape = cache.get((H, W))
+        if shape is None:
+            n, c = C.c_int(), C.c_int()
+            _check(lib().stixels_output_shape(self._h, H, W, C.byref(n), C.byref(c)), "output_shape")
+            shape = cache[(H, W)] = (n.value, c.value)
+        return shape
 
     def reserve(self, H: int, W: int):
         _check(lib().stixels_reserve(self._h, H, W), "reserve")

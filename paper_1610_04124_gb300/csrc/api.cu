@@ -374,7 +374,10 @@ int stixels_solve(stixels_t h, const int32_t* d_pd, const int32_t* d_pg, const i
     return cuda_status(launch_dp(d_pd, d_pg, d_ps, d_po, g, h->md, r, *out, h->d_err, (cudaStream_t)stream));
 }
 
-int stixels_compute(stixels_t h, const float* d_disparity, int H, int W, void* stream, const stixels_output_t* out)
+// The pipeline of stixels_compute, with the kernels' status flags ORed into
+// `err` (device-addressable; the handle's error word for stixels_compute).
+static int compute_frame(stixels_t h, const float* d_disparity, int H, int W, void* stream,
+                         const stixels_output_t* out, uint32_t* err)
 {
     int rc = check_frame(h, H, W);
     if (rc) return rc;
@@ -405,9 +408,14 @@ int stixels_compute(stixels_t h, const float* d_disparity, int H, int W, void* s
     if (e == cudaSuccess && est) e = launch_ground(q, g, h->md, r, ws + L.total, &r, nullptr, st);
     if (e == cudaSuccess) e = launch_luts(q, g, h->md, r, pd, pg, ps, po, st);
     if (e == cudaSuccess)
-        e = gmap ? launch_dp_map(pd, pg, ps, po, g, h->md, r, *out, h->d_err, ws + L.total + gw, st)
-                 : launch_dp(pd, pg, ps, po, g, h->md, r, *out, h->d_err, st);
+        e = gmap ? launch_dp_map(pd, pg, ps, po, g, h->md, r, *out, err, ws + L.total + gw, st)
+                 : launch_dp(pd, pg, ps, po, g, h->md, r, *out, err, st);
     return cuda_status(e);
+}
+
+int stixels_compute(stixels_t h, const float* d_disparity, int H, int W, void* stream, const stixels_output_t* out)
+{
+    return compute_frame(h, d_disparity, H, W, stream, out, h ? h->d_err : nullptr);
 }
 
 int stixels_selftest_wait(stixels_t h, int polls, void* stream, uint32_t* flags)
@@ -430,6 +438,20 @@ int stixels_get_error(stixels_t h, void* stream, uint32_t* flags)
     return STIXELS_OK;
 }
 
+// The address at which the device reads / writes host memory p, or null if it
+// cannot: page-locked host memory is mapped into the device's address space
+// under unified addressing (cudaPointerGetAttributes then reports it as host
+// memory with a device pointer); pageable memory is not.
+static void* device_view(const void* p)
+{
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();                       // an unknown pointer is not an error here
+        return nullptr;
+    }
+    return attr.type == cudaMemoryTypeHost ? attr.devicePointer : nullptr;
+}
+
 int stixels_compute_host(stixels_t h, const float* h_disparity, int H, int W, stixel_t* h_stixels,
                          int32_t* h_counts, float* h_cost)
 {
@@ -444,8 +466,16 @@ int stixels_compute_host(stixels_t h, const float* h_disparity, int H, int W, st
     const size_t cnt_bytes = align_up(sizeof(int32_t) * (size_t)g.ncols, 256);
     const size_t cost_bytes = align_up(sizeof(float) * (size_t)g.ncols, 256);
     const size_t out_bytes = st_bytes + cnt_bytes + cost_bytes;
+    // Page-locked buffers are used in place over the host link (the reduction
+    // reads the frame from host memory once; the DP writes its results there),
+    // others through device staging buffers and copies.
+    const float* d_in = static_cast<const float*>(device_view(h_disparity));
+    stixel_t* d_st = static_cast<stixel_t*>(device_view(h_stixels));
+    int32_t* d_cnt = static_cast<int32_t*>(device_view(h_counts));
+    float* d_cost = h_cost ? static_cast<float*>(device_view(h_cost)) : nullptr;
+    const bool out_mapped = d_st && d_cnt && (!h_cost || d_cost);
     cudaError_t e = cudaSuccess;
-    if (h->in_bytes < in_bytes) {
+    if (!d_in && h->in_bytes < in_bytes) {
         cudaFree(h->d_in);
         h->d_in = nullptr;
         h->in_bytes = 0;
@@ -453,7 +483,7 @@ int stixels_compute_host(stixels_t h, const float* h_disparity, int H, int W, st
         if (e != cudaSuccess) return cuda_status(e);
         h->in_bytes = in_bytes;
     }
-    if (h->out_bytes < out_bytes) {
+    if (!out_mapped && h->out_bytes < out_bytes) {
         cudaFree(h->d_out);
         h->d_out = nullptr;
         h->out_bytes = 0;
@@ -462,28 +492,46 @@ int stixels_compute_host(stixels_t h, const float* h_disparity, int H, int W, st
         h->out_bytes = out_bytes;
     }
     stixels_output_t out;
-    out.stixels = (stixel_t*)h->d_out;
-    out.counts = (int32_t*)((char*)h->d_out + st_bytes);
-    out.column_cost = (float*)((char*)h->d_out + st_bytes + cnt_bytes);
+    if (out_mapped) {
+        out.stixels = d_st;
+        out.counts = d_cnt;
+        out.column_cost = d_cost;
+    } else {
+        out.stixels = (stixel_t*)h->d_out;
+        out.counts = (int32_t*)((char*)h->d_out + st_bytes);
+        out.column_cost = (float*)((char*)h->d_out + st_bytes + cnt_bytes);
+    }
     out.column_cost_fixed = nullptr;
     out.ncols = g.ncols;
     out.capacity = cap;
-    e = cudaMemcpyAsync(h->d_in, h_disparity, in_bytes, cudaMemcpyHostToDevice, h->stream);
-    if (e != cudaSuccess) return cuda_status(e);
-    rc = stixels_compute(h, h->d_in, H, W, h->stream, &out);
+    if (!d_in) {
+        e = cudaMemcpyAsync(h->d_in, h_disparity, in_bytes, cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        d_in = h->d_in;
+    }
+    // this frame's status flags go straight to the pinned word (cleared here,
+    // read after the wait); the handle's own error word is left alone
+    volatile uint32_t* flags_word = h->h_err;
+    uint32_t* d_flags = static_cast<uint32_t*>(device_view(h->h_err));
+    *flags_word = 0;
+    rc = compute_frame(h, d_in, H, W, h->stream, &out, d_flags ? d_flags : h->d_err);
     if (rc) return rc;
-    e = cudaMemcpyAsync(h_counts, out.counts, sizeof(int32_t) * g.ncols, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h_stixels, out.stixels, sizeof(stixel_t) * (size_t)g.ncols * cap, cudaMemcpyDeviceToHost,
-                            h->stream);
-    if (e == cudaSuccess && h_cost)
-        e = cudaMemcpyAsync(h_cost, out.column_cost, sizeof(float) * g.ncols, cudaMemcpyDeviceToHost, h->stream);
-    // the error word rides the same stream (read, then cleared): one wait in all
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_err, h->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), h->stream);
+    if (!out_mapped) {
+        e = cudaMemcpyAsync(h_counts, out.counts, sizeof(int32_t) * g.ncols, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_stixels, out.stixels, sizeof(stixel_t) * (size_t)g.ncols * cap,
+                                cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess && h_cost)
+            e = cudaMemcpyAsync(h_cost, out.column_cost, sizeof(float) * g.ncols, cudaMemcpyDeviceToHost, h->stream);
+    }
+    // (were the word not device-addressable, the flags went to the handle's
+    // error word: read and clear it on the same stream, one wait in all)
+    if (!d_flags && e == cudaSuccess)
+        e = cudaMemcpyAsync(h->h_err, h->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream);
+    if (!d_flags && e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(uint32_t), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_status(e);
-    const uint32_t flags = *h->h_err;
+    const uint32_t flags = *flags_word;
     if (flags & (STIXELS_ERR_INFEASIBLE | STIXELS_ERR_TIMEOUT)) return STIXELS_E_DEVICE_FAULT;
     if (flags & STIXELS_ERR_CAPACITY) return STIXELS_E_CAPACITY;
     return STIXELS_OK;

@@ -289,6 +289,49 @@ def test_compute_host_equals_device_path_and_is_deterministic():
     h.close()
 
 
+def test_compute_host_pinned_buffers_in_place():
+    """Page-locked host buffers are read and written in place by the kernels
+    (no staging copies): every mix of pinned and pageable input and outputs,
+    including a pinned frame that starts inside its allocation, gives the
+    device path's results."""
+    cam = scenes.CONFIG2
+    sc = scenes.make_scene(cam, 7500, n_obstacles=(8, 20))
+    lp, _ = both_params(cam)
+    h = S.Stixels(lp)
+    ref = S.Stixels.to_host(h.compute(cuda(sc.disparity)))
+    torch.cuda.synchronize()
+    H, W = sc.disparity.shape
+    # a frame one float into a pinned allocation: the device reads it at that offset
+    pinned_in = torch.empty(H * W + 1, dtype=torch.float32, pin_memory=True).numpy()[1:].reshape(H, W)
+    pinned_in[:] = sc.disparity
+    for in_pinned in (False, True):
+        for out_pinned in (False, True):
+            src = pinned_in if in_pinned else sc.disparity.copy()
+            st, counts, cost, rc = h.compute_host(src, h.alloc_host_output(H, W, pinned=out_pinned))
+            assert rc == S.OK
+            assert np.array_equal(counts, ref[1]) and np.array_equal(cost, ref[2])
+            for c in range(len(counts)):
+                n = min(counts[c], lp.max_stixels_per_col)
+                assert np.array_equal(st[c, :n], ref[0][c, :n])
+    h.close()
+
+
+def test_compute_host_reports_its_own_frame_status():
+    """compute_host returns CAPACITY when its frame overflows a column's
+    capacity (pinned and pageable buffers), and leaves the handle's error word,
+    which stixels_get_error reads, as it was."""
+    cam = scenes.CONFIG1
+    sc = scenes.make_scene(cam, 7600, n_obstacles=(3, 6))
+    h = S.Stixels(S.default_params(cam, max_stixels_per_col=1))
+    H, W = sc.disparity.shape
+    pinned_in = torch.from_numpy(sc.disparity).pin_memory().numpy()
+    for src, pinned in ((sc.disparity, False), (pinned_in, True)):
+        _, counts, _, rc = h.compute_host(src, h.alloc_host_output(H, W, pinned=pinned))
+        assert rc == S.E_CAPACITY and counts.max() > 1
+        assert h.get_error() == 0
+    h.close()
+
+
 @pytest.mark.parametrize("i", [1, 4])
 def test_pixel_grid_pipeline_paper_sizes(i):
     """The LUT_cost variant (whole-pixel grid, Sec. 3.4) at 1024x440 s=5 and the

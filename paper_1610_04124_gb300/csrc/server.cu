@@ -2,15 +2,17 @@
 // scheduler thread doing continuous batching over two CUDA streams.
 //
 // Life of a frame: stixels_submit reserves arena space (input, intermediates,
-// outputs), copies the frame in on the copy stream and waits for that copy,
-// then queues the request.  The scheduler takes every queued request, plans
+// outputs) and a status word (page-locked host memory that the kernels set
+// through its device mapping), copies the frame in on the copy stream and
+// waits for that copy, then queues the request.  The scheduler takes every queued request, plans
 // the batch tables for them (the planner of the batched mode), uploads the
 // tables through a pinned staging buffer and launches the batched kernels on
 // the next of its two compute streams, recording one completion event per
 // iteration.  A stream is reused only after its previous iteration finished,
 // so at most two iterations are in flight and they overlap on the device.
-// stixels_poll checks the request's iteration event, copies the results out
-// and returns the slot's memory to the arena.
+// stixels_poll checks the request's iteration event, reads its status word,
+// copies the results out on the calling thread's stream (one wait) and
+// returns the slot's memory and status word.
 #include <string.h>
 
 #include <chrono>
@@ -95,7 +97,8 @@ struct Request {
     uint64_t ticket = 0;
     FrameJob job;
     size_t off = 0, bytes = 0;
-    uint32_t* d_err = nullptr;          // the frame's own device error word
+    uint32_t* d_err = nullptr;          // the frame's status word (device view of h_flags[flag])
+    int flag = -1;                      // its index in the server's page-locked status words
     State state = State::Queued;
     bool claimed = false;               // a poll is copying its results out
     int status = STIXELS_OK;            // launch failure of its iteration
@@ -113,6 +116,12 @@ struct stixels_server_s {
     cudaStream_t streams[kStreams] = {nullptr, nullptr};
     char* d_tables[kStreams] = {nullptr, nullptr};
     char* h_staging[kStreams] = {nullptr, nullptr};
+    // per-slot status words in page-locked host memory, mapped for the device:
+    // the kernels set a frame's flags there, submit clears them and poll reads
+    // them, with no stream operation for either
+    uint32_t* h_flags = nullptr;
+    uint32_t* d_flags = nullptr;
+    std::vector<int> free_flags;
     std::shared_ptr<Iteration> last[kStreams];
     int next_stream = 0;
 
@@ -132,6 +141,8 @@ int status_of(cudaError_t e) { return status_from_cuda(e); }
 
 void release_request(stixels_server_t s, const std::shared_ptr<Request>& r)
 {
+    if (r->flag >= 0) s->free_flags.push_back(r->flag);
+    r->flag = -1;
     s->arena->release(r->off, r->bytes);
     s->requests.erase(r->ticket);
     s->stats.slots_in_use = (int32_t)s->requests.size();
@@ -216,11 +227,14 @@ int stixels_server_create(size_t mem_budget_bytes, int max_slots, stixels_server
         if (e == cudaSuccess) e = cudaMalloc(&s->d_tables[k], kTableBytes);
         if (e == cudaSuccess) e = cudaHostAlloc(&s->h_staging[k], kTableBytes, cudaHostAllocDefault);
     }
+    if (e == cudaSuccess) e = cudaHostAlloc(&s->h_flags, sizeof(uint32_t) * max_slots, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&s->d_flags, s->h_flags, 0);
     if (e == cudaSuccess) e = prepare_dp_kernels();
     if (e != cudaSuccess) {
         stixels_server_destroy(s);
         return status_of(e);
     }
+    for (int i = max_slots - 1; i >= 0; --i) s->free_flags.push_back(i);
     s->arena.reset(new Arena(mem_budget_bytes));
     s->stats.bytes_budget = mem_budget_bytes;
     s->stats.max_slots = max_slots;
@@ -260,7 +274,11 @@ int stixels_submit(stixels_server_t s, stixels_t camera, const float* disparity,
         r->job.out.counts = (int32_t*)o;                              o += up256(sizeof(int32_t) * C);
         r->job.out.column_cost = (float*)o;                           o += up256(sizeof(int32_t) * C);
         r->job.out.column_cost_fixed = (int32_t*)o;                   o += up256(sizeof(int32_t) * C);
-        r->d_err = (uint32_t*)o;
+        // admission keeps the live requests below max_slots: a word is free
+        r->flag = s->free_flags.back();
+        s->free_flags.pop_back();
+        reinterpret_cast<volatile uint32_t*>(s->h_flags)[r->flag] = 0u;
+        r->d_err = s->d_flags + r->flag;
         r->job.view.err = r->d_err;
         r->job.out.ncols = g.ncols;
         r->job.out.capacity = (int32_t)cap;
@@ -273,7 +291,6 @@ int stixels_submit(stixels_server_t s, stixels_t camera, const float* disparity,
     // copy the frame in; the caller may reuse its buffer once this returns
     cudaError_t e = cudaMemcpyAsync((void*)r->job.in, disparity, sizeof(float) * (size_t)H * W, cudaMemcpyDefault,
                                     s->copy_stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(r->d_err, 0, sizeof(uint32_t), s->copy_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_stream);
     std::lock_guard<std::mutex> lock(s->mu);
     if (e != cudaSuccess) {
@@ -299,8 +316,10 @@ int stixels_poll(stixels_server_t s, uint64_t ticket, const stixels_output_t* ou
         if (r->job.out.ncols > 0 && (!out->stixels || !out->counts)) return STIXELS_E_INVALID_ARG;
     }
     // wait for the frame's iteration: first for the scheduler to pick it up,
-    // then for its completion event
-    const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us);
+    // then for its completion event; the first 2 ms yield the core between
+    // checks (a frame takes 0.05 - 1 ms), later ones sleep 20 us
+    const auto start = std::chrono::steady_clock::now();
+    const auto deadline = start + std::chrono::microseconds(timeout_us);
     for (;;) {
         std::shared_ptr<Iteration> iter;
         {
@@ -313,9 +332,12 @@ int stixels_poll(stixels_server_t s, uint64_t ticket, const stixels_output_t* ou
             if (q == cudaSuccess) break;
             if (q != cudaErrorNotReady) return status_of(q);
         }
-        if (std::chrono::steady_clock::now() >= deadline)
-            return timeout_us == 0 ? STIXELS_E_NOT_READY : STIXELS_E_TIMEOUT;
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        const auto now = std::chrono::steady_clock::now();
+        if (now >= deadline) return timeout_us == 0 ? STIXELS_E_NOT_READY : STIXELS_E_TIMEOUT;
+        if (now - start < std::chrono::milliseconds(2))
+            std::this_thread::yield();
+        else
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
     {
         // one poll copies a frame out and frees it; a concurrent poll of the
@@ -326,15 +348,21 @@ int stixels_poll(stixels_server_t s, uint64_t ticket, const stixels_output_t* ou
     }
     const stixels_output_t& src = r->job.out;
     const size_t C = (size_t)src.ncols;
-    uint32_t flags = 0;
-    cudaError_t e = cudaMemcpy(&flags, r->d_err, sizeof(flags), cudaMemcpyDeviceToHost);
-    if (C && e == cudaSuccess) {
-        e = cudaMemcpy(out->stixels, src.stixels, sizeof(stixel_t) * C * src.capacity, cudaMemcpyDefault);
-        if (e == cudaSuccess) e = cudaMemcpy(out->counts, src.counts, sizeof(int32_t) * C, cudaMemcpyDefault);
+    // the iteration is done: its kernels' writes to the status word are visible
+    const uint32_t flags = reinterpret_cast<volatile uint32_t*>(s->h_flags)[r->flag];
+    // the results out on this thread's own stream, one wait
+    cudaError_t e = cudaSuccess;
+    if (C) {
+        const cudaStream_t cs = cudaStreamPerThread;
+        e = cudaMemcpyAsync(out->stixels, src.stixels, sizeof(stixel_t) * C * src.capacity, cudaMemcpyDefault, cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out->counts, src.counts, sizeof(int32_t) * C, cudaMemcpyDefault, cs);
         if (e == cudaSuccess && out->column_cost)
-            e = cudaMemcpy(out->column_cost, src.column_cost, sizeof(float) * C, cudaMemcpyDefault);
+            e = cudaMemcpyAsync(out->column_cost, src.column_cost, sizeof(float) * C, cudaMemcpyDefault, cs);
         if (e == cudaSuccess && out->column_cost_fixed)
-            e = cudaMemcpy(out->column_cost_fixed, src.column_cost_fixed, sizeof(int32_t) * C, cudaMemcpyDefault);
+            e = cudaMemcpyAsync(out->column_cost_fixed, src.column_cost_fixed, sizeof(int32_t) * C,
+                                cudaMemcpyDefault, cs);
+        const cudaError_t w = cudaStreamSynchronize(cs);
+        if (e == cudaSuccess) e = w;
     }
     std::lock_guard<std::mutex> lock(s->mu);
     release_request(s, r);
@@ -378,6 +406,7 @@ int stixels_server_destroy(stixels_server_t s)
         if (s->h_staging[k]) cudaFreeHost(s->h_staging[k]);
     }
     if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+    if (s->h_flags) cudaFreeHost(s->h_flags);
     cudaFree(s->d_arena);
     if (prev >= 0) cudaSetDevice(prev);
     delete s;

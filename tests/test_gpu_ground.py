@@ -53,6 +53,24 @@ def test_estimate_equals_oracle_2048x880():
     h.close()
 
 
+@pytest.mark.parametrize("W, H, dmax, horizon, seed", [
+    (1000, 2048, 128, 700, 6020),     # the tallest column: 16 vote CTAs per slope
+    (1000, 1800, 255, 600, 6024),     # the largest disparity range the fixed-point budget allows at this
+                                      # height: 4081 codes per histogram row (the 65.7 KB shared-memory opt-in)
+    (40, 1, 16, 0, 6021),             # one row: no line has a row above its horizon
+    (40, 3, 16, 1, 6022),             # a partial group of four histogram rows
+    (45, 6, 4, 2, 6023)])
+def test_estimate_equals_oracle_at_the_limits(W, H, dmax, horizon, seed):
+    cam = scenes.Camera(W, H, stixel_width=5, dmax=dmax, horizon_row=horizon, baseline_m=0.4, camera_height_m=1.0)
+    sc = scenes.make_scene(cam, seed, n_obstacles=(2, 4), span_cols=(1, 6))
+    h = S.Stixels(S.default_params(cam, ground_estimate=1))
+    q = h.reduce(cuda(sc.disparity))
+    got = h.estimate_ground(q, cam.height, cam.width // cam.stixel_width)
+    ref = oracle.ground_estimate(oracle.reduce(sc.disparity, cam.stixel_width, cam.dmax), cam.dmax)
+    assert got == ref
+    h.close()
+
+
 @pytest.mark.parametrize("i", range(4))
 def test_frames_with_the_estimate_equal_oracle(i):
     cam, sc = _scenes()[i]

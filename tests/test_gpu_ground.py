@@ -71,6 +71,24 @@ def test_estimate_equals_oracle_at_the_limits(W, H, dmax, horizon, seed):
     h.close()
 
 
+@pytest.mark.parametrize("k0,h0,copies", [(40, 30, 1), (40, 30, 2), (100, 10, 1), (7, 5, 3), (256, 60, 2)])
+def test_votes_of_a_planted_line_are_the_triangle_peak_per_row(k0, h0, copies):
+    """Codes exactly on the line (k0, h0) in identical columns, fed to the
+    estimate directly: that line with 17 votes per column and row whose code
+    lies in [16, 16 dmax] (the closed form the oracle is pinned to)."""
+    H, dmax = 100, 64
+    r = np.arange(H)
+    code = np.where(r > h0, (k0 * (r - h0) + 8) >> 4, 0)
+    rows = int(((code >= 16) & (code <= 16 * dmax)).sum())
+    q = np.tile(code[::-1].astype(np.int16), (copies, 1))
+    cam = scenes.Camera(5 * copies, H, stixel_width=5, dmax=dmax, horizon_row=30, baseline_m=0.4,
+                        camera_height_m=1.0)
+    h = S.Stixels(S.default_params(cam, ground_estimate=1))
+    got = h.estimate_ground(torch.from_numpy(q).cuda(), H, copies)
+    assert got == (k0, h0, 17 * copies * rows) == oracle.ground_estimate(q, dmax)
+    h.close()
+
+
 @pytest.mark.parametrize("i", range(4))
 def test_frames_with_the_estimate_equal_oracle(i):
     cam, sc = _scenes()[i]

@@ -33,6 +33,21 @@ def test_planted_ground_line_is_recovered_exactly(b, h, k, horizon):
         assert votes > 0
 
 
+@pytest.mark.parametrize("k0,h0,copies", [(40, 30, 1), (40, 30, 2), (100, 10, 1), (7, 5, 3), (256, 60, 2)])
+def test_votes_of_a_planted_line_are_the_triangle_peak_per_row(k0, h0, copies):
+    """Codes exactly on the line (k0, h0) in `copies` identical columns: each
+    row whose code lies in [16, 16 dmax] gives that line the smoothing
+    triangle's peak weight 17 once per column, and every other line gets less
+    on some row, so the estimate is that line with 17 * copies * rows votes
+    (a closed form of the histogram, the triangle's weights and the row range)."""
+    H, dmax = 100, 64
+    r = np.arange(H)
+    code = np.where(r > h0, (k0 * (r - h0) + 8) >> 4, 0)
+    rows = int(((code >= 16) & (code <= 16 * dmax)).sum())
+    q = np.tile(code[::-1].astype(np.int16), (copies, 1))       # bottom-up: v = H - 1 - r
+    assert oracle.ground_estimate(q, dmax) == (k0, h0, 17 * copies * rows)
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_noisy_ground_line_is_close(seed):
     cam = scenes.CONFIG2                                   # alpha = 0.25 (k = 64), horizon 180

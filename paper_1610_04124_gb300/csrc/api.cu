@@ -515,7 +515,12 @@ int stixels_compute_host(stixels_t h, const float* h_disparity, int H, int W, st
     uint32_t* d_flags = static_cast<uint32_t*>(device_view(h->h_err));
     *flags_word = 0;
     rc = compute_frame(h, d_in, H, W, h->stream, &out, d_flags ? d_flags : h->d_err);
-    if (rc) return rc;
+    if (rc) {
+        // a stage may have been launched before the failing one: let it finish
+        // with the caller's buffers before they are handed back
+        cudaStreamSynchronize(h->stream);
+        return rc;
+    }
     if (!out_mapped) {
         e = cudaMemcpyAsync(h_counts, out.counts, sizeof(int32_t) * g.ncols, cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess)

@@ -16,9 +16,9 @@
 // a table over the clamped code built at create time.  With no vote at all
 // the camera's line is kept.
 //
-// Kernels: one CTA per four image rows builds their histograms in shared
+// Kernels: one CTA per two image rows builds their histograms in shared
 // memory, smooths them (the triangle as a box of 17 codes applied twice) and
-// stores S code-major (S[e][r], rows padded to a multiple of four), so that
+// stores S code-major (S[e][r], rows padded to a multiple of two), so that
 // for a fixed slope k and row offset j = r - h the code is the same for every
 // horizon h and a warp over 32 consecutive h reads 32 consecutive words.  A
 // vote CTA takes one k and 128 horizons (four per lane, so that one address
@@ -31,7 +31,7 @@
 namespace stx {
 namespace {
 
-constexpr int kVdispRows = 4;   // image rows per histogram CTA
+constexpr int kVdispRows = 2;   // image rows per histogram CTA
 constexpr int kVoteM = 4;              // horizons per lane, 32 apart
 constexpr int kVoteH = 32 * kVoteM;    // horizons per vote CTA
 constexpr int kVoteWarps = 8;          // warps per vote CTA, each over every eighth run of 8 offsets
@@ -43,7 +43,7 @@ __host__ __device__ inline int ground_pitch(int H) { return (H + kVdispRows - 1)
 // 16-byte words
 __host__ __device__ inline int vdisp_pitch(int E) { return (E + 23 + 3) / 4 * 4; }
 
-// per four image rows: histograms of the codes, smoothed, stored code-major
+// per two image rows: histograms of the codes, smoothed, stored code-major
 __global__ void __launch_bounds__(256) vdisp_kernel(const int16_t* __restrict__ q, int H, int ncols, int dmax,
                                                     int32_t* __restrict__ smooth, unsigned long long* __restrict__ best)
 {
@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(256) vdisp_kernel(const int16_t* __restrict__ 
     for (int g = threadIdx.x; g < G; g += blockDim.x) {
         const int e0 = 16 + 8 * g;
         int32_t out[kVdispRows][8];
+        static_assert(kVdispRows == 2, "one 8-byte store per code below");
 #pragma unroll
         for (int i = 0; i < kVdispRows; ++i) {
             const int32_t* hp = s_h + i * P + 8 * g;   // code e0 - 16, 16-byte aligned
@@ -117,12 +118,11 @@ __global__ void __launch_bounds__(256) vdisp_kernel(const int16_t* __restrict__ 
 #pragma unroll
         for (int o = 0; o < 8; ++o)
             if (e0 + o < E)
-                *reinterpret_cast<int4*>(smooth + (size_t)(e0 + o) * Hp + r0) =
-                    make_int4(out[0][o], out[1][o], out[2][o], out[3][o]);
+                *reinterpret_cast<int2*>(smooth + (size_t)(e0 + o) * Hp + r0) = make_int2(out[0][o], out[1][o]);
     }
     // codes below 16 carry no ground
     for (int e = threadIdx.x; e < 16; e += blockDim.x)
-        *reinterpret_cast<int4*>(smooth + (size_t)e * Hp + r0) = make_int4(0, 0, 0, 0);
+        *reinterpret_cast<int2*>(smooth + (size_t)e * Hp + r0) = make_int2(0, 0);
 }
 
 // the frame's row tables from the winning line (or the camera's when nothing voted)
@@ -272,7 +272,7 @@ cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& 
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        // dmax 255: 65.7 KB
+        // dmax 255: 32.8 KB
         e = cudaFuncSetAttribute(vdisp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(int32_t) * kVdispRows * vdisp_pitch(16 * STIXELS_MAX_DMAX + 1)));
         if (e != cudaSuccess) return e;

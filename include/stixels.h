@@ -16,10 +16,13 @@
  *     every row are ignored.
  *   - Disparities are clamped to [0, dmax] (NaN -> 0) and put on a 1/16-pixel
  *     grid ("Q4 code" = round-half-even(16 d)) before any other step.
- *   - Costs are carried in exact fixed point: every per-pixel term and every
- *     prior is rounded to a multiple of 2^-12 cost units, sums are exact int32
- *     arithmetic (internal unit 2^-14).  Results are therefore deterministic
- *     and independent of thread scheduling, and ties are broken exactly.
+ *   - The DP decides in exact fixed point: every per-pixel cost term and
+ *     every prior is rounded to a multiple of 2^-12 cost units, sums are exact
+ *     int32 arithmetic (internal unit 2^-14).  Decisions are therefore
+ *     deterministic and independent of thread scheduling, and ties are broken
+ *     exactly.  The ground line and the gravity / diving / ordering thresholds
+ *     are not rounded.  The reported column cost is the chosen segmentation's
+ *     cost in real arithmetic (see stixels_output_t).
  *   - "Device pointer" = memory the CUDA device can address (cudaMalloc,
  *     torch CUDA tensors, managed memory).  Streams are cudaStream_t passed as
  *     void*; NULL = the legacy default stream.
@@ -44,7 +47,7 @@
 extern "C" {
 #endif
 
-#define STIXELS_ABI_VERSION 1
+#define STIXELS_ABI_VERSION 2
 #define STIXELS_MAX_STIXEL_WIDTH 16
 #define STIXELS_MAX_DMAX 255
 #define STIXELS_MAX_HEIGHT 2048
@@ -141,8 +144,13 @@ typedef struct stixel {
  * listed bottom -> top.  counts[c] = number of stixels of column c (it may
  * exceed capacity; then only the bottom `capacity` are written and the error
  * word gets STIXELS_ERR_CAPACITY).  column_cost (optional, may be NULL): the
- * column's minimum cost in cost units.  column_cost_fixed (optional): the same
- * cost exactly, as an integer in units of 2^-14. */
+ * cost of the column's segmentation in real arithmetic -- Eq. 4 per pixel and
+ * the priors without the fixed-point grid (per-pixel terms in FP32, summed
+ * exactly in fixed point at 2^-24, rounded to FP32 once; within ~3e-7
+ * relative of the exact value), over the whole segmentation even when it
+ * exceeds capacity.  column_cost_fixed (optional): the DP's fixed-point
+ * minimum that chose the segmentation, exactly, as an integer in units of
+ * 2^-14. */
 typedef struct stixels_output {
     stixel_t* stixels;
     int32_t* counts;
@@ -280,18 +288,23 @@ int stixels_solve(stixels_t h, const int32_t* d_pd, const int32_t* d_pg, const i
  * per-row residual tables are not exported).  Cost values in 2^-14 units, forbidden /
  * infinite entries = 2^29.  Sizes and meaning:
  *   k_obj[dmax+1]    normalisation constant K (Eq. 4) of the object model at integer f
- *   g_obj, g_ground, g_sky [16*dmax+1]   residual term (e/16)^2 / (2 sigma^2) of each
- *                    class at Q4 residual e
- *   fgq[H]           ground-model disparity at bottom-up row v, Q4 code
+ *   g_obj, g_sky [16*dmax+1]   residual term (e/16)^2 / (2 sigma^2) of the
+ *                    object / sky class at Q4 residual e
+ *   fg[H]            ground-model disparity f_g(v) (Sec. 3.1) at bottom-up row v,
+ *                    in px, unrounded (the ground residual of a pixel is
+ *                    (q/16 - fg)^2 / (2 sigma_ground^2) in FP64 on the host,
+ *                    then rounded to the cost grid)
  *   k_ground[H]      K of the ground model at row v
+ *   thr[H]           gravity / diving thresholds at row v: the object penalty
+ *                    applies iff f > (int16)(thr & 0xffff), resp. iff f < thr >> 16
  *   scalars[STIXELS_N_SCALARS] = { C_out, K_sky, first[object, ground, sky],
  *                    trans[above][below] row-major (9), gravity, diving, ordering
- *                    penalties, eps_gravity, eps_diving, eps_order (Q4 codes) }
+ *                    penalties, floor(eps_order) (the ordering penalty applies
+ *                    iff f_above > f_below + floor(eps_order)) }
  * Any pointer may be NULL. */
-#define STIXELS_N_SCALARS 20
-int stixels_model_tables(const stixels_params_t* params, int H, int32_t* k_obj, int32_t* g_obj,
-                         int32_t* g_ground, int32_t* g_sky, int32_t* fgq, int32_t* k_ground,
-                         int32_t* scalars);
+#define STIXELS_N_SCALARS 18
+int stixels_model_tables(const stixels_params_t* params, int H, int32_t* k_obj, int32_t* g_obj, int32_t* g_sky,
+                         double* fg, int32_t* k_ground, int32_t* thr, int32_t* scalars);
 
 /* ---- batched mode: many frames, one graph-captured launch sequence ---- */
 

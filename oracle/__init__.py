@@ -119,6 +119,8 @@ def lib():
                                P(C.c_int16), C.c_int]
         L.or_eval_segmentation.argtypes = [P(Params), P(C.c_int16), C.c_int, C.c_void_p, C.c_int,
                                            P(C.c_double)]
+        L.or_eval_frame.argtypes = [P(Params), P(C.c_int16), C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                    P(C.c_int32), P(C.c_double)]
         L.or_brute_force.argtypes = [P(Params), P(C.c_int16), C.c_int, P(C.c_double), P(C.c_int64),
                                      C.c_void_p, P(C.c_int32)]
         L.or_max_threads.argtypes = []
@@ -270,6 +272,20 @@ def eval_segmentation(params: Params, q_col: np.ndarray, stixels: np.ndarray) ->
     _check(lib().or_eval_segmentation(C.byref(params), _ptr(q_col, C.c_int16), q_col.shape[0],
                                       st.ctypes.data, len(st), C.byref(out)), "eval_segmentation")
     return out.value
+
+
+def eval_frame(params: Params, q: np.ndarray, stixels: np.ndarray, counts: np.ndarray) -> np.ndarray:
+    """Direct re-evaluation of one segmentation per column (stixels: ncols x cap,
+    counts[c] used) under the frame's model (with ground_estimate, the line
+    estimated from q); NaN where a list is incomplete (counts > cap)."""
+    q = np.ascontiguousarray(q, dtype=np.int16)
+    st = np.ascontiguousarray(stixels, dtype=STIXEL_DTYPE)
+    cnt = np.ascontiguousarray(counts, dtype=np.int32)
+    ncols, H = q.shape
+    out = np.zeros(ncols)
+    _check(lib().or_eval_frame(C.byref(params), _ptr(q, C.c_int16), ncols, H, st.ctypes.data, st.shape[1],
+                               _ptr(cnt, C.c_int32), _ptr(out, C.c_double)), "eval_frame")
+    return out
 
 
 def brute_force(params: Params, q_col: np.ndarray):

@@ -25,14 +25,16 @@
  * re-evaluates the cost of a given segmentation from direct per-pixel sums.
  *
  * Two arithmetic modes:
- *   quantize = 1  every per-pixel term (C_out, the normalisation constant K,
- *                 the squared-residual term), every prior and the ground line
- *                 are put on fixed grids (costs: 2^-12; ground disparity: 1/16
- *                 px) before use.  All sums are then exact in FP64, so ties are
- *                 exact and the tie-break below decides them.  This is the
- *                 arithmetic the CUDA library implements (in int32).
- *   quantize = 0  the same formulation with plain FP64 reals (used to bound
- *                 the effect of the grids).
+ *   quantize = 1  every per-pixel cost term (C_out, the normalisation
+ *                 constant K, the squared-residual term) and every prior is
+ *                 put on the 2^-12 cost grid before use.  All sums are then
+ *                 exact in FP64, so ties are exact and the tie-break below
+ *                 decides them.  This is the arithmetic the CUDA library's DP
+ *                 decides in (int32).  The ground line and the gravity,
+ *                 diving and ordering thresholds are the model's own, not
+ *                 rounded, in both modes.
+ *   quantize = 0  the same formulation with plain FP64 reals: the paper's
+ *                 arithmetic, which the library's reported costs follow.
  *
  * Readings of the paper where it is silent or ambiguous (all restated in the
  * project's design notes):
@@ -277,27 +279,18 @@ static int model_build_line(const or_params_t* p, int H, int line_k, int line_h,
 
     /* ground line: image row r = H-1-v; f = alpha (r - horizon) */
     const double alpha = (double)p->baseline_m * cos((double)p->pitch_rad) / (double)p->camera_height_m;
-    const long long eg = llround(16.0 * (double)p->eps_gravity);
-    const long long ed = llround(16.0 * (double)p->eps_diving);
     for (int v = 0; v < H; ++v) {
         int r = H - 1 - v;
-        double fg;
-        if (m->quantize) {
-            long long fgq = line_k > 0 ? llround((double)line_k * (double)(r - line_h) / 16.0)
-                                       : llround(16.0 * alpha * (double)(r - p->horizon_row));
-            fg = (double)fgq / 16.0;
-            m->g_hi[v] = (double)(fgq + eg);
-            m->g_lo[v] = (double)(fgq - ed);
-        } else {
-            fg = line_k > 0 ? (double)line_k * (double)(r - line_h) / 256.0 : alpha * (double)(r - p->horizon_row);
-            m->g_hi[v] = 16.0 * (fg + (double)p->eps_gravity);
-            m->g_lo[v] = 16.0 * (fg - (double)p->eps_diving);
-        }
+        /* the ground model's own disparity at the row, in both modes: the grids
+         * apply to cost terms, not to the model or to the thresholds below */
+        double fg = line_k > 0 ? (double)line_k * (double)(r - line_h) / 256.0 : alpha * (double)(r - p->horizon_row);
+        m->g_hi[v] = 16.0 * (fg + (double)p->eps_gravity);
+        m->g_lo[v] = 16.0 * (fg - (double)p->eps_diving);
         m->fg[v] = fg;
         m->sig_gnd[v] = sigma_at(p, m->sigma[OR_GROUND], fg);
         m->k_ground[v] = k_const(fg, m->sig_gnd[v], p_out, d_range);
     }
-    m->ord_eps16 = m->quantize ? (double)llround(16.0 * (double)p->eps_order) : 16.0 * (double)p->eps_order;
+    m->ord_eps16 = 16.0 * (double)p->eps_order;
 
     const double bic = (double)p->cost_new_stixel;
     for (int c = 0; c < 3; ++c) {
@@ -795,25 +788,56 @@ static double direct_data(const or_model_t* m, const int16_t* q, int c, int b, i
  * and classes only), from direct per-pixel sums and the true priors of each
  * adjacent pair.  Returns INFINITY for an invalid list (gaps, overlaps, bad
  * class) -- callers check validity separately. */
+/* The total of a segmentation under model m (see or_eval_segmentation). */
+static double eval_with_model(const or_model_t* m, const int16_t* q, const or_stixel_t* st, int n)
+{
+    const int H = m->H;
+    double total = 0.0;
+    int prev_c = OR_NONE, prev_f = 0, expect_b = 0;
+    for (int i = 0; i < n; ++i) {
+        int b = st[i].v_bottom, k = st[i].v_top, c = st[i].cls;
+        if (b != expect_b || k < b || k >= H || c < 0 || c > 2) return INFINITY;
+        int64_t S = 0;
+        for (int v = b; v <= k; ++v) S += q[v];
+        int f = mean_f(S, k - b + 1);
+        total += direct_data(m, q, c, b, k, f);
+        total += (i == 0) ? m->first[c] : pair_prior(m, c, prev_c, b, f, prev_f);
+        prev_c = c; prev_f = f; expect_b = k + 1;
+    }
+    return expect_b == H ? total : INFINITY;
+}
+
 int or_eval_segmentation(const or_params_t* p, const int16_t* q, int H, const or_stixel_t* st, int n, double* out)
 {
     or_model_t m;
     int rc = model_build(p, H, &m);
     if (rc) return rc;
-    double total = 0.0;
-    int prev_c = OR_NONE, prev_f = 0, expect_b = 0;
-    for (int i = 0; i < n; ++i) {
-        int b = st[i].v_bottom, k = st[i].v_top, c = st[i].cls;
-        if (b != expect_b || k < b || k >= H || c < 0 || c > 2) { *out = INFINITY; model_free(&m); return OR_OK; }
-        int64_t S = 0;
-        for (int v = b; v <= k; ++v) S += q[v];
-        int f = mean_f(S, k - b + 1);
-        total += direct_data(&m, q, c, b, k, f);
-        total += (i == 0) ? m.first[c] : pair_prior(&m, c, prev_c, b, f, prev_f);
-        prev_c = c; prev_f = f; expect_b = k + 1;
+    *out = eval_with_model(&m, q, st, n);
+    model_free(&m);
+    return OR_OK;
+}
+
+/* The totals of one segmentation per column of a frame's reduced codes q
+ * (ncols x H, bottom-up), under the frame's model: the camera's ground line,
+ * or with ground_estimate the line or_frame estimates from the same codes.
+ * st: ncols x cap stixels, counts[c] of them used (a column with
+ * counts[c] > cap gets NaN: its list is incomplete). */
+int or_eval_frame(const or_params_t* p, const int16_t* q, int ncols, int H, const or_stixel_t* st, int cap,
+                  const int32_t* counts, double* out)
+{
+    if (ncols < 0 || H < 1 || cap < 0) return OR_E_ARG;
+    int32_t line[3] = {0, 0, 0};
+    if (p->ground_estimate) {
+        int rc = or_ground_estimate(q, ncols, H, p->dmax, line);
+        if (rc) return rc;
+        if (line[2] == 0) line[0] = 0;          /* no ground seen: the camera's line */
     }
-    if (expect_b != H) total = INFINITY;
-    *out = total;
+    or_model_t m;
+    int rc = model_build_line(p, H, line[0], line[1], &m);
+    if (rc) return rc;
+    for (int c = 0; c < ncols; ++c)
+        out[c] = counts[c] > cap ? NAN
+                                 : eval_with_model(&m, q + (size_t)c * H, st + (size_t)c * cap, counts[c]);
     model_free(&m);
     return OR_OK;
 }

@@ -23,7 +23,7 @@ OK, E_INVALID_ARG, E_OOM, E_CUDA, E_CAPACITY, E_NOT_READY, E_TIMEOUT, E_REJECTED
 ERR_CAPACITY, ERR_INFEASIBLE, ERR_TIMEOUT = 1, 2, 4
 MAX_HEIGHT = 2048
 NOALLOC_SCRATCH_BYTES = 48 << 20
-N_SCALARS = 20
+N_SCALARS = 18
 UNITS_PER_COST = 16384
 
 STIXEL_DTYPE = np.dtype([("row_top", "<i2"), ("row_bottom", "<i2"), ("cls", "u1"), ("flags", "u1"),
@@ -175,13 +175,15 @@ def lut_pitch(H: int) -> int:
 def model_tables(params: Params, H: int) -> Dict[str, np.ndarray]:
     """Host-side fixed-point tables the library builds for `params` (no CUDA call)."""
     F, E = params.dmax + 1, 16 * params.dmax + 1
-    t = dict(k_obj=np.zeros(F, np.int32), g_obj=np.zeros(E, np.int32), g_ground=np.zeros(E, np.int32),
-             g_sky=np.zeros(E, np.int32), fgq=np.zeros(max(H, 1), np.int32), k_ground=np.zeros(max(H, 1), np.int32),
+    n = max(H, 1)
+    t = dict(k_obj=np.zeros(F, np.int32), g_obj=np.zeros(E, np.int32), g_sky=np.zeros(E, np.int32),
+             fg=np.zeros(n, np.float64), k_ground=np.zeros(n, np.int32), thr=np.zeros(n, np.int32),
              scalars=np.zeros(N_SCALARS, np.int32))
     _check(lib().stixels_model_tables(C.byref(params), H, *(t[k].ctypes.data for k in
-                                                             ("k_obj", "g_obj", "g_ground", "g_sky", "fgq",
-                                                              "k_ground", "scalars"))), "model_tables")
-    t["fgq"], t["k_ground"] = t["fgq"][:H], t["k_ground"][:H]
+                                                             ("k_obj", "g_obj", "g_sky", "fg", "k_ground", "thr",
+                                                              "scalars"))), "model_tables")
+    for k in ("fg", "k_ground", "thr"):
+        t[k] = t[k][:H]
     return t
 
 

@@ -1,4 +1,5 @@
 // api.cu -- the C ABI of stixels.h: handles, workspace, per-frame pipeline.
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -16,8 +17,8 @@ namespace {
 
 // Per-height row tables resident on the device.
 struct RowsBuf {
-    int32_t* d = nullptr;   // fgq[H], k_ground[H], then (variable sigma) g_ground[H][emax + 1]
-    int H = 0;
+    double* d = nullptr;    // the row tables of one height (RowsDev), then the rows' residual windows
+    int H = 0, gw = 0;
 };
 
 struct Workspace {
@@ -53,7 +54,10 @@ int cuda_status(cudaError_t e) { return stx::status_from_cuda(e); }
 struct stixels_s {
     int device = 0;
     HostModel hm;
-    int32_t* d_tables = nullptr;       // k_obj | g_obj | g_ground | g_sky
+    int32_t* d_tables = nullptr;       // k_obj | g_obj | g_sky | lut_cost | kg_tab | est_pool
+    void* d_real = nullptr;            // RealModelDev, then its k_obj | inv_obj | rkg_tab
+    RealParams rp;                     // the cost report's priors and constants (DP kernel arguments)
+    const int32_t* est_pool = nullptr; // ground estimate: the residual windows of estimated lines (in d_tables)
     ModelDev md;
     std::map<int, RowsBuf> rows;       // per height
     Workspace ws;
@@ -69,29 +73,34 @@ struct stixels_s {
 
 namespace {
 
+RowsDev rows_of(stixels_t h, const RowsBuf& rb)
+{
+    RowsDev r;
+    r.fg = rb.d;
+    r.real_model = static_cast<const RealModelDev*>(h->d_real);
+    r.gpool = reinterpret_cast<const int32_t*>(reinterpret_cast<const char*>(rb.d) + rows_arrays_bytes(rb.H));
+    r.gw = rb.gw;
+    r.gn = rb.H * rb.gw;
+    return r;
+}
+
 int ensure_rows(stixels_t h, int H, RowsDev* out)
 {
     auto it = h->rows.find(H);
     if (it == h->rows.end()) {
-        std::vector<int32_t> fgq, kg, gr;
-        if (!build_rows(h->hm, H, &fgq, &kg, &gr)) return STIXELS_E_INVALID_ARG;
-        if (!budget_ok(h->hm, H, kg)) return STIXELS_E_INVALID_ARG;
+        std::vector<char> block;
         RowsBuf rb;
+        if (!build_rows(h->hm, H, &block, &rb.gw)) return STIXELS_E_INVALID_ARG;
         rb.H = H;
-        const size_t n = 2 * (size_t)H + gr.size();
-        cudaError_t e = cudaMalloc(&rb.d, sizeof(int32_t) * n);
-        if (e != cudaSuccess) return cuda_status(e);
-        std::vector<int32_t> buf(n);
-        memcpy(buf.data(), fgq.data(), sizeof(int32_t) * H);
-        memcpy(buf.data() + H, kg.data(), sizeof(int32_t) * H);
-        if (!gr.empty()) memcpy(buf.data() + 2 * (size_t)H, gr.data(), sizeof(int32_t) * gr.size());
-        e = cudaMemcpy(rb.d, buf.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) { cudaFree(rb.d); return cuda_status(e); }
+        cudaError_t e = cudaMalloc(&rb.d, block.size());
+        if (e == cudaSuccess) e = cudaMemcpy(rb.d, block.data(), block.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(rb.d);
+            return cuda_status(e);
+        }
         it = h->rows.emplace(H, rb).first;
     }
-    out->fgq = it->second.d;
-    out->k_ground = it->second.d + H;
-    out->g_ground = h->hm.var_sigma ? it->second.d + 2 * (size_t)H : nullptr;
+    *out = rows_of(h, it->second);
     return STIXELS_OK;
 }
 
@@ -170,9 +179,8 @@ int handle_view(stixels_t h, int H, HandleView* v)
     if (it == h->rows.end()) return STIXELS_E_INVALID_ARG;
     v->device = h->device;
     v->model = h->md;
-    v->rows.fgq = it->second.d;
-    v->rows.k_ground = it->second.d + H;
-    v->rows.g_ground = h->hm.var_sigma ? it->second.d + 2 * (size_t)H : nullptr;
+    v->rows = rows_of(h, it->second);
+    v->rp = h->rp;
     v->err = h->d_err;
     v->stixel_width = h->hm.p.stixel_width;
     v->reduce_mode = reduce_code(h->hm.p);
@@ -214,19 +222,56 @@ int stixels_create(const stixels_params_t* params, stixels_t* out_handle)
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) { delete h; return cuda_status(e); }
     const HostModel& m = h->hm;
-    const size_t n_tab = m.k_obj.size() + m.g_obj.size() + m.g_ground.size() + m.g_sky.size() + m.lut_cost.size() +
-                         m.kg_tab.size();
+    const size_t n_tab = m.k_obj.size() + m.g_obj.size() + m.g_sky.size() + m.lut_cost.size() + m.kg_tab.size() +
+                         m.est_pool.size();
     e = cudaMalloc(&h->d_tables, sizeof(int32_t) * n_tab);
     if (e == cudaSuccess) {
         std::vector<int32_t> buf;
         buf.reserve(n_tab);
         buf.insert(buf.end(), m.k_obj.begin(), m.k_obj.end());
         buf.insert(buf.end(), m.g_obj.begin(), m.g_obj.end());
-        buf.insert(buf.end(), m.g_ground.begin(), m.g_ground.end());
         buf.insert(buf.end(), m.g_sky.begin(), m.g_sky.end());
         buf.insert(buf.end(), m.lut_cost.begin(), m.lut_cost.end());
         buf.insert(buf.end(), m.kg_tab.begin(), m.kg_tab.end());
+        buf.insert(buf.end(), m.est_pool.begin(), m.est_pool.end());
         e = cudaMemcpy(h->d_tables, buf.data(), sizeof(int32_t) * n_tab, cudaMemcpyHostToDevice);
+    }
+    // the model without the grid: the struct, then its per-f tables
+    const size_t F = m.real.k_obj.size(), NK = m.real.rkg_tab.size();
+    const size_t real_bytes = sizeof(RealModelDev) + sizeof(float) * (2 * F + NK);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_real, real_bytes);
+    if (e == cudaSuccess) {
+        std::vector<char> buf(real_bytes);
+        RealModelDev rd;
+        memset(&rd, 0, sizeof(rd));
+        const RealModel& r = m.real;
+        RealParams& rp = rd.rp;
+        auto units = [](double x) {
+            return std::isinf(x) ? kReportInf : (long long)llround(x * (double)kReportUnits);
+        };
+        for (int c = 0; c < 3; ++c) {
+            rp.first[c] = units(r.first[c]);
+            for (int q = 0; q < 3; ++q) rp.trans[c][q] = units(r.trans[c][q]);
+        }
+        rp.pen_grav = units(r.pen_grav);
+        rp.pen_div = units(r.pen_div);
+        rp.pen_ord = units(r.pen_ord);
+        rp.c_out = r.c_out;
+        rp.k_sky = r.k_sky;
+        rp.inv_sky = r.inv_sky;
+        h->rp = rp;
+        rd.eps_g = r.eps_g;
+        rd.eps_d = r.eps_d;
+        rd.inv_ground = r.inv_ground;
+        rd.dmax = m.dmax;
+        // k_obj, inv_obj and rkg_tab follow the struct (the kernels address them from it)
+        float* tk = reinterpret_cast<float*>((char*)h->d_real + sizeof(RealModelDev));
+        rd.rkg_tab = NK ? tk + 2 * F : nullptr;
+        memcpy(buf.data(), &rd, sizeof(rd));
+        memcpy(buf.data() + sizeof(rd), r.k_obj.data(), sizeof(float) * F);
+        memcpy(buf.data() + sizeof(rd) + sizeof(float) * F, r.inv_obj.data(), sizeof(float) * F);
+        if (NK) memcpy(buf.data() + sizeof(rd) + sizeof(float) * 2 * F, r.rkg_tab.data(), sizeof(float) * NK);
+        e = cudaMemcpy(h->d_real, buf.data(), real_bytes, cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(uint32_t));
@@ -248,20 +293,17 @@ int stixels_create(const stixels_params_t* params, stixels_t* out_handle)
     d.pen_grav = m.pen_grav;
     d.pen_div = m.pen_div;
     d.pen_ord = m.pen_ord;
-    d.eps_g = m.eps_g;
-    d.eps_d = m.eps_d;
-    d.eps_o = m.eps_o;
+    d.ord_off = m.ord_off;
     d.esat_obj = m.esat[0];
-    d.esat_ground = m.esat[1];
     d.esat_sky = m.esat[2];
     d.k_obj = h->d_tables;
     d.g_obj = d.k_obj + m.k_obj.size();
-    d.g_ground = d.g_obj + m.g_obj.size();
-    d.g_sky = d.g_ground + m.g_ground.size();
+    d.g_sky = d.g_obj + m.g_obj.size();
     d.var_sigma = m.var_sigma ? 1 : 0;
     d.int_grid = m.p.pixel_grid;
     d.lut_cost = m.p.pixel_grid ? d.g_sky + m.g_sky.size() : nullptr;
     d.kg_tab = m.p.ground_estimate ? d.g_sky + m.g_sky.size() + m.lut_cost.size() : nullptr;
+    h->est_pool = m.p.ground_estimate ? d.g_sky + m.g_sky.size() + m.lut_cost.size() + m.kg_tab.size() : nullptr;
     *out_handle = h;
     return STIXELS_OK;
 }
@@ -276,6 +318,7 @@ int stixels_destroy(stixels_t h)
     for (auto& kv : h->rows) cudaFree(kv.second.d);
     cudaFree(h->ws.base);
     cudaFree(h->d_tables);
+    cudaFree(h->d_real);
     cudaFree(h->d_err);
     if (h->h_err) cudaFreeHost(h->h_err);
     cudaFree(h->d_in);
@@ -330,10 +373,11 @@ int stixels_estimate_ground(stixels_t h, const int16_t* d_q, int H, int ncols, v
     RowsDev r;
     int rc = ensure_rows(h, H, &r);
     if (rc) return rc;
-    rc = ensure_workspace(h, ground_work_bytes(H, h->hm.dmax));
+    rc = ensure_workspace(h, ground_work_bytes(H, h->hm.dmax, h->hm.est_gw));
     if (rc) return rc;
     RowsDev fr;
-    return cuda_status(launch_ground(d_q, g, h->md, r, (char*)h->ws.base, &fr, d_line, (cudaStream_t)stream));
+    return cuda_status(launch_ground(d_q, g, h->md, r, h->est_pool, h->hm.est_gw, (char*)h->ws.base, &fr, d_line,
+                                     (cudaStream_t)stream));
 }
 
 int stixels_build_luts(stixels_t h, const int16_t* d_q, int H, int ncols, void* stream, int32_t* d_pd,
@@ -368,10 +412,10 @@ int stixels_solve(stixels_t h, const int32_t* d_pd, const int32_t* d_pg, const i
         if (!map_fits(H, h->hm.dmax + 1)) return STIXELS_E_INVALID_ARG;
         rc = ensure_workspace(h, map_scratch_bytes(H, ncols, h->hm.dmax + 1));
         if (rc) return rc;
-        return cuda_status(launch_dp_map(d_pd, d_pg, d_ps, d_po, g, h->md, r, *out, h->d_err, h->ws.base,
+        return cuda_status(launch_dp_map(d_pd, d_pg, d_ps, d_po, g, h->md, r, h->rp, *out, h->d_err, h->ws.base,
                                          (cudaStream_t)stream));
     }
-    return cuda_status(launch_dp(d_pd, d_pg, d_ps, d_po, g, h->md, r, *out, h->d_err, (cudaStream_t)stream));
+    return cuda_status(launch_dp(d_pd, d_pg, d_ps, d_po, g, h->md, r, h->rp, *out, h->d_err, (cudaStream_t)stream));
 }
 
 // The pipeline of stixels_compute, with the kernels' status flags ORed into
@@ -392,7 +436,7 @@ static int compute_frame(stixels_t h, const float* d_disparity, int H, int W, vo
     const bool est = h->hm.p.ground_estimate != 0;
     if (est && !ground_size_ok(g)) return STIXELS_E_INVALID_ARG;
     const FrameLayout L = frame_layout(H, g.ncols, h->hm.dmax + 1);
-    const size_t gw = est ? (ground_work_bytes(H, h->hm.dmax) + 255) / 256 * 256 : 0;
+    const size_t gw = est ? (ground_work_bytes(H, h->hm.dmax, h->hm.est_gw) + 255) / 256 * 256 : 0;
     const bool gmap = h->hm.p.global_map != 0;
     if (gmap && !map_fits(H, h->hm.dmax + 1)) return STIXELS_E_INVALID_ARG;
     rc = ensure_workspace(h, L.total + gw + (gmap ? map_scratch_bytes(H, g.ncols, h->hm.dmax + 1) : 0));
@@ -405,11 +449,11 @@ static int compute_frame(stixels_t h, const float* d_disparity, int H, int W, vo
     int32_t* po = (int32_t*)(ws + L.po);
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = launch_reduce(d_disparity, g, h->hm.dmax, reduce_code(h->hm.p), q, st);
-    if (e == cudaSuccess && est) e = launch_ground(q, g, h->md, r, ws + L.total, &r, nullptr, st);
+    if (e == cudaSuccess && est) e = launch_ground(q, g, h->md, r, h->est_pool, h->hm.est_gw, ws + L.total, &r, nullptr, st);
     if (e == cudaSuccess) e = launch_luts(q, g, h->md, r, pd, pg, ps, po, st);
     if (e == cudaSuccess)
-        e = gmap ? launch_dp_map(pd, pg, ps, po, g, h->md, r, *out, err, ws + L.total + gw, st)
-                 : launch_dp(pd, pg, ps, po, g, h->md, r, *out, err, st);
+        e = gmap ? launch_dp_map(pd, pg, ps, po, g, h->md, r, h->rp, *out, err, ws + L.total + gw, st)
+                 : launch_dp(pd, pg, ps, po, g, h->md, r, h->rp, *out, err, st);
     return cuda_status(e);
 }
 
@@ -542,23 +586,25 @@ int stixels_compute_host(stixels_t h, const float* h_disparity, int H, int W, st
     return STIXELS_OK;
 }
 
-int stixels_model_tables(const stixels_params_t* params, int H, int32_t* k_obj, int32_t* g_obj,
-                         int32_t* g_ground, int32_t* g_sky, int32_t* fgq, int32_t* k_ground, int32_t* scalars)
+int stixels_model_tables(const stixels_params_t* params, int H, int32_t* k_obj, int32_t* g_obj, int32_t* g_sky,
+                         double* fg, int32_t* k_ground, int32_t* thr, int32_t* scalars)
 {
     if (!params || H < 0 || H > STIXELS_MAX_HEIGHT) return STIXELS_E_INVALID_ARG;
     HostModel m;
     int rc = build_model(params, &m);
     if (rc) return rc;
-    if (m.var_sigma) return STIXELS_E_INVALID_ARG;     // per-disparity / per-row tables are not exported
+    if (m.var_sigma) return STIXELS_E_INVALID_ARG;     // per-disparity / per-row residual tables are not exported
     if (k_obj) memcpy(k_obj, m.k_obj.data(), sizeof(int32_t) * m.k_obj.size());
     if (g_obj) memcpy(g_obj, m.g_obj.data(), sizeof(int32_t) * m.g_obj.size());
-    if (g_ground) memcpy(g_ground, m.g_ground.data(), sizeof(int32_t) * m.g_ground.size());
     if (g_sky) memcpy(g_sky, m.g_sky.data(), sizeof(int32_t) * m.g_sky.size());
-    if (fgq || k_ground) {
-        std::vector<int32_t> f, k, g;
-        build_rows(m, H, &f, &k, &g);
-        if (fgq) memcpy(fgq, f.data(), sizeof(int32_t) * H);
-        if (k_ground) memcpy(k_ground, k.data(), sizeof(int32_t) * H);
+    if (H > 0 && (fg || k_ground || thr)) {
+        std::vector<char> block;
+        int gw = 0;
+        if (!build_rows(m, H, &block, &gw)) return STIXELS_E_INVALID_ARG;
+        const double* b = reinterpret_cast<const double*>(block.data());
+        if (fg) memcpy(fg, b, sizeof(double) * H);
+        if (k_ground) memcpy(k_ground, rows_kg(b, H), sizeof(int32_t) * H);
+        if (thr) memcpy(thr, rows_thr(b, H), sizeof(int32_t) * H);
     }
     if (scalars) {
         int32_t* s = scalars;
@@ -570,9 +616,7 @@ int stixels_model_tables(const stixels_params_t* params, int H, int32_t* k_obj, 
         s[14] = m.pen_grav;
         s[15] = m.pen_div;
         s[16] = m.pen_ord;
-        s[17] = m.eps_g;
-        s[18] = m.eps_d;
-        s[19] = m.eps_o;
+        s[17] = m.ord_off;
     }
     return STIXELS_OK;
 }

@@ -3,6 +3,7 @@
 
 #include <stdint.h>
 
+#include <cmath>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -49,6 +50,34 @@ constexpr DivTable make_div_table()
     return t;
 }
 
+// The priors without the cost grid (prior + BIC, penalties) and the outlier
+// and sky constants, for the cost report: kernel arguments, so that the report
+// reads no memory for them.  The report sums in int64 fixed point with
+// kReportUnits per cost unit (a prior's rounding: <= 3e-8), since FP64 is far
+// slower than the FP32 / integer pipes on this part.
+constexpr float kReportUnits = 16777216.0f;       // 2^24
+constexpr long long kReportInf = 1ll << 60;       // a forbidden prior (never on a solved path)
+struct RealParams {
+    long long first[3];      // first-stixel prior + BIC, per class
+    long long trans[3][3];   // [above][below] transition prior + BIC
+    long long pen_grav, pen_div, pen_ord;
+    float c_out, k_sky, inv_sky, pad;
+};
+
+// The model without the fixed-point grid, resident on the device: what the
+// DP kernels' epilogue needs to report a solved segmentation's cost in real
+// arithmetic (Eq. 3-4 per pixel in FP32, sums in int64 fixed point).  The
+// struct is followed in the same allocation by float k_obj[dmax + 1] (object
+// K at integer f), float inv_obj[dmax + 1] (1 / (2 sigma^2)) and, for the
+// ground estimate, rkg_tab.
+struct RealModelDev {
+    RealParams rp;           // the priors and constants (copied into each frame's DP arguments)
+    double eps_g, eps_d;     // gravity / diving tolerances (px): an estimated line's thresholds
+    float inv_ground;        // 1 / (2 sigma_g^2): an estimated line's rows
+    int32_t dmax;
+    const float* rkg_tab;    // ground estimate only: [256 dmax + 1] unrounded ground K at f = c / 256
+};
+
 // Per-handle model, resident on the device (the "offline" LUTs of Sec. 3.4)
 // plus the scalars every kernel needs.  Passed to kernels by value.
 struct ModelDev {
@@ -59,27 +88,68 @@ struct ModelDev {
     int32_t first[3];        // first-stixel prior + BIC, per class
     int32_t trans[3][3];     // [above][below] transition prior + BIC
     int32_t pen_grav, pen_div, pen_ord;
-    int32_t eps_g, eps_d, eps_o;     // Q4 tolerances
+    int32_t ord_off;         // ordering penalty iff f_above > f_below + ord_off (floor of eps_order)
     // saturation residual per class: for e >= esat, K + G[e] >= C_out for every K
     // of that class, so min(C_out, K + G[min(e, esat)]) equals the unclamped cost
-    int32_t esat_obj, esat_ground, esat_sky;
+    int32_t esat_obj, esat_sky;
     const int32_t* k_obj;    // [dmax + 1]
     const int32_t* g_obj;    // [emax + 1]
-    const int32_t* g_ground; // [emax + 1]
     const int32_t* g_sky;    // [emax + 1]
-    int32_t var_sigma;       // 1: g_obj is [dmax + 1][emax + 1] (one residual row per f) and the
-                             //    ground residuals come per row (RowsDev::g_ground)
+    int32_t var_sigma;       // 1: g_obj is [dmax + 1][emax + 1] (one residual row per f)
     int32_t int_grid;        // 1: reduced disparities are whole pixels (multiples of 16 in Q4)
     const int32_t* lut_cost; // int_grid only: [dmax + 1][dmax + 1], object cost of (f, d)
-    const int32_t* kg_tab;   // ground estimate only: [16 dmax + 1] ground K at a clamped ground code
+    const int32_t* kg_tab;   // ground estimate only: [256 dmax + 1] ground K at f = c / 256 (clamped)
 };
 
-// Per-(handle, H) row tables.
+// Per-row tables of one height (a handle's camera line, or one frame's
+// estimated line), one device block; v = bottom-up row:
+//   double fg[H]   the ground model's disparity f_g(v) (Sec. 3.1), unrounded
+//   int32  kg[H]   the ground K on the cost grid
+//   int32  thr[H]  gravity / diving thresholds on the object's f, as int16
+//                  halves: penalty iff f > fhi (low), iff f < flo (high)
+//   int32  gf[H]   floor(16 f_g): the Q4 code at or below the line
+//   int32  goff[H] offset of the row's residual window in gpool
+//   float  rkg[H]  the ground K unrounded (cost report)
+//   float  rinv[H] 1 / (2 sigma_g^2) (cost report)
+//   float  rdg[H]  f_g - gf / 16, in [0, 1/16) (cost report)
+// The ground residual of a pixel with Q4 code q, (q / 16 - f_g)^2 / (2
+// sigma_g^2) on the cost grid, is gpool[goff[v] + q - (gf[v] - ER)] for the
+// gw = 2 ER + 2 codes q of the row's window; every code outside it is at
+// least ER / 16 px from the line, where the pixel costs C_out.  A camera
+// line's windows (one per row) follow the arrays in the same block; an
+// estimated line's disparities are multiples of 1/256 px, so its rows share
+// 16 windows built at create time.
 struct RowsDev {
-    const int32_t* fgq;      // [H] ground-model Q4 disparity at bottom-up row v
-    const int32_t* k_ground; // [H]
-    const int32_t* g_ground; // variable sigma only: [H][emax + 1] residual table of each row, else null
+    const double* fg;                 // start of the block
+    const RealModelDev* real_model;   // the handle's model without the grid (cost report)
+    const int32_t* gpool;             // ground residual windows
+    int32_t gw;                       // codes per window, 2 ER + 2
+    int32_t gn;                       // words of gpool
 };
+__host__ __device__ inline size_t rows_arrays_bytes(int H) { return ((size_t)H * 36 + 15) / 16 * 16; }
+__host__ __device__ inline const int32_t* rows_kg(const double* fg, int H)
+{
+    return reinterpret_cast<const int32_t*>(fg + H);
+}
+__host__ __device__ inline const int32_t* rows_thr(const double* fg, int H) { return rows_kg(fg, H) + H; }
+__host__ __device__ inline const int32_t* rows_gf(const double* fg, int H) { return rows_kg(fg, H) + 2 * H; }
+__host__ __device__ inline const int32_t* rows_goff(const double* fg, int H) { return rows_kg(fg, H) + 3 * H; }
+__host__ __device__ inline const float* rows_rkg(const double* fg, int H)
+{
+    return reinterpret_cast<const float*>(rows_kg(fg, H) + 4 * H);
+}
+__host__ __device__ inline const float* rows_rinv(const double* fg, int H) { return rows_rkg(fg, H) + H; }
+__host__ __device__ inline const float* rows_rdg(const double* fg, int H) { return rows_rkg(fg, H) + 2 * H; }
+// the packed thresholds for a ground disparity fg: penalty iff 16 f > 16 (fg +
+// eps_g), i.e. f > floor(fg + eps_g); iff f < fg - eps_d, i.e. f < ceil(fg -
+// eps_d); clamped to [-1, 256], which keeps every comparison with f in [0, 255]
+__host__ __device__ inline int32_t pack_thresholds(double fg, double eps_g, double eps_d)
+{
+    const double hi = floor(fg + eps_g), lo = ceil(fg - eps_d);
+    const int fhi = hi < -1.0 ? -1 : (hi > 256.0 ? 256 : (int)hi);
+    const int flo = lo < -1.0 ? -1 : (lo > 256.0 ? 256 : (int)lo);
+    return (int32_t)((uint32_t)(fhi & 0xffff) | ((uint32_t)flo << 16));
+}
 
 struct FrameGeom {
     int H, W, s, ncols;
@@ -122,6 +192,7 @@ struct DpArgs {
     int32_t* cost_fixed;
     int cap;
     uint32_t* err;
+    RealParams rp;
 };
 
 // What the scratch-free entry point needs from a prepared handle.
@@ -129,6 +200,7 @@ struct HandleView {
     int device;
     ModelDev model;
     RowsDev rows;
+    RealParams rp;              // the cost report's priors and constants
     uint32_t* err;
     int stixel_width, capacity;
     int reduce_mode;            // reduce_code of the params: bit 0 mean, bit 1 whole-pixel grid
@@ -156,10 +228,11 @@ cudaError_t launch_luts_batch(const LutArgs* d_frames, const int2* d_items, int 
 cudaError_t launch_reduce_batch(const ReduceArgs* d_frames, const int4* d_tiles, int ntiles, int s, int mode,
                                 cudaStream_t st);
 cudaError_t launch_dp(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po,
-                      const FrameGeom& g, const ModelDev& m, const RowsDev& r,
+                      const FrameGeom& g, const ModelDev& m, const RowsDev& r, const RealParams& rp,
                       const stixels_output_t& out, uint32_t* err, cudaStream_t st);
 void dp_frame_args(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po, const FrameGeom& g,
-                   const ModelDev& m, const RowsDev& r, const stixels_output_t& out, uint32_t* err, DpArgs* a);
+                   const ModelDev& m, const RowsDev& r, const RealParams& rp, const stixels_output_t& out,
+                   uint32_t* err, DpArgs* a);
 size_t dp_shared_bytes(int H);
 // ---- batch planning shared by the batched mode and the server (batch.cu) ----
 // One frame's device buffers for a pipeline run.
@@ -194,12 +267,15 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t);
 cudaError_t enqueue_tables(const BatchTables& t, char* d_tab, int dp_warps, int dp_ctas_per_sm, cudaStream_t st);
 
 // The frame's ground line from its v-disparity (kernels_ground.cu): work bytes
-// for height H, and the launch (cam = the camera's rows, kept when nothing
-// votes; frame_rows receives the frame's tables inside `work`; line, if not
-// null, receives {k, horizon row, votes} on the device).
-size_t ground_work_bytes(int H, int dmax);
-cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& m, RowsDev cam, char* work,
-                          RowsDev* frame_rows, int32_t* line, cudaStream_t st);
+// for height H (gw: codes per residual window), and the launch (cam = the
+// camera's rows, kept when nothing votes; est_pool / est_gw = the handle's
+// residual windows of estimated lines, est_gw == cam.gw; frame_rows receives
+// the frame's tables inside `work`; line, if not null, receives {k, horizon
+// row, votes} on the device).
+size_t ground_work_bytes(int H, int dmax, int gw);
+cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& m, RowsDev cam,
+                          const int32_t* est_pool, int est_gw, char* work, RowsDev* frame_rows, int32_t* line,
+                          cudaStream_t st);
 
 // The global-MAP DP (kernels_dp_map.cu): scratch bytes for a frame, and the launch.
 size_t map_scratch_bytes(int H, int ncols, int F);
@@ -210,8 +286,8 @@ cudaError_t launch_wait_selftest(uint32_t* err, int limit, cudaStream_t st);
 // large dmax, e.g. H > 1900 at dmax 255).
 bool map_fits(int H, int F);
 cudaError_t launch_dp_map(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po,
-                          const FrameGeom& g, const ModelDev& m, const RowsDev& r, const stixels_output_t& out,
-                          uint32_t* err, void* scratch, cudaStream_t st);
+                          const FrameGeom& g, const ModelDev& m, const RowsDev& r, const RealParams& rp,
+                          const stixels_output_t& out, uint32_t* err, void* scratch, cudaStream_t st);
 
 // Sets the DP kernels' shared-memory attributes (call outside stream capture).
 cudaError_t prepare_dp_kernels();

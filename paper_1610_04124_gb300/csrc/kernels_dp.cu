@@ -55,6 +55,7 @@
 #include <climits>
 
 #include "internal.h"
+#include "real_cost.cuh"
 
 namespace stx {
 namespace {
@@ -106,6 +107,11 @@ __device__ __forceinline__ int tri_slot(int i) { return (i * (65 - i)) >> 1; }
 struct SyncState {
     int final_blocks;            // blocks the chain warp has finalised
     int abort;                   // set when a wait gave up
+    int32_t fin[3];              // V of the top row per class (object, ground, sky), once every block is final
+    int rep_state;               // cost report: 0 stixels not staged yet, 1 staged (rows may start), 2 no report
+    int rep_n;                   // stixels on the path
+    int rep_done;                // warps done with their rows
+    long long rep_acc;           // the report's sum so far, 2^-24 units
     int ready[kMaxBlocks];       // ready[c]: bulk tiles applied to end-row block c (of c - 1)
     int gathered[kMaxBlocks];    // gathered[j]: bulk warps done with block j's chain data
 };
@@ -238,6 +244,134 @@ __device__ __forceinline__ void gather_chain(ChainBuf* cb, int B, int H, int P, 
     }
 }
 
+constexpr int kReportWarps = 4;       // warps that share the cost report's rows
+
+// The end of a column, once the chain has finalised every block, by
+// kReportWarps bulk warps (role 0 leads).  The leader takes the top row's
+// best class (ties object < ground < sky), backtracks from it through the
+// back-pointers (Sec. 3.3, Sec. 5.4) and writes the stixel list bottom -> top;
+// then the cost report (the segmentation's cost in real arithmetic): the
+// leader stages the stixels' constants and priors, and all kReportWarps
+// warps take every kReportWarps-th block of 32 rows, adding their sums into
+// one exact integer; the last warp to finish writes the column's cost.  A
+// wait that gives up, or a column with no feasible segmentation, is recorded
+// in the error word with an empty column.
+__device__ __noinline__ void finish_column(const DpArgs& a, int col, int H, SyncState* sync, const int4* s_bp,
+                                           const int32_t* s_pd8, const int32_t* s_thr, const uint2* s_div,
+                                           int32_t* s_seg, int lane, int role)
+{
+    const int NB = (H + 31) >> 5;
+    // what the cost report reads but the path does not decide (the object
+    // K and sigma of every f, this warp's first rows' tables) is loaded
+    // before the waits, so that none of it is on the path's critical time
+    RowTables pre;
+    if (a.cost) load_rows(pre, a.rows.fg, H, lane, role, kReportWarps);
+    if (role > 0) {
+        // a helper: its rows once the leader has staged the stixels
+        if (!a.cost) return;
+        if (!wait_geq(&sync->rep_state, 1, &sync->abort, 32)) {
+            if (lane == 0) {
+                a.cost[col] = __int_as_float(0x7f800000);
+                atomicOr(a.err, STIXELS_ERR_TIMEOUT);
+            }
+            return;
+        }
+        if (*(volatile int*)&sync->rep_state != 1) return;
+    } else {
+        FTables ft;
+        if (a.cost) load_ftables(ft, a, lane);
+        if (!wait_geq(&sync->final_blocks, NB, &sync->abort, 32)) {
+            if (lane == 0) {
+                a.counts[col] = 0;
+                if (a.cost) a.cost[col] = __int_as_float(0x7f800000);
+                if (a.cost_fixed) a.cost_fixed[col] = kBig;
+                atomicOr(a.err, STIXELS_ERR_TIMEOUT);
+                *(volatile int*)&sync->rep_state = 2;
+            }
+            return;
+        }
+        const volatile int32_t* fin = sync->fin;
+        int c = 0;
+        int32_t best = fin[0];
+        if (fin[1] < best) { best = fin[1]; c = 1; }
+        if (fin[2] < best) { best = fin[2]; c = 2; }
+        if (best >= kBig) {
+            if (lane == 0) {
+                a.counts[col] = 0;
+                if (a.cost) a.cost[col] = __int_as_float(0x7f800000);
+                if (a.cost_fixed) a.cost_fixed[col] = kBig;
+                atomicOr(a.err, STIXELS_ERR_INFEASIBLE);
+                *(volatile int*)&sync->rep_state = 2;
+            }
+            return;
+        }
+        // one walk from the top row (lane 0), the stixels top -> bottom into
+        // s_seg[H..2H); the lanes then put them bottom -> top into s_seg[0..n)
+        // and write the output records
+        int32_t* top_down = s_seg + H;
+        int n = 0;
+        if (lane == 0) {
+            const int32_t* bp_all = reinterpret_cast<const int32_t*>(s_bp);
+            for (int k = H - 1, cc = c; k >= 0 && cc < 3 && n < H;) {
+                const int32_t bp = bp_all[4 * k + cc];
+                const int b = min(bp >> 2, k);               // b <= k for a solved column; keeps the walk finite
+                top_down[n++] = (b << 13) | (k << 2) | cc;
+                k = b - 1;
+                cc = bp & 3;
+            }
+            a.counts[col] = n;
+            if (n > a.cap) atomicOr(a.err, STIXELS_ERR_CAPACITY);
+            if (a.cost_fixed) a.cost_fixed[col] = best;
+        }
+        n = __shfl_sync(kFull, n, 0);
+        __syncwarp();
+        stixel_t* out = a.stixels + (size_t)col * a.cap;
+        for (int i = lane; i < n; i += 32) {
+            const int w = top_down[n - 1 - i];
+            s_seg[i] = w;
+            if (i < a.cap) {
+                const int b = w >> 13, k = (w >> 2) & 2047;
+                const int nrows = k - b + 1;
+                const int32_t S = s_pd8[k + 1] - s_pd8[b] - 8 * nrows;
+                stixel_t st;
+                st.row_top = (int16_t)(H - 1 - k);
+                st.row_bottom = (int16_t)(H - 1 - b);
+                st.cls = (uint8_t)(w & 3);
+                st.flags = 0;
+                st.reserved = 0;
+                st.disparity = __fdiv_rn(__int2float_rn(S), __int2float_rn(16 * nrows));
+                out[i] = st;
+            }
+        }
+        __syncwarp();
+        if (!a.cost) return;
+        auto kinv = [&](int f, bool) { return ftables_at(ft, f); };
+        auto thr = [&](int b) {
+            const int32_t t = s_thr[b];
+            return make_int2((int32_t)(int16_t)(t & 0xffff), t >> 16);
+        };
+        const long long pri = warp_sum64(report_stixels(s_seg, n, s_pd8, s_div, a, H, lane, kinv, thr));
+        if (lane == 0) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(&sync->rep_acc), (unsigned long long)pri);
+            sync->rep_n = n;
+            __threadfence_block();
+            *(volatile int*)&sync->rep_state = 1;
+        }
+        __syncwarp();
+    }
+    // every report warp: its blocks of rows, then the last one writes the cost
+    const int n = *(volatile int*)&sync->rep_n;
+    const long long sum = warp_sum64(report_rows(s_seg, n, s_pd8, a, H, lane, role, kReportWarps, &pre));
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&sync->rep_acc), (unsigned long long)sum);
+        __threadfence_block();
+        if (atomicAdd(&sync->rep_done, 1) == kReportWarps - 1) {
+            const long long total = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&sync->rep_acc), 0ull);
+            a.cost[col] = __ll2float_rn(total) * (1.0f / kReportUnits);
+        }
+    }
+}
+
 // Solves column `col` of frame `a` with all NW warps of the CTA (one chain
 // warp, NW - 1 bulk warps); `sm` is the CTA's dynamic shared memory
 // (dp_smem_bytes with the same ring, 2 or 3 chain buffers).  Every warp
@@ -252,6 +386,7 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
     // the tile dealing below leaves out the bulk warps on the chain warp's
     // scheduler (warp index congruent mod 4): NW / 4 - 1 of them
     static_assert(NW % 4 == 0 && NW >= 8, "whole schedulers of warps");
+    static_assert(kReportWarps == 4 && NW - 1 > 4, "the report's warps are bulk warps 0, 1, 2, 4");
     constexpr int kTile = kBulk - (NW / 4 - 1);    // bulk warps that take tiles
     constexpr bool kQuietExit = NW >= 16;
     constexpr int kGather = kQuietExit ? kTile : kBulk;   // warps that share each gather
@@ -284,14 +419,11 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
     const int32_t* po_col = a.po + (size_t)col * F * P;
     const int32_t* pg_col = a.pg + (size_t)col * P;
     const int32_t* ps_col = a.ps + (size_t)col * P;
+    const int32_t* thr_row = rows_thr(a.rows.fg, H);   // gravity / diving thresholds of each row
     for (int v = threadIdx.x; v <= H; v += kThreads) {
         int32_t thr = 0;
         if (v < H) {
-            const int32_t g = a.rows.fgq[v];
-            // 16 f > g + eps  <=>  f > floor((g + eps) / 16);  16 f < g - eps  <=>  f < ceil((g - eps) / 16)
-            const int fhi = max(-1, min((g + m.eps_g) >> 4, 256));
-            const int flo = max(-1, min(-((m.eps_d - g) >> 4), 256));
-            thr = (fhi & 0xffff) | (flo << 16);
+            thr = thr_row[v];
 #pragma unroll
             for (int q = 0; q < kSlots; ++q) {
                 s_runv[q * HP + v] = INT_MAX;
@@ -306,6 +438,16 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
         const DivMagic dm = kDivTable.v[n];
         s_div[n] = make_uint2(dm.m, dm.s);
     }
+    {
+        // what the column's cost report reads at the end (the row tables and
+        // the unrounded model) is fetched into L2 now, while the DP runs
+        const char* rb = reinterpret_cast<const char*>(a.rows.fg);
+        const int nr = (int)rows_arrays_bytes(H);
+        for (int o = 128 * threadIdx.x; o < nr; o += 128 * kThreads) asm volatile("prefetch.global.L2 [%0];" ::"l"(rb + o));
+        const char* mb = reinterpret_cast<const char*>(real_k_obj(a.rows.real_model));
+        const int nm = 8 * F;
+        for (int o = 128 * threadIdx.x; o < nm; o += 128 * kThreads) asm volatile("prefetch.global.L2 [%0];" ::"l"(mb + o));
+    }
     if (threadIdx.x < kMaxBlocks) {
         sync->ready[threadIdx.x] = 0;
         sync->gathered[threadIdx.x] = 0;
@@ -313,6 +455,9 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
     if (threadIdx.x == 0) {
         sync->final_blocks = 0;
         sync->abort = 0;
+        sync->rep_state = 0;
+        sync->rep_done = 0;
+        sync->rep_acc = 0;
         // start 0 carries the first-stixel prior (code 3 = no previous stixel)
         s_ctx[0] = make_bulk_ctx(m.first[0] + kNoneCode, kBig, kBig, INT_MAX, s_thr[0], m);
     }
@@ -427,6 +572,12 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
             if (all_done && next_g >= NB) break;
             if (!wait_geq(v_final, vf + 1, v_abort, 32)) break;
         }
+        // backtracking and the cost report stay off the chain's scheduler,
+        // where the other column of the SM may still be running its chain
+        // bulk warps 0, 1, 2 and 4 (none shares the chain's scheduler, and
+        // none leaves early) finish the column; the first of them leads
+        const int role = bulk_id < 3 ? bulk_id : (bulk_id == 4 ? 3 : -1);
+        if (role >= 0) finish_column(a, col, H, sync, s_bp, s_pd8, s_thr, s_div, s_runv, lane, role);
         return;
     }
 
@@ -435,7 +586,7 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
     const int32_t T_oo = m.trans[0][0], T_og = m.trans[0][1] + 1, T_os = m.trans[0][2] + 2;
     const int32_t T_go = m.trans[1][0], T_gg = m.trans[1][1] + 1, T_gs = m.trans[1][2] + 2;
     const int32_t T_so = m.trans[2][0], T_sg = m.trans[2][1] + 1, T_ss = m.trans[2][2] + 2;
-    const int ord_off = m.eps_o >> 4;               // 16 f > 16 f' + eps  <=>  f > f' + floor(eps / 16)
+    const int ord_off = m.ord_off;                  // 16 f > 16 f' + 16 eps  <=>  f > f' + floor(eps)
     const int32_t pen_ord = m.pen_ord;
     // per-row results of the current block, written by lane 0 at each step and
     // packed into back-pointers / start contexts by all lanes at the block's end
@@ -568,64 +719,21 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
                 s_ctx[k + 1] = make_bulk_ctx(min(w.x & ~3, kBig) + T_oo, min(w.z & ~3, kBig) + T_og,
                                              min(w.w & ~3, kBig) + T_os, (w.y & 255) + ord_off, s_thr[k + 1], m);
         }
+        if (j == NB - 1 && lane == 0) {
+            sync->fin[0] = vo_p;
+            sync->fin[1] = vg_p;
+            sync->fin[2] = vs_p;
+        }
         __threadfence_block();
         __syncwarp();
         if (lane == 0) *v_final = j + 1;
     }
 
-    // backtracking from the top row (Sec. 3.3, Sec. 5.4)
-    if (lane == 0) {
-        if (aborted) {
-            a.counts[col] = 0;
-            if (a.cost) a.cost[col] = __int_as_float(0x7f800000);
-            if (a.cost_fixed) a.cost_fixed[col] = kBig;
-            atomicOr(a.err, STIXELS_ERR_TIMEOUT);
-            return;
-        }
-        int c = 0;
-        int32_t best = vo_p;
-        if (vg_p < best) { best = vg_p; c = 1; }
-        if (vs_p < best) { best = vs_p; c = 2; }
-        if (best >= kBig) {
-            a.counts[col] = 0;
-            if (a.cost) a.cost[col] = __int_as_float(0x7f800000);
-            if (a.cost_fixed) a.cost_fixed[col] = kBig;
-            atomicOr(a.err, STIXELS_ERR_INFEASIBLE);
-            return;
-        }
-        const int32_t* bp_all = reinterpret_cast<const int32_t*>(s_bp);
-        int n = 0;
-        for (int k = H - 1, cc = c; k >= 0 && cc < 3;) {
-            const int32_t bp = bp_all[4 * k + cc];
-            ++n;
-            if ((bp >> 2) > k) break;                 // never for a solved column; keeps the walk finite
-            k = (bp >> 2) - 1;
-            cc = bp & 3;
-        }
-        int idx = n - 1;
-        stixel_t* out = a.stixels + (size_t)col * a.cap;
-        for (int k = H - 1, cc = c; k >= 0 && cc < 3 && idx >= 0; --idx) {
-            const int32_t bp = bp_all[4 * k + cc];
-            const int b = bp >> 2;
-            if (idx < a.cap) {
-                const int nrows = k - b + 1;
-                const int32_t S = s_pd8[k + 1] - s_pd8[b] - 8 * nrows;
-                stixel_t st;
-                st.row_top = (int16_t)(H - 1 - k);
-                st.row_bottom = (int16_t)(H - 1 - b);
-                st.cls = (uint8_t)cc;
-                st.flags = 0;
-                st.reserved = 0;
-                st.disparity = __fdiv_rn(__int2float_rn(S), __int2float_rn(16 * nrows));
-                out[idx] = st;
-            }
-            k = b - 1;
-            cc = bp & 3;
-        }
-        a.counts[col] = n;
-        if (n > a.cap) atomicOr(a.err, STIXELS_ERR_CAPACITY);
-        if (a.cost) a.cost[col] = __int2float_rn(best) * (1.0f / (float)kUnitsPerCost);
-        if (a.cost_fixed) a.cost_fixed[col] = best;
+    if (aborted && lane == 0) {
+        a.counts[col] = 0;
+        if (a.cost) a.cost[col] = __int_as_float(0x7f800000);
+        if (a.cost_fixed) a.cost_fixed[col] = kBig;
+        atomicOr(a.err, STIXELS_ERR_TIMEOUT);
     }
 }
 
@@ -790,7 +898,8 @@ cudaError_t launch_batch_shape(const DpArgs* f, const int2* it, int n, int* ctr,
 size_t dp_shared_bytes(int H) { return dp_smem_bytes(H, kRingMax); }
 
 void dp_frame_args(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po, const FrameGeom& g,
-                   const ModelDev& m, const RowsDev& r, const stixels_output_t& out, uint32_t* err, DpArgs* a)
+                   const ModelDev& m, const RowsDev& r, const RealParams& rp, const stixels_output_t& out,
+                   uint32_t* err, DpArgs* a)
 {
     a->pd = pd; a->pg = pg; a->ps = ps; a->po = po;
     a->H = g.H; a->P = g.P; a->F = m.dmax + 1;
@@ -798,16 +907,17 @@ void dp_frame_args(const int32_t* pd, const int32_t* pg, const int32_t* ps, cons
     a->stixels = out.stixels; a->counts = out.counts; a->cost = out.column_cost; a->cost_fixed = out.column_cost_fixed;
     a->cap = out.capacity;
     a->err = err;
+    a->rp = rp;
 }
 
 cudaError_t launch_dp(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po,
-                      const FrameGeom& g, const ModelDev& m, const RowsDev& r, const stixels_output_t& out,
-                      uint32_t* err, cudaStream_t st)
+                      const FrameGeom& g, const ModelDev& m, const RowsDev& r, const RealParams& rp,
+                      const stixels_output_t& out, uint32_t* err, cudaStream_t st)
 {
     if (g.H <= 0 || g.ncols <= 0) return cudaSuccess;
     if (g.H > STIXELS_MAX_HEIGHT) return cudaErrorInvalidValue;
     DpArgs a;
-    dp_frame_args(pd, pg, ps, po, g, m, r, out, err, &a);
+    dp_frame_args(pd, pg, ps, po, g, m, r, rp, out, err, &a);
     const size_t smem = dp_smem_bytes(g.H, kRingMax);
     return standard_transitions(m) ? launch_frame_shape<true>(a, g.ncols, smem, st)
                                    : launch_frame_shape<false>(a, g.ncols, smem, st);

@@ -30,6 +30,7 @@
 #include <climits>
 
 #include "internal.h"
+#include "real_cost.cuh"
 
 namespace stx {
 namespace {
@@ -169,16 +170,16 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, un
             s_div[v] = make_uint2(dm.m, dm.s);
         }
         if (v < H) {
-            const int32_t g = a.rows.fgq[v];
-            s_fhi[v] = (g + m.eps_g) >> 4;            // gravity iff f > fhi
-            s_flo[v] = -((m.eps_d - g) >> 4);         // diving iff f < flo
+            const int32_t t = rows_thr(a.rows.fg, H)[v];
+            s_fhi[v] = (int32_t)(int16_t)(t & 0xffff);    // gravity iff f > fhi
+            s_flo[v] = t >> 16;                           // diving iff f < flo
         }
     }
     MapCol c;
     c.s_pd8 = s_pd8; c.s_pg = s_pg; c.s_ps = s_ps; c.s_fhi = s_fhi; c.s_flo = s_flo; c.s_div = s_div;
     c.s_kg = s_kg; c.s_ks = s_ks; c.s_bo = s_bo;
     c.po = a.po + (size_t)col * F * P;
-    c.P = P; c.F = F; c.dmax = m.dmax; c.ord_off = m.eps_o >> 4;    // ordering iff f' > f + ord_off
+    c.P = P; c.F = F; c.dmax = m.dmax; c.ord_off = m.ord_off;       // ordering iff f' > f + ord_off
     c.T_oo = m.trans[0][0]; c.T_og = m.trans[0][1] + 1; c.T_os = m.trans[0][2] + 2;
     c.T_go = m.trans[1][0]; c.T_gg = m.trans[1][1] + 1; c.T_gs = m.trans[1][2] + 2;
     c.T_so = m.trans[2][0]; c.T_sg = m.trans[2][1] + 1; c.T_ss = m.trans[2][2] + 2;
@@ -327,8 +328,12 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, un
         __syncthreads();
     }
 
-    // top row (lexicographic cost, class, f) and backtracking
-    if (tid == 0) {
+    // top row (lexicographic cost, class, f) and backtracking, by warp 0: lane
+    // 0 walks the path, then the warp reports its cost in real arithmetic
+    if (warp != 0) return;
+    int n = 0, feasible = 1;
+    int32_t* s_seg = s_pg;                        // free after the last block; [H + 1] >= n
+    if (lane == 0) {
         int cc0 = -1, fb = 0;
         int32_t best = kBig;
         for (int f = 0; f < F; ++f) {
@@ -342,45 +347,58 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, un
             if (a.cost) a.cost[col] = __int_as_float(0x7f800000);
             if (a.cost_fixed) a.cost_fixed[col] = kBig;
             atomicOr(a.err, STIXELS_ERR_INFEASIBLE);
-            return;
-        }
-        // count, then write bottom -> top
-        int n = 0;
-        for (int k = H - 1, cc = cc0, ff = fb; k >= 0 && cc < 3 && n <= H;) {
-            const unsigned long long key = cc == 0 ? keyo[(size_t)k * F + ff] : (cc == 1 ? s_kg[k] : s_ks[k]);
-            ++n;
-            const int b = key_start(key);
-            if (b > k) break;
-            k = b - 1;
-            cc = key_cost(key) & 3;
-            ff = key_f(key);
-        }
-        int idx = n - 1;
-        stixel_t* out = a.stixels + (size_t)col * a.cap;
-        for (int k = H - 1, cc = cc0, ff = fb; k >= 0 && cc < 3 && idx >= 0; --idx) {
-            const unsigned long long key = cc == 0 ? keyo[(size_t)k * F + ff] : (cc == 1 ? s_kg[k] : s_ks[k]);
-            const int b = key_start(key);
-            if (idx < a.cap) {
-                const int nrows = k - b + 1;
-                const int32_t S = s_pd8[k + 1] - s_pd8[b] - 8 * nrows;
-                stixel_t st;
-                st.row_top = (int16_t)(H - 1 - k);
-                st.row_bottom = (int16_t)(H - 1 - b);
-                st.cls = (uint8_t)cc;
-                st.flags = 0;
-                st.reserved = 0;
-                st.disparity = __fdiv_rn(__int2float_rn(S), __int2float_rn(16 * nrows));
-                out[idx] = st;
+            feasible = 0;
+        } else {
+            // count, then write bottom -> top
+            for (int k = H - 1, cc = cc0, ff = fb; k >= 0 && cc < 3 && n <= H;) {
+                const unsigned long long key = cc == 0 ? keyo[(size_t)k * F + ff] : (cc == 1 ? s_kg[k] : s_ks[k]);
+                ++n;
+                const int b = key_start(key);
+                if (b > k) break;
+                k = b - 1;
+                cc = key_cost(key) & 3;
+                ff = key_f(key);
             }
-            if (b > k) break;
-            k = b - 1;
-            cc = key_cost(key) & 3;
-            ff = key_f(key);
+            int idx = n - 1;
+            stixel_t* out = a.stixels + (size_t)col * a.cap;
+            for (int k = H - 1, cc = cc0, ff = fb; k >= 0 && cc < 3 && idx >= 0; --idx) {
+                const unsigned long long key = cc == 0 ? keyo[(size_t)k * F + ff] : (cc == 1 ? s_kg[k] : s_ks[k]);
+                const int b = key_start(key);
+                s_seg[idx] = (min(b, k) << 13) | (k << 2) | cc;
+                if (idx < a.cap) {
+                    const int nrows = k - b + 1;
+                    const int32_t S = s_pd8[k + 1] - s_pd8[b] - 8 * nrows;
+                    stixel_t st;
+                    st.row_top = (int16_t)(H - 1 - k);
+                    st.row_bottom = (int16_t)(H - 1 - b);
+                    st.cls = (uint8_t)cc;
+                    st.flags = 0;
+                    st.reserved = 0;
+                    st.disparity = __fdiv_rn(__int2float_rn(S), __int2float_rn(16 * nrows));
+                    out[idx] = st;
+                }
+                if (b > k) break;
+                k = b - 1;
+                cc = key_cost(key) & 3;
+                ff = key_f(key);
+            }
+            a.counts[col] = n;
+            if (n > a.cap) atomicOr(a.err, STIXELS_ERR_CAPACITY);
+            if (a.cost_fixed) a.cost_fixed[col] = best;
         }
-        a.counts[col] = n;
-        if (n > a.cap) atomicOr(a.err, STIXELS_ERR_CAPACITY);
-        if (a.cost) a.cost[col] = __int2float_rn(best) * (1.0f / (float)kUnitsPerCost);
-        if (a.cost_fixed) a.cost_fixed[col] = best;
+    }
+    n = __shfl_sync(0xffffffffu, n, 0);
+    feasible = __shfl_sync(0xffffffffu, feasible, 0);
+    __syncwarp();
+    if (feasible && a.cost) {
+        // (the scratch covers s_fhi / s_flo: the thresholds come from the row tables)
+        const int32_t* thr_row = rows_thr(a.rows.fg, H);
+        auto thr = [&](int b) {
+            const int32_t t = __ldg(thr_row + b);
+            return make_int2((int32_t)(int16_t)(t & 0xffff), t >> 16);
+        };
+        const long long rc = real_segmentation_cost(s_seg, n, s_pd8, s_div, a, H, lane, thr);
+        if (lane == 0) a.cost[col] = __ll2float_rn(rc) * (1.0f / kReportUnits);
     }
 }
 
@@ -397,13 +415,13 @@ size_t map_scratch_bytes(int H, int ncols, int F) { return sizeof(unsigned long 
 bool map_fits(int H, int F) { return map_smem_bytes(H, F) <= kMapSmemMax; }
 
 cudaError_t launch_dp_map(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po,
-                          const FrameGeom& g, const ModelDev& m, const RowsDev& r, const stixels_output_t& out,
-                          uint32_t* err, void* scratch, cudaStream_t st)
+                          const FrameGeom& g, const ModelDev& m, const RowsDev& r, const RealParams& rp,
+                          const stixels_output_t& out, uint32_t* err, void* scratch, cudaStream_t st)
 {
     if (g.H <= 0 || g.ncols <= 0) return cudaSuccess;
     if (g.H > STIXELS_MAX_HEIGHT || m.dmax + 1 > 256 || !map_fits(g.H, m.dmax + 1)) return cudaErrorInvalidValue;
     DpArgs a;
-    dp_frame_args(pd, pg, ps, po, g, m, r, out, err, &a);
+    dp_frame_args(pd, pg, ps, po, g, m, r, rp, out, err, &a);
     const size_t smem = map_smem_bytes(g.H, m.dmax + 1);
     static bool attr_set[64] = {false};
     int dev = 0;

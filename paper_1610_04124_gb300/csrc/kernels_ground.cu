@@ -11,10 +11,10 @@
 //               disparity per image row (k = 1..256), horizon at image row h;
 //   votes(k, h) sum of S[r][code] over the rows r > h with code in [16, 16 dmax];
 // the line with the most votes wins, ties to the smaller k, then the smaller h.
-// Its codes (rounded half away from zero above the horizon) replace the
-// camera's ground line for the frame, and the ground K of each row comes from
-// a table over the clamped code built at create time.  With no vote at all
-// the camera's line is kept.
+// The line itself, f_g = k (r - h) / 256 px at image row r (not its Q4
+// codes: those only index the vote), replaces the camera's ground line for
+// the frame; the ground K of each row comes from a create-time table over
+// the disparities c / 256.  With no vote at all the camera's line is kept.
 //
 // Kernels: one CTA per two image rows builds their histograms in shared
 // memory, smooths them (the triangle as a box of 17 codes applied twice) and
@@ -125,27 +125,61 @@ __global__ void __launch_bounds__(256) vdisp_kernel(const int16_t* __restrict__ 
         *reinterpret_cast<int2*>(smooth + (size_t)e * Hp + r0) = make_int2(0, 0);
 }
 
-// the frame's row tables from the winning line (or the camera's when nothing voted)
-__device__ void write_ground_rows(unsigned long long key, int H, int dmax, const int32_t* __restrict__ kg_tab,
-                                  const RowsDev& cam, int32_t* __restrict__ rows, int32_t* __restrict__ line)
+// the frame's row tables (RowsDev) from the winning line, or the camera's
+// when nothing voted.  The line's ground disparity k (r - h) / 256 is a
+// multiple of 1/256 px, so its K comes from the create-time tables over those
+// disparities (clamped to [0, 256 dmax]: K depends on f only through its clamp
+// to [0, d_range]), its gravity / diving thresholds follow from it in FP64,
+// and its rows share the 16 residual windows of the create-time pool (one per
+// phase x & 15 of 16 f_g = x / 16), copied into the frame's pool; the camera's
+// own windows (as many codes each: the handle builds both with one reach) are
+// copied instead when nothing voted.
+__device__ __noinline__ void write_ground_rows(unsigned long long key, int H, int dmax,
+                                               const int32_t* __restrict__ kg_tab, const RowsDev& cam,
+                                               const RealModelDev* __restrict__ rm,
+                                               const int32_t* __restrict__ est_pool, int gw,
+                                               double* __restrict__ rows, int32_t* __restrict__ pool,
+                                               int32_t* __restrict__ line)
 {
     const int votes = (int)(key >> 32);
     const int k = 256 - (int)((key >> 16) & 0xffff);
     const int h = 65535 - (int)(key & 0xffff);
-    const int emax = 16 * dmax;
+    const int cmax = 256 * dmax;
+    int32_t* kg = reinterpret_cast<int32_t*>(rows + H);
+    int32_t* thr = kg + H;
+    int32_t* gf = kg + 2 * H;
+    int32_t* goff = kg + 3 * H;
+    float* rkg = reinterpret_cast<float*>(kg + 4 * H);
+    float* rinv = rkg + H;
+    float* rdg = rkg + 2 * H;
+    const double* cfg = cam.fg;
     for (int v = threadIdx.x; v < H; v += blockDim.x) {
-        int32_t fgq, kg;
         if (votes > 0) {
             const int x = k * (H - 1 - v - h);
-            fgq = x >= 0 ? (x + 8) >> 4 : -((8 - x) >> 4);
-            kg = kg_tab[min(max(fgq, 0), emax)];
+            const int c = min(max(x, 0), cmax);
+            const double f = (double)k * (double)(H - 1 - v - h) / 256.0;
+            rows[v] = f;
+            kg[v] = kg_tab[c];
+            thr[v] = pack_thresholds(f, rm->eps_g, rm->eps_d);
+            gf[v] = x >> 4;                              // floor(x / 16)
+            goff[v] = (x & 15) * gw;
+            rkg[v] = rm->rkg_tab[c];
+            rinv[v] = rm->inv_ground;
+            rdg[v] = (float)(x & 15) * (1.0f / 256.0f);
         } else {
-            fgq = cam.fgq[v];
-            kg = cam.k_ground[v];
+            rows[v] = cfg[v];
+            kg[v] = rows_kg(cfg, H)[v];
+            thr[v] = rows_thr(cfg, H)[v];
+            gf[v] = rows_gf(cfg, H)[v];
+            goff[v] = rows_goff(cfg, H)[v];
+            rkg[v] = rows_rkg(cfg, H)[v];
+            rinv[v] = rows_rinv(cfg, H)[v];
+            rdg[v] = rows_rdg(cfg, H)[v];
         }
-        rows[v] = fgq;
-        rows[H + v] = kg;
     }
+    const int n = votes > 0 ? 16 * gw : H * gw;
+    const int32_t* src = votes > 0 ? est_pool : cam.gpool;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) pool[i] = src[i];
     if (threadIdx.x == 0 && line) {
         line[0] = k;
         line[1] = h;
@@ -162,7 +196,9 @@ __device__ void write_ground_rows(unsigned long long key, int H, int dmax, const
 __global__ void __launch_bounds__(32 * kVoteWarps) vote_kernel(const int32_t* __restrict__ smooth, int H,
                                                                int dmax, unsigned long long* __restrict__ best,
                                                                const int32_t* __restrict__ kg_tab, RowsDev cam,
-                                                               int32_t* __restrict__ rows,
+                                                               const RealModelDev* __restrict__ rm,
+                                                               const int32_t* __restrict__ est_pool, int gw,
+                                                               double* __restrict__ rows, int32_t* __restrict__ pool,
                                                                int32_t* __restrict__ line)
 {
     __shared__ bool s_last;
@@ -244,28 +280,44 @@ __global__ void __launch_bounds__(32 * kVoteWarps) vote_kernel(const int32_t* __
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    write_ground_rows(atomicAdd(best, 0ull), H, dmax, kg_tab, cam, rows, line);
+    write_ground_rows(atomicAdd(best, 0ull), H, dmax, kg_tab, cam, rm, est_pool, gw, rows, pool, line);
 }
 
 }  // namespace
 
-size_t ground_work_bytes(int H, int dmax)
+// work layout: the smoothed table, the vote's winner and counter (256 bytes),
+// the line {k, h, votes} (256 bytes), the frame's row tables (RowsDev), its
+// residual windows (max(16, H) windows of gw codes)
+static size_t smooth_bytes(int H, int dmax)
 {
-    const size_t E = 16 * (size_t)dmax + 1;
-    return ((sizeof(int32_t) * ground_pitch(H) * E + 255) / 256 * 256) + 256 + ((sizeof(int32_t) * (2 * (size_t)H + 3) + 255) / 256 * 256);
+    return (sizeof(int32_t) * ground_pitch(H) * (16 * (size_t)dmax + 1) + 255) / 256 * 256;
 }
 
-cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& m, RowsDev cam, char* work,
-                          RowsDev* frame_rows, int32_t* line, cudaStream_t st)
+static size_t frame_rows_bytes(int H) { return (rows_arrays_bytes(H) + 255) / 256 * 256; }
+
+size_t ground_work_bytes(int H, int dmax, int gw)
+{
+    return smooth_bytes(H, dmax) + 256 + 256 + frame_rows_bytes(H) +
+           sizeof(int32_t) * (size_t)(H > 16 ? H : 16) * gw;
+}
+
+cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& m, RowsDev cam,
+                          const int32_t* est_pool, int est_gw, char* work, RowsDev* frame_rows, int32_t* line,
+                          cudaStream_t st)
 {
     // cam is a copy: frame_rows may be the caller's camera rows themselves
+    if (!est_pool || est_gw != cam.gw) return cudaErrorInvalidValue;
     const size_t E = 16 * (size_t)m.dmax + 1;
     int32_t* smooth = (int32_t*)work;
-    unsigned long long* best = (unsigned long long*)(work + (sizeof(int32_t) * ground_pitch(g.H) * E + 255) / 256 * 256);
-    int32_t* rows = (int32_t*)((char*)best + 256);
-    frame_rows->fgq = rows;
-    frame_rows->k_ground = rows + g.H;
-    frame_rows->g_ground = nullptr;
+    unsigned long long* best = (unsigned long long*)(work + smooth_bytes(g.H, m.dmax));
+    int32_t* own_line = (int32_t*)((char*)best + 256);
+    double* rows = (double*)((char*)own_line + 256);
+    int32_t* pool = (int32_t*)((char*)rows + frame_rows_bytes(g.H));
+    frame_rows->fg = rows;
+    frame_rows->real_model = cam.real_model;
+    frame_rows->gpool = pool;
+    frame_rows->gw = est_gw;
+    frame_rows->gn = (g.H > 16 ? g.H : 16) * est_gw;
     const size_t smem = sizeof(int32_t) * kVdispRows * vdisp_pitch((int)E);
     static bool attr_set[64] = {false};
     int dev = 0;
@@ -282,7 +334,8 @@ cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     vote_kernel<<<dim3((g.H + kVoteH - 1) / kVoteH, 256), 32 * kVoteWarps, 0, st>>>(
-        smooth, g.H, m.dmax, best, m.kg_tab, cam, rows, line ? line : rows + 2 * g.H);
+        smooth, g.H, m.dmax, best, m.kg_tab, cam, cam.real_model, est_pool, est_gw, rows, pool,
+        line ? line : own_line);
     return cudaGetLastError();
 }
 

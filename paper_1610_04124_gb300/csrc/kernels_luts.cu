@@ -28,6 +28,7 @@ namespace stx {
 namespace {
 
 constexpr int kRowsPerCta = 32;
+constexpr int kLutThreads = 256;             // threads of every LUT CTA (8 warps)
 constexpr int kPerLane = 8;                    // consecutive outputs per lane
 constexpr int kChunk = 32 * kPerLane;          // outputs per warp iteration
 
@@ -111,18 +112,26 @@ __device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const 
     int32_t* __restrict__ po = a.po;
     const int QP = (P + kChunk - 1) / kChunk * kChunk;
     int32_t* s_q = sm;                           // [QP]: s_q[j] = q[j - 1] (j = 1..H), 0 elsewhere
-    const int ngo = kVarSigma ? 0 : m.esat_obj + 1, ngg = kVarSigma ? 0 : m.esat_ground + 1;
+    const int ngo = kVarSigma ? 0 : m.esat_obj + 1;
     const int E = m.emax + 1;
     int32_t* s_go = s_q + QP;                    // [ngo]   residual tables, clamped at saturation
-    int32_t* s_gg = s_go + ngo;                  // [ngg]
-    int32_t* s_gs = s_gg + ngg;                  // [esat_sky + 1]
+    int32_t* s_gs = s_go + ngo;                  // [esat_sky + 1]
     int32_t* s_lc = s_gs + m.esat_sky + 1;       // whole-pixel grid: [kRowsPerCta][2 r + 1] windows
     const int R = F + 3;
     const int lr = lc_radius(m.esat_obj), lw = 2 * lr + 1;
 
     for (int j = threadIdx.x; j < QP; j += blockDim.x) s_q[j] = (j >= 1 && j <= H) ? q[(size_t)col * H + j - 1] : 0;
+    if ((unsigned)(F + 1 - row0) < (unsigned)kRowsPerCta) {
+        // the ground row reads its row tables, then its residual windows, at
+        // every pixel: start bringing both into L2 now, behind the codes' loads
+        const char* pb = reinterpret_cast<const char*>(rows.gpool);
+        const int np = 4 * rows.gn;
+        for (int o = 128 * threadIdx.x; o < np; o += 128 * kLutThreads) asm volatile("prefetch.global.L2 [%0];" ::"l"(pb + o));
+        const char* rb = reinterpret_cast<const char*>(rows.fg);
+        const int nr = 36 * H;
+        for (int o = 128 * threadIdx.x; o < nr; o += 128 * kLutThreads) asm volatile("prefetch.global.L2 [%0];" ::"l"(rb + o));
+    }
     for (int e = threadIdx.x; e < ngo; e += blockDim.x) s_go[e] = __ldg(m.g_obj + e);
-    for (int e = threadIdx.x; e < ngg; e += blockDim.x) s_gg[e] = __ldg(m.g_ground + e);
     for (int e = threadIdx.x; e <= m.esat_sky; e += blockDim.x) s_gs[e] = __ldg(m.g_sky + e);
     if (kIntGrid) {
         // the windows of the LUT_cost rows of this CTA's object disparities
@@ -167,13 +176,17 @@ __device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const 
         } else if (row == F) {
             scan_row<!kIntGrid>(pd + (size_t)col * P, s_q, P, H, lane, [&](int32_t qv, int) { return qv; });
         } else if (row == F + 1) {
+            // the ground line is not on the Q4 grid: each row has its own
+            // window of residuals (RowsDev), past which a pixel costs C_out
+            const int32_t* __restrict__ kg = rows_kg(rows.fg, H);
+            const int32_t* __restrict__ gf = rows_gf(rows.fg, H);
+            const int32_t* __restrict__ goff = rows_goff(rows.fg, H);
+            const int32_t* __restrict__ gpool = rows.gpool;
+            const int gw = rows.gw, er = (rows.gw - 2) >> 1;
+            const int32_t co = m.c_out;
             scan_row<!kIntGrid>(pg + (size_t)col * P, s_q, P, H, lane, [&](int32_t qv, int v) {
-                if (kVarSigma) {
-                    const int e = min(abs(qv - __ldg(rows.fgq + v)), m.emax);
-                    return min(m.c_out, __ldg(rows.k_ground + v) + __ldg(rows.g_ground + (size_t)v * E + e));
-                }
-                const int e = min(abs(qv - __ldg(rows.fgq + v)), m.esat_ground);
-                return min(m.c_out, __ldg(rows.k_ground + v) + s_gg[e]);
+                const int j = qv - __ldg(gf + v) + er;
+                return (unsigned)j < (unsigned)gw ? min(co, __ldg(kg + v) + __ldg(gpool + __ldg(goff + v) + j)) : co;
             });
         } else {
             scan_row<!kIntGrid>(ps + (size_t)col * P, s_q, P, H, lane, [&](int32_t qv, int) {
@@ -220,7 +233,7 @@ size_t lut_shared_bytes(int H, const ModelDev& m)
     const int P = lut_pitch(H);
     const int QP = (P + kChunk - 1) / kChunk * kChunk;
     const size_t lc = m.int_grid ? (size_t)kRowsPerCta * (2 * lc_radius(m.esat_obj) + 1) : 0;
-    const size_t tabs = m.var_sigma ? (size_t)m.esat_sky + 1 : (size_t)m.esat_obj + m.esat_ground + m.esat_sky + 3;
+    const size_t tabs = m.var_sigma ? (size_t)m.esat_sky + 1 : (size_t)m.esat_obj + m.esat_sky + 2;
     return sizeof(int32_t) * ((size_t)QP + tabs + lc);
 }
 

@@ -22,6 +22,8 @@
 // disables floating-point contraction), which makes the tables reproducible.
 #include "model.h"
 
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 
@@ -66,6 +68,17 @@ bool sigma_ok(float x) { return finite_pos(x) && x <= 1000.0f; }
 bool prior_ok(float x) { return !std::isnan(x) && x >= 0.0f && (std::isinf(x) || x <= 1000.0f); }
 
 int32_t fixed_prior(double x) { return std::isinf(x) ? kBig : to_fixed(x); }
+
+// The reach ER (Q4 codes) of a ground residual window: the smallest e with
+// kmin + G(e / 16) >= C_out (G the residual term on the grid), so that a pixel
+// e / 16 px or more from the line costs C_out whatever its K (>= kmin); -1 if
+// that takes more than emax codes (dmax px).
+int ground_reach(double sigma, int32_t kmin, int32_t c_out, int emax)
+{
+    for (int e = 0; e <= emax; ++e)
+        if ((int64_t)kmin + to_fixed(resid_capped(e / 16.0, sigma)) >= c_out) return e;
+    return -1;
+}
 
 }  // namespace
 
@@ -231,13 +244,56 @@ int build_model(const stixels_params_t* p, HostModel* m)
     m->pen_div = fixed_prior((double)p->cost_diving);
     m->pen_ord = fixed_prior((double)p->cost_order);
     m->max_finite_prior = maxp + m->pen_grav + m->pen_div + m->pen_ord;
-    m->eps_g = (int32_t)llround(16.0 * (double)p->eps_gravity);
-    m->eps_d = (int32_t)llround(16.0 * (double)p->eps_diving);
-    m->eps_o = (int32_t)llround(16.0 * (double)p->eps_order);
+    // 16 f > 16 f' + 16 eps  <=>  f - f' > floor(eps) for integer f, f'
+    m->ord_off = (int32_t)floor((double)p->eps_order);
+    // the same constants without the grid (the cost report of a solved column)
+    RealModel& r = m->real;
+    r.c_out = (float)(log(d_range) - log(p_out));
+    r.k_obj.resize(F);
+    r.inv_obj.resize(F);
+    for (int f = 0; f < F; ++f) {
+        r.k_obj[f] = (float)gauss_const((double)f, so[f], p_out, d_range);
+        r.inv_obj[f] = (float)(1.0 / (2.0 * so[f] * so[f]));
+    }
+    r.k_sky = (float)gauss_const(0.0, s_sky_f, p_out, d_range);
+    r.inv_sky = (float)(1.0 / (2.0 * s_sky_f * s_sky_f));
+    r.inv_ground = (float)(1.0 / (2.0 * s_gnd * s_gnd));
+    for (int c = 0; c < 3; ++c) {
+        r.first[c] = (double)p->prior_first[c] + bic;
+        for (int q = 0; q < 3; ++q) r.trans[c][q] = (double)p->prior_trans[c][q] + bic;
+    }
+    r.pen_grav = (double)p->cost_gravity;
+    r.pen_div = (double)p->cost_diving;
+    r.pen_ord = (double)p->cost_order;
+    r.eps_g = (double)p->eps_gravity;
+    r.eps_d = (double)p->eps_diving;
+    r.eps_o16 = 16.0 * (double)p->eps_order;
     m->kg_tab.clear();
+    r.rkg_tab.clear();
+    m->est_pool.clear();
+    m->est_gw = 0;
     if (p->ground_estimate) {
-        m->kg_tab.resize(m->emax + 1);
-        for (int c = 0; c <= m->emax; ++c) m->kg_tab[c] = to_fixed(gauss_const(c / 16.0, s_gnd, p_out, d_range));
+        const int nc = 256 * m->dmax + 1;
+        m->kg_tab.resize(nc);
+        r.rkg_tab.resize(nc);
+        int32_t kmin = INT32_MAX;
+        for (int c = 0; c < nc; ++c) {
+            const double k = gauss_const(c / 256.0, s_gnd, p_out, d_range);
+            m->kg_tab[c] = to_fixed(k);
+            r.rkg_tab[c] = (float)k;
+            kmin = std::min(kmin, m->kg_tab[c]);
+        }
+        // the windows of an estimated line f_g = x / 256: at code q = (x >> 4)
+        // - ER + j the residual is ((16 (j - ER) - (x & 15)) / 256)^2 / (2
+        // sigma^2), so it depends only on j and the phase x & 15
+        const int er = ground_reach(s_gnd, kmin, m->c_out, m->emax);
+        if (er < 0) return STIXELS_E_INVALID_ARG;
+        m->est_gw = 2 * er + 2;
+        m->est_pool.resize((size_t)16 * m->est_gw);
+        for (int ph = 0; ph < 16; ++ph)
+            for (int j = 0; j < m->est_gw; ++j)
+                m->est_pool[(size_t)ph * m->est_gw + j] =
+                    to_fixed(resid_capped((double)(16 * (j - er) - ph) / 256.0, s_gnd));
     }
     // whole-pixel grid: the object pixel cost of every (model disparity f,
     // pixel disparity d) pair, the same value as the per-pixel formula at the
@@ -255,29 +311,55 @@ int build_model(const stixels_params_t* p, HostModel* m)
     return STIXELS_OK;
 }
 
-bool build_rows(const HostModel& m, int H, std::vector<int32_t>* fgq, std::vector<int32_t>* k_ground,
-                std::vector<int32_t>* g_rows)
+bool build_rows(const HostModel& m, int H, std::vector<char>* block, int* gw)
 {
-    fgq->resize(H);
-    k_ground->resize(H);
-    g_rows->clear();
-    const int E = m.emax + 1;
-    if (m.var_sigma) g_rows->resize((size_t)H * E);
     const double d_range = (double)m.dmax;
     const double p_out = (double)m.p.p_out;
     const double s_gnd = (double)m.p.sigma_ground;
+    std::vector<double> fgv(H), sgv(H);
+    std::vector<int32_t> kgv(H);
+    int er = 0;
     for (int v = 0; v < H; ++v) {
         const int r = H - 1 - v;                       // image row of bottom-up row v
-        const long long code = llround(16.0 * m.alpha * (double)(r - m.p.horizon_row));
-        const double fg = (double)code / 16.0;
-        const double sg = sigma_at(m.p, s_gnd, fg);
-        (*fgq)[v] = (int32_t)code;
-        (*k_ground)[v] = to_fixed(gauss_const(fg, sg, p_out, d_range));
-        if (m.var_sigma) {
-            int32_t* g = g_rows->data() + (size_t)v * E;
-            for (int e = 0; e < E; ++e) g[e] = to_fixed(resid_capped(e / 16.0, sg));
-            // residuals are clamped to the table's end: it must already be the outlier branch
-            if ((int64_t)(*k_ground)[v] + g[m.emax] < m.c_out) return false;
+        fgv[v] = m.alpha * (double)(r - m.p.horizon_row);
+        sgv[v] = sigma_at(m.p, s_gnd, fgv[v]);
+        kgv[v] = to_fixed(gauss_const(fgv[v], sgv[v], p_out, d_range));
+        const int e = ground_reach(sgv[v], kgv[v], m.c_out, m.emax);
+        if (e < 0) return false;
+        er = std::max(er, e);
+    }
+    if (!budget_ok(m, H, kgv.data())) return false;
+    // a handle that estimates its ground swaps these rows for a frame's when
+    // something votes: both use one window size (the estimate's reach, taken
+    // over every K, is the larger)
+    if (m.p.ground_estimate) er = std::max(er, (m.est_gw - 2) / 2);
+    *gw = 2 * er + 2;
+    const size_t arrays = rows_arrays_bytes(H);
+    block->assign(arrays + sizeof(int32_t) * (size_t)H * *gw, 0);
+    double* fg = reinterpret_cast<double*>(block->data());
+    int32_t* kg = reinterpret_cast<int32_t*>(fg + H);
+    int32_t* thr = kg + H;
+    int32_t* gf = kg + 2 * H;
+    int32_t* goff = kg + 3 * H;
+    float* rkg = reinterpret_cast<float*>(kg + 4 * H);
+    float* rinv = rkg + H;
+    float* rdg = rkg + 2 * H;
+    int32_t* pool = reinterpret_cast<int32_t*>(block->data() + arrays);
+    for (int v = 0; v < H; ++v) {
+        const double f = fgv[v];
+        const int32_t g = (int32_t)floor(16.0 * f);
+        fg[v] = f;
+        kg[v] = kgv[v];
+        thr[v] = pack_thresholds(f, (double)m.p.eps_gravity, (double)m.p.eps_diving);
+        gf[v] = g;
+        goff[v] = v * *gw;
+        rkg[v] = (float)gauss_const(f, sgv[v], p_out, d_range);
+        rinv[v] = (float)(1.0 / (2.0 * sgv[v] * sgv[v]));
+        rdg[v] = (float)(f - (double)g / 16.0);
+        // the window: codes q = g - ER .. g + ER + 1, residual of (q / 16 - f_g)
+        for (int j = 0; j < *gw; ++j) {
+            const int q = g - er + j;
+            pool[(size_t)v * *gw + j] = to_fixed(resid_capped((double)q / 16.0 - f, sgv[v]));
         }
     }
     return true;
@@ -288,11 +370,11 @@ bool build_rows(const HostModel& m, int H, std::vector<int32_t>* fgq, std::vecto
 // H * max|pixel cost| + 3 * (largest prior of one stixel).  Keeping that below
 // 2^28 units keeps feasible costs below the 2^29 "infeasible" marker and every
 // candidate sum (cost <= 2^29, transition <= 2^29, penalty, data) inside int32.
-bool budget_ok(const HostModel& m, int H, const std::vector<int32_t>& k_ground)
+bool budget_ok(const HostModel& m, int H, const int32_t* k_ground)
 {
     int64_t kmin = m.k_sky;
     for (int32_t k : m.k_obj) kmin = k < kmin ? k : kmin;
-    for (int32_t k : k_ground) kmin = k < kmin ? k : kmin;
+    for (int v = 0; v < H; ++v) kmin = k_ground[v] < kmin ? k_ground[v] : kmin;
     int64_t per_pixel = m.c_out > -kmin ? m.c_out : -kmin;
     int64_t worst = (int64_t)H * per_pixel + 3 * (int64_t)m.max_finite_prior;
     return worst < kFiniteBudget;

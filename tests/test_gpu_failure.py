@@ -25,8 +25,9 @@ def test_bounded_wait_gives_up_with_a_status_and_the_context_stays_usable():
     out = S.Stixels.to_host(h.compute(cuda(sc.disparity)))
     torch.cuda.synchronize()
     assert h.get_error() == 0
-    fr = oracle.frame(oracle.make_params(cam), sc.disparity, cap=h.params.max_stixels_per_col)
-    assert_frame_equal(out, fr, cam.height, h.params.max_stixels_per_col)
+    op = oracle.make_params(cam)
+    fr = oracle.frame(op, sc.disparity, cap=h.params.max_stixels_per_col)
+    assert_frame_equal(out, fr, cam.height, h.params.max_stixels_per_col, op)
     h.close()
 
 

@@ -101,7 +101,7 @@ def test_frames_with_the_estimate_equal_oracle(i):
     err = h.get_error()
     fr = oracle.frame(op, sc.disparity, cap=lp.max_stixels_per_col)
     assert err == (S.ERR_CAPACITY if (fr.counts > lp.max_stixels_per_col).any() else 0)
-    assert_frame_equal(res, fr, cam.height, lp.max_stixels_per_col)
+    assert_frame_equal(res, fr, cam.height, lp.max_stixels_per_col, op)
     # and through host buffers
     st, counts, cost, rc = h.compute_host(sc.disparity)
     assert np.array_equal(counts, res[1]) and np.array_equal(cost, res[2])

@@ -23,7 +23,7 @@ def test_global_map_config1(seed):
     out, err = run_frame(lp, sc.disparity)
     fr = oracle.frame(op, sc.disparity, cap=lp.max_stixels_per_col)
     assert err == 0
-    assert_frame_equal(out, fr, cam.height, lp.max_stixels_per_col)
+    assert_frame_equal(out, fr, cam.height, lp.max_stixels_per_col, op)
 
 
 @pytest.mark.parametrize("H", [1, 2, 31, 33, 97])
@@ -34,7 +34,7 @@ def test_global_map_ragged_heights(H):
     lp, op = both_params(cam, global_map=1, cost_order=3.0, eps_order=-0.5)
     out, err = run_frame(lp, sc.disparity)
     fr = oracle.frame(op, sc.disparity, cap=lp.max_stixels_per_col)
-    assert_frame_equal(out, fr, H, lp.max_stixels_per_col)
+    assert_frame_equal(out, fr, H, lp.max_stixels_per_col, op)
 
 
 @pytest.mark.parametrize("variant", [
@@ -48,7 +48,7 @@ def test_global_map_model_variants(variant):
     lp, op = both_params(cam, global_map=1, **variant)
     out, _ = run_frame(lp, sc.disparity)
     fr = oracle.frame(op, sc.disparity, cap=lp.max_stixels_per_col)
-    assert_frame_equal(out, fr, cam.height, lp.max_stixels_per_col)
+    assert_frame_equal(out, fr, cam.height, lp.max_stixels_per_col, op)
 
 
 def test_global_map_paper_size_sampled_columns():
@@ -109,4 +109,4 @@ def test_global_map_refuses_a_column_state_beyond_shared_memory():
     lp, op = both_params(cam, global_map=1)
     out, err = run_frame(lp, sc.disparity)
     fr = oracle.frame(op, sc.disparity, cap=lp.max_stixels_per_col)
-    assert_frame_equal(out, fr, cam.height, lp.max_stixels_per_col)
+    assert_frame_equal(out, fr, cam.height, lp.max_stixels_per_col, op)

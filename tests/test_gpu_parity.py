@@ -1,8 +1,13 @@
 """Parity of the CUDA library with the CPU oracle, element by element, on seeded
-synthetic inputs (all through the C ABI).  The library's arithmetic is exact
-fixed point, so the expected bar is bit-exact: identical Q4 codes, identical
-prefix LUTs, identical stixel boundaries / classes / counts, identical column
-costs, and disparities equal to the float of the exact mean."""
+synthetic inputs (all through the C ABI).  The library's DP decides in exact
+fixed point, so the bar against the oracle's fixed-grid mode is bit-exact:
+identical Q4 codes, identical prefix LUTs, identical stixel boundaries /
+classes / counts, identical fixed-point column minima, and disparities equal
+to the float of the exact mean.  The reported column cost is the segmentation's
+cost in real arithmetic: it must equal the oracle's real-arithmetic evaluation
+of the same segmentation within 1e-6 relative (FP32 per-pixel terms, a few
+1e-8 relative each; their sum exact in fixed point at 2^-24, which rounds each
+pixel by at most 3e-8; the total rounded to FP32 once)."""
 import math
 
 import numpy as np
@@ -25,11 +30,37 @@ def both_params(cam, **kw):
     return S.default_params(cam, **kw), oracle.make_params(cam, **kw)
 
 
-def assert_frame_equal(out, fr, H, cap):
+REAL_COST_RTOL = 1e-6
+
+
+def real_params(op):
+    """The same oracle parameters in plain real arithmetic (no cost grid)."""
+    pu = type(op).from_buffer_copy(op)
+    pu.quantize = 0
+    return pu
+
+
+def real_costs(op, fr):
+    """Costs of the oracle's own segmentations of frame fr in real arithmetic
+    (NaN where a column's list exceeds the capacity and is incomplete)."""
+    return oracle.eval_frame(real_params(op), fr.q, fr.stixels, fr.counts)
+
+
+def assert_real_costs(cost, expected):
+    ok = ~np.isnan(expected)
+    e = expected[ok]
+    g = cost[ok].astype(np.float64)
+    fin = np.isfinite(e)
+    assert np.array_equal(np.isfinite(g), fin)
+    rel = np.abs(g[fin] - e[fin]) / np.abs(e[fin])
+    assert rel.size == 0 or rel.max() <= REAL_COST_RTOL, (rel.max(), int(np.argmax(rel)))
+
+
+def assert_frame_equal(out, fr, H, cap, op):
     st, counts, cost, cost_fixed = out
     assert np.array_equal(counts, fr.counts), np.nonzero(counts != fr.counts)[0][:10]
     assert np.array_equal(cost_fixed, (fr.cost * S.UNITS_PER_COST).astype(np.int64))
-    assert np.array_equal(cost, fr.cost.astype(np.float32))
+    assert_real_costs(cost, real_costs(op, fr))
     for c in range(len(counts)):
         n = min(int(counts[c]), cap)
         g = st[c, :n]
@@ -115,7 +146,7 @@ def test_pipeline_config1(seed):
     out, err = run_frame(lp, sc.disparity)
     fr = oracle.frame(op, sc.disparity, cap=lp.max_stixels_per_col)
     assert err == 0
-    assert_frame_equal(out, fr, cam.height, lp.max_stixels_per_col)
+    assert_frame_equal(out, fr, cam.height, lp.max_stixels_per_col, op)
 
 
 def test_pipeline_config2():
@@ -125,7 +156,7 @@ def test_pipeline_config2():
     out, err = run_frame(lp, sc.disparity)
     fr = oracle.frame(op, sc.disparity, cap=lp.max_stixels_per_col)
     assert err == 0
-    assert_frame_equal(out, fr, cam.height, lp.max_stixels_per_col)
+    assert_frame_equal(out, fr, cam.height, lp.max_stixels_per_col, op)
 
 
 @pytest.mark.parametrize("i", range(len(scenes.CONFIG3)))
@@ -136,7 +167,7 @@ def test_pipeline_config3_sweep(i):
     out, err = run_frame(lp, sc.disparity)
     fr = oracle.frame(op, sc.disparity, cap=lp.max_stixels_per_col)
     assert err == 0
-    assert_frame_equal(out, fr, cam.height, lp.max_stixels_per_col)
+    assert_frame_equal(out, fr, cam.height, lp.max_stixels_per_col, op)
 
 
 @pytest.mark.parametrize("H", [1, 2, 3, 31, 32, 33, 63, 64, 65, 97])
@@ -147,7 +178,7 @@ def test_pipeline_ragged_heights(H):
     lp, op = both_params(cam)
     out, err = run_frame(lp, sc.disparity)
     fr = oracle.frame(op, sc.disparity, cap=lp.max_stixels_per_col)
-    assert_frame_equal(out, fr, H, lp.max_stixels_per_col)
+    assert_frame_equal(out, fr, H, lp.max_stixels_per_col, op)
 
 
 @pytest.mark.parametrize("s", [3, 5, 7])
@@ -168,16 +199,18 @@ def test_compute_equals_the_staged_pipeline(s, mode):
     torch.cuda.synchronize()
     for a, b in zip(fused, staged):
         assert np.array_equal(np.asarray(a), np.asarray(b))
-    fr = oracle.frame(oracle.make_params(cam, reduce_mode=mode), D, cap=h.params.max_stixels_per_col)
-    assert_frame_equal(fused, fr, H, h.params.max_stixels_per_col)
+    op = oracle.make_params(cam, reduce_mode=mode)
+    fr = oracle.frame(op, D, cap=h.params.max_stixels_per_col)
+    assert_frame_equal(fused, fr, H, h.params.max_stixels_per_col, op)
     h.close()
 
 
 @pytest.mark.parametrize("ncols,H", [(153, 1), (153, 97), (200, 33), (257, 440), (304, 450), (304, 500)])
 def test_pipeline_column_counts_between_one_and_two_per_sm(ncols, H):
     """Frames with more columns than SMs (up to twice as many on a 152-SM
-    part) run each column on a two-CTA cluster; every column must still equal
-    the oracle, at ragged heights and at the tallest height that form takes."""
+    part) run two 8-warp CTAs per SM instead of one 16-warp CTA per column;
+    every column must still equal the oracle, at ragged heights and at the
+    tallest height that launch shape takes."""
     cam = scenes.Camera(ncols * 5, H, stixel_width=5, dmax=64, horizon_row=H // 3, baseline_m=0.4,
                         camera_height_m=1.2)
     sc = scenes.make_scene(cam, 900 + ncols + H, n_obstacles=(3, 12), span_cols=(1, 12))
@@ -185,7 +218,7 @@ def test_pipeline_column_counts_between_one_and_two_per_sm(ncols, H):
     out, err = run_frame(lp, sc.disparity)
     fr = oracle.frame(op, sc.disparity, cap=lp.max_stixels_per_col)
     assert err == (S.ERR_CAPACITY if (fr.counts > lp.max_stixels_per_col).any() else 0)
-    assert_frame_equal(out, fr, H, lp.max_stixels_per_col)
+    assert_frame_equal(out, fr, H, lp.max_stixels_per_col, op)
 
 
 @pytest.mark.parametrize("H,dmax", [(2048, 128), (1800, 255)])
@@ -199,7 +232,7 @@ def test_pipeline_maximum_height(H, dmax):
     out, err = run_frame(lp, sc.disparity)
     fr = oracle.frame(op, sc.disparity, cap=lp.max_stixels_per_col)
     assert err == (S.ERR_CAPACITY if (fr.counts > lp.max_stixels_per_col).any() else 0)
-    assert_frame_equal(out, fr, H, lp.max_stixels_per_col)
+    assert_frame_equal(out, fr, H, lp.max_stixels_per_col, op)
 
 
 @pytest.mark.parametrize("variant", [
@@ -220,7 +253,7 @@ def test_pipeline_model_variants(variant):
     lp, op = both_params(cam, **variant)
     out, _ = run_frame(lp, sc.disparity)
     fr = oracle.frame(op, sc.disparity, cap=lp.max_stixels_per_col)
-    assert_frame_equal(out, fr, cam.height, lp.max_stixels_per_col)
+    assert_frame_equal(out, fr, cam.height, lp.max_stixels_per_col, op)
 
 
 def test_capacity_overflow_is_flagged():
@@ -231,7 +264,7 @@ def test_capacity_overflow_is_flagged():
     fr = oracle.frame(op, sc.disparity, cap=2)
     assert (fr.counts > 2).any()
     assert err & S.ERR_CAPACITY
-    assert_frame_equal(out, fr, cam.height, 2)
+    assert_frame_equal(out, fr, cam.height, 2, op)
 
 
 def test_infeasible_columns_are_flagged():
@@ -344,4 +377,4 @@ def test_pixel_grid_pipeline_paper_sizes(i):
     # the mean keeps outliers, so a few columns may need more than the capacity:
     # the flag is raised exactly then, and the stored prefix still matches
     assert err == (S.ERR_CAPACITY if (fr.counts > lp.max_stixels_per_col).any() else 0)
-    assert_frame_equal(out, fr, cam.height, lp.max_stixels_per_col)
+    assert_frame_equal(out, fr, cam.height, lp.max_stixels_per_col, op)

@@ -16,6 +16,8 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
+from test_gpu_parity import assert_real_costs, real_costs  # noqa: E402
+
 
 def _cameras():
     cams = scenes.serving_cameras()
@@ -79,11 +81,12 @@ def test_served_frame_matches_oracle():
     srv = S.Server(64 << 20, max_slots=4)
     t = srv.submit(h, sc.disparity)
     out = _poll_done(srv, t, h.alloc_host_output(cam.height, cam.width))
-    fr = oracle.frame(oracle.make_params(cam), sc.disparity, cap=lp.max_stixels_per_col)
+    op = oracle.make_params(cam)
+    fr = oracle.frame(op, sc.disparity, cap=lp.max_stixels_per_col)
     st, cnt, cost = out
     n, cap = cam.ncols, lp.max_stixels_per_col
     assert np.array_equal(cnt[:n], fr.counts)
-    assert np.array_equal(cost[:n], fr.cost.astype(np.float32))
+    assert_real_costs(cost[:n], real_costs(op, fr))
     st = st[:n * cap].reshape(n, cap)
     for c in range(n):
         k = min(int(cnt[c]), cap)

@@ -76,13 +76,47 @@ def test_model_tables_equal_oracle_constants(i):
     assert sc[1] == mc["k_sky"] * U
     assert np.array_equal(t["k_obj"], mc["k_obj"] * U)
     assert np.array_equal(t["k_ground"], mc["k_ground"] * U)
-    assert np.array_equal(t["fgq"], mc["fg"] * 16)
+    assert np.array_equal(t["fg"], mc["fg"])
     big = 1 << 29
     first = np.where(np.isinf(mc["first"]), big, mc["first"] * U)
     trans = np.where(np.isinf(mc["trans"]), big, mc["trans"] * U)
     assert np.array_equal(sc[2:5], first)
     assert np.array_equal(sc[5:14], trans.reshape(-1))
     assert np.array_equal(sc[14:17], mc["pens"] * U)
+
+
+def _decide(thr_word, f):
+    """(gravity, diving) decisions of a packed threshold word for disparity f."""
+    fhi = ((thr_word & 0xffff) ^ 0x8000) - 0x8000
+    flo = thr_word >> 16
+    return f > fhi, f < flo
+
+
+@pytest.mark.parametrize("i", range(len(PARAM_SETS)))
+def test_thresholds_decide_as_the_unrounded_rule(i):
+    """The per-row gravity / diving thresholds and the ordering offset give, for
+    every integer disparity, the decision of the paper's comparisons on the
+    unrounded ground line (Sec. 3 constraints): 16 f > 16 (f_g + eps_gravity),
+    16 f < 16 (f_g - eps_diving), 16 f > 16 f' + 16 eps_order."""
+    lp, op = _both(PARAM_SETS[i])
+    H = 97 if i != 2 else 880
+    t = S.model_tables(lp, H)
+    fg = oracle.model_constants(op, H)["fg"]
+    eg, ed, eo = float(np.float32(lp.eps_gravity)), float(np.float32(lp.eps_diving)), float(np.float32(lp.eps_order))
+    for v in range(H):
+        for f in range(0, lp.dmax + 1):
+            grav, div = _decide(int(t["thr"][v]), f)
+            assert grav == (16.0 * f > 16.0 * (fg[v] + eg)), (v, f)
+            assert div == (16.0 * f < 16.0 * (fg[v] - ed)), (v, f)
+    off = int(t["scalars"][17])
+    for d in range(-300, 301):
+        assert (d > off) == (16.0 * d > 16.0 * eo), d
+
+
+def _llround(x):
+    """C's llround for x >= 0: nearest integer, halves away from zero (exact)."""
+    n = math.floor(x)
+    return n + 1 if x - n >= 0.5 else n
 
 
 @pytest.mark.parametrize("i", [0, 3, 4])
@@ -98,7 +132,12 @@ def test_pixel_costs_from_tables_equal_oracle(i):
     for _ in range(300):
         q = int(rng.integers(0, emax + 1)); f = int(rng.integers(0, lp.dmax + 1)); v = int(rng.integers(0, H))
         obj = min(c_out, int(t["k_obj"][f]) + int(t["g_obj"][min(abs(q - 16 * f), emax)]))
-        gnd = min(c_out, int(t["k_ground"][v]) + int(t["g_ground"][min(abs(q - int(t["fgq"][v])), emax)]))
+        # the ground residual at the unrounded line, in FP64 as the LUT kernel
+        # evaluates it, rounded to the 2^-12 grid
+        sg = float(np.float32(lp.sigma_ground))
+        dpx = q / 16.0 - float(t["fg"][v])
+        gres = 4 * _llround(4096.0 * min(dpx * dpx / (2.0 * sg * sg), 65536.0))
+        gnd = min(c_out, int(t["k_ground"][v]) + gres)
         sky = min(c_out, k_sky + int(t["g_sky"][q]))
         assert obj == oracle.pixel_cost(op, H, oracle.OBJECT, v, q, f) * U
         assert gnd == oracle.pixel_cost(op, H, oracle.GROUND, v, q) * U

@@ -88,9 +88,9 @@ def test_ground_line_geometry_and_row_direction():
     pq = oracle.make_params(dmax=64, horizon_row=hz, baseline_m=0.5, camera_height_m=1.0,
                             pitch_rad=0.1, quantize=1)
     fg = oracle.model_constants(pq, H)["fg"]
+    # the cost grid leaves the ground model itself alone: the line is not rounded
     for v in range(H):
-        assert abs(fg[v] - alpha * (H - 1 - v - hz)) <= 1.0 / 32 + 1e-12
-        assert (fg[v] * 16).is_integer()
+        assert abs(fg[v] - alpha * (H - 1 - v - hz)) <= 1e-12
 
 
 def test_cost_grid_resolution():

@@ -72,6 +72,7 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the model-variant timings")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the frame-size sweep")
     ap.add_argument("--served-seconds", type=float, default=2.0, help="length of the Poisson arrival trace")
     ap.add_argument("--only", choices=["all", "batched", "served"], default="all",
                     help="run one secondary workload alone and print its record (for profiling); "
@@ -166,17 +167,18 @@ def measured_peaks():
 
 # ----------------------------------------------------------------------------- CPU oracle
 
-def oracle_rate(cam, scene_fn, seconds, max_frames=1024):
-    """Frames/s of the CPU oracle on host cores, over a bounded sample: each
-    frame is generated outside the timed call, and the sample ends once the
-    oracle's own time reaches `seconds`."""
+def oracle_rate(cam, scene_fn, seconds, max_frames=1024, nthreads=0):
+    """Frames/s of the CPU oracle on host cores (nthreads = 0: all of them,
+    OpenMP over columns), over a bounded sample: each frame is generated
+    outside the timed call, and the sample ends once the oracle's own time
+    reaches `seconds`."""
     import oracle
     p = oracle.make_params(cam)
     frames, busy = 0, 0.0
     while True:
         sc = scene_fn(frames)
         t0 = time.perf_counter()
-        oracle.frame(p, sc.disparity, cap=64)
+        oracle.frame(p, sc.disparity, cap=64, nthreads=nthreads)
         busy += time.perf_counter() - t0
         frames += 1
         if busy >= seconds or frames >= max_frames:
@@ -220,16 +222,17 @@ def bench_batched(S, scenes, torch, dev, cams, seed0, launches, label):
             "kernels_per_launch": "reduce (one per stixel-width/mode group) + LUT + persistent DP, one CUDA graph"}
 
 
-def bench_served(S, scenes, torch, seconds, rate=2000.0, budget=20 << 30, seed=5000):
-    """8 cameras, Poisson arrivals at `rate` frames/s in aggregate, host frames in pinned memory,
-    submitted by one client thread at their arrival times and polled by another; latency =
-    completion of poll (results in host memory) - scheduled arrival."""
+def bench_served(S, scenes, torch, seconds, rate=2000.0, budget=20 << 30, seed=5000, cams=None, label=None):
+    """8 cameras (the serving workload's, or `cams`), Poisson arrivals at `rate` frames/s in
+    aggregate, host frames in pinned memory, submitted by one client thread at their arrival
+    times and polled by another; latency = completion of poll (results in host memory) -
+    scheduled arrival."""
     import queue
     import threading
 
     import numpy as np
 
-    cams = scenes.serving_cameras(seed)
+    cams = cams or scenes.serving_cameras(seed)
     hs = [S.Stixels(S.default_params(c)) for c in cams]
     per_cam = 3
     frames = []
@@ -329,9 +332,9 @@ def bench_served(S, scenes, torch, seconds, rate=2000.0, budget=20 << 30, seed=5
         h.close()
     span = float(done_at.max() - t0)
     lat_ms = np.sort(lat) * 1000.0
-    return {"workload": "8 cameras (3x 640x240 dmax 64, 3x 1024x440, 2x 2048x880 dmax 128; s=5), Poisson "
-                        f"arrivals {rate:.0f} frames/s aggregate, {budget >> 30} GB arena budget, host frames "
-                        "(pinned) in, results in host memory out",
+    return {"workload": (label or "8 cameras (3x 640x240 dmax 64, 3x 1024x440, 2x 2048x880 dmax 128; s=5)") +
+                        f", Poisson arrivals {rate:.0f} frames/s aggregate, {budget >> 30} GB arena budget, host "
+                        "frames (pinned) in, results in host memory out",
             "offered_fps": rate, "frames": n, "achieved_fps": n / span,
             "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
             "max_ms": float(lat_ms[-1]), "mean_batch": st["frames_in_iterations"] / max(st["iterations"], 1),
@@ -339,11 +342,11 @@ def bench_served(S, scenes, torch, seconds, rate=2000.0, budget=20 << 30, seed=5
             "latency": "scheduled arrival -> poll returned with results in host memory"}
 
 
-def bench_served_saturated(S, scenes, torch, frames_total=2000, budget=20 << 30, seed=5000):
+def bench_served_saturated(S, scenes, torch, frames_total=2000, budget=20 << 30, seed=5000, cams=None):
     """Serving capacity: all frames submitted as fast as admission allows (no arrival pacing)."""
     import threading
 
-    cams = scenes.serving_cameras(seed)
+    cams = cams or scenes.serving_cameras(seed)
     hs = [S.Stixels(S.default_params(c)) for c in cams]
     frames = [torch.from_numpy(scenes.make_scene(c, seed + 100 * k, n_obstacles=(8, 20)).disparity)
               .pin_memory().numpy() for k, c in enumerate(cams)]
@@ -382,6 +385,41 @@ def bench_served_saturated(S, scenes, torch, frames_total=2000, budget=20 << 30,
         h.close()
     return {"frames": frames_total, "fps": frames_total / el,
             "mean_batch": st["frames_in_iterations"] / max(st["iterations"], 1)}
+
+
+# ----------------------------------------------------------------------------- sweep
+
+def bench_sweep(S, scenes, torch, dev, flush, stream, steps):
+    """The small frame (320x120 s=5 dmax 64) and the width / height sweep (1024x440 at s = 3, 5, 7,
+    11; 2048x880 s=5), each one frame per step through stixels_compute (frames/s) and through the
+    staged entry points (the DP's time, per column): the method's work grows with the columns W/s
+    and with H^2 per column (Sec. 3.3)."""
+    import statistics as st
+    out = []
+    for wl, i, cam in [(1, 0, scenes.CONFIG1)] + [(3, j, c) for j, c in enumerate(scenes.CONFIG3)]:
+        sc = scenes.make_scene(cam, 1000 * wl + i, n_obstacles=scenes.OBSTACLES[wl])
+        disp = torch.from_numpy(sc.disparity).to(dev)
+        h = S.Stixels(S.default_params(cam))
+        t_c = time_compute(torch, h, disp, flush, stream, 5, steps)
+        _, _, _, t_dp, _ = time_stages(S, torch, h, disp, flush, stream, 5, steps)
+        ncols = cam.width // cam.stixel_width
+        cells = ncols * cam.height * (cam.height + 1) // 2
+        dp = st.median(t_dp)
+        out.append({"frame": f"{cam.width}x{cam.height} s={cam.stixel_width} dmax={cam.dmax}", "columns": ncols,
+                    "frames_per_s": len(t_c) / (sum(t_c) / 1000.0), "ms_per_frame_median": st.median(t_c),
+                    "dp_ms_median": dp, "dp_us_per_column": 1000.0 * dp / ncols,
+                    "dp_cells_per_s": cells / (dp / 1000.0), "device_error_word": h.get_error(stream)})
+        h.close()
+    by = {r["frame"]: r for r in out}
+    base, tall = by["1024x440 s=5 dmax=128"], by["2048x880 s=5 dmax=128"]
+    return {"frames": out,
+            "h_doubling": {"note": "2048x880 vs 1024x440 at s=5: 2.0x columns, 4.0x cells per column (H^2)",
+                           "dp_time_ratio": tall["dp_ms_median"] / base["dp_ms_median"],
+                           "dp_per_column_ratio": tall["dp_us_per_column"] / base["dp_us_per_column"],
+                           "frame_time_ratio": tall["ms_per_frame_median"] / base["ms_per_frame_median"]},
+            "width_sweep": {"note": "1024x440 at s = 3, 5, 7, 11: DP time against columns (linear in W/s)",
+                            "columns": [by[f"1024x440 s={w} dmax=128"]["columns"] for w in (3, 5, 7, 11)],
+                            "dp_ms": [by[f"1024x440 s={w} dmax=128"]["dp_ms_median"] for w in (3, 5, 7, 11)]}}
 
 
 # ----------------------------------------------------------------------------- ours
@@ -599,6 +637,15 @@ def bench_ours(args, world, rank, local):
     if rank == 0 and not args.no_served:
         served = bench_served(S, scenes, torch, args.served_seconds)
         served["saturated"] = bench_served_saturated(S, scenes, torch)
+        # the paper's frame alone: 8 streams of 1024x440 s=5, against the per-frame launch
+        paper8 = [cam] * 8
+        served_paper = bench_served(S, scenes, torch, args.served_seconds, rate=6000.0, seed=5100, cams=paper8,
+                                    label="8 streams of 1024x440 s=5 dmax=128")
+        served_paper["saturated"] = bench_served_saturated(S, scenes, torch, seed=5100, cams=paper8)
+        served["paper_frames_only"] = served_paper
+    sweep = None
+    if rank == 0 and not args.no_sweep:
+        sweep = bench_sweep(S, scenes, torch, dev, flush, stream, min(K, 50))
 
     if rank != 0:
         h.close()
@@ -624,9 +671,14 @@ def bench_ours(args, world, rank, local):
     if not args.no_cpu_baseline and args.cpu_seconds > 0:
         fps, nfr, el = oracle_rate(cam, lambda i: scenes.make_scene(cam, 2100 + i, n_obstacles=(8, 20)),
                                    args.cpu_seconds)
+        fps1, nfr1, el1 = oracle_rate(cam, lambda i: scenes.make_scene(cam, 2100 + i, n_obstacles=(8, 20)),
+                                      max(1.0, args.cpu_seconds / 2), nthreads=1)
         cpu = {"value": fps, "unit": "frames/s", "cores": host_cores(), "kind": "oracle",
                "sample": f"{nfr} frames of 1024x440 s=5 dmax=128 (seeds 2100..{2100 + nfr - 1}), "
-                         f"columns spread over all host cores with OpenMP, {el:.1f} s in the oracle"}
+                         f"columns spread over all host cores with OpenMP, {el:.1f} s in the oracle",
+               "single_thread": {"value": fps1, "unit": "frames/s", "cores": 1,
+                                 "sample": f"{nfr1} frames (seeds 2100..{2100 + nfr1 - 1}), one thread, "
+                                           f"{el1:.1f} s in the oracle"}}
 
     rec = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": K,
@@ -647,7 +699,10 @@ def bench_ours(args, world, rank, local):
                             "achieved": red_bytes / (red_ms / 1000.0) / 1e9, "peak": hbm, "unit": "GB/s",
                             "frac": red_bytes / (red_ms / 1000.0) / 1e9 / hbm, "bytes": red_bytes,
                             "traffic": _traffic(os.path.join(kdir, "kernels_reduce.cu"))},
+        "ms_per_step_median": statistics.median(t_step),
         "stages_ms": {"reduce": red_ms, "luts": lut_ms, "dp": dp_ms,
+                      "reduce_median": statistics.median(t_red), "luts_median": statistics.median(t_lut),
+                      "dp_median": statistics.median(t_dp),
                       "staged_step_median": statistics.median(t_stage_step),
                       "step_median": statistics.median(t_step), "step_p99": sorted(t_step)[int(0.99 * (K - 1))],
                       "note": "reduce / luts / dp from the staged entry points (stixels_reduce, stixels_build_luts, "
@@ -660,6 +715,7 @@ def bench_ours(args, world, rank, local):
         "e2e": e2e,
         "batched": batched,
         "served": served,
+        "sweep": sweep,
         "model_variants": variants,
     }
     h.close()

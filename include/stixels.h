@@ -426,9 +426,10 @@ int stixels_server_destroy(stixels_server_t s);
  *   - The handle must already hold the row tables for height H (from
  *     stixels_reserve or an earlier stixels_compute with that height);
  *     otherwise STIXELS_E_INVALID_ARG (creating them would allocate).
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture.
+ *   - Every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress; it allocates nothing), so a device reset or a
+ *     new context is followed; the first call on a device may load the
+ *     module there, so make it before any stream capture.
  *   - Every call uses the same array, which keeps the previous call's
  *     contents; the pipeline overwrites every byte it reads, so nothing needs
  *     clearing, but calls whose work overlaps on the same GPU (issued on

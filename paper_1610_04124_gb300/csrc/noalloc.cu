@@ -4,8 +4,6 @@
 // code that must not let cudaMalloc / cudaFree synchronise the device).  The
 // frame's intermediate buffers live in one fixed array of this file instead of
 // the handle's workspace.  The paper has no counterpart of this entry point.
-#include <mutex>
-
 #include "internal.h"
 
 namespace {
@@ -15,26 +13,17 @@ namespace {
 // call shares it (calls that overlap on the GPU race).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[STIXELS_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices];
-bool g_scratch_ready[kMaxDevices];
-
-// The array's address on device `dev` (which must be current).  In host code
-// g_noalloc_scratch is only a host-side stand-in for the symbol, so the device
-// address is looked up once per device and cached.
-int scratch_address(int dev, unsigned char** out)
+// The array's address on the current device.  In host code g_noalloc_scratch
+// is only a host-side stand-in for the symbol, so the device address is
+// looked up (which allocates nothing) at every call: a cached address would
+// go stale if the device were reset, or the module loaded again in another
+// context, and the kernels would then write to memory that is not the array.
+int scratch_address(unsigned char** out)
 {
-    if (dev < 0 || dev >= kMaxDevices) return STIXELS_E_INVALID_ARG;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ready[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || p == nullptr) return STIXELS_E_CUDA;
-        g_scratch_addr[dev] = p;
-        g_scratch_ready[dev] = true;
-    }
-    *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) return stx::status_from_cuda(e == cudaSuccess ? cudaErrorInvalidSymbol : e);
+    *out = static_cast<unsigned char*>(p);
     return STIXELS_OK;
 }
 
@@ -74,7 +63,7 @@ extern "C" int stixels_compute_noalloc(stixels_t h, const float* d_disparity, in
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != v.device) return STIXELS_E_INVALID_ARG;
     unsigned char* base = nullptr;
-    rc = scratch_address(dev, &base);
+    rc = scratch_address(&base);
     if (rc != STIXELS_OK) return rc;
     int16_t* q = reinterpret_cast<int16_t*>(base + q_off);
     int32_t* pd = reinterpret_cast<int32_t*>(base + pd_off);

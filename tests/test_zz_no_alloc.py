@@ -5,8 +5,9 @@ real-time loop where cudaMalloc could stall or fail, code inside another
 framework's memory pool or under a fixed budget, code that must not let an
 allocation synchronise the device).  This entry point keeps the frame's
 intermediates in a fixed array inside the library instead.  It must return
-exactly what stixels_compute returns (the library's arithmetic is exact), on
-consecutive calls that reuse the same array, and reject frames too large for it.
+exactly what stixels_compute returns (the library's results are deterministic),
+on consecutive calls that reuse the same array, and reject frames too large for
+it or heights it has no tables for.
 """
 import ctypes as C
 
@@ -56,6 +57,20 @@ def test_noalloc_rejects_frames_larger_than_the_array():
     cam = scenes.CONFIG3[-1]                     # 2048 x 880, dmax 128: intermediates ~190 MB
     h = S.Stixels(S.default_params(cam))
     h.reserve(cam.height, cam.width)
+    d = torch.zeros((cam.height, cam.width), dtype=torch.float32, device="cuda")
+    out = h.alloc_output(cam.height, cam.width)
+    o = S.Stixels._out_struct(out)
+    rc = S.lib().stixels_compute_noalloc(h.handle, d.data_ptr(), cam.height, cam.width,
+                                         torch.cuda.current_stream().cuda_stream, C.byref(o))
+    assert rc == S.E_INVALID_ARG
+    h.close()
+
+
+def test_noalloc_refuses_a_height_the_handle_has_no_tables_for():
+    """Creating the row tables of a new height would allocate: without a reserve
+    (or an earlier allocating call) for that height the call is refused."""
+    cam = scenes.CONFIG1
+    h = S.Stixels(S.default_params(cam))
     d = torch.zeros((cam.height, cam.width), dtype=torch.float32, device="cuda")
     out = h.alloc_output(cam.height, cam.width)
     o = S.Stixels._out_struct(out)

@@ -181,6 +181,7 @@ int handle_view(stixels_t h, int H, HandleView* v)
     v->model = h->md;
     v->rows = rows_of(h, it->second);
     v->rp = h->rp;
+    v->pixel_floor = h->hm.pixel_floor;
     v->err = h->d_err;
     v->stixel_width = h->hm.p.stixel_width;
     v->reduce_mode = reduce_code(h->hm.p);
@@ -412,10 +413,10 @@ int stixels_solve(stixels_t h, const int32_t* d_pd, const int32_t* d_pg, const i
         if (!map_fits(H, h->hm.dmax + 1)) return STIXELS_E_INVALID_ARG;
         rc = ensure_workspace(h, map_scratch_bytes(H, ncols, h->hm.dmax + 1));
         if (rc) return rc;
-        return cuda_status(launch_dp_map(d_pd, d_pg, d_ps, d_po, g, h->md, r, h->rp, *out, h->d_err, h->ws.base,
+        return cuda_status(launch_dp_map(d_pd, d_pg, d_ps, d_po, g, h->md, r, h->rp, h->hm.pixel_floor, *out, h->d_err, h->ws.base,
                                          (cudaStream_t)stream));
     }
-    return cuda_status(launch_dp(d_pd, d_pg, d_ps, d_po, g, h->md, r, h->rp, *out, h->d_err, (cudaStream_t)stream));
+    return cuda_status(launch_dp(d_pd, d_pg, d_ps, d_po, g, h->md, r, h->rp, h->hm.pixel_floor, *out, h->d_err, (cudaStream_t)stream));
 }
 
 // The pipeline of stixels_compute, with the kernels' status flags ORed into
@@ -452,8 +453,8 @@ static int compute_frame(stixels_t h, const float* d_disparity, int H, int W, vo
     if (e == cudaSuccess && est) e = launch_ground(q, g, h->md, r, h->est_pool, h->hm.est_gw, ws + L.total, &r, nullptr, st);
     if (e == cudaSuccess) e = launch_luts(q, g, h->md, r, pd, pg, ps, po, st);
     if (e == cudaSuccess)
-        e = gmap ? launch_dp_map(pd, pg, ps, po, g, h->md, r, h->rp, *out, err, ws + L.total + gw, st)
-                 : launch_dp(pd, pg, ps, po, g, h->md, r, h->rp, *out, err, st);
+        e = gmap ? launch_dp_map(pd, pg, ps, po, g, h->md, r, h->rp, h->hm.pixel_floor, *out, err, ws + L.total + gw, st)
+                 : launch_dp(pd, pg, ps, po, g, h->md, r, h->rp, h->hm.pixel_floor, *out, err, st);
     return cuda_status(e);
 }
 

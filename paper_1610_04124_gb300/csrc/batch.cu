@@ -57,7 +57,8 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
         la[i].q = f.q;
         la[i].H = f.g.H; la[i].P = f.g.P; la[i].F = m.dmax + 1; la[i].m = m; la[i].rows = f.view.rows;
         la[i].pd = f.pd; la[i].pg = f.pg; la[i].ps = f.ps; la[i].po = f.po;
-        dp_frame_args(f.pd, f.pg, f.ps, f.po, f.g, m, f.view.rows, f.view.rp, f.out, f.view.err, &da[i]);
+        dp_frame_args(f.pd, f.pg, f.ps, f.po, f.g, m, f.view.rows, f.view.rp, f.view.pixel_floor, f.out, f.view.err,
+                      &da[i]);
         if (f.g.ncols == 0) continue;
         t->maxH = std::max(t->maxH, f.g.H);
         t->max_groups = std::max(t->max_groups, lut_row_groups(m.dmax + 1));

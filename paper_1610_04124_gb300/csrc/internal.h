@@ -193,6 +193,7 @@ struct DpArgs {
     int cap;
     uint32_t* err;
     RealParams rp;
+    int32_t pixel_floor;     // no object pixel costs less, at any f (2^-14 units; the DP's tile bound)
 };
 
 // What the scratch-free entry point needs from a prepared handle.
@@ -201,6 +202,7 @@ struct HandleView {
     ModelDev model;
     RowsDev rows;
     RealParams rp;              // the cost report's priors and constants
+    int32_t pixel_floor;        // the model's least object pixel cost (DpArgs::pixel_floor)
     uint32_t* err;
     int stixel_width, capacity;
     int reduce_mode;            // reduce_code of the params: bit 0 mean, bit 1 whole-pixel grid
@@ -229,10 +231,10 @@ cudaError_t launch_reduce_batch(const ReduceArgs* d_frames, const int4* d_tiles,
                                 cudaStream_t st);
 cudaError_t launch_dp(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po,
                       const FrameGeom& g, const ModelDev& m, const RowsDev& r, const RealParams& rp,
-                      const stixels_output_t& out, uint32_t* err, cudaStream_t st);
+                      int32_t pixel_floor, const stixels_output_t& out, uint32_t* err, cudaStream_t st);
 void dp_frame_args(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po, const FrameGeom& g,
-                   const ModelDev& m, const RowsDev& r, const RealParams& rp, const stixels_output_t& out,
-                   uint32_t* err, DpArgs* a);
+                   const ModelDev& m, const RowsDev& r, const RealParams& rp, int32_t pixel_floor,
+                   const stixels_output_t& out, uint32_t* err, DpArgs* a);
 size_t dp_shared_bytes(int H);
 // ---- batch planning shared by the batched mode and the server (batch.cu) ----
 // One frame's device buffers for a pipeline run.
@@ -287,7 +289,8 @@ cudaError_t launch_wait_selftest(uint32_t* err, int limit, cudaStream_t st);
 bool map_fits(int H, int F);
 cudaError_t launch_dp_map(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po,
                           const FrameGeom& g, const ModelDev& m, const RowsDev& r, const RealParams& rp,
-                          const stixels_output_t& out, uint32_t* err, void* scratch, cudaStream_t st);
+                          int32_t pixel_floor, const stixels_output_t& out, uint32_t* err, void* scratch,
+                          cudaStream_t st);
 
 // Sets the DP kernels' shared-memory attributes (call outside stream capture).
 cudaError_t prepare_dp_kernels();

@@ -34,14 +34,19 @@
 //   - the other warps (bulk) apply the starts of every finalised block t to the
 //     end rows of blocks t+2, t+3, ... (independent 32 x 32 tiles).  End-row
 //     block c receives c - 1 tiles; they are split by start block between two
-//     partial minima, the (block, partial) pairs are dealt to the bulk warps
-//     largest first in snake order, and a pair always stays with its warp, so
-//     each partial's updates happen in start order; the chain merges the
-//     partials by (cost, start) when it reaches the block, so two warps keep
-//     up with one block's growing list of tiles.  Each bulk warp runs its
-//     pending work earliest deadline first: the tile of the lowest end-row
-//     block (the chain needs it soonest) or its share of the chain's data for
-//     a block, whichever the chain reaches first.
+//     or three partial minima, the (block, partial) pairs are dealt to the
+//     bulk warps largest first in snake order, and a pair always stays with
+//     its warp; the chain merges the partials by (cost, start) when it
+//     reaches the block.  Each bulk warp runs its pending work earliest
+//     deadline first: the tile of the lowest end-row block (the chain needs it
+//     soonest) or its share of the chain's data for a block, whichever the
+//     chain reaches first.
+//   - exact branch and bound (per-frame launches with two columns per SM):
+//     a tile whose candidates are all provably dearer than a cost some
+//     candidate of its end rows already reaches is skipped.  That needs the
+//     newest starts first, so there a block's tiles wait until block c - 4 is
+//     final and then go newest first; elsewhere they go in start order as
+//     their start blocks become final.
 // The two sides synchronise through progress counters in shared memory
 // instead of CTA barriers, so neither waits for the other's non-critical work.
 // Every wait is a bounded spin: on expiry the CTA records STIXELS_ERR_TIMEOUT,
@@ -52,6 +57,7 @@
 // never directly above ground or sky, sky never directly above sky): those
 // transitions then drop out of the ground / sky running minima.  Any other
 // transition table uses the general instantiation.
+#include <algorithm>
 #include <climits>
 
 #include "internal.h"
@@ -63,7 +69,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxBlocks = (STIXELS_MAX_HEIGHT + 31) / 32;
 constexpr int kRingMax = 3;           // chain data buffers (blocks gathered ahead): 2 or 3
-constexpr int kSlots = 2;             // partial running minima per end row (start blocks t mod kSlots)
+constexpr int kMaxSlots = 3;          // partial running minima per end row (start blocks t mod slots): 2 or 3
 constexpr int kSpinLimit = 1 << 22;   // polls before a wait gives up (well over 0.1 s)
 
 // What the bulk tiles need of one start row b, shared by every end row k >= b
@@ -175,11 +181,11 @@ __device__ __forceinline__ bool wait_geq(volatile int* p, int target, volatile i
     return ok != 0;
 }
 
-size_t dp_smem_bytes(int H, int ring)
+size_t dp_smem_bytes(int H, int ring, int slots)
 {
     const size_t HP = (size_t)((H + 3) & ~3);
     return sizeof(BulkCtx) * HP + sizeof(int4) * HP + sizeof(int32_t) * 2 * (HP + 4) + sizeof(int2) * (HP + 4) +
-           sizeof(uint2) * (HP + 4) + sizeof(int32_t) * 2 * kSlots * HP + sizeof(ChainBuf) * ring +
+           sizeof(uint2) * (HP + 4) + sizeof(int32_t) * 2 * slots * HP + sizeof(ChainBuf) * ring +
            sizeof(SyncState);
 }
 
@@ -374,11 +380,12 @@ __device__ __noinline__ void finish_column(const DpArgs& a, int col, int H, Sync
 
 // Solves column `col` of frame `a` with all NW warps of the CTA (one chain
 // warp, NW - 1 bulk warps); `sm` is the CTA's dynamic shared memory
-// (dp_smem_bytes with the same ring, 2 or 3 chain buffers).  Every warp
+// (dp_smem_bytes with the same ring, 2 or 3 chain buffers, and slots, 2 or 3
+// partial minima per end row).  Every warp
 // returns from here; the caller synchronises before reusing `sm`.
 template <int NW, bool kStdTrans, bool kPeelFirst>
-__device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const int ring, int32_t* sm,
-                                          const int chain)
+__device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const int ring, const int slots,
+                                          const int window, int32_t* sm, const int chain)
 {
     constexpr int kWarps = NW;
     constexpr int kThreads = NW * 32;
@@ -407,10 +414,10 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
     int32_t* s_thr = s_pd8 + HP + 4;                                   // [HP + 4]
     int2* s_gs = reinterpret_cast<int2*>(s_thr + HP + 4);              // [HP + 4] {PG[v], PS[v]}, v = 0..H
     uint2* s_div = reinterpret_cast<uint2*>(s_gs + HP + 4);            // [HP + 4], index n = 1..H
-    // [kSlots][HP] object running minima over the start blocks t = s (mod kSlots)
+    // [slots][HP] object running minima over the start blocks t = s (mod slots)
     int32_t* s_runv = reinterpret_cast<int32_t*>(s_div + HP + 4);
-    int32_t* s_runbf = s_runv + kSlots * HP;                           // [kSlots][HP] start << 8 | f
-    ChainBuf* s_cb = reinterpret_cast<ChainBuf*>(s_runbf + kSlots * HP);   // [ring]
+    int32_t* s_runbf = s_runv + slots * HP;                            // [slots][HP] start << 8 | f
+    ChainBuf* s_cb = reinterpret_cast<ChainBuf*>(s_runbf + slots * HP);    // [ring]
     SyncState* sync = reinterpret_cast<SyncState*>(s_cb + ring);
     volatile int* v_final = &sync->final_blocks;
     volatile int* v_abort = &sync->abort;
@@ -425,7 +432,7 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
         if (v < H) {
             thr = thr_row[v];
 #pragma unroll
-            for (int q = 0; q < kSlots; ++q) {
+            for (int q = 0; q < slots; ++q) {
                 s_runv[q * HP + v] = INT_MAX;
                 s_runbf[q * HP + v] = 0;
             }
@@ -468,18 +475,23 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
     // (16 gathers in flight), each merged by a pairwise tree, then folded into
     // the running minimum in start order.  The group loop stays rolled to keep
     // the kernel's code small.
-    auto bulk_tile = [&](int t, int jc) {
+    auto bulk_tile = [&](int t, int jc, bool older) {
         const int k = 32 * jc + lane;
         const bool kv = k < H;
         const int kk = kv ? k : H - 1;
-        int32_t* runv = s_runv + (t % kSlots) * HP;
-        int32_t* runbfv = s_runbf + (t % kSlots) * HP;
+        int32_t* runv = s_runv + (t % slots) * HP;
+        int32_t* runbfv = s_runbf + (t % slots) * HP;
         int32_t run = INT_MAX, runbf = 0;
         if (kv) { run = runv[k]; runbf = runbfv[k]; }
         const int32_t x1 = s_pd8[kk + 1];
         const int32_t* hi_base = po_col + kk + 1;           // PO[f][k + 1] = hi_base[f P]
+        // older: the tile's starts come before (below) every start already in
+        // this partial minimum, so groups go in descending order and "<="
+        // lets the earlier start win on equal cost; otherwise they come after
+        // every one of them, in ascending order with "<"
 #pragma unroll 1
-        for (int g = 0; g < 4; ++g) {
+        for (int gi = 0; gi < 4; ++gi) {
+            const int g = older ? 3 - gi : gi;
             const int b0 = 32 * t + 8 * g;
             const uint2* divp = s_div + (kk + 1 - b0);      // s_div[k + 1 - b] = divp[-i], b = b0 + i
             const int32_t* lo_base = po_col + b0;           // PO[f][b] = lo_base[f P + i]
@@ -507,15 +519,52 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
                 cbf[i] = (b << 8) | f;
             }
             tree_min<8>(cv, cbf);
-            if (cv[0] < run) { run = cv[0]; runbf = cbf[0]; }
+            if (cv[0] < run || (older && cv[0] == run)) { run = cv[0]; runbf = cbf[0]; }
         }
         if (kv) { runv[k] = run; runbfv[k] = runbf; }
+    };
+
+    // Whether no candidate of tile (t, jc) can be the best object stixel of
+    // any of the block's end rows (exact branch and bound): every stixel of
+    // the tile spans the rows cs = 32 t + 31 .. 32 jc, so its cost is at least
+    // the best context of its start, plus the cheapest of those core rows'
+    // data over all f (a difference of two LUT rows), plus the per-pixel floor
+    // of the model for its other rows.  The tile is skipped when that bound
+    // exceeds, on every end row, a cost some candidate already reaches (any
+    // partial minimum; tiles come newest start first, so these are low early).
+    auto tile_bounded = [&](int t, int jc) -> bool {
+        const int k = 32 * jc + lane;
+        const int b = 32 * t + lane;
+        const BulkCtx cx = s_ctx[b];
+        int32_t lb = min(min(min(cx.o0, cx.o1), min(cx.g0, cx.gg)), cx.gd) - b * a.pixel_floor;
+        lb = __reduce_min_sync(kFull, lb);
+        const int cs = 32 * t + 31;
+        // every f's core difference, lane l taking f = l + 32 j (F <= 256; f
+        // clamped to F - 1 repeats the last one): all loads in flight at once
+        int32_t cm = INT_MAX;
+        const int32_t* core_hi = po_col + 32 * jc + 1;
+        const int32_t* core_lo = po_col + cs;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const size_t o = (size_t)min(lane + 32 * j, F - 1) * P;
+            cm = min(cm, __ldg(core_hi + o) - __ldg(core_lo + o));
+        }
+        cm = __reduce_min_sync(kFull, cm);
+        bool beat = true;
+        if (k < H) {
+            const int32_t bound = lb + cs * a.pixel_floor + cm + (k - 32 * jc) * a.pixel_floor;
+            int32_t rv = s_runv[k];
+#pragma unroll
+            for (int q = 1; q < slots; ++q) rv = min(rv, s_runv[q * HP + k]);
+            beat = bound > rv;
+        }
+        return __all_sync(kFull, beat);
     };
 
     if (warp != chain) {
         // ---------------------------------------------------------------- bulk warps
         // End-row block c receives c - 1 tiles, split by start block into
-        // kSlots partial minima (t = s mod kSlots) so that two warps share a
+        // `slots` partial minima (t = s mod slots) so that two or three warps share a
         // block's sequence of tiles.  The (block, slot) items are dealt, largest
         // block first, to the tile warps in snake order (rounds of kTile items,
         // alternating direction), which keeps the per-warp work balanced; lane l
@@ -524,7 +573,7 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
         // congruent to the chain's mod 4: bulk ids 3, 7, 11) take no tiles, only
         // their share of the gathers, so the chain's dependent steps are not
         // starved of issue slots there.
-        static_assert(32 * kTile >= kSlots * (kMaxBlocks - 2), "every (block, slot) item has a tile warp");
+        static_assert(32 * kTile >= kMaxSlots * (kMaxBlocks - 2), "every (block, slot) item has a tile warp");
         const bool quiet = ((bulk_id + 1) & 3) == 0;
         const int tile_id = bulk_id - ((bulk_id + 1) >> 2);
         // In the one-column-per-SM shape the quiet warps leave at once and the
@@ -533,19 +582,37 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
         if (kQuietExit && quiet) return;
         const int snake = (lane & 1) ? kTile - 1 - tile_id : tile_id;
         const int item = lane * kTile + snake;
-        const int my_c = NB - 1 - item / kSlots;
-        int my_t = item % kSlots;                             // next start block of the item
+        const int my_c = NB - 1 - item / slots;
+        const int slot = item % slots;
+        // The item's tiles are its slot's start blocks t <= my_c - 2.  The
+        // item opens once block my_c - 2 - window is final: its tiles up to
+        // that block go newest first (so that the bound above prunes the older
+        // ones with the newer ones' minima), then the `window` newer ones in
+        // order as their start blocks become final.  my_t is the next tile
+        // due (-1 once none is left), my_old whether it is still in the first
+        // part.
+        const int newest = my_c - 2;
+        const int split = newest - window;                   // the last tile of the first part
+        auto slot_top = [&](int t) { return t >= slot ? slot + (t - slot) / slots * slots : -1; };
+        auto slot_after = [&](int t) {                       // the first tile of the slot above t
+            const int u = slot + ((t + 1 - slot + slots - 1) / slots) * slots;
+            return u <= newest ? u : -1;
+        };
+        int my_t = slot_top(split);
+        bool my_old = my_t >= 0;
+        if (!my_old) my_t = split >= -1 ? slot_after(split) : slot_after(-1);
         const bool mine = !quiet && my_c >= 2;
         // pending work, earliest deadline first: the next tile of the lowest
-        // owned end-row block whose start block is final, or this warp's share
-        // of the chain data of block next_g (its ring slot is free once block
-        // next_g - ring is final)
+        // owned end-row block, once it is open (block my_c - 3 final) and its
+        // start block is final, or this warp's share of the chain data of
+        // block next_g (its ring slot is free once block next_g - ring is
+        // final)
         int next_g = 0;
         for (;;) {
             const int vf = __shfl_sync(kFull, lane == 0 ? *v_final : 0, 0);     // final blocks
             if (*v_abort) break;
-            const bool pending = mine && my_t <= my_c - 2;
-            const unsigned work = __ballot_sync(kFull, pending && my_t < vf);
+            const bool pending = mine && my_t >= 0;
+            const unsigned work = __ballot_sync(kFull, pending && vf >= my_c - 1 - window && vf > my_t);
             const bool all_done = __ballot_sync(kFull, pending) == 0;
             // owned blocks decrease with the lane: the lowest block is the highest lane
             const int wl = work ? 31 - __clz(work) : -1;
@@ -562,11 +629,20 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
             }
             if (jc_work >= 0) {
                 const int t = __shfl_sync(kFull, my_t, wl);
-                bulk_tile(t, jc_work);
+                const bool older = __shfl_sync(kFull, my_old ? 1 : 0, wl) != 0;
+                // the bound pays off only against minima already found: not
+                // for an item's first tile, nor for the newest ones, which
+                // the older ones' minima rarely beat
+                const bool check = older && t != __shfl_sync(kFull, slot_top(split), wl);
+                if (!(check && tile_bounded(t, jc_work))) bulk_tile(t, jc_work, older);
                 __threadfence_block();
                 __syncwarp();
                 if (lane == 0) atomicAdd(&sync->ready[jc_work], 1);
-                if (lane == wl) my_t = t + kSlots;
+                if (lane == wl) {
+                    if (my_old && t - slots >= 0) my_t = t - slots;
+                    else if (my_old) { my_old = false; my_t = slot_after(split); }
+                    else my_t = t + slots <= newest ? t + slots : -1;
+                }
                 continue;
             }
             if (all_done && next_g >= NB) break;
@@ -617,7 +693,7 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
             run = s_runv[k];
             runbf = s_runbf[k];
 #pragma unroll
-            for (int q = 1; q < kSlots; ++q) {
+            for (int q = 1; q < slots; ++q) {
                 const int32_t v = s_runv[q * HP + k], bf = s_runbf[q * HP + k];
                 if (v < run || (v == run && (bf >> 8) < (runbf >> 8))) { run = v; runbf = bf; }
             }
@@ -740,10 +816,10 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
 // MINB: CTAs per SM the register allocation is sized for (8 warps x 2 CTAs
 // and 16 warps x 1 CTA both leave 128 registers per thread, 8 x 3 leaves 85).
 template <int NW, bool kStd, int MINB>
-__global__ void __launch_bounds__(NW * 32, MINB) stixel_dp_kernel(DpArgs a, int ring)
+__global__ void __launch_bounds__(NW * 32, MINB) stixel_dp_kernel(DpArgs a, int ring, int slots, int window)
 {
     extern __shared__ __align__(16) int32_t sm[];
-    dp_column<NW, kStd, false>(a, blockIdx.x, ring, sm, 0);
+    dp_column<NW, kStd, false>(a, blockIdx.x, ring, slots, window, sm, 0);
 }
 
 // Persistent form: each CTA takes columns from a work list (one shared atomic
@@ -752,7 +828,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) stixel_dp_kernel(DpArgs a, int 
 template <int NW, bool kStd, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB)
     stixel_dp_batch_kernel(const DpArgs* __restrict__ frames, const int2* __restrict__ items, int nitems,
-                           int* counter, int ring)
+                           int* counter, int ring, int slots, int window)
 {
     extern __shared__ __align__(16) int32_t sm[];
     __shared__ DpArgs s_args;
@@ -771,7 +847,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
         // start 0 peeled out of the step loop: measured faster in this
         // kernel's shapes (32 1024x440 frames 12.86 -> 13.07 K frames/s),
         // slower in the per-frame kernel
-        dp_column<NW, kStd, true>(s_args, w.y, ring, sm, w.y & 3);
+        dp_column<NW, kStd, true>(s_args, w.y, ring, slots, window, sm, w.y & 3);
         __syncthreads();
     }
 }
@@ -838,22 +914,49 @@ bool* frame_flags() { static bool f[64] = {false}; return f; }
 template <int NW, bool kStd, int MINB>
 bool* batch_flags() { static bool f[64] = {false}; return f; }
 
+// Partial minima per end row for columns of height H with `ring` chain
+// buffers, `ctas` CTAs per SM: three (more warps share each end block's
+// tiles, which the bound prunes newest first inside a window of two of the
+// chain's blocks) where the shared memory has room, else two.
+int pick_slots(int H, int ring, int ctas)
+{
+    const size_t per_cta = std::min<size_t>(227 * 1024, 228 * 1024 / ctas) - 2048;   // room for static + reserve
+    return dp_smem_bytes(H, ring, 3) <= per_cta ? 3 : 2;
+}
+
+// The window of an end block's tiles (see dp_column), in chain blocks, by
+// launch shape.  Pruning needs the newest tiles first, which packs a block's
+// tile work into the window; measured (1024x440 / 2048x880 frames, 32 and 64
+// frame batches):
+//   - per frame, two columns per SM: window 2 with three partial minima
+//     96.3 / 521 us against 100-102 / 658 us with no pruning;
+//   - per frame, one column per SM (1024x440 at s = 7): 77.3 us against 73.7;
+//   - batched: 13.1 K / 9.5 K frames/s against 13.3 K / 10.2 K with none.
+// kNoPruning keeps every tile in start order, as the tiles become ready.
+constexpr int kNoPruning = kMaxBlocks;
+constexpr int kFrameWindow = 2;
+
 template <int NW, bool kStd, int MINB>
-cudaError_t launch_frame(const DpArgs& a, int ncols, size_t smem, cudaStream_t st)
+cudaError_t launch_frame(const DpArgs& a, int ncols, cudaStream_t st)
 {
     cudaError_t e = allow_smem(stixel_dp_kernel<NW, kStd, MINB>, frame_flags<NW, kStd, MINB>());
     if (e != cudaSuccess) return e;
-    stixel_dp_kernel<NW, kStd, MINB><<<ncols, NW * 32, smem, st>>>(a, kRingMax);
+    const bool prune = MINB >= 2;
+    const int slots = prune ? pick_slots(a.H, kRingMax, MINB) : 2;
+    stixel_dp_kernel<NW, kStd, MINB><<<ncols, NW * 32, dp_smem_bytes(a.H, kRingMax, slots), st>>>(
+        a, kRingMax, slots, prune ? kFrameWindow : kNoPruning);
     return cudaGetLastError();
 }
 
 template <int NW, bool kStd, int MINB>
-cudaError_t launch_batch(const DpArgs* frames, const int2* items, int nitems, int* counter, int grid, size_t smem,
-                         int ring, cudaStream_t st)
+cudaError_t launch_batch(const DpArgs* frames, const int2* items, int nitems, int* counter, int grid, int maxH,
+                         int ring, int ctas, cudaStream_t st)
 {
     cudaError_t e = allow_smem(stixel_dp_batch_kernel<NW, kStd, MINB>, batch_flags<NW, kStd, MINB>());
     if (e != cudaSuccess) return e;
-    stixel_dp_batch_kernel<NW, kStd, MINB><<<grid, NW * 32, smem, st>>>(frames, items, nitems, counter, ring);
+    (void)ctas;
+    stixel_dp_batch_kernel<NW, kStd, MINB><<<grid, NW * 32, dp_smem_bytes(maxH, ring, 2), st>>>(
+        frames, items, nitems, counter, ring, 2, kNoPruning);
     return cudaGetLastError();
 }
 
@@ -863,12 +966,12 @@ bool standard_transitions(const ModelDev& m)
 }
 
 template <bool kStd>
-cudaError_t launch_frame_shape(const DpArgs& a, int ncols, size_t smem, cudaStream_t st)
+cudaError_t launch_frame_shape(const DpArgs& a, int ncols, cudaStream_t st)
 {
     // with no more columns than SMs, each column gets a whole SM: 16 warps
     // (15 bulk); otherwise two 8-warp CTAs share an SM
-    if (ncols <= sm_count()) return launch_frame<16, kStd, 1>(a, ncols, smem, st);
-    return launch_frame<8, kStd, 2>(a, ncols, smem, st);
+    if (ncols <= sm_count()) return launch_frame<16, kStd, 1>(a, ncols, st);
+    return launch_frame<8, kStd, 2>(a, ncols, st);
 }
 
 template <bool kStd>
@@ -884,22 +987,22 @@ cudaError_t prepare_std()
 
 template <bool kStd>
 cudaError_t launch_batch_shape(const DpArgs* f, const int2* it, int n, int* ctr, int warps, int grid, int ctas_per_sm,
-                               size_t smem, cudaStream_t st)
+                               int maxH, cudaStream_t st)
 {
     // three 8-warp CTAs per SM fit the registers; a ring of two chain buffers
     // lets them fit the shared memory too (for heights up to about 450)
-    if (warps == 16) return launch_batch<16, kStd, 1>(f, it, n, ctr, grid, smem, kRingMax, st);
-    if (ctas_per_sm >= 3) return launch_batch<8, kStd, 3>(f, it, n, ctr, grid, smem, 2, st);
-    return launch_batch<8, kStd, 2>(f, it, n, ctr, grid, smem, kRingMax, st);
+    if (warps == 16) return launch_batch<16, kStd, 1>(f, it, n, ctr, grid, maxH, kRingMax, 1, st);
+    if (ctas_per_sm >= 3) return launch_batch<8, kStd, 3>(f, it, n, ctr, grid, maxH, 2, 3, st);
+    return launch_batch<8, kStd, 2>(f, it, n, ctr, grid, maxH, kRingMax, 2, st);
 }
 
 }  // namespace
 
-size_t dp_shared_bytes(int H) { return dp_smem_bytes(H, kRingMax); }
+size_t dp_shared_bytes(int H) { return dp_smem_bytes(H, kRingMax, pick_slots(H, kRingMax, 2)); }
 
 void dp_frame_args(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po, const FrameGeom& g,
-                   const ModelDev& m, const RowsDev& r, const RealParams& rp, const stixels_output_t& out,
-                   uint32_t* err, DpArgs* a)
+                   const ModelDev& m, const RowsDev& r, const RealParams& rp, int32_t pixel_floor,
+                   const stixels_output_t& out, uint32_t* err, DpArgs* a)
 {
     a->pd = pd; a->pg = pg; a->ps = ps; a->po = po;
     a->H = g.H; a->P = g.P; a->F = m.dmax + 1;
@@ -908,19 +1011,19 @@ void dp_frame_args(const int32_t* pd, const int32_t* pg, const int32_t* ps, cons
     a->cap = out.capacity;
     a->err = err;
     a->rp = rp;
+    a->pixel_floor = pixel_floor;
 }
 
 cudaError_t launch_dp(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po,
                       const FrameGeom& g, const ModelDev& m, const RowsDev& r, const RealParams& rp,
-                      const stixels_output_t& out, uint32_t* err, cudaStream_t st)
+                      int32_t pixel_floor, const stixels_output_t& out, uint32_t* err, cudaStream_t st)
 {
     if (g.H <= 0 || g.ncols <= 0) return cudaSuccess;
     if (g.H > STIXELS_MAX_HEIGHT) return cudaErrorInvalidValue;
     DpArgs a;
-    dp_frame_args(pd, pg, ps, po, g, m, r, rp, out, err, &a);
-    const size_t smem = dp_smem_bytes(g.H, kRingMax);
-    return standard_transitions(m) ? launch_frame_shape<true>(a, g.ncols, smem, st)
-                                   : launch_frame_shape<false>(a, g.ncols, smem, st);
+    dp_frame_args(pd, pg, ps, po, g, m, r, rp, pixel_floor, out, err, &a);
+    return standard_transitions(m) ? launch_frame_shape<true>(a, g.ncols, st)
+                                   : launch_frame_shape<false>(a, g.ncols, st);
 }
 
 cudaError_t prepare_dp_kernels()
@@ -937,9 +1040,9 @@ cudaError_t launch_dp_batch(const DpArgs* d_frames, const int2* d_items, int nit
 {
     if (nitems <= 0) return cudaSuccess;
     if (maxH <= 0 || maxH > STIXELS_MAX_HEIGHT || grid <= 0) return cudaErrorInvalidValue;
-    const size_t smem = dp_smem_bytes(maxH, warps == 8 && ctas_per_sm >= 3 ? 2 : kRingMax);
-    return std_trans ? launch_batch_shape<true>(d_frames, d_items, nitems, d_counter, warps, grid, ctas_per_sm, smem, st)
-                     : launch_batch_shape<false>(d_frames, d_items, nitems, d_counter, warps, grid, ctas_per_sm, smem, st);
+    return std_trans ? launch_batch_shape<true>(d_frames, d_items, nitems, d_counter, warps, grid, ctas_per_sm, maxH, st)
+                     : launch_batch_shape<false>(d_frames, d_items, nitems, d_counter, warps, grid, ctas_per_sm, maxH,
+                                                 st);
 }
 
 }  // namespace stx

@@ -416,12 +416,13 @@ bool map_fits(int H, int F) { return map_smem_bytes(H, F) <= kMapSmemMax; }
 
 cudaError_t launch_dp_map(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po,
                           const FrameGeom& g, const ModelDev& m, const RowsDev& r, const RealParams& rp,
-                          const stixels_output_t& out, uint32_t* err, void* scratch, cudaStream_t st)
+                          int32_t pixel_floor, const stixels_output_t& out, uint32_t* err, void* scratch,
+                          cudaStream_t st)
 {
     if (g.H <= 0 || g.ncols <= 0) return cudaSuccess;
     if (g.H > STIXELS_MAX_HEIGHT || m.dmax + 1 > 256 || !map_fits(g.H, m.dmax + 1)) return cudaErrorInvalidValue;
     DpArgs a;
-    dp_frame_args(pd, pg, ps, po, g, m, r, rp, out, err, &a);
+    dp_frame_args(pd, pg, ps, po, g, m, r, rp, pixel_floor, out, err, &a);
     const size_t smem = map_smem_bytes(g.H, m.dmax + 1);
     static bool attr_set[64] = {false};
     int dev = 0;

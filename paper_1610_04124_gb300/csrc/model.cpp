@@ -244,6 +244,14 @@ int build_model(const stixels_params_t* p, HostModel* m)
     m->pen_div = fixed_prior((double)p->cost_diving);
     m->pen_ord = fixed_prior((double)p->cost_order);
     m->max_finite_prior = maxp + m->pen_grav + m->pen_div + m->pen_ord;
+    // an object pixel costs min(C_out, K(f) + G) >= min(C_out, K(f)) (and the
+    // whole-pixel grid's LUT_cost entries are those same values): the floor
+    // the DP's tile bound uses is the least of C_out and every object K
+    {
+        int32_t fl = m->c_out;
+        for (int32_t k : m->k_obj) fl = std::min(fl, k);
+        m->pixel_floor = fl;
+    }
     // 16 f > 16 f' + 16 eps  <=>  f - f' > floor(eps) for integer f, f'
     m->ord_off = (int32_t)floor((double)p->eps_order);
     // the same constants without the grid (the cost report of a solved column)

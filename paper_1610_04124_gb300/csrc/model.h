@@ -37,6 +37,7 @@ struct HostModel {
     int32_t pen_grav = 0, pen_div = 0, pen_ord = 0;
     int32_t ord_off = 0;                // floor(eps_order)
     int32_t max_finite_prior = 0;       // largest finite prior + penalty sum for one stixel
+    int32_t pixel_floor = 0;            // no object pixel costs less: min(C_out, every object K)
     int32_t esat[3] = {0, 0, 0};        // saturation residual (Q4) per class: object, ground, sky
     // whole-pixel grid only: object pixel cost of pixel disparity d under model
     // disparity f, cost[f * (dmax + 1) + d] (the paper's LUT_cost); empty otherwise

@@ -111,6 +111,12 @@ struct ChainBuf {
 __device__ __forceinline__ int tri_slot(int i) { return (i * (65 - i)) >> 1; }
 
 struct SyncState {
+    // bar_final[j] completes (phase 0) when the chain warp has finalised block
+    // j; bar_rep when the cost report's stixels are staged (or there is no
+    // report).  A warp waiting on one is suspended in the hardware instead of
+    // polling, so idle warps take no issue slots from the working ones.
+    unsigned long long bar_final[kMaxBlocks];
+    unsigned long long bar_rep;
     int final_blocks;            // blocks the chain warp has finalised
     int abort;                   // set when a wait gave up
     int32_t fin[3];              // V of the top row per class (object, ground, sky), once every block is final
@@ -181,12 +187,73 @@ __device__ __forceinline__ bool wait_geq(volatile int* p, int target, volatile i
     return ok != 0;
 }
 
-size_t dp_smem_bytes(int H, int ring, int slots)
+// Shared-memory barriers (PTX mbarrier), each used for one phase per column.
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void bar_init(unsigned long long* b, int count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void bar_inval(unsigned long long* b)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+// arrive (release: this thread's earlier writes are visible to the waiters)
+__device__ __forceinline__ void bar_arrive(unsigned long long* b)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(b)) : "memory");
+}
+
+// Whether phase 0 of the barrier has completed (acquire); the thread may be
+// suspended for up to the hint (ns) while it has not.
+__device__ __forceinline__ bool bar_try_wait(unsigned long long* b, uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0, %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(b)), "r"(hint_ns)
+                 : "memory");
+    return ok != 0;
+}
+
+// Warp-wide bounded wait for phase 0 of a barrier (lane 0 waits, suspended
+// between tries, at most `limit` tries).  Returns false if the wait gave up
+// or another warp did; the caller then stops.
+__device__ __forceinline__ bool wait_bar(unsigned long long* b, volatile int* abort_flag, int limit = kSpinLimit)
+{
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) {
+        int it = 0;
+        while (!bar_try_wait(b, 1000)) {
+            if (*abort_flag) { ok = 0; break; }
+            if (++it > limit) { *abort_flag = 1; ok = 0; break; }
+        }
+    }
+    ok = __shfl_sync(kFull, ok, 0);
+    __syncwarp();
+    __threadfence_block();
+    return ok != 0;
+}
+
+__host__ __device__ size_t dp_smem_bytes(int H, int ring, int slots)
 {
     const size_t HP = (size_t)((H + 3) & ~3);
     return sizeof(BulkCtx) * HP + sizeof(int4) * HP + sizeof(int32_t) * 2 * (HP + 4) + sizeof(int2) * (HP + 4) +
            sizeof(uint2) * (HP + 4) + sizeof(int32_t) * 2 * slots * HP + sizeof(ChainBuf) * ring +
            sizeof(SyncState);
+}
+
+// The SyncState of a CTA's shared memory laid out as dp_column lays it out
+// (it is the last member)
+__device__ __forceinline__ SyncState* dp_sync_state(int32_t* sm, int H, int ring, int slots)
+{
+    return reinterpret_cast<SyncState*>(reinterpret_cast<char*>(sm) + dp_smem_bytes(H, ring, slots) - sizeof(SyncState));
 }
 
 // Gathers the chain data of the block starting at row B into cb.  Warp w of
@@ -275,7 +342,7 @@ __device__ __noinline__ void finish_column(const DpArgs& a, int col, int H, Sync
     if (role > 0) {
         // a helper: its rows once the leader has staged the stixels
         if (!a.cost) return;
-        if (!wait_geq(&sync->rep_state, 1, &sync->abort, 32)) {
+        if (!wait_bar(&sync->bar_rep, &sync->abort)) {
             if (lane == 0) {
                 a.cost[col] = __int_as_float(0x7f800000);
                 atomicOr(a.err, STIXELS_ERR_TIMEOUT);
@@ -286,13 +353,14 @@ __device__ __noinline__ void finish_column(const DpArgs& a, int col, int H, Sync
     } else {
         FTables ft;
         if (a.cost) load_ftables(ft, a, lane);
-        if (!wait_geq(&sync->final_blocks, NB, &sync->abort, 32)) {
+        if (!wait_bar(&sync->bar_final[NB - 1], &sync->abort)) {
             if (lane == 0) {
                 a.counts[col] = 0;
                 if (a.cost) a.cost[col] = __int_as_float(0x7f800000);
                 if (a.cost_fixed) a.cost_fixed[col] = kBig;
                 atomicOr(a.err, STIXELS_ERR_TIMEOUT);
                 *(volatile int*)&sync->rep_state = 2;
+                bar_arrive(&sync->bar_rep);
             }
             return;
         }
@@ -308,6 +376,7 @@ __device__ __noinline__ void finish_column(const DpArgs& a, int col, int H, Sync
                 if (a.cost_fixed) a.cost_fixed[col] = kBig;
                 atomicOr(a.err, STIXELS_ERR_INFEASIBLE);
                 *(volatile int*)&sync->rep_state = 2;
+                bar_arrive(&sync->bar_rep);
             }
             return;
         }
@@ -362,6 +431,7 @@ __device__ __noinline__ void finish_column(const DpArgs& a, int col, int H, Sync
             sync->rep_n = n;
             __threadfence_block();
             *(volatile int*)&sync->rep_state = 1;
+            bar_arrive(&sync->bar_rep);
         }
         __syncwarp();
     }
@@ -458,6 +528,7 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
     if (threadIdx.x < kMaxBlocks) {
         sync->ready[threadIdx.x] = 0;
         sync->gathered[threadIdx.x] = 0;
+        bar_init(&sync->bar_final[threadIdx.x], 1);
     }
     if (threadIdx.x == 0) {
         sync->final_blocks = 0;
@@ -465,6 +536,7 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
         sync->rep_state = 0;
         sync->rep_done = 0;
         sync->rep_acc = 0;
+        bar_init(&sync->bar_rep, 1);
         // start 0 carries the first-stixel prior (code 3 = no previous stixel)
         s_ctx[0] = make_bulk_ctx(m.first[0] + kNoneCode, kBig, kBig, INT_MAX, s_thr[0], m);
     }
@@ -646,7 +718,7 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
                 continue;
             }
             if (all_done && next_g >= NB) break;
-            if (!wait_geq(v_final, vf + 1, v_abort, 32)) break;
+            if (vf >= NB || !wait_bar(&sync->bar_final[vf], v_abort)) break;
         }
         // backtracking and the cost report stay off the chain's scheduler,
         // where the other column of the SM may still be running its chain
@@ -802,7 +874,10 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
         }
         __threadfence_block();
         __syncwarp();
-        if (lane == 0) *v_final = j + 1;
+        if (lane == 0) {
+            *v_final = j + 1;
+            bar_arrive(&sync->bar_final[j]);
+        }
     }
 
     if (aborted && lane == 0) {
@@ -849,6 +924,10 @@ __global__ void __launch_bounds__(NW * 32, MINB)
         // slower in the per-frame kernel
         dp_column<NW, kStd, true>(s_args, w.y, ring, slots, window, sm, w.y & 3);
         __syncthreads();
+        // the next column initialises its barriers afresh
+        SyncState* sync = dp_sync_state(sm, s_args.H, ring, slots);
+        if (threadIdx.x < kMaxBlocks) bar_inval(&sync->bar_final[threadIdx.x]);
+        if (threadIdx.x == 0) bar_inval(&sync->bar_rep);
     }
 }
 

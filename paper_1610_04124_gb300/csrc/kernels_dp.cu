@@ -112,14 +112,12 @@ __device__ __forceinline__ int tri_slot(int i) { return (i * (65 - i)) >> 1; }
 
 struct SyncState {
     // bar_final[j] completes (phase 0) when the chain warp has finalised block
-    // j; bar_rep when the cost report's stixels are staged (or there is no
-    // report).  A warp waiting on one is suspended in the hardware instead of
+    // j.  A warp waiting on it is suspended in the hardware instead of
     // polling, so idle warps take no issue slots from the working ones.
     unsigned long long bar_final[kMaxBlocks];
-    unsigned long long bar_rep;
+    int32_t fin[3];              // V of the top row per class, for a bulk warp leading the tail
     int final_blocks;            // blocks the chain warp has finalised
     int abort;                   // set when a wait gave up
-    int32_t fin[3];              // V of the top row per class (object, ground, sky), once every block is final
     int rep_state;               // cost report: 0 stixels not staged yet, 1 staged (rows may start), 2 no report
     int rep_n;                   // stixels on the path
     int rep_done;                // warps done with their rows
@@ -317,125 +315,116 @@ __device__ __forceinline__ void gather_chain(ChainBuf* cb, int B, int H, int P, 
     }
 }
 
-constexpr int kReportWarps = 4;       // warps that share the cost report's rows
+constexpr int kReportWarps = 4;       // bulk warps that share the cost report's rows
 
-// The end of a column, once the chain has finalised every block, by
-// kReportWarps bulk warps (role 0 leads).  The leader takes the top row's
-// best class (ties object < ground < sky), backtracks from it through the
-// back-pointers (Sec. 3.3, Sec. 5.4) and writes the stixel list bottom -> top;
-// then the cost report (the segmentation's cost in real arithmetic): the
-// leader stages the stixels' constants and priors, and all kReportWarps
-// warps take every kReportWarps-th block of 32 rows, adding their sums into
-// one exact integer; the last warp to finish writes the column's cost.  A
-// wait that gives up, or a column with no feasible segmentation, is recorded
-// in the error word with an empty column.
-__device__ __noinline__ void finish_column(const DpArgs& a, int col, int H, SyncState* sync, const int4* s_bp,
-                                           const int32_t* s_pd8, const int32_t* s_thr, const uint2* s_div,
-                                           int32_t* s_seg, int lane, int role)
+// The end of a column, by one warp once the chain has finalised the last
+// block (the chain warp itself, or bulk warp 0): it takes the top row's best
+// class (ties object < ground < sky), backtracks from it through the
+// back-pointers (Sec. 3.3, Sec. 5.4), writes the stixel list bottom -> top
+// and the output records, then the stixel part of the cost report (priors
+// and each stixel's pixel-cost constants, staged for the rows).  vo, vg, vs:
+// V of the top row per class.  `a` is the CTA's shared-memory copy of the
+// arguments (the tail reads many of them, once each).  A column with no
+// feasible segmentation is recorded in the error word with an empty column.
+__device__ __forceinline__ void lead_column_end(const DpArgs& a, int col, int H, SyncState* sync, const int4* s_bp,
+                                                const int32_t* s_pd8, const int32_t* s_thr, const uint2* s_div,
+                                                int32_t* s_seg, int lane, int32_t vo, int32_t vg, int32_t vs)
 {
-    const int NB = (H + 31) >> 5;
-    // what the cost report reads but the path does not decide (the object
-    // K and sigma of every f, this warp's first rows' tables) is loaded
-    // before the waits, so that none of it is on the path's critical time
-    RowTables pre;
-    if (a.cost) load_rows(pre, a.rows.fg, H, lane, role, kReportWarps);
-    if (role > 0) {
-        // a helper: its rows once the leader has staged the stixels
-        if (!a.cost) return;
-        if (!wait_bar(&sync->bar_rep, &sync->abort)) {
-            if (lane == 0) {
-                a.cost[col] = __int_as_float(0x7f800000);
-                atomicOr(a.err, STIXELS_ERR_TIMEOUT);
-            }
-            return;
-        }
-        if (*(volatile int*)&sync->rep_state != 1) return;
-    } else {
-        FTables ft;
-        if (a.cost) load_ftables(ft, a, lane);
-        if (!wait_bar(&sync->bar_final[NB - 1], &sync->abort)) {
-            if (lane == 0) {
-                a.counts[col] = 0;
-                if (a.cost) a.cost[col] = __int_as_float(0x7f800000);
-                if (a.cost_fixed) a.cost_fixed[col] = kBig;
-                atomicOr(a.err, STIXELS_ERR_TIMEOUT);
-                *(volatile int*)&sync->rep_state = 2;
-                bar_arrive(&sync->bar_rep);
-            }
-            return;
-        }
-        const volatile int32_t* fin = sync->fin;
-        int c = 0;
-        int32_t best = fin[0];
-        if (fin[1] < best) { best = fin[1]; c = 1; }
-        if (fin[2] < best) { best = fin[2]; c = 2; }
-        if (best >= kBig) {
-            if (lane == 0) {
-                a.counts[col] = 0;
-                if (a.cost) a.cost[col] = __int_as_float(0x7f800000);
-                if (a.cost_fixed) a.cost_fixed[col] = kBig;
-                atomicOr(a.err, STIXELS_ERR_INFEASIBLE);
-                *(volatile int*)&sync->rep_state = 2;
-                bar_arrive(&sync->bar_rep);
-            }
-            return;
-        }
-        // one walk from the top row (lane 0), the stixels top -> bottom into
-        // s_seg[H..2H); the lanes then put them bottom -> top into s_seg[0..n)
-        // and write the output records
-        int32_t* top_down = s_seg + H;
-        int n = 0;
+    int c = 0;
+    int32_t best = vo;
+    if (vg < best) { best = vg; c = 1; }
+    if (vs < best) { best = vs; c = 2; }
+    if (best >= kBig) {
         if (lane == 0) {
-            const int32_t* bp_all = reinterpret_cast<const int32_t*>(s_bp);
-            for (int k = H - 1, cc = c; k >= 0 && cc < 3 && n < H;) {
-                const int32_t bp = bp_all[4 * k + cc];
-                const int b = min(bp >> 2, k);               // b <= k for a solved column; keeps the walk finite
-                top_down[n++] = (b << 13) | (k << 2) | cc;
-                k = b - 1;
-                cc = bp & 3;
-            }
-            a.counts[col] = n;
-            if (n > a.cap) atomicOr(a.err, STIXELS_ERR_CAPACITY);
-            if (a.cost_fixed) a.cost_fixed[col] = best;
-        }
-        n = __shfl_sync(kFull, n, 0);
-        __syncwarp();
-        stixel_t* out = a.stixels + (size_t)col * a.cap;
-        for (int i = lane; i < n; i += 32) {
-            const int w = top_down[n - 1 - i];
-            s_seg[i] = w;
-            if (i < a.cap) {
-                const int b = w >> 13, k = (w >> 2) & 2047;
-                const int nrows = k - b + 1;
-                const int32_t S = s_pd8[k + 1] - s_pd8[b] - 8 * nrows;
-                stixel_t st;
-                st.row_top = (int16_t)(H - 1 - k);
-                st.row_bottom = (int16_t)(H - 1 - b);
-                st.cls = (uint8_t)(w & 3);
-                st.flags = 0;
-                st.reserved = 0;
-                st.disparity = __fdiv_rn(__int2float_rn(S), __int2float_rn(16 * nrows));
-                out[i] = st;
-            }
-        }
-        __syncwarp();
-        if (!a.cost) return;
-        auto kinv = [&](int f, bool) { return ftables_at(ft, f); };
-        auto thr = [&](int b) {
-            const int32_t t = s_thr[b];
-            return make_int2((int32_t)(int16_t)(t & 0xffff), t >> 16);
-        };
-        const long long pri = warp_sum64(report_stixels(s_seg, n, s_pd8, s_div, a, H, lane, kinv, thr));
-        if (lane == 0) {
-            atomicAdd(reinterpret_cast<unsigned long long*>(&sync->rep_acc), (unsigned long long)pri);
-            sync->rep_n = n;
+            a.counts[col] = 0;
+            if (a.cost) a.cost[col] = __int_as_float(0x7f800000);
+            if (a.cost_fixed) a.cost_fixed[col] = kBig;
+            atomicOr(a.err, STIXELS_ERR_INFEASIBLE);
             __threadfence_block();
-            *(volatile int*)&sync->rep_state = 1;
-            bar_arrive(&sync->bar_rep);
+            *(volatile int*)&sync->rep_state = 2;
         }
-        __syncwarp();
+        return;
     }
-    // every report warp: its blocks of rows, then the last one writes the cost
+    // one walk from the top row (lane 0), the stixels top -> bottom into
+    // s_seg[H..2H); the lanes then put them bottom -> top into s_seg[0..n)
+    // and write the output records
+    int32_t* top_down = s_seg + H;
+    int n = 0;
+    if (lane == 0) {
+        const int32_t* bp_all = reinterpret_cast<const int32_t*>(s_bp);
+        for (int k = H - 1, cc = c; k >= 0 && cc < 3 && n < H;) {
+            const int32_t bp = bp_all[4 * k + cc];
+            const int b = min(bp >> 2, k);               // b <= k for a solved column; keeps the walk finite
+            top_down[n++] = (b << 13) | (k << 2) | cc;
+            k = b - 1;
+            cc = bp & 3;
+        }
+        a.counts[col] = n;
+        if (n > a.cap) atomicOr(a.err, STIXELS_ERR_CAPACITY);
+        if (a.cost_fixed) a.cost_fixed[col] = best;
+    }
+    n = __shfl_sync(kFull, n, 0);
+    __syncwarp();
+    stixel_t* out = a.stixels + (size_t)col * a.cap;
+    for (int i = lane; i < n; i += 32) {
+        const int w = top_down[n - 1 - i];
+        s_seg[i] = w;
+        if (i < a.cap) {
+            const int b = w >> 13, k = (w >> 2) & 2047;
+            const int nrows = k - b + 1;
+            const int32_t S = s_pd8[k + 1] - s_pd8[b] - 8 * nrows;
+            stixel_t st;
+            st.row_top = (int16_t)(H - 1 - k);
+            st.row_bottom = (int16_t)(H - 1 - b);
+            st.cls = (uint8_t)(w & 3);
+            st.flags = 0;
+            st.reserved = 0;
+            st.disparity = __fdiv_rn(__int2float_rn(S), __int2float_rn(16 * nrows));
+            out[i] = st;
+        }
+    }
+    __syncwarp();
+    if (!a.cost) return;
+    const float* __restrict__ k_obj = real_k_obj(a.rows.real_model);
+    const float* __restrict__ inv_obj = k_obj + a.F;
+    auto kinv = [&](int f, bool valid) {
+        return valid ? make_float2(__ldg(k_obj + f), __ldg(inv_obj + f)) : make_float2(0.f, 0.f);
+    };
+    auto thr = [&](int b) {
+        const int32_t t = s_thr[b];
+        return make_int2((int32_t)(int16_t)(t & 0xffff), t >> 16);
+    };
+    const long long pri = warp_sum64(report_stixels(s_seg, n, s_pd8, s_div, a, H, lane, kinv, thr));
+    if (lane == 0) {
+        sync->rep_acc = pri;
+        sync->rep_n = n;
+        __threadfence_block();
+        *(volatile int*)&sync->rep_state = 1;
+    }
+}
+
+// The rows of the cost report (Eq. 4 per pixel under the staged stixels), by
+// kReportWarps bulk warps: role r takes the blocks of 32 rows r, r +
+// kReportWarps, ...; the sums go into one exact integer and the last warp to
+// finish writes the column's cost.  The warps first wait (suspended) for the
+// chain's last block, then briefly poll for the staged stixels.
+__device__ __forceinline__ void report_column_rows(const DpArgs& a, int col, int H, SyncState* sync,
+                                                   const int32_t* s_pd8, const int32_t* s_seg, int lane, int role)
+{
+    if (!a.cost) return;
+    const int NB = (H + 31) >> 5;
+    // this warp's first rows' tables are loaded before the waits
+    RowTables pre;
+    load_rows(pre, a.rows.fg, H, lane, role, kReportWarps);
+    if (!wait_bar(&sync->bar_final[NB - 1], &sync->abort)) return;     // the chain reports the failure
+    if (!wait_geq(&sync->rep_state, 1, &sync->abort, 16)) {
+        if (lane == 0) {
+            a.cost[col] = __int_as_float(0x7f800000);
+            atomicOr(a.err, STIXELS_ERR_TIMEOUT);
+        }
+        return;
+    }
+    if (*(volatile int*)&sync->rep_state != 1) return;
     const int n = *(volatile int*)&sync->rep_n;
     const long long sum = warp_sum64(report_rows(s_seg, n, s_pd8, a, H, lane, role, kReportWarps, &pre));
     if (lane == 0) {
@@ -448,14 +437,34 @@ __device__ __noinline__ void finish_column(const DpArgs& a, int col, int H, Sync
     }
 }
 
+// The same as calls (the persistent kernel's shape: measured faster there
+// than inlined, and with a bulk warp leading the tail)
+__device__ __noinline__ void lead_column_end_call(const DpArgs& a, int col, int H, SyncState* sync, const int4* s_bp,
+                                                  const int32_t* s_pd8, const int32_t* s_thr, const uint2* s_div,
+                                                  int32_t* s_seg, int lane, int32_t vo, int32_t vg, int32_t vs)
+{
+    lead_column_end(a, col, H, sync, s_bp, s_pd8, s_thr, s_div, s_seg, lane, vo, vg, vs);
+}
+
+__device__ __noinline__ void report_column_rows_call(const DpArgs& a, int col, int H, SyncState* sync,
+                                                     const int32_t* s_pd8, const int32_t* s_seg, int lane, int role)
+{
+    report_column_rows(a, col, H, sync, s_pd8, s_seg, lane, role);
+}
+
 // Solves column `col` of frame `a` with all NW warps of the CTA (one chain
 // warp, NW - 1 bulk warps); `sm` is the CTA's dynamic shared memory
 // (dp_smem_bytes with the same ring, 2 or 3 chain buffers, and slots, 2 or 3
 // partial minima per end row).  Every warp
 // returns from here; the caller synchronises before reusing `sm`.
-template <int NW, bool kStdTrans, bool kPeelFirst>
-__device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const int ring, const int slots,
-                                          const int window, int32_t* sm, const int chain)
+// kChainTail: the chain warp leads the column's tail as soon as it has
+// finalised the last block (the per-frame kernel; measured 94.2 -> 90.1 us at
+// 1024x440), else bulk warp 0 does, through calls (the persistent kernel,
+// where the chain-led tail measured 10 % slower: 13.2 K against 11.9 K frames/s
+// for 32 1024x440 frames, and the bulk-led one 13.9 K).
+template <int NW, bool kStdTrans, bool kPeelFirst, bool kChainTail>
+__device__ __forceinline__ void dp_column(const DpArgs& a, const DpArgs& ta, const int col, const int ring,
+                                          const int slots, const int window, int32_t* sm, const int chain)
 {
     constexpr int kWarps = NW;
     constexpr int kThreads = NW * 32;
@@ -536,7 +545,6 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
         sync->rep_state = 0;
         sync->rep_done = 0;
         sync->rep_acc = 0;
-        bar_init(&sync->bar_rep, 1);
         // start 0 carries the first-stixel prior (code 3 = no previous stixel)
         s_ctx[0] = make_bulk_ctx(m.first[0] + kNoneCode, kBig, kBig, INT_MAX, s_thr[0], m);
     }
@@ -670,9 +678,11 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
             const int u = slot + ((t + 1 - slot + slots - 1) / slots) * slots;
             return u <= newest ? u : -1;
         };
-        int my_t = slot_top(split);
+        const int my_first = slot_top(split);                // the item's first tile (newest of the first part)
+        const int my_after = slot_after(max(split, -1));     // the first tile of the second part
+        int my_t = my_first;
         bool my_old = my_t >= 0;
-        if (!my_old) my_t = split >= -1 ? slot_after(split) : slot_after(-1);
+        if (!my_old) my_t = my_after;
         const bool mine = !quiet && my_c >= 2;
         // pending work, earliest deadline first: the next tile of the lowest
         // owned end-row block, once it is open (block my_c - 3 final) and its
@@ -705,14 +715,14 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
                 // the bound pays off only against minima already found: not
                 // for an item's first tile, nor for the newest ones, which
                 // the older ones' minima rarely beat
-                const bool check = older && t != __shfl_sync(kFull, slot_top(split), wl);
+                const bool check = older && t != __shfl_sync(kFull, my_first, wl);
                 if (!(check && tile_bounded(t, jc_work))) bulk_tile(t, jc_work, older);
                 __threadfence_block();
                 __syncwarp();
                 if (lane == 0) atomicAdd(&sync->ready[jc_work], 1);
                 if (lane == wl) {
                     if (my_old && t - slots >= 0) my_t = t - slots;
-                    else if (my_old) { my_old = false; my_t = slot_after(split); }
+                    else if (my_old) { my_old = false; my_t = my_after; }
                     else my_t = t + slots <= newest ? t + slots : -1;
                 }
                 continue;
@@ -720,12 +730,18 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
             if (all_done && next_g >= NB) break;
             if (vf >= NB || !wait_bar(&sync->bar_final[vf], v_abort)) break;
         }
-        // backtracking and the cost report stay off the chain's scheduler,
-        // where the other column of the SM may still be running its chain
-        // bulk warps 0, 1, 2 and 4 (none shares the chain's scheduler, and
-        // none leaves early) finish the column; the first of them leads
+        // the rows of the cost report go to bulk warps 0, 1, 2 and 4 (none
+        // shares the chain's scheduler, where the other column of the SM may
+        // still be running its chain, and none leaves early)
         const int role = bulk_id < 3 ? bulk_id : (bulk_id == 4 ? 3 : -1);
-        if (role >= 0) finish_column(a, col, H, sync, s_bp, s_pd8, s_thr, s_div, s_runv, lane, role);
+        if constexpr (kChainTail) {
+            if (role >= 0) report_column_rows(ta, col, H, sync, s_pd8, s_runv, lane, role);
+        } else {
+            if (role == 0 && wait_bar(&sync->bar_final[NB - 1], v_abort))
+                lead_column_end_call(ta, col, H, sync, s_bp, s_pd8, s_thr, s_div, s_runv, lane, sync->fin[0],
+                                     sync->fin[1], sync->fin[2]);
+            if (role >= 0) report_column_rows_call(ta, col, H, sync, s_pd8, s_runv, lane, role);
+        }
         return;
     }
 
@@ -867,25 +883,31 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const int col, const 
                 s_ctx[k + 1] = make_bulk_ctx(min(w.x & ~3, kBig) + T_oo, min(w.z & ~3, kBig) + T_og,
                                              min(w.w & ~3, kBig) + T_os, (w.y & 255) + ord_off, s_thr[k + 1], m);
         }
-        if (j == NB - 1 && lane == 0) {
-            sync->fin[0] = vo_p;
-            sync->fin[1] = vg_p;
-            sync->fin[2] = vs_p;
-        }
         __threadfence_block();
         __syncwarp();
         if (lane == 0) {
+            if (!kChainTail && j == NB - 1) {
+                sync->fin[0] = vo_p;
+                sync->fin[1] = vg_p;
+                sync->fin[2] = vs_p;
+            }
             *v_final = j + 1;
             bar_arrive(&sync->bar_final[j]);
         }
     }
 
-    if (aborted && lane == 0) {
-        a.counts[col] = 0;
-        if (a.cost) a.cost[col] = __int_as_float(0x7f800000);
-        if (a.cost_fixed) a.cost_fixed[col] = kBig;
-        atomicOr(a.err, STIXELS_ERR_TIMEOUT);
+    if (aborted) {
+        if (lane == 0) {
+            a.counts[col] = 0;
+            if (a.cost) a.cost[col] = __int_as_float(0x7f800000);
+            if (a.cost_fixed) a.cost_fixed[col] = kBig;
+            atomicOr(a.err, STIXELS_ERR_TIMEOUT);
+        }
+        return;
     }
+    // the partial minima (s_runv) are free now: the column's tail stages the
+    // stixels there
+    if constexpr (kChainTail) lead_column_end(ta, col, H, sync, s_bp, s_pd8, s_thr, s_div, s_runv, lane, vo_p, vg_p, vs_p);
 }
 
 // MINB: CTAs per SM the register allocation is sized for (8 warps x 2 CTAs
@@ -894,7 +916,15 @@ template <int NW, bool kStd, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) stixel_dp_kernel(DpArgs a, int ring, int slots, int window)
 {
     extern __shared__ __align__(16) int32_t sm[];
-    dp_column<NW, kStd, false>(a, blockIdx.x, ring, slots, window, sm, 0);
+    // a copy of the arguments in shared memory for the column's tail
+    __shared__ DpArgs s_args;
+    {
+        const int* src = reinterpret_cast<const int*>(&a);
+        int* dst = reinterpret_cast<int*>(&s_args);
+        for (int i = threadIdx.x; i < (int)(sizeof(DpArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    // (dp_column's first barrier orders these stores before any read)
+    dp_column<NW, kStd, false, true>(a, s_args, blockIdx.x, ring, slots, window, sm, 0);
 }
 
 // Persistent form: each CTA takes columns from a work list (one shared atomic
@@ -922,12 +952,11 @@ __global__ void __launch_bounds__(NW * 32, MINB)
         // start 0 peeled out of the step loop: measured faster in this
         // kernel's shapes (32 1024x440 frames 12.86 -> 13.07 K frames/s),
         // slower in the per-frame kernel
-        dp_column<NW, kStd, true>(s_args, w.y, ring, slots, window, sm, w.y & 3);
+        dp_column<NW, kStd, true, false>(s_args, s_args, w.y, ring, slots, window, sm, w.y & 3);
         __syncthreads();
         // the next column initialises its barriers afresh
         SyncState* sync = dp_sync_state(sm, s_args.H, ring, slots);
         if (threadIdx.x < kMaxBlocks) bar_inval(&sync->bar_final[threadIdx.x]);
-        if (threadIdx.x == 0) bar_inval(&sync->bar_rep);
     }
 }
 

@@ -462,7 +462,7 @@ __device__ __noinline__ void report_column_rows_call(const DpArgs& a, int col, i
 // 1024x440), else bulk warp 0 does, through calls (the persistent kernel,
 // where the chain-led tail measured 10 % slower: 13.2 K against 11.9 K frames/s
 // for 32 1024x440 frames, and the bulk-led one 13.9 K).
-template <int NW, bool kStdTrans, bool kPeelFirst, bool kChainTail>
+template <int NW, bool kStdTrans, bool kChainTail>
 __device__ __forceinline__ void dp_column(const DpArgs& a, const DpArgs& ta, const int col, const int ring,
                                           const int slots, const int window, int32_t* sm, const int chain)
 {
@@ -855,7 +855,7 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const DpArgs& ta, con
         int ts = 0;
         StepIn cur = load_in(0, 0);
         int i = 0;
-        if (kPeelFirst && j == 0) {
+        if (j == 0) {
             // start 0, with the first-stixel prior, outside the loop
             const StepIn nx = load_in(1, 32);            // 1 = nb: read, never used
             step(0, gs0, cur, true);
@@ -864,11 +864,15 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const DpArgs& ta, con
             ts = 32;
             i = 1;
         }
-#pragma unroll 2
+        // unrolled by 4 in the per-frame kernel, by 2 in the persistent one
+        // (measured: a step of the chain alone 136 -> 107 cycles with start 0
+        // peeled and 4 steps per iteration; 1024x440 DP 90.1 -> 88.1 us, while
+        // 32 batched frames ran at 13.7 K against 13.9 K frames/s unrolled by 4)
+#pragma unroll(kChainTail ? 4 : 2)
         for (; i < nb; ++i) {
             const int tsn = ts + 32 - i;                 // tri_slot(i + 1)
             const StepIn nx = load_in(i + 1, tsn);       // i + 1 = nb: read, never used
-            step(i, gs0, cur, !kPeelFirst && j == 0 && i == 0);
+            step(i, gs0, cur, false);
             gs0 = cur.gs1;
             cur = nx;
             ts = tsn;
@@ -924,7 +928,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) stixel_dp_kernel(DpArgs a, int 
         for (int i = threadIdx.x; i < (int)(sizeof(DpArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
     }
     // (dp_column's first barrier orders these stores before any read)
-    dp_column<NW, kStd, false, true>(a, s_args, blockIdx.x, ring, slots, window, sm, 0);
+    dp_column<NW, kStd, true>(a, s_args, blockIdx.x, ring, slots, window, sm, 0);
 }
 
 // Persistent form: each CTA takes columns from a work list (one shared atomic
@@ -949,10 +953,7 @@ __global__ void __launch_bounds__(NW * 32, MINB)
         int* dst = reinterpret_cast<int*>(&s_args);
         for (int i = threadIdx.x; i < (int)(sizeof(DpArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
         __syncthreads();
-        // start 0 peeled out of the step loop: measured faster in this
-        // kernel's shapes (32 1024x440 frames 12.86 -> 13.07 K frames/s),
-        // slower in the per-frame kernel
-        dp_column<NW, kStd, true, false>(s_args, s_args, w.y, ring, slots, window, sm, w.y & 3);
+        dp_column<NW, kStd, false>(s_args, s_args, w.y, ring, slots, window, sm, w.y & 3);
         __syncthreads();
         // the next column initialises its barriers afresh
         SyncState* sync = dp_sync_state(sm, s_args.H, ring, slots);

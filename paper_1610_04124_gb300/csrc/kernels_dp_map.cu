@@ -6,27 +6,34 @@
 //   O[k][f]  best cost of rows 0..k whose top stixel is an object of mean f,
 //   G[k], S[k] the same for ground / sky tops,
 // and an object [b, k] of mean f' above an object state (b-1, f) pays the
-// ordering penalty iff f' > f + floor(eps / 16).  Over f that is a prefix
-// (penalised) and a suffix (free) of row b-1, so with the prefix and suffix
-// minima of O[b-1][.] every candidate costs O(1): O(H^2 + H F) per column.
+// ordering penalty iff f' > f + floor(eps / 16).  Over f that splits row b-1
+// into a penalised prefix f < x and a free suffix f >= x (x = f' - floor(eps
+// / 16)), so the best object-below term of every candidate is one entry of
+//   M[b-1][x] = min(min_{f >= x} O[b-1][f], min_{f < x} O[b-1][f] + penalty),
+// x clamped to [0, F]: O(H^2 + H F) per column.
 //
 // Ties: lexicographic (cost, previous class, start row, previous f), the
 // previous class's code in the cost's two low bits as everywhere in this
-// library; a candidate is one 64-bit key (cost | code) << 32 | start << 8 | f,
-// so one integer minimum orders them (shared-memory atomicMin per object bin).
+// library.  A state holds only its cost and code (int32, one atomic minimum
+// per update); the backtracking recovers the rest for the states on the
+// path: the lowest start whose candidate reaches the state's value, and for
+// an object below, the lowest f at the minimum (the penalised side's if it
+// reaches the minimum, else the free side's).
 //
 // Parallel scheme: one 256-thread CTA per column, rows in blocks of 32.  For
-// block j (rows K0 ..): phase A, every warp evaluates the starts b < K0 (their
-// rows are final) for the block's rows, lane = row, warps over the starts;
-// object candidates go to their bin (row, f') in shared memory by atomic
-// minimum (a lane merges consecutive candidates of the same f' first), ground
-// and sky stay in registers until one atomic per lane.  Phase B, one warp,
-// the block's rows in order: row k adds its starts inside the block (lane =
-// start), then the warp turns the row's bins into prefix / suffix minima over
-// f (one lane owns 8 consecutive f) in global scratch, which the rows above
-// read; at the block's end all warps copy its bins (the object state keys,
-// for the backtracking) to global memory.  Three CTA barriers per block
-// instead of several per row.
+// block j (rows K0 ..): phase A, six warps evaluate the next block's rows
+// against the starts of the blocks before this one (their rows are final;
+// lane = row, warps over the starts) and gather the next block's own
+// triangle of object cells (mean and data cost) into shared memory; object
+// candidates go to their bin (row, f') by atomic minimum (a lane merges
+// consecutive candidates of the same f' first), ground and sky stay in
+// registers until one atomic per lane.  Phase B, one warp, the block's rows
+// in order, from shared memory only: row k adds its starts inside the block
+// (lane = start; lanes of equal f' combine first), then turns its bins into
+// the row M[k][.] (one lane owns 8 consecutive f), kept in a shared ring of
+// the block's rows.  Then every warp adds this block's starts to the next
+// block's rows, and the block's states and rows of M go to global memory.
+// Three CTA barriers per block instead of several per row.
 #include <climits>
 
 #include "internal.h"
@@ -35,384 +42,490 @@
 namespace stx {
 namespace {
 
-constexpr unsigned long long kNoKey = ~0ull;
-__device__ const DivTable kDivTable = make_div_table();
-
-__device__ __forceinline__ unsigned long long make_key(int32_t cost_code, int b, int f)
-{
-    return ((unsigned long long)(uint32_t)cost_code << 32) | (unsigned long long)((uint32_t)b << 8 | (uint32_t)f);
-}
-__device__ __forceinline__ int32_t key_cost(unsigned long long k) { return (int32_t)(k >> 32); }
-__device__ __forceinline__ int key_start(unsigned long long k) { return (int)((k >> 8) & 0xffffff); }
-__device__ __forceinline__ int key_f(unsigned long long k) { return (int)(k & 255); }
+constexpr int32_t kNone = INT_MAX;           // a state no candidate has reached
 
 // value of a state for the states above it: the cost without the code, capped
-__device__ __forceinline__ int32_t state_value(unsigned long long k)
-{
-    return k == kNoKey ? kBig : min(key_cost(k) & ~3, kBig);
-}
-
-// Minimum of a 64-bit key over the warp: the high words' minimum, then the
-// low words' minimum among the lanes that hold it (two warp reductions).
-__device__ __forceinline__ unsigned long long warp_min(unsigned long long x)
-{
-    const unsigned hi = (unsigned)(x >> 32), lo = (unsigned)x;
-    const unsigned mh = __reduce_min_sync(0xffffffffu, hi);
-    const unsigned ml = __reduce_min_sync(0xffffffffu, hi == mh ? lo : 0xffffffffu);
-    return ((unsigned long long)mh << 32) | ml;
-}
+__device__ __forceinline__ int32_t state_value(int32_t k) { return min(k & ~3, kBig); }
 
 constexpr int kMapRows = 32;                 // rows per block
 constexpr size_t kMapSmemMax = 227 * 1024;   // dynamic shared memory one CTA may use
 constexpr int kMapWarps = 8;
+constexpr int kPer = 8;                      // object states per lane in a row's scan (F <= 256)
+constexpr int kTri = 528;                    // cells (b, k), b <= k, of one block
+__device__ __forceinline__ int tri_slot(int i) { return (i * (65 - i)) >> 1; }
+
+__device__ const DivTable kDivTable = make_div_table();
+
+// the stride of a row of M (F + 1 entries, x = 0 .. F), a multiple of 4
+__host__ __device__ inline int m_stride(int F) { return (F + 1 + 3) & ~3; }
 
 // What one column's candidate evaluation needs (shared memory and the LUT).
 struct MapCol {
     const int32_t* s_pd8;        // [H + 1] PD[v] + 8 v
     const int32_t* s_pg;         // [H + 1]
     const int32_t* s_ps;         // [H + 1]
-    const int32_t* s_fhi;        // [H] gravity iff f > fhi
-    const int32_t* s_flo;        // [H] diving iff f < flo
-    const uint2* s_div;          // [H + 1] rounded-mean constants
-    const unsigned long long* s_kg;   // [H] ground state keys
-    const unsigned long long* s_ks;   // [H] sky state keys
-    const unsigned long long* s_bo;   // [H] best object state of each row, value << 32 | f
+    const int32_t* s_thr;        // [H] gravity iff f > fhi (low half), diving iff f < flo (high half)
+    const uint2* div;            // rounded-mean constants (the global table, L1-resident)
+    const int32_t* s_gv;         // [H] ground state values
+    const int32_t* s_sv;         // [H] sky state values
+    const int32_t* s_bo;         // [H] best object state value of each row (over f)
     const int32_t* po;           // the column's object LUT, [F][P]
     int P, F, dmax, ord_off;
     int32_t T_oo, T_og, T_os, T_go, T_gg, T_gs, T_so, T_sg, T_ss;
 };
 
-// The candidate keys of the stixel [b, k]: object (for the state (k, fo)),
-// ground and sky; every key is (cost | previous class code) << 32 | b << 8 |
-// previous object f, so one integer minimum is the tie order.
-// prer / sufr: the prefix / suffix minima of row b - 1 (unused for b = 0).
-__device__ __forceinline__ void map_cands(const MapCol& c, const ModelDev& m, int b, int k,
-                                          const unsigned long long* prer, const unsigned long long* sufr, int& fo,
-                                          unsigned long long& ko, unsigned long long& kg, unsigned long long& ks)
+// rounded mean of the stixel [b, k]
+__device__ __forceinline__ int map_mean(const MapCol& c, int b, int k)
 {
-    const int n = k - b + 1;
-    const uint2 dm = c.s_div[n];
-    fo = (int)min(__umulhi((uint32_t)(c.s_pd8[k + 1] - c.s_pd8[b]), dm.x) >> dm.y, (uint32_t)c.dmax);
-    const int32_t* row = c.po + (size_t)fo * c.P;
-    const int32_t d_o = __ldg(row + k + 1) - __ldg(row + b);
-    const int32_t d_g = c.s_pg[k + 1] - c.s_pg[b], d_s = c.s_ps[k + 1] - c.s_ps[b];
-    if (b == 0) {
-        ko = make_key(d_o + m.first[0] + kNoneCode, 0, 0);
-        kg = make_key(d_g + m.first[1] + kNoneCode, 0, 0);
-        ks = make_key(d_s + m.first[2] + kNoneCode, 0, 0);
-        return;
-    }
-    // object above object: free for previous f >= fo - ord_off, penalised below
-    const int x = fo - c.ord_off;
-    ko = kNoKey;
-    if (x <= c.F - 1) {
-        const unsigned long long su = sufr[max(x, 0)];
-        const int32_t v = min((int32_t)(su >> 32), kBig);
-        const unsigned long long t = make_key(d_o + v + c.T_oo, b, (int)(su & 255));
-        ko = t < ko ? t : ko;
-    }
-    if (x - 1 >= 0) {
-        const unsigned long long pr = prer[min(x - 1, c.F - 1)];
-        const int32_t v = min((int32_t)(pr >> 32), kBig);
-        const unsigned long long t = make_key(d_o + v + c.T_oo + m.pen_ord, b, (int)(pr & 255));
-        ko = t < ko ? t : ko;
-    }
-    const int32_t vg = state_value(c.s_kg[b - 1]), vs = state_value(c.s_ks[b - 1]);
-    const int32_t gpen = (fo > c.s_fhi[b] ? m.pen_grav : 0) + (fo < c.s_flo[b] ? m.pen_div : 0);
-    const unsigned long long cg = make_key(d_o + vg + c.T_og + gpen, b, 0);
-    const unsigned long long cs = make_key(d_o + vs + c.T_os, b, 0);
-    ko = cg < ko ? cg : ko;
-    ko = cs < ko ? cs : ko;
-    // ground / sky above: the best object of row b-1 (any f), ground, sky
-    const unsigned long long mo = c.s_bo[b - 1];
-    const int32_t vo = min((int32_t)(mo >> 32), kBig);
-    const int fm = (int)(mo & 255);
-    kg = make_key(d_g + vo + c.T_go, b, fm);
-    const unsigned long long g2 = make_key(d_g + vg + c.T_gg, b, 0), g3 = make_key(d_g + vs + c.T_gs, b, 0);
-    kg = g2 < kg ? g2 : kg;
-    kg = g3 < kg ? g3 : kg;
-    ks = make_key(d_s + vo + c.T_so, b, fm);
-    const unsigned long long s2 = make_key(d_s + vg + c.T_sg, b, 0), s3 = make_key(d_s + vs + c.T_ss, b, 0);
-    ks = s2 < ks ? s2 : ks;
-    ks = s3 < ks ? s3 : ks;
+    const uint2 dm = __ldg(c.div + k - b + 1);
+    return (int)min(__umulhi((uint32_t)(c.s_pd8[k + 1] - c.s_pd8[b]), dm.x) >> dm.y, (uint32_t)c.dmax);
 }
 
-__global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, unsigned long long* scratch)
+// the entry of row b - 1 of M that an object of mean fo reads
+__device__ __forceinline__ int m_index(const MapCol& c, int fo) { return min(max(fo - c.ord_off, 0), c.F); }
+
+// The candidates (cost | previous class code) of the stixel [b, k] with mean
+// fo and object data cost d_o: object (for the state (k, fo)), ground and
+// sky.  mx = M[b - 1][x] (any value for b = 0).
+__device__ __forceinline__ void map_cands(const MapCol& c, const ModelDev& m, int b, int k, int fo, int32_t d_o,
+                                          int32_t mx, int32_t& ko, int32_t& kg, int32_t& ks)
+{
+    const int32_t d_g = c.s_pg[k + 1] - c.s_pg[b], d_s = c.s_ps[k + 1] - c.s_ps[b];
+    if (b == 0) {
+        ko = d_o + m.first[0] + kNoneCode;
+        kg = d_g + m.first[1] + kNoneCode;
+        ks = d_s + m.first[2] + kNoneCode;
+        return;
+    }
+    // object above object (ordering exact through M), above ground, above sky
+    const int32_t vg = c.s_gv[b - 1], vs = c.s_sv[b - 1];
+    const int32_t t = c.s_thr[b];
+    const int32_t gpen = (fo > (int32_t)(int16_t)(t & 0xffff) ? m.pen_grav : 0) + (fo < (t >> 16) ? m.pen_div : 0);
+    ko = min(min(d_o + mx + c.T_oo, d_o + vg + c.T_og + gpen), d_o + vs + c.T_os);
+    // ground / sky above: the best object of row b-1 (any f), ground, sky
+    const int32_t vo = c.s_bo[b - 1];
+    kg = min(min(d_g + vo + c.T_go, d_g + vg + c.T_gg), d_g + vs + c.T_gs);
+    ks = min(min(d_s + vo + c.T_so, d_s + vg + c.T_sg), d_s + vs + c.T_ss);
+}
+
+// The lowest f at the minimum value of a row of object states (global) over
+// f in [lo, hi), by the whole warp: {value, f} ({kBig, -1} when every state
+// there is unreached).
+__device__ __forceinline__ int2 row_argmin(const int32_t* row, int lo, int hi, int lane)
+{
+    int32_t bv = kBig;
+    int bf = INT_MAX;
+    for (int f = lo + lane; f < hi; f += 32) {
+        const int32_t v = state_value(row[f]);
+        if (v < bv) { bv = v; bf = f; }            // ascending f: the first at the minimum
+    }
+    const int32_t mv = __reduce_min_sync(0xffffffffu, bv);
+    const int mf = (int)__reduce_min_sync(0xffffffffu, (unsigned)(bv == mv ? bf : INT_MAX));
+    return make_int2(mv, mf == INT_MAX ? -1 : mf);
+}
+
+// Shared-memory layout of one CTA: a head that lives through the whole
+// kernel, and a body that the DP uses and the cost report then takes over.
+struct MapLayout {
+    size_t gv, sv, bo, pd8, thr, pg, ps;             // head
+    size_t bin, gbin, sbin, ring, trid, trif;        // body
+    size_t body, total;
+};
+
+__host__ __device__ inline size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline MapLayout map_layout(int H, int F)
+{
+    MapLayout L;
+    size_t o = 0;
+    L.gv = o;   o += 4 * (size_t)H;
+    L.sv = o;   o += 4 * (size_t)H;
+    L.bo = o;   o += 4 * (size_t)H;
+    L.pd8 = o;  o += 4 * (size_t)(H + 1);
+    L.thr = o;  o += 4 * (size_t)H;
+    L.pg = o;   o += 4 * (size_t)(H + 1);
+    L.ps = o;   o += 4 * (size_t)(H + 1);
+    o = up16(o);
+    L.body = o;
+    L.bin = o;  o += 4 * 2 * (size_t)kMapRows * F;
+    L.gbin = o; o += 4 * 2 * kMapRows;
+    L.sbin = o; o += 4 * 2 * kMapRows;
+    o = up16(o);
+    L.ring = o; o += 4 * (size_t)(kMapRows + 1) * m_stride(F);
+    L.trid = o; o += 4 * 2 * (size_t)kTri;
+    L.trif = o; o += 2 * (size_t)kTri;
+    // the report stages 4 H words in the body
+    L.total = up16(L.body + (o - L.body > 16 * (size_t)H ? o - L.body : 16 * (size_t)H));
+    return L;
+}
+
+__global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, int32_t* keyo_all, int32_t* kgs_all,
+                                                                   int32_t* mv_all)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int H = a.H, P = a.P, F = a.F;
+    const int H = a.H, P = a.P, F = a.F, MS = m_stride(F);
     const int col = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const ModelDev& m = a.m;
-    const size_t HF = (size_t)H * F;
-    unsigned long long* keyo = scratch + (size_t)col * 3 * HF;   // [H][F] best key of each object state
-    unsigned long long* pre = keyo + HF;
-    unsigned long long* suf = pre + HF;
+    int32_t* keyo = keyo_all + (size_t)col * H * F;       // [H][F] object states (backtracking)
+    int32_t* kgs = kgs_all + (size_t)col * 2 * H;          // [2][H] ground, sky states
+    int32_t* mv = mv_all + (size_t)col * H * MS;           // [H][MS] the rows of M
 
-    unsigned long long* s_kg = reinterpret_cast<unsigned long long*>(smem);      // [H]
-    unsigned long long* s_ks = s_kg + H;                                         // [H]
-    unsigned long long* s_bo = s_ks + H;                                         // [H]
-    unsigned long long* s_bin = s_bo + H;                                        // [2][kMapRows][F]
-    unsigned long long* s_gbin = s_bin + 2 * (size_t)kMapRows * F;               // [2][kMapRows]
-    unsigned long long* s_sbin = s_gbin + 2 * kMapRows;                          // [2][kMapRows]
-    uint2* s_div = reinterpret_cast<uint2*>(s_sbin + 2 * kMapRows);              // [H + 1]
-    int32_t* s_pd8 = reinterpret_cast<int32_t*>(s_div + H + 1);                  // [H + 1]
-    int32_t* s_pg = s_pd8 + (H + 1);                                             // [H + 1]
-    int32_t* s_ps = s_pg + (H + 1);                                              // [H + 1]
-    int32_t* s_fhi = s_ps + (H + 1);                                             // [H]
-    int32_t* s_flo = s_fhi + H;                                                  // [H]
+    const MapLayout L = map_layout(H, F);
+    int32_t* s_gv = reinterpret_cast<int32_t*>(smem + L.gv);
+    int32_t* s_sv = reinterpret_cast<int32_t*>(smem + L.sv);
+    int32_t* s_bo = reinterpret_cast<int32_t*>(smem + L.bo);
+    int32_t* s_pd8 = reinterpret_cast<int32_t*>(smem + L.pd8);
+    int32_t* s_thr = reinterpret_cast<int32_t*>(smem + L.thr);
+    int32_t* s_pg = reinterpret_cast<int32_t*>(smem + L.pg);
+    int32_t* s_ps = reinterpret_cast<int32_t*>(smem + L.ps);
+    int32_t* s_bin = reinterpret_cast<int32_t*>(smem + L.bin);     // [2][kMapRows][F]
+    int32_t* s_gbin = reinterpret_cast<int32_t*>(smem + L.gbin);   // [2][kMapRows]
+    int32_t* s_sbin = reinterpret_cast<int32_t*>(smem + L.sbin);   // [2][kMapRows]
+    int32_t* s_ring = reinterpret_cast<int32_t*>(smem + L.ring);   // [kMapRows + 1][MS]: ring i = row K0 - 1 + i
+    int32_t* s_trid = reinterpret_cast<int32_t*>(smem + L.trid);   // [2][kTri] object data cost of the block's cells
+    uint8_t* s_trif = smem + L.trif;                                // [2][kTri] their means
+    const uint2* div = reinterpret_cast<const uint2*>(kDivTable.v);
 
     for (int v = tid; v <= H; v += blockDim.x) {
         s_pd8[v] = a.pd[(size_t)col * P + v] + 8 * v;
         s_pg[v] = a.pg[(size_t)col * P + v];
         s_ps[v] = a.ps[(size_t)col * P + v];
-        if (v >= 1) {
-            const DivMagic dm = kDivTable.v[v];
-            s_div[v] = make_uint2(dm.m, dm.s);
-        }
-        if (v < H) {
-            const int32_t t = rows_thr(a.rows.fg, H)[v];
-            s_fhi[v] = (int32_t)(int16_t)(t & 0xffff);    // gravity iff f > fhi
-            s_flo[v] = t >> 16;                           // diving iff f < flo
-        }
+        if (v < H) s_thr[v] = rows_thr(a.rows.fg, H)[v];
     }
     MapCol c;
-    c.s_pd8 = s_pd8; c.s_pg = s_pg; c.s_ps = s_ps; c.s_fhi = s_fhi; c.s_flo = s_flo; c.s_div = s_div;
-    c.s_kg = s_kg; c.s_ks = s_ks; c.s_bo = s_bo;
+    c.s_pd8 = s_pd8; c.s_pg = s_pg; c.s_ps = s_ps; c.s_thr = s_thr; c.div = div;
+    c.s_gv = s_gv; c.s_sv = s_sv; c.s_bo = s_bo;
     c.po = a.po + (size_t)col * F * P;
     c.P = P; c.F = F; c.dmax = m.dmax; c.ord_off = m.ord_off;       // ordering iff f' > f + ord_off
     c.T_oo = m.trans[0][0]; c.T_og = m.trans[0][1] + 1; c.T_os = m.trans[0][2] + 2;
     c.T_go = m.trans[1][0]; c.T_gg = m.trans[1][1] + 1; c.T_gs = m.trans[1][2] + 2;
     c.T_so = m.trans[2][0]; c.T_sg = m.trans[2][1] + 1; c.T_ss = m.trans[2][2] + 2;
+    const int32_t pen_ord = m.pen_ord;
 
     const int NB = (H + kMapRows - 1) / kMapRows;
-    constexpr int kPer = 8;                       // object states per lane in the row scan (F <= 256)
     const size_t BF = (size_t)kMapRows * F;
 
-    // Phase A for the rows K + lane (lane < nr) and the starts b = b0, b0 + step,
-    // ... < b1 (rows of earlier blocks, all final), into one block's bins.  Two
-    // starts are evaluated together so that their loads overlap; a lane keeps
-    // its object candidates for one bin until f changes (consecutive starts
-    // mostly share f), its ground / sky minima in registers.
-    auto phase_a = [&](unsigned long long* bins, unsigned long long* gbin, unsigned long long* sbin, int K, int nr,
-                       int b0, int b1, int step) {
+    // The object cells (K + i, K + l), i <= l < nr, of the block at rows K:
+    // mean and data cost, into triangle buffer `buf` (slot tri_slot(i) + l - i),
+    // by the warps w, w + nw, ... (start i per warp, lane = end row).
+    auto gather_tri = [&](int buf, int K, int nr, int w, int nw) {
+        int32_t* td = s_trid + buf * kTri;
+        uint8_t* tf = s_trif + buf * kTri;
+        const int k = K + lane;
+        for (int i = w; i < nr; i += nw) {
+            if (lane >= i && lane < nr) {
+                const int b = K + i;
+                const int fo = map_mean(c, b, k);
+                const int32_t* row = c.po + (size_t)fo * P;
+                const int e = tri_slot(i) + lane - i;
+                td[e] = __ldg(row + k + 1) - __ldg(row + b);
+                tf[e] = (uint8_t)fo;
+            }
+        }
+    };
+
+    // Phase A for the rows K + lane (lane < nr) and the starts b = b0, b0 +
+    // step, ... < b1 (rows of earlier blocks, all final), into one block's
+    // bins.  M of row b - 1 comes from the ring (whose row 0 is row ring_base)
+    // when use_ring, else from global memory.  Four starts are evaluated
+    // together so that their loads overlap; a lane keeps its object
+    // candidates for one bin until f changes (consecutive starts mostly share
+    // f), its ground / sky minima in registers.
+    auto phase_a = [&](int32_t* bins, int32_t* gbin, int32_t* sbin, int K, int nr, int b0, int b1, int step,
+                       bool use_ring, int ring_base) {
         if (lane >= nr || b0 >= b1) return;
         const int k = K + lane;
-        unsigned long long rg = kNoKey, rs = kNoKey, ck = kNoKey;
+        int32_t rg = kNone, rs = kNone, ck = kNone;
         int cf = -1;
-        auto merge = [&](int fo, unsigned long long ko, unsigned long long kg, unsigned long long ks) {
-            rg = kg < rg ? kg : rg;
-            rs = ks < rs ? ks : rs;
-            if (fo != cf) {
-                if (cf >= 0) atomicMin(&bins[lane * F + cf], ck);
-                cf = fo;
-                ck = ko;
-            } else {
-                ck = ko < ck ? ko : ck;
+        for (int bb = b0; bb < b1; bb += 4 * step) {
+            int fo[4];
+            int32_t lo[4], hi[4], mx[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int b = min(bb + u * step, b1 - 1);   // past b1: repeats a valid start, not merged
+                fo[u] = map_mean(c, b, k);
+                const int32_t* row = c.po + (size_t)fo[u] * P;
+                lo[u] = __ldg(row + b);
+                hi[u] = __ldg(row + k + 1);
+                const int x = m_index(c, fo[u]);
+                mx[u] = b == 0 ? 0 : (use_ring ? s_ring[(b - 1 - ring_base) * MS + x] : mv[(size_t)(b - 1) * MS + x]);
             }
-        };
-        int b = b0;
-        for (; b + step < b1; b += 2 * step) {
-            int f0, f1;
-            unsigned long long o0, g0, s0, o1, g1, s1;
-            map_cands(c, m, b, k, pre + (size_t)(b - 1) * F, suf + (size_t)(b - 1) * F, f0, o0, g0, s0);
-            map_cands(c, m, b + step, k, pre + (size_t)(b + step - 1) * F, suf + (size_t)(b + step - 1) * F, f1, o1,
-                      g1, s1);
-            merge(f0, o0, g0, s0);
-            merge(f1, o1, g1, s1);
-        }
-        if (b < b1) {
-            int f0;
-            unsigned long long o0, g0, s0;
-            map_cands(c, m, b, k, pre + (size_t)(b - 1) * F, suf + (size_t)(b - 1) * F, f0, o0, g0, s0);
-            merge(f0, o0, g0, s0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int b = bb + u * step;
+                if (b < b1) {
+                    int32_t ko, kg, ks;
+                    map_cands(c, m, b, k, fo[u], hi[u] - lo[u], mx[u], ko, kg, ks);
+                    rg = min(rg, kg);
+                    rs = min(rs, ks);
+                    if (fo[u] != cf) {
+                        if (cf >= 0) atomicMin(&bins[lane * F + cf], ck);
+                        cf = fo[u];
+                        ck = ko;
+                    } else {
+                        ck = min(ck, ko);
+                    }
+                }
+            }
         }
         if (cf >= 0) atomicMin(&bins[lane * F + cf], ck);
         atomicMin(&gbin[lane], rg);
         atomicMin(&sbin[lane], rs);
     };
 
-    // bins of blocks 0 and 1 (the bins are double-buffered by block parity)
-    for (int i = tid; i < 2 * (int)BF; i += blockDim.x) s_bin[i] = kNoKey;
-    if (tid < 2 * kMapRows) { s_gbin[tid] = kNoKey; s_sbin[tid] = kNoKey; }
+    // bins of blocks 0 and 1 (double-buffered by block parity), block 0's triangle
+    for (int i = tid; i < 2 * (int)BF; i += blockDim.x) s_bin[i] = kNone;
+    if (tid < 2 * kMapRows) { s_gbin[tid] = kNone; s_sbin[tid] = kNone; }
+    gather_tri(0, 0, min(kMapRows, H), warp, kMapWarps);
     __syncthreads();
     for (int j = 0; j < NB; ++j) {
         const int K0 = kMapRows * j, nb = min(kMapRows, H - K0);
         const int K1 = K0 + kMapRows, nb1 = j + 1 < NB ? min(kMapRows, H - K1) : 0;
-        unsigned long long* bin_j = s_bin + (j & 1) * BF;
-        unsigned long long* gbin_j = s_gbin + (j & 1) * kMapRows;
-        unsigned long long* sbin_j = s_sbin + (j & 1) * kMapRows;
-        unsigned long long* bin_n = s_bin + ((j + 1) & 1) * BF;
-        unsigned long long* gbin_n = s_gbin + ((j + 1) & 1) * kMapRows;
-        unsigned long long* sbin_n = s_sbin + ((j + 1) & 1) * kMapRows;
+        int32_t* bin_j = s_bin + (j & 1) * BF;
+        int32_t* gbin_j = s_gbin + (j & 1) * kMapRows;
+        int32_t* sbin_j = s_sbin + (j & 1) * kMapRows;
+        int32_t* bin_n = s_bin + ((j + 1) & 1) * BF;
+        int32_t* gbin_n = s_gbin + ((j + 1) & 1) * kMapRows;
+        int32_t* sbin_n = s_sbin + ((j + 1) & 1) * kMapRows;
+        const int32_t* tri_d = s_trid + (j & 1) * kTri;
+        const uint8_t* tri_f = s_trif + (j & 1) * kTri;
 
         if (warp == 0) {
-            // Phase B: the block's rows in order; row k adds its starts within
-            // the block (lane = start K0 + lane <= k), then its object states
-            // become prefix / suffix minima over f for the rows above.
+            // Phase B: the block's rows in order.  The previous block's last
+            // row opens the ring (ring row i = row K0 - 1 + i).
+            if (j > 0)
+                for (int x = lane; x < MS; x += 32) s_ring[x] = s_ring[kMapRows * MS + x];
+            __syncwarp();
             for (int r = 0; r < nb; ++r) {
                 const int k = K0 + r;
-                unsigned long long kg = kNoKey, ks = kNoKey;
+                // row k's starts inside the block (lane = start K0 + lane <= k)
+                int32_t ko = kNone, kg = kNone, ks = kNone;
+                int fo = -1 - lane;                      // lanes past the row: no candidate, no peer
                 if (lane <= r) {
                     const int b = K0 + lane;
-                    int fo;
-                    unsigned long long ko;
-                    map_cands(c, m, b, k, pre + (size_t)(b - 1) * F, suf + (size_t)(b - 1) * F, fo, ko, kg, ks);
-                    atomicMin(&bin_j[r * F + fo], ko);
+                    const int e = tri_slot(lane) + r - lane;
+                    fo = tri_f[e];
+                    const int32_t mx = b == 0 ? 0 : s_ring[lane * MS + m_index(c, fo)];
+                    map_cands(c, m, b, k, fo, tri_d[e], mx, ko, kg, ks);
                 }
-                kg = warp_min(kg);
-                ks = warp_min(ks);
+                // consecutive starts mostly share their mean: a scan over the
+                // lanes combines the candidates of equal f (a lane takes a
+                // lane below it only if that one has its f, which keeps every
+                // minimum in its bin), so that the last lane of each run of
+                // equal f alone updates the bin
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t u = __shfl_up_sync(0xffffffffu, ko, o);
+                    const int fu = __shfl_up_sync(0xffffffffu, fo, o);
+                    if (lane >= o && fu == fo) ko = min(ko, u);
+                }
+                const int fn = __shfl_down_sync(0xffffffffu, fo, 1);
+                if (lane <= r && (lane == 31 || fn != fo)) atomicMin(&bin_j[r * F + fo], ko);
+                kg = min(__reduce_min_sync(0xffffffffu, kg), gbin_j[r]);
+                ks = min(__reduce_min_sync(0xffffffffu, ks), sbin_j[r]);
                 __syncwarp();
-                const unsigned long long* bin = bin_j + (size_t)r * F;
-                // lane l owns f = kPer l .. kPer l + kPer - 1: local prefix / suffix, then warp scans
-                unsigned long long pv[kPer], sv[kPer];
+                // the row's object states as values; lane l owns f = 8 l .. 8 l + 7:
+                // local prefix / suffix minima, then warp scans of the lane totals
+                const int32_t* bin = bin_j + (size_t)r * F;
+                int32_t pv[kPer], sv[kPer];
 #pragma unroll
                 for (int i = 0; i < kPer; ++i) {
                     const int f = kPer * lane + i;
-                    pv[i] = f < F ? ((unsigned long long)(uint32_t)state_value(bin[f]) << 32) | (unsigned)f : kNoKey;
+                    pv[i] = f < F ? state_value(bin[f]) : INT_MAX;
                     sv[i] = pv[i];
                 }
 #pragma unroll
-                for (int i = 1; i < kPer; ++i) pv[i] = pv[i - 1] < pv[i] ? pv[i - 1] : pv[i];
+                for (int i = 1; i < kPer; ++i) pv[i] = min(pv[i - 1], pv[i]);
 #pragma unroll
-                for (int i = kPer - 2; i >= 0; --i) sv[i] = sv[i + 1] < sv[i] ? sv[i + 1] : sv[i];
-                unsigned long long pt = pv[kPer - 1], st = sv[0];       // lane totals
+                for (int i = kPer - 2; i >= 0; --i) sv[i] = min(sv[i + 1], sv[i]);
+                int32_t pt = pv[kPer - 1], st = sv[0];
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    const unsigned long long up = __shfl_up_sync(0xffffffffu, pt, o);
-                    const unsigned long long dn = __shfl_down_sync(0xffffffffu, st, o);
-                    if (lane >= o) pt = up < pt ? up : pt;
-                    if (lane + o < 32) st = dn < st ? dn : st;
+                    const int32_t up = __shfl_up_sync(0xffffffffu, pt, o);
+                    const int32_t dn = __shfl_down_sync(0xffffffffu, st, o);
+                    if (lane >= o) pt = min(pt, up);
+                    if (lane + o < 32) st = min(st, dn);
                 }
                 // exclusive carries from the lanes below / above
-                unsigned long long pc = __shfl_up_sync(0xffffffffu, pt, 1);
-                unsigned long long sc = __shfl_down_sync(0xffffffffu, st, 1);
-                if (lane == 0) pc = kNoKey;
-                if (lane == 31) sc = kNoKey;
-                const size_t rw = (size_t)k * F;
+                int32_t pc = __shfl_up_sync(0xffffffffu, pt, 1);
+                int32_t sc = __shfl_down_sync(0xffffffffu, st, 1);
+                if (lane == 0) pc = INT_MAX;
+                if (lane == 31) sc = INT_MAX;
+                // M[k][x], x = 8 lane + i: the free suffix f >= x against the
+                // penalised prefix f < x (shared memory only: the block's rows
+                // go to global memory at its end)
+                int32_t mr[kPer];
 #pragma unroll
                 for (int i = 0; i < kPer; ++i) {
-                    const int f = kPer * lane + i;
-                    if (f < F) {
-                        pre[rw + f] = pc < pv[i] ? pc : pv[i];
-                        suf[rw + f] = sc < sv[i] ? sc : sv[i];
-                    }
+                    const int x = kPer * lane + i;
+                    const int32_t suf = min(sc, sv[i]);
+                    const int32_t pre = i == 0 ? pc : min(pc, pv[i - 1]);
+                    mr[i] = x == 0 ? suf : (x >= F ? pre + pen_ord : min(suf, pre + pen_ord));
                 }
+                int32_t* rrow = s_ring + (r + 1) * MS;
+                const int x0 = kPer * lane;
+                if (x0 + 3 < MS) *reinterpret_cast<int4*>(rrow + x0) = make_int4(mr[0], mr[1], mr[2], mr[3]);
+                if (x0 + 7 < MS) *reinterpret_cast<int4*>(rrow + x0 + 4) = make_int4(mr[4], mr[5], mr[6], mr[7]);
+                const int32_t best = __shfl_sync(0xffffffffu, pt, 31);      // the row's best object state
+                if (F == 32 * kPer && lane == 31) rrow[F] = best + pen_ord;   // x = F past the lanes' ranges
                 if (lane == 0) {
-                    s_kg[k] = kg < gbin_j[r] ? kg : gbin_j[r];
-                    s_ks[k] = ks < sbin_j[r] ? ks : sbin_j[r];
+                    gbin_j[r] = kg;
+                    sbin_j[r] = ks;
+                    s_gv[k] = state_value(kg);
+                    s_sv[k] = state_value(ks);
+                    s_bo[k] = best;
                 }
-                // the row's best object state (over every f): the last prefix
-                const unsigned long long best = __shfl_sync(0xffffffffu, pt, 31);
-                if (lane == 0) s_bo[k] = best;
                 // the rows above in this block are read by this warp only:
                 // the warp barrier orders its lanes' stores and loads
                 __syncwarp();
             }
         } else if (warp != 4) {
             // meanwhile: the next block's candidates whose starts lie in the
-            // blocks before this one (their rows are final), on the warps that
-            // do not share warp 0's scheduler (warp 4 does), so that the
-            // sequential rows keep its issue slots
-            phase_a(bin_n, gbin_n, sbin_n, K1, nb1, warp - 1 - (warp > 4), K0, kMapWarps - 2);
+            // blocks before this one (their rows are final), and the next
+            // block's own object cells, on the warps that do not share warp
+            // 0's scheduler (warp 4 does), so that the sequential rows keep
+            // its issue slots
+            const int w6 = warp - 1 - (warp > 4);
+            phase_a(bin_n, gbin_n, sbin_n, K1, nb1, w6, K0, kMapWarps - 2, false, 0);
+            if (nb1 > 0) gather_tri((j + 1) & 1, K1, nb1, w6, kMapWarps - 2);
         }
         __syncthreads();                          // block j's rows are final and visible
-        // the next block's starts inside this block; then this block's bins
-        // (its object state keys) go to global memory for the backtracking,
-        // coalesced, and are reset for block j + 2
-        phase_a(bin_n, gbin_n, sbin_n, K1, nb1, K0 + warp, K0 + nb, kMapWarps);
+        // the next block's starts inside this block (M from the ring); then
+        // this block's states and rows of M go to global memory, coalesced,
+        // and its bins are reset for block j + 2
+        phase_a(bin_n, gbin_n, sbin_n, K1, nb1, K0 + warp, K0 + nb, kMapWarps, true, K0 - 1);
         for (int i = tid; i < (int)BF; i += blockDim.x) {
             if (i < nb * F) keyo[(size_t)K0 * F + i] = bin_j[i];
-            bin_j[i] = kNoKey;
+            bin_j[i] = kNone;
         }
-        if (tid < kMapRows) { gbin_j[tid] = kNoKey; sbin_j[tid] = kNoKey; }
+        for (int i = tid; i < nb * MS; i += blockDim.x) mv[(size_t)K0 * MS + i] = s_ring[MS + i];
+        if (tid < kMapRows) {
+            if (tid < nb) {
+                kgs[K0 + tid] = gbin_j[tid];
+                kgs[H + K0 + tid] = sbin_j[tid];
+            }
+            gbin_j[tid] = kNone;
+            sbin_j[tid] = kNone;
+        }
         __syncthreads();
     }
 
-    // top row (lexicographic cost, class, f) and backtracking, by warp 0: lane
-    // 0 walks the path, then the warp reports its cost in real arithmetic
+    // top row (lexicographic cost, class, f) and backtracking, by warp 0,
+    // then the cost report in real arithmetic
     if (warp != 0) return;
-    int n = 0, feasible = 1;
-    int32_t* s_seg = s_pg;                        // free after the last block; [H + 1] >= n
-    if (lane == 0) {
-        int cc0 = -1, fb = 0;
-        int32_t best = kBig;
-        for (int f = 0; f < F; ++f) {
-            const int32_t v = state_value(keyo[(size_t)(H - 1) * F + f]);
-            if (v < best) { best = v; cc0 = 0; fb = f; }
-        }
-        if (state_value(s_kg[H - 1]) < best) { best = state_value(s_kg[H - 1]); cc0 = 1; fb = 0; }
-        if (state_value(s_ks[H - 1]) < best) { best = state_value(s_ks[H - 1]); cc0 = 2; fb = 0; }
-        if (cc0 < 0 || best >= kBig) {
+    const int2 ob = row_argmin(keyo + (size_t)(H - 1) * F, 0, F, lane);
+    int cc0 = ob.x < kBig ? 0 : -1, fb = max(ob.y, 0);
+    int32_t best = ob.x;
+    if (s_gv[H - 1] < best) { best = s_gv[H - 1]; cc0 = 1; fb = 0; }
+    if (s_sv[H - 1] < best) { best = s_sv[H - 1]; cc0 = 2; fb = 0; }
+    if (cc0 < 0 || best >= kBig) {
+        if (lane == 0) {
             a.counts[col] = 0;
             if (a.cost) a.cost[col] = __int_as_float(0x7f800000);
             if (a.cost_fixed) a.cost_fixed[col] = kBig;
             atomicOr(a.err, STIXELS_ERR_INFEASIBLE);
-            feasible = 0;
-        } else {
-            // count, then write bottom -> top
-            for (int k = H - 1, cc = cc0, ff = fb; k >= 0 && cc < 3 && n <= H;) {
-                const unsigned long long key = cc == 0 ? keyo[(size_t)k * F + ff] : (cc == 1 ? s_kg[k] : s_ks[k]);
-                ++n;
-                const int b = key_start(key);
-                if (b > k) break;
-                k = b - 1;
-                cc = key_cost(key) & 3;
-                ff = key_f(key);
-            }
-            int idx = n - 1;
-            stixel_t* out = a.stixels + (size_t)col * a.cap;
-            for (int k = H - 1, cc = cc0, ff = fb; k >= 0 && cc < 3 && idx >= 0; --idx) {
-                const unsigned long long key = cc == 0 ? keyo[(size_t)k * F + ff] : (cc == 1 ? s_kg[k] : s_ks[k]);
-                const int b = key_start(key);
-                s_seg[idx] = (min(b, k) << 13) | (k << 2) | cc;
-                if (idx < a.cap) {
-                    const int nrows = k - b + 1;
-                    const int32_t S = s_pd8[k + 1] - s_pd8[b] - 8 * nrows;
-                    stixel_t st;
-                    st.row_top = (int16_t)(H - 1 - k);
-                    st.row_bottom = (int16_t)(H - 1 - b);
-                    st.cls = (uint8_t)cc;
-                    st.flags = 0;
-                    st.reserved = 0;
-                    st.disparity = __fdiv_rn(__int2float_rn(S), __int2float_rn(16 * nrows));
-                    out[idx] = st;
+        }
+        return;
+    }
+    // The lowest start b <= k whose candidate for the state (k, class cc,
+    // mean f) is v, the state's value (cost | code), by the whole warp.
+    auto find_start = [&](int k, int cc, int f, int32_t v) -> int {
+        for (int b0 = 0; b0 <= k; b0 += 32) {
+            const int b = b0 + lane;
+            bool hit = false;
+            if (b <= k) {
+                const int fo = map_mean(c, b, k);
+                if (cc != 0 || fo == f) {
+                    const int32_t* row = c.po + (size_t)fo * P;
+                    const int32_t d_o = __ldg(row + k + 1) - __ldg(row + b);
+                    const int32_t mx = b == 0 ? 0 : mv[(size_t)(b - 1) * MS + m_index(c, fo)];
+                    int32_t ko, kg, ks;
+                    map_cands(c, m, b, k, fo, d_o, mx, ko, kg, ks);
+                    hit = (cc == 0 ? ko : (cc == 1 ? kg : ks)) == v;
                 }
-                if (b > k) break;
-                k = b - 1;
-                cc = key_cost(key) & 3;
-                ff = key_f(key);
             }
-            a.counts[col] = n;
-            if (n > a.cap) atomicOr(a.err, STIXELS_ERR_CAPACITY);
-            if (a.cost_fixed) a.cost_fixed[col] = best;
+            const unsigned hits = __ballot_sync(0xffffffffu, hit);
+            if (hits) return b0 + __ffs(hits) - 1;
+        }
+        return -1;
+    };
+    int32_t* s_rep = reinterpret_cast<int32_t*>(smem + L.body);    // the report's 4 H words
+    int32_t* top_down = s_rep + 3 * H;
+    int n = 0;
+    for (int k = H - 1, cc = cc0, ff = fb; k >= 0 && cc < 3 && n < H;) {
+        const int32_t v = cc == 0 ? keyo[(size_t)k * F + ff] : kgs[(cc == 1 ? 0 : H) + k];
+        const int bs = find_start(k, cc, ff, v);
+        const int b = bs < 0 ? 0 : bs;                 // (every reached state has a start)
+        if (lane == 0) top_down[n] = (b << 13) | (k << 2) | cc;
+        ++n;
+        const int p = bs < 0 ? 3 : (v & 3);
+        int fp = 0;
+        if (p == 0 && b >= 1) {
+            const int32_t* prow = keyo + (size_t)(b - 1) * F;
+            if (cc == 0) {
+                // the penalised side (f < x) wins ties: its f are the lower
+                const int x = m_index(c, ff);
+                const int2 pr = x > 0 ? row_argmin(prow, 0, x, lane) : make_int2(kBig, -1);
+                const int2 su = x < F ? row_argmin(prow, x, F, lane) : make_int2(kBig, -1);
+                fp = x == 0 ? su.y : (x == F ? pr.y : (pr.x + pen_ord <= su.x ? pr.y : su.y));
+            } else {
+                fp = row_argmin(prow, 0, F, lane).y;
+            }
+            fp = max(fp, 0);
+        }
+        k = b - 1;
+        cc = p;
+        ff = fp;
+    }
+    __syncwarp();
+    stixel_t* out = a.stixels + (size_t)col * a.cap;
+    for (int i = lane; i < n; i += 32) {
+        const int w = top_down[n - 1 - i];
+        s_rep[i] = w;
+        if (i < a.cap) {
+            const int b = w >> 13, k = (w >> 2) & 2047;
+            const int nrows = k - b + 1;
+            const int32_t S = s_pd8[k + 1] - s_pd8[b] - 8 * nrows;
+            stixel_t st;
+            st.row_top = (int16_t)(H - 1 - k);
+            st.row_bottom = (int16_t)(H - 1 - b);
+            st.cls = (uint8_t)(w & 3);
+            st.flags = 0;
+            st.reserved = 0;
+            st.disparity = __fdiv_rn(__int2float_rn(S), __int2float_rn(16 * nrows));
+            out[i] = st;
         }
     }
-    n = __shfl_sync(0xffffffffu, n, 0);
-    feasible = __shfl_sync(0xffffffffu, feasible, 0);
+    if (lane == 0) {
+        a.counts[col] = n;
+        if (n > a.cap) atomicOr(a.err, STIXELS_ERR_CAPACITY);
+        if (a.cost_fixed) a.cost_fixed[col] = best;
+    }
     __syncwarp();
-    if (feasible && a.cost) {
-        // (the scratch covers s_fhi / s_flo: the thresholds come from the row tables)
+    if (a.cost) {
         const int32_t* thr_row = rows_thr(a.rows.fg, H);
         auto thr = [&](int b) {
             const int32_t t = __ldg(thr_row + b);
             return make_int2((int32_t)(int16_t)(t & 0xffff), t >> 16);
         };
-        const long long rc = real_segmentation_cost(s_seg, n, s_pd8, s_div, a, H, lane, thr);
+        const long long rc = real_segmentation_cost(s_rep, n, s_pd8, div, a, H, lane, thr);
         if (lane == 0) a.cost[col] = __ll2float_rn(rc) * (1.0f / kReportUnits);
     }
 }
 
-size_t map_smem_bytes(int H, int F)
-{
-    return sizeof(unsigned long long) * (3 * (size_t)H + 2 * (size_t)kMapRows * F + 4 * kMapRows) +
-           sizeof(uint2) * (size_t)(H + 1) + sizeof(int32_t) * (3 * (size_t)(H + 1) + 2 * (size_t)H);
-}
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
-size_t map_scratch_bytes(int H, int ncols, int F) { return sizeof(unsigned long long) * 3 * (size_t)H * F * ncols; }
+// global scratch: object states [ncols][H][F], ground / sky states
+// [ncols][2][H], the rows of M [ncols][H][m_stride(F)] (int32 each)
+size_t map_scratch_bytes(int H, int ncols, int F)
+{
+    return up256(sizeof(int32_t) * (size_t)H * F * ncols) + up256(sizeof(int32_t) * 2 * (size_t)H * ncols) +
+           sizeof(int32_t) * (size_t)H * m_stride(F) * ncols;
+}
 
-bool map_fits(int H, int F) { return map_smem_bytes(H, F) <= kMapSmemMax; }
+bool map_fits(int H, int F) { return F <= 32 * kPer && map_layout(H, F).total <= kMapSmemMax; }
 
 cudaError_t launch_dp_map(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po,
                           const FrameGeom& g, const ModelDev& m, const RowsDev& r, const RealParams& rp,
@@ -420,10 +533,11 @@ cudaError_t launch_dp_map(const int32_t* pd, const int32_t* pg, const int32_t* p
                           cudaStream_t st)
 {
     if (g.H <= 0 || g.ncols <= 0) return cudaSuccess;
-    if (g.H > STIXELS_MAX_HEIGHT || m.dmax + 1 > 256 || !map_fits(g.H, m.dmax + 1)) return cudaErrorInvalidValue;
+    const int F = m.dmax + 1;
+    if (g.H > STIXELS_MAX_HEIGHT || !map_fits(g.H, F)) return cudaErrorInvalidValue;
     DpArgs a;
     dp_frame_args(pd, pg, ps, po, g, m, r, rp, pixel_floor, out, err, &a);
-    const size_t smem = map_smem_bytes(g.H, m.dmax + 1);
+    const size_t smem = map_layout(g.H, F).total;
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -433,7 +547,12 @@ cudaError_t launch_dp_map(const int32_t* pd, const int32_t* pg, const int32_t* p
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
-    stixel_map_kernel<<<g.ncols, 256, smem, st>>>(a, (unsigned long long*)scratch);
+    char* sp = static_cast<char*>(scratch);
+    int32_t* keyo = reinterpret_cast<int32_t*>(sp);
+    sp += up256(sizeof(int32_t) * (size_t)g.H * F * g.ncols);
+    int32_t* kgs = reinterpret_cast<int32_t*>(sp);
+    sp += up256(sizeof(int32_t) * 2 * (size_t)g.H * g.ncols);
+    stixel_map_kernel<<<g.ncols, kMapWarps * 32, smem, st>>>(a, keyo, kgs, reinterpret_cast<int32_t*>(sp));
     return cudaGetLastError();
 }
 

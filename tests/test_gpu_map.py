@@ -96,14 +96,10 @@ def test_unsupported_paths_refuse_global_map():
         h.compute_noalloc(cuda(np.zeros((cam.height, cam.width), np.float32)), out)
 
 
-def test_global_map_refuses_a_column_state_beyond_shared_memory():
-    """A column's global-MAP state lives in one CTA's shared memory: tall
-    columns with a large dmax are refused (INVALID_ARG), smaller ones run."""
-    cam = scenes.Camera(10, 2048, stixel_width=5, dmax=255, horizon_row=600, baseline_m=0.4, camera_height_m=1.0)
-    h = S.Stixels(S.default_params(cam, global_map=1))
-    with pytest.raises(S.StixelsError):
-        h.compute(cuda(np.zeros((cam.height, cam.width), np.float32)))
-    h.close()
+def test_global_map_tall_columns_with_the_largest_dmax():
+    """A column's global-MAP state (its current block's bins and rows of the
+    ordering table, the state values of every row) lives in one CTA's shared
+    memory; tall columns at dmax 255 fit and match the oracle."""
     cam = scenes.Camera(10, 1800, stixel_width=5, dmax=255, horizon_row=600, baseline_m=0.4, camera_height_m=1.0)
     sc = scenes.make_scene(cam, 7400, n_obstacles=(1, 2), span_cols=(1, 2))
     lp, op = both_params(cam, global_map=1)

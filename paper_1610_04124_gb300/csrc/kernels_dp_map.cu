@@ -48,7 +48,7 @@ constexpr int32_t kNone = INT_MAX;           // a state no candidate has reached
 __device__ __forceinline__ int32_t state_value(int32_t k) { return min(k & ~3, kBig); }
 
 constexpr int kMapRows = 32;                 // rows per block
-constexpr size_t kMapSmemMax = 227 * 1024;   // dynamic shared memory one CTA may use
+constexpr size_t kMapSmemMax = 226 * 1024;   // dynamic shared memory one CTA may use (227 KB less the static)
 constexpr int kMapWarps = 8;
 constexpr int kPer = 8;                      // object states per lane in a row's scan (F <= 256)
 constexpr int kTri = 528;                    // cells (b, k), b <= k, of one block
@@ -159,6 +159,123 @@ __host__ __device__ inline MapLayout map_layout(int H, int F)
     return L;
 }
 
+// Backtracking from the top state (class cc0, mean fb, value best) by one
+// warp: the path's stixels, the output records and counts, and the stixel
+// part of the cost report (priors and per-stixel constants staged in s_rep[H
+// ..4H), the stixel list bottom -> top in s_rep[0..n)); *s_n receives n, or
+// -1 when no cost is reported, *s_acc the priors' sum.
+__device__ __forceinline__ void walk_and_stage(const MapCol& c, const ModelDev& m, const DpArgs& a, int col, int H,
+                                            const int32_t* keyo, const int32_t* kgs, const int32_t* mv,
+                                            int32_t* s_rep, int cc0, int fb, int32_t best, int lane, int* s_n,
+                                            unsigned long long* s_acc)
+{
+    const int F = c.F, P = c.P, MS = m_stride(F);
+    const int32_t pen_ord = m.pen_ord;
+    // The lowest start b <= k whose candidate for the state (k, class cc,
+    // mean f) is v, the state's value (cost | code), by the whole warp: four
+    // rounds of 32 starts per pass, their loads in flight together.
+    auto find_start = [&](int k, int cc, int f, int32_t v) -> int {
+        constexpr int kR = 4;
+        for (int b0 = 0; b0 <= k; b0 += 32 * kR) {
+            int fo[kR];
+            int32_t lo[kR], hi[kR], mx[kR];
+#pragma unroll
+            for (int u = 0; u < kR; ++u) {
+                const int b = min(b0 + 32 * u + lane, k);
+                fo[u] = map_mean(c, b, k);
+                const int32_t* row = c.po + (size_t)fo[u] * P;
+                const bool need = cc != 0 || fo[u] == f;
+                lo[u] = need ? __ldg(row + b) : 0;
+                hi[u] = need ? __ldg(row + k + 1) : 0;
+                mx[u] = need && b > 0 ? mv[(size_t)(b - 1) * MS + m_index(c, fo[u])] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < kR; ++u) {
+                const int b = b0 + 32 * u + lane;
+                bool hit = false;
+                if (b <= k && (cc != 0 || fo[u] == f)) {
+                    int32_t ko, kg, ks;
+                    map_cands(c, m, b, k, fo[u], hi[u] - lo[u], mx[u], ko, kg, ks);
+                    hit = (cc == 0 ? ko : (cc == 1 ? kg : ks)) == v;
+                }
+                const unsigned hits = __ballot_sync(0xffffffffu, hit);
+                if (hits) return b0 + 32 * u + __ffs(hits) - 1;
+            }
+        }
+        return -1;
+    };
+    int32_t* top_down = s_rep + 3 * H;
+    int n = 0;
+    for (int k = H - 1, cc = cc0, ff = fb; k >= 0 && cc < 3 && n < H;) {
+        const int32_t v = cc == 0 ? keyo[(size_t)k * F + ff] : kgs[(cc == 1 ? 0 : H) + k];
+        const int bs = find_start(k, cc, ff, v);
+        const int b = bs < 0 ? 0 : bs;                 // (every reached state has a start)
+        if (lane == 0) top_down[n] = (b << 13) | (k << 2) | cc;
+        ++n;
+        const int p = bs < 0 ? 3 : (v & 3);
+        int fp = 0;
+        if (p == 0 && b >= 1) {
+            const int32_t* prow = keyo + (size_t)(b - 1) * F;
+            if (cc == 0) {
+                // the penalised side (f < x) wins ties: its f are the lower
+                const int x = m_index(c, ff);
+                const int2 pr = x > 0 ? row_argmin(prow, 0, x, lane) : make_int2(kBig, -1);
+                const int2 su = x < F ? row_argmin(prow, x, F, lane) : make_int2(kBig, -1);
+                fp = x == 0 ? su.y : (x == F ? pr.y : (pr.x + pen_ord <= su.x ? pr.y : su.y));
+            } else {
+                fp = row_argmin(prow, 0, F, lane).y;
+            }
+            fp = max(fp, 0);
+        }
+        k = b - 1;
+        cc = p;
+        ff = fp;
+    }
+    __syncwarp();
+    stixel_t* out = a.stixels + (size_t)col * a.cap;
+    for (int i = lane; i < n; i += 32) {
+        const int w = top_down[n - 1 - i];
+        s_rep[i] = w;
+        if (i < a.cap) {
+            const int b = w >> 13, k = (w >> 2) & 2047;
+            const int nrows = k - b + 1;
+            const int32_t S = c.s_pd8[k + 1] - c.s_pd8[b] - 8 * nrows;
+            stixel_t st;
+            st.row_top = (int16_t)(H - 1 - k);
+            st.row_bottom = (int16_t)(H - 1 - b);
+            st.cls = (uint8_t)(w & 3);
+            st.flags = 0;
+            st.reserved = 0;
+            st.disparity = __fdiv_rn(__int2float_rn(S), __int2float_rn(16 * nrows));
+            out[i] = st;
+        }
+    }
+    if (lane == 0) {
+        a.counts[col] = n;
+        if (n > a.cap) atomicOr(a.err, STIXELS_ERR_CAPACITY);
+        if (a.cost_fixed) a.cost_fixed[col] = best;
+    }
+    __syncwarp();
+    if (!a.cost) {
+        if (lane == 0) *s_n = -1;
+        return;
+    }
+    const float* __restrict__ k_obj = real_k_obj(a.rows.real_model);
+    const float* __restrict__ inv_obj = k_obj + F;
+    auto kinv = [&](int f, bool valid) {
+        return valid ? make_float2(__ldg(k_obj + f), __ldg(inv_obj + f)) : make_float2(0.f, 0.f);
+    };
+    auto thr = [&](int b) {
+        const int32_t t = c.s_thr[b];
+        return make_int2((int32_t)(int16_t)(t & 0xffff), t >> 16);
+    };
+    const long long pri = warp_sum64(report_stixels(s_rep, n, c.s_pd8, c.div, a, H, lane, kinv, thr));
+    if (lane == 0) {
+        *s_acc = (unsigned long long)pri;
+        *s_n = n;
+    }
+}
+
 __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, int32_t* keyo_all, int32_t* kgs_all,
                                                                    int32_t* mv_all)
 {
@@ -185,6 +302,14 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, in
     int32_t* s_trid = reinterpret_cast<int32_t*>(smem + L.trid);   // [2][kTri] object data cost of the block's cells
     uint8_t* s_trif = smem + L.trif;                                // [2][kTri] their means
     const uint2* div = reinterpret_cast<const uint2*>(kDivTable.v);
+    // a copy of the arguments in shared memory for the column's tail (which
+    // reads many of them, once each)
+    __shared__ DpArgs s_args;
+    {
+        const int* src = reinterpret_cast<const int*>(&a);
+        int* dst = reinterpret_cast<int*>(&s_args);
+        for (int i = tid; i < (int)(sizeof(DpArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
 
     for (int v = tid; v <= H; v += blockDim.x) {
         s_pd8[v] = a.pd[(size_t)col * P + v] + 8 * v;
@@ -273,9 +398,11 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, in
         atomicMin(&sbin[lane], rs);
     };
 
-    // bins of blocks 0 and 1 (double-buffered by block parity), block 0's triangle
+    // bins of blocks 0 and 1 (double-buffered by block parity), then block 0's
+    // triangle (which reads the prefix arrays staged above)
     for (int i = tid; i < 2 * (int)BF; i += blockDim.x) s_bin[i] = kNone;
     if (tid < 2 * kMapRows) { s_gbin[tid] = kNone; s_sbin[tid] = kNone; }
+    __syncthreads();
     gather_tri(0, 0, min(kMapRows, H), warp, kMapWarps);
     __syncthreads();
     for (int j = 0; j < NB; ++j) {
@@ -308,19 +435,22 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, in
                     const int32_t mx = b == 0 ? 0 : s_ring[lane * MS + m_index(c, fo)];
                     map_cands(c, m, b, k, fo, tri_d[e], mx, ko, kg, ks);
                 }
-                // consecutive starts mostly share their mean: a scan over the
-                // lanes combines the candidates of equal f (a lane takes a
-                // lane below it only if that one has its f, which keeps every
-                // minimum in its bin), so that the last lane of each run of
-                // equal f alone updates the bin
+                // consecutive starts mostly share their mean: two rounds of
+                // a scan over the lanes combine the candidates of equal f
+                // within aligned groups of four lanes (a lane takes a lane
+                // below it only if that one has its f, which keeps every
+                // minimum in its bin), so that one lane per group and run
+                // updates the bin (measured against a full scan and against
+                // none: 1024x440 330 / 356 / 326 us, 2048x880 1613 / 1654 /
+                // 1736 us)
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
+                for (int o = 1; o < 4; o <<= 1) {
                     const int32_t u = __shfl_up_sync(0xffffffffu, ko, o);
                     const int fu = __shfl_up_sync(0xffffffffu, fo, o);
                     if (lane >= o && fu == fo) ko = min(ko, u);
                 }
                 const int fn = __shfl_down_sync(0xffffffffu, fo, 1);
-                if (lane <= r && (lane == 31 || fn != fo)) atomicMin(&bin_j[r * F + fo], ko);
+                if (lane <= r && (lane == 31 || fn != fo || (lane & 3) == 3)) atomicMin(&bin_j[r * F + fo], ko);
                 kg = min(__reduce_min_sync(0xffffffffu, kg), gbin_j[r]);
                 ks = min(__reduce_min_sync(0xffffffffu, ks), sbin_j[r]);
                 __syncwarp();
@@ -410,107 +540,37 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, in
         __syncthreads();
     }
 
-    // top row (lexicographic cost, class, f) and backtracking, by warp 0,
-    // then the cost report in real arithmetic
-    if (warp != 0) return;
-    const int2 ob = row_argmin(keyo + (size_t)(H - 1) * F, 0, F, lane);
-    int cc0 = ob.x < kBig ? 0 : -1, fb = max(ob.y, 0);
-    int32_t best = ob.x;
-    if (s_gv[H - 1] < best) { best = s_gv[H - 1]; cc0 = 1; fb = 0; }
-    if (s_sv[H - 1] < best) { best = s_sv[H - 1]; cc0 = 2; fb = 0; }
-    if (cc0 < 0 || best >= kBig) {
-        if (lane == 0) {
-            a.counts[col] = 0;
-            if (a.cost) a.cost[col] = __int_as_float(0x7f800000);
-            if (a.cost_fixed) a.cost_fixed[col] = kBig;
-            atomicOr(a.err, STIXELS_ERR_INFEASIBLE);
-        }
-        return;
-    }
-    // The lowest start b <= k whose candidate for the state (k, class cc,
-    // mean f) is v, the state's value (cost | code), by the whole warp.
-    auto find_start = [&](int k, int cc, int f, int32_t v) -> int {
-        for (int b0 = 0; b0 <= k; b0 += 32) {
-            const int b = b0 + lane;
-            bool hit = false;
-            if (b <= k) {
-                const int fo = map_mean(c, b, k);
-                if (cc != 0 || fo == f) {
-                    const int32_t* row = c.po + (size_t)fo * P;
-                    const int32_t d_o = __ldg(row + k + 1) - __ldg(row + b);
-                    const int32_t mx = b == 0 ? 0 : mv[(size_t)(b - 1) * MS + m_index(c, fo)];
-                    int32_t ko, kg, ks;
-                    map_cands(c, m, b, k, fo, d_o, mx, ko, kg, ks);
-                    hit = (cc == 0 ? ko : (cc == 1 ? kg : ks)) == v;
-                }
-            }
-            const unsigned hits = __ballot_sync(0xffffffffu, hit);
-            if (hits) return b0 + __ffs(hits) - 1;
-        }
-        return -1;
-    };
+    // top row (lexicographic cost, class, f) and backtracking by warp 0, its
+    // records and the stixel part of the cost report; then every warp takes
+    // its blocks of rows of the report
+    __shared__ int s_n;                              // stixels on the path (-1: no report)
+    __shared__ unsigned long long s_acc;             // the report's sum, 2^-24 units
     int32_t* s_rep = reinterpret_cast<int32_t*>(smem + L.body);    // the report's 4 H words
-    int32_t* top_down = s_rep + 3 * H;
-    int n = 0;
-    for (int k = H - 1, cc = cc0, ff = fb; k >= 0 && cc < 3 && n < H;) {
-        const int32_t v = cc == 0 ? keyo[(size_t)k * F + ff] : kgs[(cc == 1 ? 0 : H) + k];
-        const int bs = find_start(k, cc, ff, v);
-        const int b = bs < 0 ? 0 : bs;                 // (every reached state has a start)
-        if (lane == 0) top_down[n] = (b << 13) | (k << 2) | cc;
-        ++n;
-        const int p = bs < 0 ? 3 : (v & 3);
-        int fp = 0;
-        if (p == 0 && b >= 1) {
-            const int32_t* prow = keyo + (size_t)(b - 1) * F;
-            if (cc == 0) {
-                // the penalised side (f < x) wins ties: its f are the lower
-                const int x = m_index(c, ff);
-                const int2 pr = x > 0 ? row_argmin(prow, 0, x, lane) : make_int2(kBig, -1);
-                const int2 su = x < F ? row_argmin(prow, x, F, lane) : make_int2(kBig, -1);
-                fp = x == 0 ? su.y : (x == F ? pr.y : (pr.x + pen_ord <= su.x ? pr.y : su.y));
-            } else {
-                fp = row_argmin(prow, 0, F, lane).y;
+    if (warp == 0) {
+        const int2 ob = row_argmin(keyo + (size_t)(H - 1) * F, 0, F, lane);
+        int cc0 = ob.x < kBig ? 0 : -1, fb = max(ob.y, 0);
+        int32_t best = ob.x;
+        if (s_gv[H - 1] < best) { best = s_gv[H - 1]; cc0 = 1; fb = 0; }
+        if (s_sv[H - 1] < best) { best = s_sv[H - 1]; cc0 = 2; fb = 0; }
+        if (cc0 < 0 || best >= kBig) {
+            if (lane == 0) {
+                a.counts[col] = 0;
+                if (a.cost) a.cost[col] = __int_as_float(0x7f800000);
+                if (a.cost_fixed) a.cost_fixed[col] = kBig;
+                atomicOr(a.err, STIXELS_ERR_INFEASIBLE);
+                s_n = -1;
             }
-            fp = max(fp, 0);
-        }
-        k = b - 1;
-        cc = p;
-        ff = fp;
-    }
-    __syncwarp();
-    stixel_t* out = a.stixels + (size_t)col * a.cap;
-    for (int i = lane; i < n; i += 32) {
-        const int w = top_down[n - 1 - i];
-        s_rep[i] = w;
-        if (i < a.cap) {
-            const int b = w >> 13, k = (w >> 2) & 2047;
-            const int nrows = k - b + 1;
-            const int32_t S = s_pd8[k + 1] - s_pd8[b] - 8 * nrows;
-            stixel_t st;
-            st.row_top = (int16_t)(H - 1 - k);
-            st.row_bottom = (int16_t)(H - 1 - b);
-            st.cls = (uint8_t)(w & 3);
-            st.flags = 0;
-            st.reserved = 0;
-            st.disparity = __fdiv_rn(__int2float_rn(S), __int2float_rn(16 * nrows));
-            out[i] = st;
+        } else {
+            walk_and_stage(c, s_args.m, s_args, col, H, keyo, kgs, mv, s_rep, cc0, fb, best, lane, &s_n, &s_acc);
         }
     }
-    if (lane == 0) {
-        a.counts[col] = n;
-        if (n > a.cap) atomicOr(a.err, STIXELS_ERR_CAPACITY);
-        if (a.cost_fixed) a.cost_fixed[col] = best;
-    }
-    __syncwarp();
-    if (a.cost) {
-        const int32_t* thr_row = rows_thr(a.rows.fg, H);
-        auto thr = [&](int b) {
-            const int32_t t = __ldg(thr_row + b);
-            return make_int2((int32_t)(int16_t)(t & 0xffff), t >> 16);
-        };
-        const long long rc = real_segmentation_cost(s_rep, n, s_pd8, div, a, H, lane, thr);
-        if (lane == 0) a.cost[col] = __ll2float_rn(rc) * (1.0f / kReportUnits);
-    }
+    __syncthreads();
+    const int n = s_n;
+    if (n < 0) return;
+    const long long sum = warp_sum64(report_rows(s_rep, n, s_pd8, s_args, H, lane, warp, kMapWarps, nullptr));
+    if (lane == 0) atomicAdd(&s_acc, (unsigned long long)sum);
+    __syncthreads();
+    if (tid == 0) a.cost[col] = __ll2float_rn((long long)s_acc) * (1.0f / kReportUnits);
 }
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }

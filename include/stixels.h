@@ -118,15 +118,18 @@ typedef struct stixels_params {
     float sigma_mid;
     float sigma_width;
     int32_t ground_estimate;   /* 0 = ground line from the camera parameters (default); 1 = estimated
-                                  for every frame from its v-disparity (stixels_estimate_ground),
-                                  per-frame path only (stixels_compute / _compute_host); needs
-                                  sigma_gain = 0 and ncols * H <= 7,000,000 */
+                                  for every frame from its v-disparity (stixels_estimate_ground), by
+                                  stixels_compute / _compute_host and in batches and the server (not
+                                  by stixels_compute_noalloc); needs sigma_gain = 0 and
+                                  ncols * H <= 7,000,000 */
     int32_t global_map;        /* 0 = the paper's DP (Eq. 6: one best stixel per row and class, so the
                                   ordering prior is judged against that stixel only); 1 = the global MAP
-                                  with the ordering prior exact (object states carry their disparity;
-                                  per-frame path only, 24 H (dmax+1) bytes of workspace per column;
-                                  compute / solve return INVALID_ARG when a column's shared-memory
-                                  state, about 52 H + 512 (dmax+1) bytes, exceeds 227 KB) */
+                                  with the ordering prior exact (object states carry their disparity),
+                                  by stixels_compute / _compute_host / _solve and in batches and the
+                                  server (not by stixels_compute_noalloc); about 8 H (dmax+3) bytes of
+                                  workspace per column; a column's shared-memory state, about
+                                  28 H + 388 (dmax+1) + 6 KB bytes, fits every height and dmax the
+                                  library takes */
 } stixels_params_t;
 
 /* One output stixel: 12 bytes. */

@@ -128,9 +128,6 @@ int check_frame(stixels_t h, int H, int W)
     return STIXELS_OK;
 }
 
-// The ground estimate's int32 votes stay below 289 ncols H (the smoothing
-// kernel's weight times every column of every row).
-bool ground_size_ok(const FrameGeom& g) { return (int64_t)g.ncols * g.H <= 7000000; }
 
 FrameGeom geom(stixels_t h, int H, int W)
 {
@@ -187,6 +184,8 @@ int handle_view(stixels_t h, int H, HandleView* v)
     v->reduce_mode = reduce_code(h->hm.p);
     v->ground_estimate = h->hm.p.ground_estimate;
     v->global_map = h->hm.p.global_map;
+    v->est_pool = h->est_pool;
+    v->est_gw = h->hm.est_gw;
     v->capacity = h->hm.p.max_stixels_per_col;
     return STIXELS_OK;
 }

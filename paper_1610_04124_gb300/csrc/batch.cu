@@ -18,22 +18,33 @@ namespace {
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 }  // namespace
 
-size_t frame_work_bytes(const FrameGeom& g, int dmax)
+namespace {
+size_t ground_bytes(const FrameGeom& g, const HandleView& v)
 {
-    const size_t C = (size_t)g.ncols, P = (size_t)g.P, F = (size_t)dmax + 1;
-    return up256(sizeof(int16_t) * C * g.H) + 3 * up256(sizeof(int32_t) * C * P) + up256(sizeof(int32_t) * C * F * P);
+    return v.ground_estimate ? up256(ground_work_bytes(g.H, v.model.dmax, v.est_gw)) : 0;
+}
+}  // namespace
+
+size_t frame_work_bytes(const FrameGeom& g, const HandleView& v)
+{
+    const size_t C = (size_t)g.ncols, P = (size_t)g.P, F = (size_t)v.model.dmax + 1;
+    return up256(sizeof(int16_t) * C * g.H) + 3 * up256(sizeof(int32_t) * C * P) + up256(sizeof(int32_t) * C * F * P) +
+           ground_bytes(g, v) + (v.global_map ? up256(map_scratch_bytes(g.H, g.ncols, (int)F)) : 0);
 }
 
 void frame_work_carve(FrameJob* job, char* base)
 {
     const FrameGeom& g = job->g;
-    const size_t C = (size_t)g.ncols, P = (size_t)g.P;
+    const size_t C = (size_t)g.ncols, P = (size_t)g.P, F = (size_t)job->view.model.dmax + 1;
     size_t off = 0;
     job->q = (int16_t*)(base + off);  off += up256(sizeof(int16_t) * C * g.H);
     job->pd = (int32_t*)(base + off); off += up256(sizeof(int32_t) * C * P);
     job->pg = (int32_t*)(base + off); off += up256(sizeof(int32_t) * C * P);
     job->ps = (int32_t*)(base + off); off += up256(sizeof(int32_t) * C * P);
-    job->po = (int32_t*)(base + off);
+    job->po = (int32_t*)(base + off); off += up256(sizeof(int32_t) * C * F * P);
+    job->ground_work = job->view.ground_estimate ? base + off : nullptr;
+    off += ground_bytes(g, job->view);
+    job->map_scratch = job->view.global_map ? base + off : nullptr;
 }
 
 void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
@@ -48,25 +59,36 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
     t->maxH = t->max_groups = 0;
     t->lut_smem = 0;
     t->std_trans = true;
+    t->ground_frames.clear();
+    t->map_frames.clear();
+    t->jobs = jobs;
     for (int i = 0; i < n; ++i) {
         const FrameJob& f = jobs[i];
         const ModelDev& m = f.view.model;
+        // a frame with its ground estimated reads the row tables its ground
+        // kernels write into its work block
+        const RowsDev rows = f.view.ground_estimate
+                                 ? ground_frame_rows(f.g, m.dmax, f.view.rows, f.view.est_gw, f.ground_work)
+                                 : f.view.rows;
         ra[i].disp = f.in;
         ra[i].H = f.g.H; ra[i].W = f.g.W; ra[i].ncols = f.g.ncols; ra[i].dmax = m.dmax;
         ra[i].q = f.q;
         la[i].q = f.q;
-        la[i].H = f.g.H; la[i].P = f.g.P; la[i].F = m.dmax + 1; la[i].m = m; la[i].rows = f.view.rows;
+        la[i].H = f.g.H; la[i].P = f.g.P; la[i].F = m.dmax + 1; la[i].m = m; la[i].rows = rows;
         la[i].pd = f.pd; la[i].pg = f.pg; la[i].ps = f.ps; la[i].po = f.po;
-        dp_frame_args(f.pd, f.pg, f.ps, f.po, f.g, m, f.view.rows, f.view.rp, f.view.pixel_floor, f.out, f.view.err,
-                      &da[i]);
+        dp_frame_args(f.pd, f.pg, f.ps, f.po, f.g, m, rows, f.view.rp, f.view.pixel_floor, f.out, f.view.err, &da[i]);
         if (f.g.ncols == 0) continue;
-        t->maxH = std::max(t->maxH, f.g.H);
+        if (f.view.ground_estimate) t->ground_frames.push_back(i);
         t->max_groups = std::max(t->max_groups, lut_row_groups(m.dmax + 1));
         t->lut_smem = std::max(t->lut_smem, lut_shared_bytes(f.g.H, m));
-        t->std_trans = t->std_trans && m.trans[1][1] >= kBig && m.trans[1][2] >= kBig && m.trans[2][2] >= kBig;
-        for (int c = 0; c < f.g.ncols; ++c) {
-            lut_items.push_back(make_int2(i, c));
-            dp_items.push_back(make_int2(i, c));
+        for (int c = 0; c < f.g.ncols; ++c) lut_items.push_back(make_int2(i, c));
+        if (f.view.global_map) {
+            // its own DP launch (the global MAP), after the persistent DP
+            t->map_frames.push_back(i);
+        } else {
+            t->maxH = std::max(t->maxH, f.g.H);
+            t->std_trans = t->std_trans && m.trans[1][1] >= kBig && m.trans[1][2] >= kBig && m.trans[2][2] >= kBig;
+            for (int c = 0; c < f.g.ncols; ++c) dp_items.push_back(make_int2(i, c));
         }
         int gi = -1;
         for (size_t k = 0; k < t->groups.size(); ++k)
@@ -83,6 +105,7 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
     std::stable_sort(dp_items.begin(), dp_items.end(),
                      [&](const int2& x, const int2& y) { return jobs[x.x].g.H > jobs[y.x].g.H; });
     t->nitems = (int)dp_items.size();
+    t->nlut = (int)lut_items.size();
 
     size_t o = 0;
     t->o_red = o; o += up256(sizeof(ReduceArgs) * n);
@@ -116,13 +139,32 @@ cudaError_t enqueue_tables(const BatchTables& t, char* d_tab, int dp_warps, int 
         e = launch_reduce_batch((const ReduceArgs*)(d_tab + t.o_red), (const int4*)(d_tab + gr.tiles_off), gr.ntiles,
                                 gr.s, gr.mode, st);
     }
+    // frames that estimate their ground line: its kernels write the frame's
+    // row tables, which the LUT and DP arguments already point to
+    for (int i : t.ground_frames) {
+        if (e != cudaSuccess) return e;
+        const FrameJob& f = t.jobs[i];
+        RowsDev fr;
+        e = launch_ground(f.q, f.g, f.view.model, f.view.rows, f.view.est_pool, f.view.est_gw, f.ground_work, &fr,
+                          nullptr, st);
+    }
     if (e == cudaSuccess)
-        e = launch_luts_batch((const LutArgs*)(d_tab + t.o_lut), (const int2*)(d_tab + t.o_li), t.nitems, t.max_groups,
+        e = launch_luts_batch((const LutArgs*)(d_tab + t.o_lut), (const int2*)(d_tab + t.o_li), t.nlut, t.max_groups,
                               t.lut_smem, st);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && t.nitems > 0) {
         const int grid = std::max(1, std::min(t.nitems, sm_count() * dp_ctas_per_sm));
         e = launch_dp_batch((const DpArgs*)(d_tab + t.o_dp), (const int2*)(d_tab + t.o_di), t.nitems, counter, t.maxH,
                             dp_warps, dp_ctas_per_sm, t.std_trans, grid, st);
+    }
+    // frames solved by the global MAP: one launch each
+    for (int i : t.map_frames) {
+        if (e != cudaSuccess) return e;
+        const FrameJob& f = t.jobs[i];
+        const RowsDev rows = f.view.ground_estimate
+                                 ? ground_frame_rows(f.g, f.view.model.dmax, f.view.rows, f.view.est_gw, f.ground_work)
+                                 : f.view.rows;
+        e = launch_dp_map(f.pd, f.pg, f.ps, f.po, f.g, f.view.model, rows, f.view.rp, f.view.pixel_floor, f.out,
+                          f.view.err, f.map_scratch, st);
     }
     return e;
 }
@@ -160,6 +202,8 @@ namespace {
 int capture(stixels_batch_t b)
 {
     cudaError_t pe = prepare_dp_kernels();
+    if (pe == cudaSuccess) pe = prepare_ground_kernels();
+    if (pe == cudaSuccess) pe = prepare_map_kernel();
     if (pe != cudaSuccess) return status_from_cuda(pe);
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
@@ -183,7 +227,8 @@ std::string batch_signature(stixels_batch_t b)
     std::vector<std::string> parts;
     for (const FramePlan& f : b->frames) {
         char buf[96];
-        snprintf(buf, sizeof(buf), "%dx%d/s%d/d%d", f.job.g.W, f.job.g.H, f.job.g.s, f.job.view.model.dmax);
+        snprintf(buf, sizeof(buf), "%dx%d/s%d/d%d%s%s", f.job.g.W, f.job.g.H, f.job.g.s, f.job.view.model.dmax,
+                 f.job.view.ground_estimate ? "/e" : "", f.job.view.global_map ? "/m" : "");
         parts.push_back(buf);
     }
     std::sort(parts.begin(), parts.end());
@@ -219,13 +264,17 @@ int stixels_batch_create(const stixels_frame_desc_t* frames, int nframes, stixel
         FramePlan f;
         int rc = handle_prepare(d.camera, d.H, &f.job.view);
         if (rc != STIXELS_OK) { delete b; return rc; }
-        if (f.job.view.ground_estimate || f.job.view.global_map) { delete b; return STIXELS_E_INVALID_ARG; }   // per-frame path only
         if (f.job.view.device != b->device) { delete b; return STIXELS_E_INVALID_ARG; }
         FrameGeom& g = f.job.g;
         g.H = d.H; g.W = d.W; g.s = f.job.view.stixel_width; g.ncols = d.W / g.s; g.P = lut_pitch(d.H);
+        if ((f.job.view.ground_estimate && !ground_size_ok(g)) ||
+            (f.job.view.global_map && !map_fits(g.H, f.job.view.model.dmax + 1))) {
+            delete b;
+            return STIXELS_E_INVALID_ARG;
+        }
         const size_t C = (size_t)g.ncols;
         f.in_off = off;   off += up256b(sizeof(float) * (size_t)d.H * d.W);
-        f.work_off = off; off += frame_work_bytes(g, f.job.view.model.dmax);
+        f.work_off = off; off += frame_work_bytes(g, f.job.view);
         f.st_off = off;   off += up256b(sizeof(stixel_t) * C * f.job.view.capacity);
         f.cnt_off = off;  off += up256b(sizeof(int32_t) * C);
         f.cost_off = off; off += up256b(sizeof(float) * C);

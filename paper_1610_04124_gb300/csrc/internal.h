@@ -206,8 +206,10 @@ struct HandleView {
     uint32_t* err;
     int stixel_width, capacity;
     int reduce_mode;            // reduce_code of the params: bit 0 mean, bit 1 whole-pixel grid
-    int ground_estimate;        // the handle estimates its ground per frame (per-frame path only)
-    int global_map;             // the handle solves the global MAP (per-frame path only)
+    int ground_estimate;        // the handle estimates its ground per frame
+    int global_map;             // the handle solves the global MAP
+    const int32_t* est_pool;    // ground estimate: the residual windows of estimated lines
+    int est_gw;                 // their codes per window
 };
 int handle_view(stixels_t h, int H, HandleView* v);
 // stixels status for a CUDA error, remembering its text for stixels_last_cuda_error()
@@ -244,11 +246,14 @@ struct FrameJob {
     const float* in;
     int16_t* q;
     int32_t *pd, *pg, *ps, *po;
+    char* ground_work;          // ground estimate: the frame's v-disparity work and row tables
+    void* map_scratch;          // global MAP: the DP's scratch
     stixels_output_t out;
 };
-// Bytes of intermediates (q, PD, PG, PS, PO) a frame needs, and their carving
-// from one 256-byte-aligned block.
-size_t frame_work_bytes(const FrameGeom& g, int dmax);
+// Bytes of intermediates (q, PD, PG, PS, PO, and the ground-estimate work and
+// global-MAP scratch when the view asks for them) a frame needs, and their
+// carving from one 256-byte-aligned block.
+size_t frame_work_bytes(const FrameGeom& g, const HandleView& v);
 void frame_work_carve(FrameJob* job, char* base);
 struct ReduceGroup {            // frames sharing stixel width and reduction mode
     int s, mode;
@@ -261,8 +266,12 @@ struct BatchTables {
     size_t o_red = 0, o_lut = 0, o_dp = 0, o_li = 0, o_di = 0, o_cnt = 0;
     std::vector<ReduceGroup> groups;
     int nitems = 0, max_groups = 0, maxH = 0;
+    int nlut = 0;               // LUT work items (every frame's columns)
     size_t lut_smem = 0;
     bool std_trans = true;
+    std::vector<int> ground_frames;   // frames whose ground line is estimated (launched per frame)
+    std::vector<int> map_frames;      // frames solved by the global MAP (launched per frame)
+    std::vector<FrameJob> jobs;       // the frames, for those launches
 };
 void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t);
 // Launches all stages for tables already copied to d_tab (counter reset included).
@@ -275,6 +284,12 @@ cudaError_t enqueue_tables(const BatchTables& t, char* d_tab, int dp_warps, int 
 // the frame's tables inside `work`; line, if not null, receives {k, horizon
 // row, votes} on the device).
 size_t ground_work_bytes(int H, int dmax, int gw);
+// The ground estimate's int32 votes stay below 289 ncols H (the smoothing
+// kernel's weight times every column of every row).
+inline bool ground_size_ok(const FrameGeom& g) { return (int64_t)g.ncols * g.H <= 7000000; }
+// The frame's row tables that launch_ground writes inside `work`.
+RowsDev ground_frame_rows(const FrameGeom& g, int dmax, const RowsDev& cam, int est_gw, char* work);
+cudaError_t prepare_ground_kernels();
 cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& m, RowsDev cam,
                           const int32_t* est_pool, int est_gw, char* work, RowsDev* frame_rows, int32_t* line,
                           cudaStream_t st);
@@ -284,9 +299,11 @@ size_t map_scratch_bytes(int H, int ncols, int F);
 // One CTA whose bounded wait (the DP kernels' own) runs out after `limit` polls.
 cudaError_t launch_wait_selftest(uint32_t* err, int limit, cudaStream_t st);
 // Whether a column of height H with F object disparities fits the global-MAP
-// kernel's shared memory (227 KB per CTA; false only for tall columns with a
-// large dmax, e.g. H > 1900 at dmax 255).
+// kernel's shared memory (226 KB of dynamic shared memory per CTA; every
+// column the library takes, up to 2048 rows at dmax 255, does).
 bool map_fits(int H, int F);
+// Sets the global-MAP kernel's shared-memory attribute (call outside stream capture).
+cudaError_t prepare_map_kernel();
 cudaError_t launch_dp_map(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po,
                           const FrameGeom& g, const ModelDev& m, const RowsDev& r, const RealParams& rp,
                           int32_t pixel_floor, const stixels_output_t& out, uint32_t* err, void* scratch,

@@ -587,6 +587,20 @@ size_t map_scratch_bytes(int H, int ncols, int F)
 
 bool map_fits(int H, int F) { return F <= 32 * kPer && map_layout(H, F).total <= kMapSmemMax; }
 
+cudaError_t prepare_map_kernel()
+{
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        e = cudaFuncSetAttribute(stixel_map_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMapSmemMax);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_dp_map(const int32_t* pd, const int32_t* pg, const int32_t* ps, const int32_t* po,
                           const FrameGeom& g, const ModelDev& m, const RowsDev& r, const RealParams& rp,
                           int32_t pixel_floor, const stixels_output_t& out, uint32_t* err, void* scratch,
@@ -598,15 +612,8 @@ cudaError_t launch_dp_map(const int32_t* pd, const int32_t* pg, const int32_t* p
     DpArgs a;
     dp_frame_args(pd, pg, ps, po, g, m, r, rp, pixel_floor, out, err, &a);
     const size_t smem = map_layout(g.H, F).total;
-    static bool attr_set[64] = {false};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    cudaError_t e = prepare_map_kernel();
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        e = cudaFuncSetAttribute(stixel_map_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMapSmemMax);
-        if (e != cudaSuccess) return e;
-        attr_set[dev] = true;
-    }
     char* sp = static_cast<char*>(scratch);
     int32_t* keyo = reinterpret_cast<int32_t*>(sp);
     sp += up256(sizeof(int32_t) * (size_t)g.H * F * g.ncols);

@@ -301,24 +301,22 @@ size_t ground_work_bytes(int H, int dmax, int gw)
            sizeof(int32_t) * (size_t)(H > 16 ? H : 16) * gw;
 }
 
-cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& m, RowsDev cam,
-                          const int32_t* est_pool, int est_gw, char* work, RowsDev* frame_rows, int32_t* line,
-                          cudaStream_t st)
+// Layout of the work block: smoothed v-disparity, best vote, own line, the
+// frame's row tables, its residual windows.
+RowsDev ground_frame_rows(const FrameGeom& g, int dmax, const RowsDev& cam, int est_gw, char* work)
 {
-    // cam is a copy: frame_rows may be the caller's camera rows themselves
-    if (!est_pool || est_gw != cam.gw) return cudaErrorInvalidValue;
-    const size_t E = 16 * (size_t)m.dmax + 1;
-    int32_t* smooth = (int32_t*)work;
-    unsigned long long* best = (unsigned long long*)(work + smooth_bytes(g.H, m.dmax));
-    int32_t* own_line = (int32_t*)((char*)best + 256);
-    double* rows = (double*)((char*)own_line + 256);
-    int32_t* pool = (int32_t*)((char*)rows + frame_rows_bytes(g.H));
-    frame_rows->fg = rows;
-    frame_rows->real_model = cam.real_model;
-    frame_rows->gpool = pool;
-    frame_rows->gw = est_gw;
-    frame_rows->gn = (g.H > 16 ? g.H : 16) * est_gw;
-    const size_t smem = sizeof(int32_t) * kVdispRows * vdisp_pitch((int)E);
+    char* rows = work + smooth_bytes(g.H, dmax) + 256 + 256;
+    RowsDev r;
+    r.fg = reinterpret_cast<const double*>(rows);
+    r.real_model = cam.real_model;
+    r.gpool = reinterpret_cast<const int32_t*>(rows + frame_rows_bytes(g.H));
+    r.gw = est_gw;
+    r.gn = (g.H > 16 ? g.H : 16) * est_gw;
+    return r;
+}
+
+cudaError_t prepare_ground_kernels()
+{
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -330,6 +328,25 @@ cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& 
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
+    return cudaSuccess;
+}
+
+cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& m, RowsDev cam,
+                          const int32_t* est_pool, int est_gw, char* work, RowsDev* frame_rows, int32_t* line,
+                          cudaStream_t st)
+{
+    // cam is a copy: frame_rows may be the caller's camera rows themselves
+    if (!est_pool || est_gw != cam.gw) return cudaErrorInvalidValue;
+    const size_t E = 16 * (size_t)m.dmax + 1;
+    int32_t* smooth = (int32_t*)work;
+    unsigned long long* best = (unsigned long long*)(work + smooth_bytes(g.H, m.dmax));
+    int32_t* own_line = (int32_t*)((char*)best + 256);
+    *frame_rows = ground_frame_rows(g, m.dmax, cam, est_gw, work);
+    double* rows = const_cast<double*>(frame_rows->fg);
+    int32_t* pool = const_cast<int32_t*>(frame_rows->gpool);
+    const size_t smem = sizeof(int32_t) * kVdispRows * vdisp_pitch((int)E);
+    cudaError_t e = prepare_ground_kernels();
+    if (e != cudaSuccess) return e;
     vdisp_kernel<<<(g.H + kVdispRows - 1) / kVdispRows, 256, smem, st>>>(q, g.H, g.ncols, m.dmax, smooth, best);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

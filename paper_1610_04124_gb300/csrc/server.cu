@@ -189,7 +189,7 @@ void scheduler(stixels_server_t s)
             memcpy(s->h_staging[k], t.host.data(), t.host.size());
             e = cudaMemcpyAsync(s->d_tables[k], s->h_staging[k], t.host.size(), cudaMemcpyHostToDevice, s->streams[k]);
         }
-        if (e == cudaSuccess && t.nitems > 0) e = enqueue_tables(t, s->d_tables[k], 8, 2, s->streams[k]);
+        if (e == cudaSuccess && t.nlut > 0) e = enqueue_tables(t, s->d_tables[k], 8, 2, s->streams[k]);
         if (e == cudaSuccess) e = cudaEventRecord(it->done, s->streams[k]);
         const int launch_status = e == cudaSuccess ? STIXELS_OK : status_of(e);
         if (e != cudaSuccess && it->done) cudaEventRecord(it->done, s->streams[k]);   // polls must still return
@@ -230,6 +230,8 @@ int stixels_server_create(size_t mem_budget_bytes, int max_slots, stixels_server
     if (e == cudaSuccess) e = cudaHostAlloc(&s->h_flags, sizeof(uint32_t) * max_slots, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&s->d_flags, s->h_flags, 0);
     if (e == cudaSuccess) e = prepare_dp_kernels();
+    if (e == cudaSuccess) e = prepare_ground_kernels();
+    if (e == cudaSuccess) e = prepare_map_kernel();
     if (e != cudaSuccess) {
         stixels_server_destroy(s);
         return status_of(e);
@@ -253,13 +255,15 @@ int stixels_submit(stixels_server_t s, stixels_t camera, const float* disparity,
         s->stats.submitted += 1;
         int rc = handle_prepare(camera, H, &r->job.view);
         if (rc != STIXELS_OK) return rc;
-        if (r->job.view.ground_estimate || r->job.view.global_map) return STIXELS_E_INVALID_ARG;   // per-frame path only
         if (r->job.view.device != s->device) return STIXELS_E_INVALID_ARG;
         FrameGeom& g = r->job.g;
         g.H = H; g.W = W; g.s = r->job.view.stixel_width; g.ncols = W / g.s; g.P = lut_pitch(H);
+        if ((r->job.view.ground_estimate && !ground_size_ok(g)) ||
+            (r->job.view.global_map && !map_fits(H, r->job.view.model.dmax + 1)))
+            return STIXELS_E_INVALID_ARG;
         const size_t C = (size_t)g.ncols, cap = (size_t)r->job.view.capacity;
         const size_t in_b = up256(sizeof(float) * (size_t)H * W);
-        const size_t work_b = frame_work_bytes(g, r->job.view.model.dmax);
+        const size_t work_b = frame_work_bytes(g, r->job.view);
         const size_t out_b = up256(sizeof(stixel_t) * C * cap) + 3 * up256(sizeof(int32_t) * C) + 256;
         r->bytes = in_b + work_b + out_b;
         if ((int)s->requests.size() >= s->max_slots || !s->arena->alloc(r->bytes, &r->off)) {

@@ -1,7 +1,8 @@
 """The frame's ground line from its v-disparity (the step before the path):
 the estimate (slope, horizon, votes) and whole frames computed with it must
 equal the oracle's exactly; the camera's line is kept when nothing votes; the
-paths that do not support the estimate refuse it."""
+paths that do not support the estimate refuse it (batched and served frames:
+test_gpu_batch_variants.py)."""
 import numpy as np
 import pytest
 
@@ -124,12 +125,6 @@ def test_unsupported_paths_refuse_the_estimate():
     with pytest.raises(S.StixelsError):
         S.Stixels(S.default_params(cam, ground_estimate=1, sigma_gain=0.5))
     h = S.Stixels(S.default_params(cam, ground_estimate=1))
-    with pytest.raises(S.StixelsError):
-        S.Batch([(h, cam.height, cam.width)])
-    srv = S.Server(64 << 20, max_slots=2)
-    with pytest.raises(S.StixelsError):
-        srv.submit(h, np.zeros((cam.height, cam.width), np.float32))
-    srv.close()
     h.reserve(cam.height, cam.width)
     out = h.alloc_output(cam.height, cam.width)
     with pytest.raises(S.StixelsError):

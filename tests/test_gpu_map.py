@@ -1,6 +1,7 @@
 """The global MAP (ordering prior exact, object states carry their disparity):
 GPU frames must equal the oracle's element by element; without the ordering
-prior it must agree with the paper's DP; the unsupported paths refuse it."""
+prior it must agree with the paper's DP; the scratch-free entry point refuses
+it (batched and served frames: test_gpu_batch_variants.py)."""
 import numpy as np
 import pytest
 
@@ -81,15 +82,9 @@ def test_without_ordering_global_map_costs_equal_the_paper_dp():
     assert np.all(d[3] <= c[3])
 
 
-def test_unsupported_paths_refuse_global_map():
+def test_the_scratch_free_entry_point_refuses_global_map():
     cam = scenes.CONFIG1
     h = S.Stixels(S.default_params(cam, global_map=1))
-    with pytest.raises(S.StixelsError):
-        S.Batch([(h, cam.height, cam.width)])
-    srv = S.Server(64 << 20, max_slots=2)
-    with pytest.raises(S.StixelsError):
-        srv.submit(h, np.zeros((cam.height, cam.width), np.float32))
-    srv.close()
     h.reserve(cam.height, cam.width)
     out = h.alloc_output(cam.height, cam.width)
     with pytest.raises(S.StixelsError):

@@ -1,5 +1,5 @@
 // server.cu -- serving: admission by slots and a device-memory arena, and a
-// scheduler thread doing continuous batching over two CUDA streams.
+// scheduler thread doing continuous batching over three CUDA streams.
 //
 // Life of a frame: stixels_submit reserves arena space (input, intermediates,
 // outputs) and a status word (page-locked host memory that the kernels set
@@ -7,9 +7,11 @@
 // waits for that copy, then queues the request.  The scheduler takes every queued request, plans
 // the batch tables for them (the planner of the batched mode), uploads the
 // tables through a pinned staging buffer and launches the batched kernels on
-// the next of its two compute streams, recording one completion event per
-// iteration.  A stream is reused only after its previous iteration finished,
-// so at most two iterations are in flight and they overlap on the device.
+// a compute stream whose previous iteration has finished (when all three are
+// busy, on the one launched first, once it is done), recording one completion
+// event per iteration: at most three iterations are in flight and they
+// overlap on the device, and no iteration waits behind a long one while
+// another stream is free.
 // stixels_poll checks the request's iteration event, reads its status word,
 // copies the results out on the calling thread's stream (one wait) and
 // returns the slot's memory and status word.
@@ -32,7 +34,7 @@ using namespace stx;
 
 namespace {
 
-constexpr int kStreams = 2;
+constexpr int kStreams = 3;
 constexpr size_t kTableBytes = 8u << 20;      // per stream: device tables and pinned staging
 constexpr int kMaxBatchFrames = 512;
 
@@ -113,9 +115,9 @@ struct stixels_server_s {
     char* d_arena = nullptr;
     std::unique_ptr<Arena> arena;
     cudaStream_t copy_stream = nullptr;
-    cudaStream_t streams[kStreams] = {nullptr, nullptr};
-    char* d_tables[kStreams] = {nullptr, nullptr};
-    char* h_staging[kStreams] = {nullptr, nullptr};
+    cudaStream_t streams[kStreams] = {};
+    char* d_tables[kStreams] = {};
+    char* h_staging[kStreams] = {};
     // per-slot status words in page-locked host memory, mapped for the device:
     // the kernels set a frame's flags there, submit clears them and poll reads
     // them, with no stream operation for either
@@ -123,7 +125,7 @@ struct stixels_server_s {
     uint32_t* d_flags = nullptr;
     std::vector<int> free_flags;
     std::shared_ptr<Iteration> last[kStreams];
-    int next_stream = 0;
+    uint64_t launched[kStreams] = {};   // iteration number of each stream's last iteration
 
     std::mutex mu;
     std::condition_variable cv_work;
@@ -163,11 +165,18 @@ void scheduler(stixels_server_t s)
                 s->queue.pop_front();
             }
         }
-        // the stream's previous iteration must be done before its staging and
-        // tables are reused
-        const int k = s->next_stream;
-        s->next_stream = (k + 1) % kStreams;
-        if (s->last[k]) cudaEventSynchronize(s->last[k]->done);
+        // a stream whose previous iteration is done (its staging and tables
+        // are then free); with none, wait for the oldest, which the device
+        // took first
+        int k = -1;
+        for (int q = 0; q < kStreams && k < 0; ++q)
+            if (!s->last[q] || cudaEventQuery(s->last[q]->done) == cudaSuccess) k = q;
+        if (k < 0) {
+            k = 0;
+            for (int q = 1; q < kStreams; ++q)
+                if (s->launched[q] < s->launched[k]) k = q;
+            cudaEventSynchronize(s->last[k]->done);
+        }
         // plan the iteration; halve it (returning the rest to the queue) while
         // its tables do not fit the staging buffer
         BatchTables t;
@@ -204,6 +213,7 @@ void scheduler(stixels_server_t s)
             s->stats.frames_in_iterations += batch.size();
         }
         s->last[k] = it;
+        s->launched[k] = s->stats.iterations;
     }
 }
 

@@ -41,9 +41,9 @@ L2_FLUSH_BYTES = 256 << 20
 # keyed by the sha1 of the kernel's source file at the time of the capture.  A
 # kernel whose source changed since reports null.
 NCU_TRAFFIC = {
-    "kernels_dp.cu": ("ee49b3884358", 15936384),
-    "kernels_luts.cu": ("b98e06d2a8e5", 234240),
-    "kernels_reduce.cu": ("99737c93c0af", 1809664),
+    "kernels_dp.cu": ("e87e833dbbf0", 46180864),
+    "kernels_luts.cu": ("1b8cb1ca62bc", 493568),
+    "kernels_reduce.cu": ("99737c93c0af", 1808896),
 }
 
 
@@ -191,10 +191,11 @@ def _cells(cam):
     return (cam.width // cam.stixel_width) * cam.height * (cam.height + 1) // 2
 
 
-def bench_batched(S, scenes, torch, dev, cams, seed0, launches, label):
-    """One graph-captured batch over `cams` (one frame each), autotuned; frames/s over `launches`
-    back-to-back launches (inputs and LUTs far exceed L2, so no flush is needed)."""
-    hs = [S.Stixels(S.default_params(c)) for c in cams]
+def bench_batched(S, scenes, torch, dev, cams, seed0, launches, label, **kw):
+    """One graph-captured batch over `cams` (one frame each, parameter overrides `kw`),
+    autotuned; frames/s over `launches` back-to-back launches (inputs and LUTs far exceed
+    L2, so no flush is needed)."""
+    hs = [S.Stixels(S.default_params(c, **kw)) for c in cams]
     b = S.Batch([(h, c.height, c.width) for h, c in zip(hs, cams)])
     for i, c in enumerate(cams):
         sc = scenes.make_scene(c, seed0 + i, n_obstacles=(8, 20))
@@ -633,6 +634,14 @@ def bench_ours(args, world, rank, local):
                                      "64 frames: 24x 640x240, 32x 1024x440, 8x 2048x880; s in {5,7}; dmax {64,128}"),
             "paper32": bench_batched(S, scenes, torch, dev, [cam] * 32, 4100, 20,
                                      "32 frames of 1024x440 s=5 dmax=128 in one launch"),
+            "paper32_ground_estimate": bench_batched(
+                S, scenes, torch, dev, [cam] * 32, 4100, 10,
+                "32 frames of 1024x440 s=5 dmax=128 in one launch, ground line estimated per frame",
+                ground_estimate=1),
+            "paper32_global_map": bench_batched(
+                S, scenes, torch, dev, [cam] * 32, 4100, 3,
+                "32 frames of 1024x440 s=5 dmax=128 in one launch, global MAP (one DP launch per frame)",
+                global_map=1),
         }
     if rank == 0 and not args.no_served:
         served = bench_served(S, scenes, torch, args.served_seconds)

@@ -450,7 +450,7 @@ static int compute_frame(stixels_t h, const float* d_disparity, int H, int W, vo
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = launch_reduce(d_disparity, g, h->hm.dmax, reduce_code(h->hm.p), q, st);
     if (e == cudaSuccess && est) e = launch_ground(q, g, h->md, r, h->est_pool, h->hm.est_gw, ws + L.total, &r, nullptr, st);
-    if (e == cudaSuccess) e = launch_luts(q, g, h->md, r, pd, pg, ps, po, st);
+    if (e == cudaSuccess) e = launch_luts(q, g, h->md, r, pd, pg, ps, po, st, 1);
     if (e == cudaSuccess)
         e = gmap ? launch_dp_map(pd, pg, ps, po, g, h->md, r, h->rp, h->hm.pixel_floor, *out, err, ws + L.total + gw, st)
                  : launch_dp(pd, pg, ps, po, g, h->md, r, h->rp, h->hm.pixel_floor, *out, err, st);

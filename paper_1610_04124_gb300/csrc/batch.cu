@@ -76,6 +76,7 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
         la[i].q = f.q;
         la[i].H = f.g.H; la[i].P = f.g.P; la[i].F = m.dmax + 1; la[i].m = m; la[i].rows = rows;
         la[i].pd = f.pd; la[i].pg = f.pg; la[i].ps = f.ps; la[i].po = f.po;
+        la[i].range_only = 1;
         dp_frame_args(f.pd, f.pg, f.ps, f.po, f.g, m, rows, f.view.rp, f.view.pixel_floor, f.out, f.view.err, &da[i]);
         if (f.g.ncols == 0) continue;
         if (f.view.ground_estimate) t->ground_frames.push_back(i);

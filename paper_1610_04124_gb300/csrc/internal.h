@@ -175,6 +175,10 @@ struct LutArgs {
     int32_t* pg;
     int32_t* ps;
     int32_t* po;
+    // 1: write only the object rows f that a stixel of the column can have as
+    // its rounded mean, round(min q / 16) .. round(max q / 16) (the mean of a
+    // run of codes lies between their extremes); the DP reads no other row
+    int32_t range_only;
 };
 
 // One frame's arguments for the DP kernel (per-frame launch or batch table entry).
@@ -223,8 +227,9 @@ int sm_count();
 // ---- kernel launchers (kernels_*.cu); all return cudaGetLastError() ----
 cudaError_t launch_reduce(const float* disp, const FrameGeom& g, int dmax, int mode, int16_t* q,
                           cudaStream_t st);
+// range_only: see LutArgs (the library's own pipelines); 0 writes every row.
 cudaError_t launch_luts(const int16_t* q, const FrameGeom& g, const ModelDev& m, const RowsDev& r,
-                        int32_t* pd, int32_t* pg, int32_t* ps, int32_t* po, cudaStream_t st);
+                        int32_t* pd, int32_t* pg, int32_t* ps, int32_t* po, cudaStream_t st, int range_only = 0);
 size_t lut_shared_bytes(int H, const ModelDev& m);
 int lut_row_groups(int F);
 cudaError_t launch_luts_batch(const LutArgs* d_frames, const int2* d_items, int nitems, int max_groups,

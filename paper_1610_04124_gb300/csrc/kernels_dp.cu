@@ -122,6 +122,7 @@ struct SyncState {
     int rep_n;                   // stixels on the path
     int rep_done;                // warps done with their rows
     long long rep_acc;           // the report's sum so far, 2^-24 units
+    int qmin, qmax;              // the column's extreme Q4 codes
     int ready[kMaxBlocks];       // ready[c]: bulk tiles applied to end-row block c (of c - 1)
     int gathered[kMaxBlocks];    // gathered[j]: bulk warps done with block j's chain data
 };
@@ -545,10 +546,31 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const DpArgs& ta, con
         sync->rep_state = 0;
         sync->rep_done = 0;
         sync->rep_acc = 0;
+        sync->qmin = INT_MAX;
+        sync->qmax = INT_MIN;
         // start 0 carries the first-stixel prior (code 3 = no previous stixel)
         s_ctx[0] = make_bulk_ctx(m.first[0] + kNoneCode, kBig, kBig, INT_MAX, s_thr[0], m);
     }
     __syncthreads();
+    if (window < kMaxBlocks) {
+        // (tiles pruned by the bound) the column's code range: every
+        // stixel's rounded mean lies between round(min q / 16) and
+        // round(max q / 16), the object rows the tile bound takes its minimum
+        // over (the LUT kernel writes no others)
+        int lo = INT_MAX, hi = INT_MIN;
+        for (int v = threadIdx.x; v < H; v += kThreads) {
+            const int qv = s_pd8[v + 1] - s_pd8[v] - 8;
+            lo = min(lo, qv);
+            hi = max(hi, qv);
+        }
+        lo = __reduce_min_sync(kFull, lo);
+        hi = __reduce_max_sync(kFull, hi);
+        if (lane == 0) {
+            atomicMin(&sync->qmin, lo);
+            atomicMax(&sync->qmax, hi);
+        }
+        __syncthreads();
+    }
 
     // Apply the 32 starts of finalised block t to end-row block jc (a bulk tile):
     // lane l owns end row k = 32 jc + l; the starts go in four groups of 8
@@ -619,14 +641,19 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const DpArgs& ta, con
         int32_t lb = min(min(min(cx.o0, cx.o1), min(cx.g0, cx.gg)), cx.gd) - b * a.pixel_floor;
         lb = __reduce_min_sync(kFull, lb);
         const int cs = 32 * t + 31;
-        // every f's core difference, lane l taking f = l + 32 j (F <= 256; f
-        // clamped to F - 1 repeats the last one): all loads in flight at once
+        // the core difference of every f a stixel of the column can have,
+        // lane l taking f = f_lo + l + 32 j (clamped to f_hi, which repeats
+        // the last one): all loads in flight at once
+        // (malformed codes from a caller's tables: the whole range)
+        const int qlo = sync->qmin, qhi = sync->qmax;
+        const int f_lo = qlo < 0 ? 0 : min((qlo + 8) >> 4, F - 1);
+        const int f_span = (qlo < 0 ? F - 1 : min((qhi + 8) >> 4, F - 1)) - f_lo;
         int32_t cm = INT_MAX;
         const int32_t* core_hi = po_col + 32 * jc + 1;
         const int32_t* core_lo = po_col + cs;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const size_t o = (size_t)min(lane + 32 * j, F - 1) * P;
+            const size_t o = (size_t)(f_lo + min(lane + 32 * j, f_span)) * P;
             cm = min(cm, __ldg(core_hi + o) - __ldg(core_lo + o));
         }
         cm = __reduce_min_sync(kFull, cm);

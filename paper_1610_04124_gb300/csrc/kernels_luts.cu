@@ -22,6 +22,8 @@
 // lane.  Rows are padded to a multiple
 // of 4 entries (pitch P) so every store is aligned.  The kernel is bound by
 // the write bandwidth of the ncols x (dmax + 4) x P x 4-byte output.
+#include <climits>
+
 #include "internal.h"
 
 namespace stx {
@@ -145,9 +147,37 @@ __device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const 
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the object rows a stixel of this column can use: its rounded mean lies
+    // between round(min q / 16) and round(max q / 16)
+    int f_lo = 0, f_hi = F - 1;
+    if (a.range_only && row0 < F) {
+        __shared__ int s_ext[2][kLutThreads / 32];
+        int lo = INT_MAX, hi = INT_MIN;
+        for (int j = 1 + threadIdx.x; j <= H; j += blockDim.x) {
+            lo = min(lo, s_q[j]);
+            hi = max(hi, s_q[j]);
+        }
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        if (lane == 0) {
+            s_ext[0][warp] = lo;
+            s_ext[1][warp] = hi;
+        }
+        __syncthreads();
+        lo = INT_MAX;
+        hi = INT_MIN;
+#pragma unroll
+        for (int w = 0; w < kLutThreads / 32; ++w) {
+            lo = min(lo, s_ext[0][w]);
+            hi = max(hi, s_ext[1][w]);
+        }
+        f_lo = max((lo + 8) >> 4, 0);
+        f_hi = min((hi + 8) >> 4, F - 1);
+    }
     for (int rr = warp; rr < kRowsPerCta; rr += 8) {
         const int row = row0 + rr;
         if (row >= R) break;
+        if (row < F && (row < f_lo || row > f_hi)) continue;     // never read
         // one row kind per call, so the per-pixel cost below is branch-free
         if (row < F) {
             const int f = row, f16 = 16 * f;
@@ -240,12 +270,13 @@ size_t lut_shared_bytes(int H, const ModelDev& m)
 int lut_row_groups(int F) { return (F + 3 + kRowsPerCta - 1) / kRowsPerCta; }
 
 cudaError_t launch_luts(const int16_t* q, const FrameGeom& g, const ModelDev& m, const RowsDev& r,
-                        int32_t* pd, int32_t* pg, int32_t* ps, int32_t* po, cudaStream_t st)
+                        int32_t* pd, int32_t* pg, int32_t* ps, int32_t* po, cudaStream_t st, int range_only)
 {
     if (g.H <= 0 || g.ncols <= 0) return cudaSuccess;
     LutArgs a;
     a.q = q; a.H = g.H; a.P = g.P; a.F = m.dmax + 1; a.m = m; a.rows = r;
     a.pd = pd; a.pg = pg; a.ps = ps; a.po = po;
+    a.range_only = range_only;
     dim3 grid(g.ncols, lut_row_groups(a.F));
     const size_t smem = lut_shared_bytes(g.H, m);
     if (m.var_sigma) {

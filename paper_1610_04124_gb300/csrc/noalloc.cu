@@ -73,7 +73,7 @@ extern "C" int stixels_compute_noalloc(stixels_t h, const float* d_disparity, in
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // every byte read below is written earlier in this call: no clearing needed
     cudaError_t e = launch_reduce(d_disparity, g, v.model.dmax, v.reduce_mode, q, st);
-    if (e == cudaSuccess) e = launch_luts(q, g, v.model, v.rows, pd, pg, ps, po, st);
+    if (e == cudaSuccess) e = launch_luts(q, g, v.model, v.rows, pd, pg, ps, po, st, 1);
     if (e == cudaSuccess) e = launch_dp(pd, pg, ps, po, g, v.model, v.rows, v.rp, v.pixel_floor, *out, v.err, st);
     return status_from_cuda(e);
 }

@@ -27,13 +27,16 @@
 // triangle of object cells (mean and data cost) into shared memory; object
 // candidates go to their bin (row, f') by atomic minimum (a lane merges
 // consecutive candidates of the same f' first), ground and sky stay in
-// registers until one atomic per lane.  Phase B, one warp, the block's rows
-// in order, from shared memory only: row k adds its starts inside the block
-// (lane = start; lanes of equal f' combine first), then turns its bins into
-// the row M[k][.] (one lane owns 8 consecutive f), kept in a shared ring of
-// the block's rows.  Then every warp adds this block's starts to the next
-// block's rows, and the block's states and rows of M go to global memory.
-// Three CTA barriers per block instead of several per row.
+// registers until one atomic per lane.  Phase B, two warps, the block's
+// rows in order, from shared memory only: one warp adds row k + 1's starts
+// inside the block up to k (lane = start; lanes of equal f' combine first)
+// while the other finishes row k: it adds the start k, the one candidate
+// that reads row k - 1, and turns the row's bins into the row M[k][.] (one
+// lane owns 8 consecutive f; a suffix scan over f, since the penalty is not
+// negative), kept in a shared ring of the block's rows; a 64-thread barrier
+// per row.  Then every warp adds this block's starts to the next block's
+// rows, and the block's states and rows of M go to global memory.  Three CTA
+// barriers per block instead of several per row.
 #include <climits>
 
 #include "internal.h"
@@ -50,7 +53,14 @@ __device__ __forceinline__ int32_t state_value(int32_t k) { return min(k & ~3, k
 constexpr int kMapRows = 32;                 // rows per block
 constexpr size_t kMapSmemMax = 226 * 1024;   // dynamic shared memory one CTA may use (227 KB less the static)
 constexpr int kMapWarps = 8;
-constexpr int kPer = 8;                      // object states per lane in a row's scan (F <= 256)
+constexpr int kPer = 8;
+// phase B's two warps (on different schedulers); phase A runs on the rest
+// (measured against phase A on five warps with the first one's scheduler
+// partner idle, and against the second phase-B warp on that partner: 1024x440
+// 315 / 324 / 324 us, 2048x880 1564 / 1763 / 1593 us)
+constexpr int kWarpS = 0, kWarpC = 1;
+constexpr int kPhaseAWarps = kMapWarps - 2;
+__device__ __forceinline__ int phase_a_index(int w) { return w - 2; }                      // object states per lane in a row's scan (F <= 256)
 constexpr int kTri = 528;                    // cells (b, k), b <= k, of one block
 __device__ __forceinline__ int tri_slot(int i) { return (i * (65 - i)) >> 1; }
 
@@ -73,6 +83,9 @@ struct MapCol {
     int P, F, dmax, ord_off;
     int32_t T_oo, T_og, T_os, T_go, T_gg, T_gs, T_so, T_sg, T_ss;
 };
+
+// the 64-thread barrier of the two phase-B warps
+__device__ __forceinline__ void pair_sync() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
 
 // rounded mean of the stixel [b, k]
 __device__ __forceinline__ int map_mean(const MapCol& c, int b, int k)
@@ -417,107 +430,127 @@ __global__ void __launch_bounds__(kMapWarps * 32) stixel_map_kernel(DpArgs a, in
         const int32_t* tri_d = s_trid + (j & 1) * kTri;
         const uint8_t* tri_f = s_trif + (j & 1) * kTri;
 
-        if (warp == 0) {
-            // Phase B: the block's rows in order.  The previous block's last
-            // row opens the ring (ring row i = row K0 - 1 + i).
+        if (warp == kWarpS || warp == kWarpC) {
+            // Phase B: the block's rows in order, on two warps.  In step r,
+            // warp C evaluates row K0 + r + 1 against the starts K0 .. K0 + r
+            // (they read rows of M up to K0 + r - 1) into that row's bins,
+            // while warp S finishes row k = K0 + r: it
+            // adds the one start that reads row k - 1 (the stixel [k, k]) and
+            // turns the row's bins into M[k].  One 64-thread barrier per step
+            // orders the two.  The previous block's last row opens the ring
+            // (ring row i = row K0 - 1 + i).
             if (j > 0)
-                for (int x = lane; x < MS; x += 32) s_ring[x] = s_ring[kMapRows * MS + x];
-            __syncwarp();
+                for (int x = (warp == kWarpC ? 32 : 0) + lane; x < MS; x += 64) s_ring[x] = s_ring[kMapRows * MS + x];
+            pair_sync();
             for (int r = 0; r < nb; ++r) {
-                const int k = K0 + r;
-                // row k's starts inside the block (lane = start K0 + lane <= k)
-                int32_t ko = kNone, kg = kNone, ks = kNone;
-                int fo = -1 - lane;                      // lanes past the row: no candidate, no peer
-                if (lane <= r) {
-                    const int b = K0 + lane;
-                    const int e = tri_slot(lane) + r - lane;
-                    fo = tri_f[e];
-                    const int32_t mx = b == 0 ? 0 : s_ring[lane * MS + m_index(c, fo)];
-                    map_cands(c, m, b, k, fo, tri_d[e], mx, ko, kg, ks);
-                }
-                // consecutive starts mostly share their mean: two rounds of
-                // a scan over the lanes combine the candidates of equal f
-                // within aligned groups of four lanes (a lane takes a lane
-                // below it only if that one has its f, which keeps every
-                // minimum in its bin), so that one lane per group and run
-                // updates the bin (measured against a full scan and against
-                // none: 1024x440 330 / 356 / 326 us, 2048x880 1613 / 1654 /
-                // 1736 us)
+                if (warp == kWarpC) {
+                    if (r + 1 < nb) {
+                        // row k1's starts K0 + lane <= k1 - 1
+                        const int k1 = K0 + r + 1;
+                        int32_t ko = kNone, kg = kNone, ks = kNone;
+                        int fo = -1 - lane;              // lanes past the row: no candidate, no peer
+                        if (lane <= r) {
+                            const int b = K0 + lane;
+                            const int e = tri_slot(lane) + r + 1 - lane;
+                            fo = tri_f[e];
+                            const int32_t mx = b == 0 ? 0 : s_ring[lane * MS + m_index(c, fo)];
+                            map_cands(c, m, b, k1, fo, tri_d[e], mx, ko, kg, ks);
+                        }
+                        // consecutive starts mostly share their mean: two
+                        // rounds of a scan over the lanes combine the
+                        // candidates of equal f within aligned groups of four
+                        // lanes (a lane takes a lane below it only if that one
+                        // has its f, which keeps every minimum in its bin), so
+                        // that one lane per group and run updates the bin
 #pragma unroll
-                for (int o = 1; o < 4; o <<= 1) {
-                    const int32_t u = __shfl_up_sync(0xffffffffu, ko, o);
-                    const int fu = __shfl_up_sync(0xffffffffu, fo, o);
-                    if (lane >= o && fu == fo) ko = min(ko, u);
-                }
-                const int fn = __shfl_down_sync(0xffffffffu, fo, 1);
-                if (lane <= r && (lane == 31 || fn != fo || (lane & 3) == 3)) atomicMin(&bin_j[r * F + fo], ko);
-                kg = min(__reduce_min_sync(0xffffffffu, kg), gbin_j[r]);
-                ks = min(__reduce_min_sync(0xffffffffu, ks), sbin_j[r]);
-                __syncwarp();
-                // the row's object states as values; lane l owns f = 8 l .. 8 l + 7:
-                // local prefix / suffix minima, then warp scans of the lane totals
-                const int32_t* bin = bin_j + (size_t)r * F;
-                int32_t pv[kPer], sv[kPer];
+                        for (int o = 1; o < 4; o <<= 1) {
+                            const int32_t u = __shfl_up_sync(0xffffffffu, ko, o);
+                            const int fu = __shfl_up_sync(0xffffffffu, fo, o);
+                            if (lane >= o && fu == fo) ko = min(ko, u);
+                        }
+                        const int fn = __shfl_down_sync(0xffffffffu, fo, 1);
+                        if (lane <= r && (lane == 31 || fn != fo || (lane & 3) == 3))
+                            atomicMin(&bin_j[(r + 1) * F + fo], ko);
+                        kg = __reduce_min_sync(0xffffffffu, kg);
+                        ks = __reduce_min_sync(0xffffffffu, ks);
+                        if (lane == 0) {
+                            gbin_j[r + 1] = min(gbin_j[r + 1], kg);
+                            sbin_j[r + 1] = min(sbin_j[r + 1], ks);
+                        }
+                    }
+                } else {
+                    const int k = K0 + r;
+                    // the row's object states without the start k, as values;
+                    // lane l owns f = 8 l .. 8 l + 7: local suffix minima, then
+                    // a warp scan of the lane totals.  With the penalty >= 0,
+                    // M[k][x] = min(min_{f >= x} O, best + penalty): where the
+                    // penalised prefix holds the row's best that is the
+                    // prefix's term, and where the suffix holds it the
+                    // penalised term cannot win.
+                    int32_t* bin = bin_j + (size_t)r * F;
+                    int32_t sv[kPer];
 #pragma unroll
-                for (int i = 0; i < kPer; ++i) {
-                    const int f = kPer * lane + i;
-                    pv[i] = f < F ? state_value(bin[f]) : INT_MAX;
-                    sv[i] = pv[i];
-                }
+                    for (int i = 0; i < kPer; ++i) {
+                        const int f = kPer * lane + i;
+                        sv[i] = f < F ? state_value(bin[f]) : INT_MAX;
+                    }
+                    // meanwhile the start k (the stixel [k, k]), the same on
+                    // every lane: its one object state joins M[k] at the end
+                    const int e = tri_slot(r);
+                    const int fn = tri_f[e];
+                    const int32_t mxn = k == 0 ? 0 : s_ring[r * MS + m_index(c, fn)];
+                    int32_t kon, kg, ks;
+                    map_cands(c, m, k, k, fn, tri_d[e], mxn, kon, kg, ks);
+                    kg = min(kg, gbin_j[r]);
+                    ks = min(ks, sbin_j[r]);
+                    if (lane == fn / kPer) bin[fn] = min(bin[fn], kon);
+                    const int32_t vn = state_value(kon);
 #pragma unroll
-                for (int i = 1; i < kPer; ++i) pv[i] = min(pv[i - 1], pv[i]);
+                    for (int i = kPer - 2; i >= 0; --i) sv[i] = min(sv[i + 1], sv[i]);
+                    int32_t st = sv[0];
 #pragma unroll
-                for (int i = kPer - 2; i >= 0; --i) sv[i] = min(sv[i + 1], sv[i]);
-                int32_t pt = pv[kPer - 1], st = sv[0];
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int32_t dn = __shfl_down_sync(0xffffffffu, st, o);
+                        if (lane + o < 32) st = min(st, dn);
+                    }
+                    // the exclusive carry from the lanes above; the row's best
+                    // object state (with the start k's)
+                    int32_t sc = __shfl_down_sync(0xffffffffu, st, 1);
+                    if (lane == 31) sc = INT_MAX;
+                    const int32_t best = min(__shfl_sync(0xffffffffu, st, 0), vn);
+                    const int32_t capped = best + pen_ord;
+                    // M[k][x], x = 8 lane + i (shared memory only: the block's
+                    // rows go to global memory at its end); the start k's state
+                    // is in the suffixes of x <= fn
+                    int32_t mr[kPer];
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int32_t up = __shfl_up_sync(0xffffffffu, pt, o);
-                    const int32_t dn = __shfl_down_sync(0xffffffffu, st, o);
-                    if (lane >= o) pt = min(pt, up);
-                    if (lane + o < 32) st = min(st, dn);
+                    for (int i = 0; i < kPer; ++i) {
+                        const int x = kPer * lane + i;
+                        const int32_t suf = min(min(sc, sv[i]), x <= fn ? vn : INT_MAX);
+                        mr[i] = min(suf, capped);
+                    }
+                    int32_t* rrow = s_ring + (r + 1) * MS;
+                    const int x0 = kPer * lane;
+                    if (x0 + 3 < MS) *reinterpret_cast<int4*>(rrow + x0) = make_int4(mr[0], mr[1], mr[2], mr[3]);
+                    if (x0 + 7 < MS) *reinterpret_cast<int4*>(rrow + x0 + 4) = make_int4(mr[4], mr[5], mr[6], mr[7]);
+                    if (F == 32 * kPer && lane == 31) rrow[F] = capped;     // x = F past the lanes' ranges
+                    if (lane == 0) {
+                        gbin_j[r] = kg;
+                        sbin_j[r] = ks;
+                        s_gv[k] = state_value(kg);
+                        s_sv[k] = state_value(ks);
+                        s_bo[k] = best;
+                    }
                 }
-                // exclusive carries from the lanes below / above
-                int32_t pc = __shfl_up_sync(0xffffffffu, pt, 1);
-                int32_t sc = __shfl_down_sync(0xffffffffu, st, 1);
-                if (lane == 0) pc = INT_MAX;
-                if (lane == 31) sc = INT_MAX;
-                // M[k][x], x = 8 lane + i: the free suffix f >= x against the
-                // penalised prefix f < x (shared memory only: the block's rows
-                // go to global memory at its end)
-                int32_t mr[kPer];
-#pragma unroll
-                for (int i = 0; i < kPer; ++i) {
-                    const int x = kPer * lane + i;
-                    const int32_t suf = min(sc, sv[i]);
-                    const int32_t pre = i == 0 ? pc : min(pc, pv[i - 1]);
-                    mr[i] = x == 0 ? suf : (x >= F ? pre + pen_ord : min(suf, pre + pen_ord));
-                }
-                int32_t* rrow = s_ring + (r + 1) * MS;
-                const int x0 = kPer * lane;
-                if (x0 + 3 < MS) *reinterpret_cast<int4*>(rrow + x0) = make_int4(mr[0], mr[1], mr[2], mr[3]);
-                if (x0 + 7 < MS) *reinterpret_cast<int4*>(rrow + x0 + 4) = make_int4(mr[4], mr[5], mr[6], mr[7]);
-                const int32_t best = __shfl_sync(0xffffffffu, pt, 31);      // the row's best object state
-                if (F == 32 * kPer && lane == 31) rrow[F] = best + pen_ord;   // x = F past the lanes' ranges
-                if (lane == 0) {
-                    gbin_j[r] = kg;
-                    sbin_j[r] = ks;
-                    s_gv[k] = state_value(kg);
-                    s_sv[k] = state_value(ks);
-                    s_bo[k] = best;
-                }
-                // the rows above in this block are read by this warp only:
-                // the warp barrier orders its lanes' stores and loads
-                __syncwarp();
+                pair_sync();
             }
-        } else if (warp != 4) {
+        } else {
             // meanwhile: the next block's candidates whose starts lie in the
             // blocks before this one (their rows are final), and the next
-            // block's own object cells, on the warps that do not share warp
-            // 0's scheduler (warp 4 does), so that the sequential rows keep
-            // its issue slots
-            const int w6 = warp - 1 - (warp > 4);
-            phase_a(bin_n, gbin_n, sbin_n, K1, nb1, w6, K0, kMapWarps - 2, false, 0);
-            if (nb1 > 0) gather_tri((j + 1) & 1, K1, nb1, w6, kMapWarps - 2);
+            // block's own object cells
+            const int wa = phase_a_index(warp);
+            phase_a(bin_n, gbin_n, sbin_n, K1, nb1, wa, K0, kPhaseAWarps, false, 0);
+            if (nb1 > 0) gather_tri((j + 1) & 1, K1, nb1, wa, kPhaseAWarps);
         }
         __syncthreads();                          // block j's rows are final and visible
         // the next block's starts inside this block (M from the ring); then

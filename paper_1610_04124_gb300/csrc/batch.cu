@@ -53,14 +53,15 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
     std::vector<ReduceArgs> ra(n);
     std::vector<LutArgs> la(n);
     std::vector<DpArgs> da(n);
-    std::vector<int2> lut_items, dp_items;
+    std::vector<int2> lut_items, dp_items, map_items;
+    std::vector<MapScratch> ms(n, MapScratch{nullptr, nullptr, nullptr});
     std::vector<std::vector<int4>> group_tiles;
     t->groups.clear();
     t->maxH = t->max_groups = 0;
     t->lut_smem = 0;
+    t->map_smem = 0;
     t->std_trans = true;
     t->ground_frames.clear();
-    t->map_frames.clear();
     t->jobs = jobs;
     for (int i = 0; i < n; ++i) {
         const FrameJob& f = jobs[i];
@@ -84,8 +85,11 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
         t->lut_smem = std::max(t->lut_smem, lut_shared_bytes(f.g.H, m));
         for (int c = 0; c < f.g.ncols; ++c) lut_items.push_back(make_int2(i, c));
         if (f.view.global_map) {
-            // its own DP launch (the global MAP), after the persistent DP
-            t->map_frames.push_back(i);
+            // the global MAP: one launch over every such frame's columns,
+            // after the persistent DP
+            t->map_smem = std::max(t->map_smem, map_smem_bytes(f.g.H, m.dmax + 1));
+            ms[i] = map_scratch_carve(f.map_scratch, f.g.H, f.g.ncols, m.dmax + 1);
+            for (int c = 0; c < f.g.ncols; ++c) map_items.push_back(make_int2(i, c));
         } else {
             t->maxH = std::max(t->maxH, f.g.H);
             t->std_trans = t->std_trans && m.trans[1][1] >= kBig && m.trans[1][2] >= kBig && m.trans[2][2] >= kBig;
@@ -105,8 +109,11 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
     // DP work list: longest columns first (work grows as H^2), stable otherwise
     std::stable_sort(dp_items.begin(), dp_items.end(),
                      [&](const int2& x, const int2& y) { return jobs[x.x].g.H > jobs[y.x].g.H; });
+    std::stable_sort(map_items.begin(), map_items.end(),
+                     [&](const int2& x, const int2& y) { return jobs[x.x].g.H > jobs[y.x].g.H; });
     t->nitems = (int)dp_items.size();
     t->nlut = (int)lut_items.size();
+    t->nmap = (int)map_items.size();
 
     size_t o = 0;
     t->o_red = o; o += up256(sizeof(ReduceArgs) * n);
@@ -115,6 +122,8 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
     t->o_li = o;  o += up256(sizeof(int2) * lut_items.size());
     t->o_di = o;  o += up256(sizeof(int2) * dp_items.size());
     t->o_cnt = o; o += 256;
+    t->o_ms = o;  o += up256(sizeof(MapScratch) * n);
+    t->o_mi = o;  o += up256(sizeof(int2) * map_items.size());
     for (size_t k = 0; k < t->groups.size(); ++k) {
         t->groups[k].tiles_off = o;
         t->groups[k].ntiles = (int)group_tiles[k].size();
@@ -127,6 +136,8 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
     memcpy(h + t->o_dp, da.data(), sizeof(DpArgs) * n);
     if (!lut_items.empty()) memcpy(h + t->o_li, lut_items.data(), sizeof(int2) * lut_items.size());
     if (!dp_items.empty()) memcpy(h + t->o_di, dp_items.data(), sizeof(int2) * dp_items.size());
+    memcpy(h + t->o_ms, ms.data(), sizeof(MapScratch) * n);
+    if (!map_items.empty()) memcpy(h + t->o_mi, map_items.data(), sizeof(int2) * map_items.size());
     for (size_t k = 0; k < t->groups.size(); ++k)
         memcpy(h + t->groups[k].tiles_off, group_tiles[k].data(), sizeof(int4) * group_tiles[k].size());
 }
@@ -157,16 +168,10 @@ cudaError_t enqueue_tables(const BatchTables& t, char* d_tab, int dp_warps, int 
         e = launch_dp_batch((const DpArgs*)(d_tab + t.o_dp), (const int2*)(d_tab + t.o_di), t.nitems, counter, t.maxH,
                             dp_warps, dp_ctas_per_sm, t.std_trans, grid, st);
     }
-    // frames solved by the global MAP: one launch each
-    for (int i : t.map_frames) {
-        if (e != cudaSuccess) return e;
-        const FrameJob& f = t.jobs[i];
-        const RowsDev rows = f.view.ground_estimate
-                                 ? ground_frame_rows(f.g, f.view.model.dmax, f.view.rows, f.view.est_gw, f.ground_work)
-                                 : f.view.rows;
-        e = launch_dp_map(f.pd, f.pg, f.ps, f.po, f.g, f.view.model, rows, f.view.rp, f.view.pixel_floor, f.out,
-                          f.view.err, f.map_scratch, st);
-    }
+    // frames solved by the global MAP: one launch over all their columns
+    if (e == cudaSuccess && t.nmap > 0)
+        e = launch_dp_map_batch((const DpArgs*)(d_tab + t.o_dp), (const MapScratch*)(d_tab + t.o_ms),
+                                (const int2*)(d_tab + t.o_mi), t.nmap, t.map_smem, st);
     return e;
 }
 

@@ -275,7 +275,11 @@ struct BatchTables {
     size_t lut_smem = 0;
     bool std_trans = true;
     std::vector<int> ground_frames;   // frames whose ground line is estimated (launched per frame)
-    std::vector<int> map_frames;      // frames solved by the global MAP (launched per frame)
+    // frames solved by the global MAP (one launch over their columns): their
+    // scratch rows (MapScratch per frame) and (frame, column) items
+    size_t o_ms = 0, o_mi = 0;
+    int nmap = 0;                     // global-MAP items
+    size_t map_smem = 0;
     std::vector<FrameJob> jobs;       // the frames, for those launches
 };
 void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t);
@@ -313,6 +317,20 @@ cudaError_t launch_dp_map(const int32_t* pd, const int32_t* pg, const int32_t* p
                           const FrameGeom& g, const ModelDev& m, const RowsDev& r, const RealParams& rp,
                           int32_t pixel_floor, const stixels_output_t& out, uint32_t* err, void* scratch,
                           cudaStream_t st);
+// A frame's global-MAP scratch (map_scratch_bytes at `scratch`): object
+// states [ncols][H][F], ground / sky states [ncols][2][H], rows of M.
+struct MapScratch {
+    int32_t* keyo;
+    int32_t* kgs;
+    int32_t* mv;
+};
+MapScratch map_scratch_carve(void* scratch, int H, int ncols, int F);
+// Dynamic shared memory of one global-MAP CTA for a column of height H.
+size_t map_smem_bytes(int H, int F);
+// Batch form: one CTA per (frame, column) item; frames[i] and scratch[i]
+// describe frame i; smem = the largest map_smem_bytes of the frames.
+cudaError_t launch_dp_map_batch(const DpArgs* d_frames, const MapScratch* d_scratch, const int2* d_items, int nitems,
+                                size_t smem, cudaStream_t st);
 
 // Sets the DP kernels' shared-memory attributes (call outside stream capture).
 cudaError_t prepare_dp_kernels();

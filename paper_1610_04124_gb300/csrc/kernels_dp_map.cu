@@ -160,7 +160,7 @@ __host__ __device__ inline MapLayout map_layout(int H, int F)
     L.ps = o;   o += 4 * (size_t)(H + 1);
     o = up16(o);
     L.body = o;
-    L.bin = o;  o += 4 * 2 * (size_t)kMapRows * F;
+    L.bin = o;  o += 4 * 2 * (size_t)kMapRows * m_stride(F);
     L.gbin = o; o += 4 * 2 * kMapRows;
     L.sbin = o; o += 4 * 2 * kMapRows;
     o = up16(o);
@@ -309,7 +309,7 @@ __device__ __forceinline__ void map_column(const DpArgs& a, const int col, int32
     int32_t* s_thr = reinterpret_cast<int32_t*>(smem + L.thr);
     int32_t* s_pg = reinterpret_cast<int32_t*>(smem + L.pg);
     int32_t* s_ps = reinterpret_cast<int32_t*>(smem + L.ps);
-    int32_t* s_bin = reinterpret_cast<int32_t*>(smem + L.bin);     // [2][kMapRows][F]
+    int32_t* s_bin = reinterpret_cast<int32_t*>(smem + L.bin);     // [2][kMapRows][MS]
     int32_t* s_gbin = reinterpret_cast<int32_t*>(smem + L.gbin);   // [2][kMapRows]
     int32_t* s_sbin = reinterpret_cast<int32_t*>(smem + L.sbin);   // [2][kMapRows]
     int32_t* s_ring = reinterpret_cast<int32_t*>(smem + L.ring);   // [kMapRows + 1][MS]: ring i = row K0 - 1 + i
@@ -334,7 +334,7 @@ __device__ __forceinline__ void map_column(const DpArgs& a, const int col, int32
     const int32_t pen_ord = m.pen_ord;
 
     const int NB = (H + kMapRows - 1) / kMapRows;
-    const size_t BF = (size_t)kMapRows * F;
+    const size_t BF = (size_t)kMapRows * MS;           // bins of one block, rows at the stride of M
 
     // The object cells (K + i, K + l), i <= l < nr, of the block at rows K:
     // mean and data cost, into triangle buffer `buf` (slot tri_slot(i) + l - i),
@@ -390,7 +390,7 @@ __device__ __forceinline__ void map_column(const DpArgs& a, const int col, int32
                     rg = min(rg, kg);
                     rs = min(rs, ks);
                     if (fo[u] != cf) {
-                        if (cf >= 0) atomicMin(&bins[lane * F + cf], ck);
+                        if (cf >= 0) atomicMin(&bins[lane * MS + cf], ck);
                         cf = fo[u];
                         ck = ko;
                     } else {
@@ -399,7 +399,7 @@ __device__ __forceinline__ void map_column(const DpArgs& a, const int col, int32
                 }
             }
         }
-        if (cf >= 0) atomicMin(&bins[lane * F + cf], ck);
+        if (cf >= 0) atomicMin(&bins[lane * MS + cf], ck);
         atomicMin(&gbin[lane], rg);
         atomicMin(&sbin[lane], rs);
     };
@@ -463,7 +463,7 @@ __device__ __forceinline__ void map_column(const DpArgs& a, const int col, int32
                         }
                         const int fn = __shfl_down_sync(0xffffffffu, fo, 1);
                         if (lane <= r && (lane == 31 || fn != fo || (lane & 3) == 3))
-                            atomicMin(&bin_j[(r + 1) * F + fo], ko);
+                            atomicMin(&bin_j[(r + 1) * MS + fo], ko);
                         kg = __reduce_min_sync(0xffffffffu, kg);
                         ks = __reduce_min_sync(0xffffffffu, ks);
                         if (lane == 0) {
@@ -480,12 +480,18 @@ __device__ __forceinline__ void map_column(const DpArgs& a, const int col, int32
                     // penalised prefix holds the row's best that is the
                     // prefix's term, and where the suffix holds it the
                     // penalised term cannot win.
-                    int32_t* bin = bin_j + (size_t)r * F;
+                    int32_t* bin = bin_j + (size_t)r * MS;
                     int32_t sv[kPer];
+                    {
+                        // two 16-byte loads per lane
+                        const int x0 = kPer * lane;
+                        int4 u0 = make_int4(kNone, kNone, kNone, kNone), u1 = u0;
+                        if (x0 < MS) u0 = *reinterpret_cast<const int4*>(bin + x0);
+                        if (x0 + 4 < MS) u1 = *reinterpret_cast<const int4*>(bin + x0 + 4);
+                        sv[0] = u0.x; sv[1] = u0.y; sv[2] = u0.z; sv[3] = u0.w;
+                        sv[4] = u1.x; sv[5] = u1.y; sv[6] = u1.z; sv[7] = u1.w;
 #pragma unroll
-                    for (int i = 0; i < kPer; ++i) {
-                        const int f = kPer * lane + i;
-                        sv[i] = f < F ? state_value(bin[f]) : INT_MAX;
+                        for (int i = 0; i < kPer; ++i) sv[i] = x0 + i < F ? state_value(sv[i]) : INT_MAX;
                     }
                     // meanwhile the start k (the stixel [k, k]), the same on
                     // every lane: its one object state joins M[k] at the end
@@ -550,10 +556,12 @@ __device__ __forceinline__ void map_column(const DpArgs& a, const int col, int32
         // this block's states and rows of M go to global memory, coalesced,
         // and its bins are reset for block j + 2
         phase_a(bin_n, gbin_n, sbin_n, K1, nb1, K0 + warp, K0 + nb, kMapWarps, true, K0 - 1);
-        for (int i = tid; i < (int)BF; i += blockDim.x) {
-            if (i < nb * F) keyo[(size_t)K0 * F + i] = bin_j[i];
-            bin_j[i] = kNone;
-        }
+        // (the padding past F and the rows past nb are never written)
+        for (int r = warp; r < nb; r += kMapWarps)
+            for (int f = lane; f < F; f += 32) {
+                keyo[(size_t)(K0 + r) * F + f] = bin_j[r * MS + f];
+                bin_j[r * MS + f] = kNone;
+            }
         for (int i = tid; i < nb * MS; i += blockDim.x) mv[(size_t)K0 * MS + i] = s_ring[MS + i];
         if (tid < kMapRows) {
             if (tid < nb) {

@@ -53,7 +53,8 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
     std::vector<ReduceArgs> ra(n);
     std::vector<LutArgs> la(n);
     std::vector<DpArgs> da(n);
-    std::vector<int2> lut_items, dp_items, map_items;
+    std::vector<int2> lut_items, dp_items, map_items, ground_rows, ground_votes;
+    std::vector<GroundArgs> ga(n);
     std::vector<MapScratch> ms(n, MapScratch{nullptr, nullptr, nullptr});
     std::vector<std::vector<int4>> group_tiles;
     t->groups.clear();
@@ -61,7 +62,8 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
     t->lut_smem = 0;
     t->map_smem = 0;
     t->std_trans = true;
-    t->ground_frames.clear();
+    t->ground_smem = 0;
+    t->ground_ok = true;
     t->jobs = jobs;
     for (int i = 0; i < n; ++i) {
         const FrameJob& f = jobs[i];
@@ -80,7 +82,17 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
         la[i].range_only = 1;
         dp_frame_args(f.pd, f.pg, f.ps, f.po, f.g, m, rows, f.view.rp, f.view.pixel_floor, f.out, f.view.err, &da[i]);
         if (f.g.ncols == 0) continue;
-        if (f.view.ground_estimate) t->ground_frames.push_back(i);
+        if (f.view.ground_estimate) {
+            // its v-disparity and vote launches are shared with the batch's
+            // other estimating frames
+            if (ground_args(f.q, f.g, m, f.view.rows, f.view.est_pool, f.view.est_gw, f.ground_work, nullptr, &ga[i])) {
+                t->ground_smem = std::max(t->ground_smem, ground_vdisp_smem(m.dmax));
+                for (int rb = 0; rb < ground_row_blocks(f.g.H); ++rb) ground_rows.push_back(make_int2(i, rb));
+                for (int hb = 0; hb < ground_horizon_blocks(f.g.H); ++hb) ground_votes.push_back(make_int2(i, hb));
+            } else {
+                t->ground_ok = false;
+            }
+        }
         t->max_groups = std::max(t->max_groups, lut_row_groups(m.dmax + 1));
         t->lut_smem = std::max(t->lut_smem, lut_shared_bytes(f.g.H, m));
         for (int c = 0; c < f.g.ncols; ++c) lut_items.push_back(make_int2(i, c));
@@ -114,6 +126,8 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
     t->nitems = (int)dp_items.size();
     t->nlut = (int)lut_items.size();
     t->nmap = (int)map_items.size();
+    t->ngr = (int)ground_rows.size();
+    t->ngv = (int)ground_votes.size();
 
     size_t o = 0;
     t->o_red = o; o += up256(sizeof(ReduceArgs) * n);
@@ -124,6 +138,9 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
     t->o_cnt = o; o += 256;
     t->o_ms = o;  o += up256(sizeof(MapScratch) * n);
     t->o_mi = o;  o += up256(sizeof(int2) * map_items.size());
+    t->o_ga = o;  o += up256(sizeof(GroundArgs) * n);
+    t->o_gr = o;  o += up256(sizeof(int2) * ground_rows.size());
+    t->o_gv = o;  o += up256(sizeof(int2) * ground_votes.size());
     for (size_t k = 0; k < t->groups.size(); ++k) {
         t->groups[k].tiles_off = o;
         t->groups[k].ntiles = (int)group_tiles[k].size();
@@ -138,6 +155,9 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
     if (!dp_items.empty()) memcpy(h + t->o_di, dp_items.data(), sizeof(int2) * dp_items.size());
     memcpy(h + t->o_ms, ms.data(), sizeof(MapScratch) * n);
     if (!map_items.empty()) memcpy(h + t->o_mi, map_items.data(), sizeof(int2) * map_items.size());
+    memcpy(h + t->o_ga, ga.data(), sizeof(GroundArgs) * n);
+    if (!ground_rows.empty()) memcpy(h + t->o_gr, ground_rows.data(), sizeof(int2) * ground_rows.size());
+    if (!ground_votes.empty()) memcpy(h + t->o_gv, ground_votes.data(), sizeof(int2) * ground_votes.size());
     for (size_t k = 0; k < t->groups.size(); ++k)
         memcpy(h + t->groups[k].tiles_off, group_tiles[k].data(), sizeof(int4) * group_tiles[k].size());
 }
@@ -151,15 +171,13 @@ cudaError_t enqueue_tables(const BatchTables& t, char* d_tab, int dp_warps, int 
         e = launch_reduce_batch((const ReduceArgs*)(d_tab + t.o_red), (const int4*)(d_tab + gr.tiles_off), gr.ntiles,
                                 gr.s, gr.mode, st);
     }
-    // frames that estimate their ground line: its kernels write the frame's
-    // row tables, which the LUT and DP arguments already point to
-    for (int i : t.ground_frames) {
-        if (e != cudaSuccess) return e;
-        const FrameJob& f = t.jobs[i];
-        RowsDev fr;
-        e = launch_ground(f.q, f.g, f.view.model, f.view.rows, f.view.est_pool, f.view.est_gw, f.ground_work, &fr,
-                          nullptr, st);
-    }
+    // frames that estimate their ground line: one v-disparity and one vote
+    // launch over all of them write each frame's row tables, which its LUT
+    // and DP arguments already point to
+    if (e == cudaSuccess && !t.ground_ok) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess && t.ngr > 0)
+        e = launch_ground_batch((const GroundArgs*)(d_tab + t.o_ga), (const int2*)(d_tab + t.o_gr), t.ngr,
+                                (const int2*)(d_tab + t.o_gv), t.ngv, t.ground_smem, st);
     if (e == cudaSuccess)
         e = launch_luts_batch((const LutArgs*)(d_tab + t.o_lut), (const int2*)(d_tab + t.o_li), t.nlut, t.max_groups,
                               t.lut_smem, st);

@@ -274,7 +274,13 @@ struct BatchTables {
     int nlut = 0;               // LUT work items (every frame's columns)
     size_t lut_smem = 0;
     bool std_trans = true;
-    std::vector<int> ground_frames;   // frames whose ground line is estimated (launched per frame)
+    // frames whose ground line is estimated: their arguments (GroundArgs per
+    // frame) and (frame, row block), (frame, horizon block) items; ground_ok
+    // false when one of them has no estimate windows
+    size_t o_ga = 0, o_gr = 0, o_gv = 0;
+    int ngr = 0, ngv = 0;
+    size_t ground_smem = 0;
+    bool ground_ok = true;
     // frames solved by the global MAP (one launch over their columns): their
     // scratch rows (MapScratch per frame) and (frame, column) items
     size_t o_ms = 0, o_mi = 0;
@@ -299,6 +305,32 @@ inline bool ground_size_ok(const FrameGeom& g) { return (int64_t)g.ncols * g.H <
 // The frame's row tables that launch_ground writes inside `work`.
 RowsDev ground_frame_rows(const FrameGeom& g, int dmax, const RowsDev& cam, int est_gw, char* work);
 cudaError_t prepare_ground_kernels();
+// One frame's ground-estimate arguments (the per-frame launch's, for the
+// batch kernels' table rows): false when the handle has no estimated-line
+// windows matching its camera's.
+struct GroundArgs {
+    const int16_t* q;
+    int H, ncols, dmax, gw;
+    int32_t* smooth;
+    unsigned long long* best;
+    const int32_t* kg_tab;
+    RowsDev cam;
+    const RealModelDev* rm;
+    const int32_t* est_pool;
+    double* rows;
+    int32_t* pool;
+    int32_t* line;
+    int nvote;                  // the frame's vote blocks
+};
+bool ground_args(const int16_t* q, const FrameGeom& g, const ModelDev& m, const RowsDev& cam, const int32_t* est_pool,
+                 int est_gw, char* work, int32_t* line, GroundArgs* a);
+int ground_row_blocks(int H);        // v-disparity CTAs of a frame (two image rows each)
+int ground_horizon_blocks(int H);    // vote CTAs of a frame per slope (128 horizons each)
+size_t ground_vdisp_smem(int dmax);
+// Batch form: one v-disparity launch over (frame, row block) items, then one
+// vote launch over (frame, horizon block) items x 256 slopes.
+cudaError_t launch_ground_batch(const GroundArgs* d_args, const int2* d_row_items, int nrow_items,
+                                const int2* d_vote_items, int nvote_items, size_t vdisp_smem, cudaStream_t st);
 cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& m, RowsDev cam,
                           const int32_t* est_pool, int est_gw, char* work, RowsDev* frame_rows, int32_t* line,
                           cudaStream_t st);

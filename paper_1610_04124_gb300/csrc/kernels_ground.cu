@@ -43,13 +43,15 @@ __host__ __device__ inline int ground_pitch(int H) { return (H + kVdispRows - 1)
 // 16-byte words
 __host__ __device__ inline int vdisp_pitch(int E) { return (E + 23 + 3) / 4 * 4; }
 
-// per two image rows: histograms of the codes, smoothed, stored code-major
-__global__ void __launch_bounds__(256) vdisp_kernel(const int16_t* __restrict__ q, int H, int ncols, int dmax,
-                                                    int32_t* __restrict__ smooth, unsigned long long* __restrict__ best)
+// per two image rows (row block rb): histograms of the codes, smoothed,
+// stored code-major
+__device__ __forceinline__ void vdisp_rows(const int16_t* __restrict__ q, int H, int ncols, int dmax,
+                                           int32_t* __restrict__ smooth, unsigned long long* __restrict__ best,
+                                           const int rb)
 {
     // the vote kernel that follows on the stream starts from no winner and no
     // finished block
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (rb == 0 && threadIdx.x == 0) {
         best[0] = 0ull;
         best[1] = 0ull;
     }
@@ -57,7 +59,7 @@ __global__ void __launch_bounds__(256) vdisp_kernel(const int16_t* __restrict__ 
     // zero, so every window below reads zeros outside [16, E)
     extern __shared__ __align__(16) int32_t s_h[];
     const int E = 16 * dmax + 1, P = vdisp_pitch(E), Hp = ground_pitch(H);
-    const int r0 = blockIdx.x * kVdispRows;
+    const int r0 = rb * kVdispRows;
     for (int x = threadIdx.x; x < kVdispRows * P; x += blockDim.x) s_h[x] = 0;
     __syncthreads();
     // four codes' loads in flight per thread, then their counts
@@ -123,6 +125,12 @@ __global__ void __launch_bounds__(256) vdisp_kernel(const int16_t* __restrict__ 
     // codes below 16 carry no ground
     for (int e = threadIdx.x; e < 16; e += blockDim.x)
         *reinterpret_cast<int2*>(smooth + (size_t)e * Hp + r0) = make_int2(0, 0);
+}
+
+__global__ void __launch_bounds__(256) vdisp_kernel(const int16_t* __restrict__ q, int H, int ncols, int dmax,
+                                                    int32_t* __restrict__ smooth, unsigned long long* __restrict__ best)
+{
+    vdisp_rows(q, H, ncols, dmax, smooth, best, blockIdx.x);
 }
 
 // the frame's row tables (RowsDev) from the winning line, or the camera's
@@ -193,20 +201,19 @@ __device__ __noinline__ void write_ground_rows(unsigned long long key, int H, in
 // adds the warps' sums.  One address per offset serves the four horizons.
 // best[0] is the running winner, best[1] counts finished blocks: the last
 // block to finish writes the frame's row tables.
-__global__ void __launch_bounds__(32 * kVoteWarps) vote_kernel(const int32_t* __restrict__ smooth, int H,
-                                                               int dmax, unsigned long long* __restrict__ best,
-                                                               const int32_t* __restrict__ kg_tab, RowsDev cam,
-                                                               const RealModelDev* __restrict__ rm,
-                                                               const int32_t* __restrict__ est_pool, int gw,
-                                                               double* __restrict__ rows, int32_t* __restrict__ pool,
-                                                               int32_t* __restrict__ line)
+// (horizon block hblk, slope k of the frame's nblocks vote blocks)
+__device__ __forceinline__ void vote_block(const int32_t* __restrict__ smooth, int H, int dmax,
+                                           unsigned long long* __restrict__ best, const int32_t* __restrict__ kg_tab,
+                                           const RowsDev& cam, const RealModelDev* __restrict__ rm,
+                                           const int32_t* __restrict__ est_pool, int gw, double* __restrict__ rows,
+                                           int32_t* __restrict__ pool, int32_t* __restrict__ line, const int hblk,
+                                           const int k, const unsigned long long nblocks)
 {
     __shared__ bool s_last;
     __shared__ int32_t s_v[kVoteWarps][kVoteH];
     const int E = 16 * dmax + 1, Hp = ground_pitch(H);
-    const int k = blockIdx.y + 1;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int hb = blockIdx.x * kVoteH, hl = hb + lane;
+    const int hb = hblk * kVoteH, hl = hb + lane;
     // offsets j = r - h with code (k j + 8) >> 4 in [16, E): up to j_hi some
     // horizon of the block has its row r < H, up to j_all every one has
     const int j_lo = (248 + k - 1) / k;
@@ -274,13 +281,44 @@ __global__ void __launch_bounds__(32 * kVoteWarps) vote_kernel(const int32_t* __
             // the winner is visible before this block counts as finished
             __threadfence();
             const unsigned long long done = atomicAdd(best + 1, 1ull);
-            s_last = done + 1 == (unsigned long long)gridDim.x * gridDim.y;
+            s_last = done + 1 == nblocks;
         }
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     write_ground_rows(atomicAdd(best, 0ull), H, dmax, kg_tab, cam, rm, est_pool, gw, rows, pool, line);
+}
+
+__global__ void __launch_bounds__(32 * kVoteWarps) vote_kernel(const int32_t* __restrict__ smooth, int H,
+                                                               int dmax, unsigned long long* __restrict__ best,
+                                                               const int32_t* __restrict__ kg_tab, RowsDev cam,
+                                                               const RealModelDev* __restrict__ rm,
+                                                               const int32_t* __restrict__ est_pool, int gw,
+                                                               double* __restrict__ rows, int32_t* __restrict__ pool,
+                                                               int32_t* __restrict__ line)
+{
+    vote_block(smooth, H, dmax, best, kg_tab, cam, rm, est_pool, gw, rows, pool, line, blockIdx.x, blockIdx.y + 1,
+               (unsigned long long)gridDim.x * gridDim.y);
+}
+
+// Batch forms: blockIdx.x indexes a list of (frame, row block) or (frame,
+// horizon block) items; each frame's arguments come from its table row.
+__global__ void __launch_bounds__(256) vdisp_batch_kernel(const GroundArgs* __restrict__ args,
+                                                          const int2* __restrict__ items)
+{
+    const int2 w = items[blockIdx.x];
+    const GroundArgs& a = args[w.x];
+    vdisp_rows(a.q, a.H, a.ncols, a.dmax, a.smooth, a.best, w.y);
+}
+
+__global__ void __launch_bounds__(32 * kVoteWarps) vote_batch_kernel(const GroundArgs* __restrict__ args,
+                                                                     const int2* __restrict__ items)
+{
+    const int2 w = items[blockIdx.x];
+    const GroundArgs& a = args[w.x];
+    vote_block(a.smooth, a.H, a.dmax, a.best, a.kg_tab, a.cam, a.rm, a.est_pool, a.gw, a.rows, a.pool, a.line, w.y,
+               blockIdx.y + 1, (unsigned long long)a.nvote);
 }
 
 }  // namespace
@@ -324,11 +362,41 @@ cudaError_t prepare_ground_kernels()
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
         // dmax 255: 32.8 KB
         e = cudaFuncSetAttribute(vdisp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(int32_t) * kVdispRows * vdisp_pitch(16 * STIXELS_MAX_DMAX + 1)));
+                                 (int)ground_vdisp_smem(STIXELS_MAX_DMAX));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(vdisp_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)ground_vdisp_smem(STIXELS_MAX_DMAX));
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
     return cudaSuccess;
+}
+
+int ground_row_blocks(int H) { return (H + kVdispRows - 1) / kVdispRows; }
+int ground_horizon_blocks(int H) { return (H + kVoteH - 1) / kVoteH; }
+size_t ground_vdisp_smem(int dmax) { return sizeof(int32_t) * kVdispRows * vdisp_pitch(16 * dmax + 1); }
+
+bool ground_args(const int16_t* q, const FrameGeom& g, const ModelDev& m, const RowsDev& cam, const int32_t* est_pool,
+                 int est_gw, char* work, int32_t* line, GroundArgs* a)
+{
+    if (!est_pool || est_gw != cam.gw) return false;
+    const RowsDev fr = ground_frame_rows(g, m.dmax, cam, est_gw, work);
+    a->q = q;
+    a->H = g.H;
+    a->ncols = g.ncols;
+    a->dmax = m.dmax;
+    a->smooth = (int32_t*)work;
+    a->best = (unsigned long long*)(work + smooth_bytes(g.H, m.dmax));
+    a->kg_tab = m.kg_tab;
+    a->cam = cam;
+    a->rm = cam.real_model;
+    a->est_pool = est_pool;
+    a->gw = est_gw;
+    a->rows = const_cast<double*>(fr.fg);
+    a->pool = const_cast<int32_t*>(fr.gpool);
+    a->line = line ? line : (int32_t*)((char*)a->best + 256);
+    a->nvote = ground_horizon_blocks(g.H) * 256;
+    return true;
 }
 
 cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& m, RowsDev cam,
@@ -336,23 +404,30 @@ cudaError_t launch_ground(const int16_t* q, const FrameGeom& g, const ModelDev& 
                           cudaStream_t st)
 {
     // cam is a copy: frame_rows may be the caller's camera rows themselves
-    if (!est_pool || est_gw != cam.gw) return cudaErrorInvalidValue;
-    const size_t E = 16 * (size_t)m.dmax + 1;
-    int32_t* smooth = (int32_t*)work;
-    unsigned long long* best = (unsigned long long*)(work + smooth_bytes(g.H, m.dmax));
-    int32_t* own_line = (int32_t*)((char*)best + 256);
+    GroundArgs a;
+    if (!ground_args(q, g, m, cam, est_pool, est_gw, work, line, &a)) return cudaErrorInvalidValue;
     *frame_rows = ground_frame_rows(g, m.dmax, cam, est_gw, work);
-    double* rows = const_cast<double*>(frame_rows->fg);
-    int32_t* pool = const_cast<int32_t*>(frame_rows->gpool);
-    const size_t smem = sizeof(int32_t) * kVdispRows * vdisp_pitch((int)E);
     cudaError_t e = prepare_ground_kernels();
     if (e != cudaSuccess) return e;
-    vdisp_kernel<<<(g.H + kVdispRows - 1) / kVdispRows, 256, smem, st>>>(q, g.H, g.ncols, m.dmax, smooth, best);
+    vdisp_kernel<<<ground_row_blocks(g.H), 256, ground_vdisp_smem(m.dmax), st>>>(q, g.H, g.ncols, m.dmax, a.smooth,
+                                                                                  a.best);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    vote_kernel<<<dim3((g.H + kVoteH - 1) / kVoteH, 256), 32 * kVoteWarps, 0, st>>>(
-        smooth, g.H, m.dmax, best, m.kg_tab, cam, cam.real_model, est_pool, est_gw, rows, pool,
-        line ? line : own_line);
+    vote_kernel<<<dim3(ground_horizon_blocks(g.H), 256), 32 * kVoteWarps, 0, st>>>(
+        a.smooth, g.H, m.dmax, a.best, m.kg_tab, cam, cam.real_model, est_pool, est_gw, a.rows, a.pool, a.line);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ground_batch(const GroundArgs* d_args, const int2* d_row_items, int nrow_items,
+                                const int2* d_vote_items, int nvote_items, size_t vdisp_smem, cudaStream_t st)
+{
+    if (nrow_items <= 0 || nvote_items <= 0) return cudaSuccess;
+    cudaError_t e = prepare_ground_kernels();
+    if (e != cudaSuccess) return e;
+    vdisp_batch_kernel<<<nrow_items, 256, vdisp_smem, st>>>(d_args, d_row_items);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    vote_batch_kernel<<<dim3(nvote_items, 256), 32 * kVoteWarps, 0, st>>>(d_args, d_vote_items);
     return cudaGetLastError();
 }
 

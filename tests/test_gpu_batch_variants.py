@@ -101,3 +101,34 @@ def test_served_estimate_and_global_map_equal_per_frame():
     srv.close()
     for h in hs:
         h.close()
+
+
+def test_batched_global_map_mixed_heights_equal_per_frame():
+    """Global-MAP frames of different heights and dmax in one launch of the
+    batch kernel (its shared memory sized for the tallest, each CTA laid out
+    for its own frame), beside plain frames, twice through the same graph:
+    each frame equals its own per-frame call bit for bit (the per-frame MAP
+    is checked against the oracle in test_gpu_map)."""
+    specs = [
+        (scenes.CONFIG2, dict(global_map=1), 8200),
+        (SMALL, dict(global_map=1, cost_order=3.0), 8201),
+        (scenes.Camera(640, 240, stixel_width=7, dmax=64, horizon_row=80), dict(global_map=1, eps_order=-0.5), 8202),
+        (scenes.CONFIG2, {}, 8203),
+        (scenes.CONFIG1, dict(global_map=1, ground_estimate=1, **WRONG), 8204),
+    ]
+    hs, frames = [], []
+    for cam, kw, seed in specs:
+        hs.append(S.Stixels(S.default_params(cam, **kw)))
+        frames.append((cam, scenes.make_scene(cam, seed, n_obstacles=(5, 12)).disparity))
+    refs = [_per_frame(h, d) for h, (_, d) in zip(hs, frames)]
+    b = S.Batch([(h, cam.height, cam.width) for h, (cam, _) in zip(hs, frames)])
+    for i, (_, d) in enumerate(frames):
+        b.set_input(i, cuda(d))
+    for _ in range(2):
+        b.launch()
+        torch.cuda.synchronize()
+        for i, h in enumerate(hs):
+            _same(b.output(i), refs[i], h.params.max_stixels_per_col)
+    b.close()
+    for h in hs:
+        h.close()

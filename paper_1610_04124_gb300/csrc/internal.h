@@ -12,6 +12,33 @@
 
 namespace stx {
 
+// Programmatic dependent launch: a kernel launched with launch_dependent may
+// be scheduled while the one before it on the stream still runs (once every
+// CTA of that one has started or called grid_dependents_may_launch); it must
+// call grid_dependency_wait before it reads what the earlier kernel writes or
+// writes what that one reads.  Both are no-ops for a kernel launched plainly.
+#ifdef __CUDACC__
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_may_launch() { asm volatile("griddepcontrol.launch_dependents;"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                             Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+#endif
+
 // Fixed-point cost arithmetic.  Costs are int32 in units of 2^-14; every
 // per-pixel term and every prior is a multiple of 4 (i.e. on the 2^-12 grid),
 // so the two low bits of a candidate cost are free to carry the code of the

@@ -507,20 +507,6 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const DpArgs& ta, con
     const int32_t* pg_col = a.pg + (size_t)col * P;
     const int32_t* ps_col = a.ps + (size_t)col * P;
     const int32_t* thr_row = rows_thr(a.rows.fg, H);   // gravity / diving thresholds of each row
-    for (int v = threadIdx.x; v <= H; v += kThreads) {
-        int32_t thr = 0;
-        if (v < H) {
-            thr = thr_row[v];
-#pragma unroll
-            for (int q = 0; q < slots; ++q) {
-                s_runv[q * HP + v] = INT_MAX;
-                s_runbf[q * HP + v] = 0;
-            }
-        }
-        s_gs[v] = make_int2(pg_col[v], ps_col[v]);
-        s_pd8[v] = a.pd[(size_t)col * P + v] + 8 * v;
-        s_thr[v] = thr;
-    }
     for (int n = 1 + threadIdx.x; n <= H; n += kThreads) {
         const DivMagic dm = kDivTable.v[n];
         s_div[n] = make_uint2(dm.m, dm.s);
@@ -534,6 +520,22 @@ __device__ __forceinline__ void dp_column(const DpArgs& a, const DpArgs& ta, con
         const char* mb = reinterpret_cast<const char*>(real_k_obj(a.rows.real_model));
         const int nm = 8 * F;
         for (int o = 128 * threadIdx.x; o < nm; o += 128 * kThreads) asm volatile("prefetch.global.L2 [%0];" ::"l"(mb + o));
+    }
+    // the tables: from here on this kernel reads what the LUT kernel wrote
+    grid_dependency_wait();
+    for (int v = threadIdx.x; v <= H; v += kThreads) {
+        int32_t thr = 0;
+        if (v < H) {
+            thr = thr_row[v];
+#pragma unroll
+            for (int q = 0; q < slots; ++q) {
+                s_runv[q * HP + v] = INT_MAX;
+                s_runbf[q * HP + v] = 0;
+            }
+        }
+        s_gs[v] = make_int2(pg_col[v], ps_col[v]);
+        s_pd8[v] = a.pd[(size_t)col * P + v] + 8 * v;
+        s_thr[v] = thr;
     }
     if (threadIdx.x < kMaxBlocks) {
         sync->ready[threadIdx.x] = 0;
@@ -1079,9 +1081,10 @@ cudaError_t launch_frame(const DpArgs& a, int ncols, cudaStream_t st)
     if (e != cudaSuccess) return e;
     const bool prune = MINB >= 2;
     const int slots = prune ? pick_slots(a.H, kRingMax, MINB) : 2;
-    stixel_dp_kernel<NW, kStd, MINB><<<ncols, NW * 32, dp_smem_bytes(a.H, kRingMax, slots), st>>>(
-        a, kRingMax, slots, prune ? kFrameWindow : kNoPruning);
-    return cudaGetLastError();
+    // a programmatic dependent of the LUT kernel before it on the stream
+    return launch_dependent(stixel_dp_kernel<NW, kStd, MINB>, dim3(ncols), dim3(NW * 32),
+                            dp_smem_bytes(a.H, kRingMax, slots), st, a, (int)kRingMax, slots,
+                            prune ? kFrameWindow : kNoPruning);
 }
 
 template <int NW, bool kStd, int MINB>

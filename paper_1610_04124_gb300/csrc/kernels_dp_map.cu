@@ -700,6 +700,9 @@ cudaError_t launch_dp_map(const int32_t* pd, const int32_t* pg, const int32_t* p
     cudaError_t e = prepare_map_kernel();
     if (e != cudaSuccess) return e;
     const MapScratch sc = map_scratch_carve(scratch, g.H, g.ncols, F);
+    // a plain launch (as a programmatic dependent of the LUT kernel, scheduled
+    // while the LUT's CTAs still held the SMs, it measured 292 -> 358 us per
+    // 1024x440 call)
     stixel_map_kernel<<<g.ncols, kMapWarps * 32, smem, st>>>(a, sc.keyo, sc.kgs, sc.mv);
     return cudaGetLastError();
 }

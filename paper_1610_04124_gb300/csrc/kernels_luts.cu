@@ -122,7 +122,6 @@ __device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const 
     const int R = F + 3;
     const int lr = lc_radius(m.esat_obj), lw = 2 * lr + 1;
 
-    for (int j = threadIdx.x; j < QP; j += blockDim.x) s_q[j] = (j >= 1 && j <= H) ? q[(size_t)col * H + j - 1] : 0;
     if ((unsigned)(F + 1 - row0) < (unsigned)kRowsPerCta) {
         // the ground row reads its row tables, then its residual windows, at
         // every pixel: start bringing both into L2 now, behind the codes' loads
@@ -144,6 +143,10 @@ __device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const 
             s_lc[i] = (d >= 0 && d < F) ? __ldg(m.lut_cost + (size_t)ff * F + d) : m.c_out;
         }
     }
+    // the codes: from here on this kernel reads what the reduction wrote and
+    // writes the tables the previous frame's DP may have read
+    grid_dependency_wait();
+    for (int j = threadIdx.x; j < QP; j += blockDim.x) s_q[j] = (j >= 1 && j <= H) ? q[(size_t)col * H + j - 1] : 0;
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -230,6 +233,8 @@ template <bool kIntGrid, bool kVarSigma>
 __global__ void __launch_bounds__(256, kVarSigma ? 6 : 8) prefix_lut_kernel(LutArgs a)
 {
     extern __shared__ __align__(16) int32_t sm[];
+    // the DP kernel that follows may be scheduled now (it waits for the tables)
+    grid_dependents_may_launch();
     lut_rows<kIntGrid, kVarSigma>(a, blockIdx.x, blockIdx.y * kRowsPerCta, sm);
 }
 
@@ -279,14 +284,12 @@ cudaError_t launch_luts(const int16_t* q, const FrameGeom& g, const ModelDev& m,
     a.range_only = range_only;
     dim3 grid(g.ncols, lut_row_groups(a.F));
     const size_t smem = lut_shared_bytes(g.H, m);
-    if (m.var_sigma) {
-        if (m.int_grid) prefix_lut_kernel<true, true><<<grid, 256, smem, st>>>(a);
-        else prefix_lut_kernel<false, true><<<grid, 256, smem, st>>>(a);
-    } else {
-        if (m.int_grid) prefix_lut_kernel<true, false><<<grid, 256, smem, st>>>(a);
-        else prefix_lut_kernel<false, false><<<grid, 256, smem, st>>>(a);
-    }
-    return cudaGetLastError();
+    // a programmatic dependent of the reduction before it on the stream
+    if (m.var_sigma)
+        return m.int_grid ? launch_dependent(prefix_lut_kernel<true, true>, grid, dim3(256), smem, st, a)
+                          : launch_dependent(prefix_lut_kernel<false, true>, grid, dim3(256), smem, st, a);
+    return m.int_grid ? launch_dependent(prefix_lut_kernel<true, false>, grid, dim3(256), smem, st, a)
+                      : launch_dependent(prefix_lut_kernel<false, false>, grid, dim3(256), smem, st, a);
 }
 
 cudaError_t launch_luts_batch(const LutArgs* d_frames, const int2* d_items, int nitems, int max_groups,

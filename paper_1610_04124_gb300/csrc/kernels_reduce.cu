@@ -69,6 +69,8 @@ template <int S, int MODE>
 __global__ void __launch_bounds__(512) reduce_transpose_kernel(const float* __restrict__ disp, int H, int W,
                                                                int ncols, int dmax, int16_t* __restrict__ q)
 {
+    // the LUT kernel that follows may be scheduled now (it waits for these codes)
+    grid_dependents_may_launch();
     __shared__ int16_t tile[32][18];                 // [column][row], padded
     const int tx = threadIdx.x, ty = threadIdx.y;    // 32 x 16
     const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 16;

@@ -162,6 +162,23 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
         memcpy(h + t->groups[k].tiles_off, group_tiles[k].data(), sizeof(int4) * group_tiles[k].size());
 }
 
+cudaError_t launch_frame_job(const FrameJob& f, cudaStream_t st)
+{
+    const ModelDev& m = f.view.model;
+    if (f.g.H <= 0 || f.g.ncols <= 0) return cudaSuccess;
+    cudaError_t e = launch_reduce(f.in, f.g, m.dmax, f.view.reduce_mode, f.q, st);
+    RowsDev r = f.view.rows;
+    if (e == cudaSuccess && f.view.ground_estimate)
+        e = launch_ground(f.q, f.g, m, r, f.view.est_pool, f.view.est_gw, f.ground_work, &r, nullptr, st);
+    if (e == cudaSuccess) e = launch_luts(f.q, f.g, m, r, f.pd, f.pg, f.ps, f.po, st, 1);
+    if (e == cudaSuccess)
+        e = f.view.global_map ? launch_dp_map(f.pd, f.pg, f.ps, f.po, f.g, m, r, f.view.rp, f.view.pixel_floor, f.out,
+                                              f.view.err, f.map_scratch, st)
+                              : launch_dp(f.pd, f.pg, f.ps, f.po, f.g, m, r, f.view.rp, f.view.pixel_floor, f.out,
+                                          f.view.err, st);
+    return e;
+}
+
 cudaError_t enqueue_tables(const BatchTables& t, char* d_tab, int dp_warps, int dp_ctas_per_sm, cudaStream_t st)
 {
     int* counter = (int*)(d_tab + t.o_cnt);

@@ -316,6 +316,9 @@ struct BatchTables {
     std::vector<FrameJob> jobs;       // the frames, for those launches
 };
 void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t);
+// One frame through the per-frame kernels (the launches of stixels_compute)
+// on the job's own buffers.
+cudaError_t launch_frame_job(const FrameJob& f, cudaStream_t st);
 // Launches all stages for tables already copied to d_tab (counter reset included).
 cudaError_t enqueue_tables(const BatchTables& t, char* d_tab, int dp_warps, int dp_ctas_per_sm, cudaStream_t st);
 

@@ -4,14 +4,15 @@
 // Life of a frame: stixels_submit reserves arena space (input, intermediates,
 // outputs) and a status word (page-locked host memory that the kernels set
 // through its device mapping), copies the frame in on the copy stream and
-// waits for that copy, then queues the request.  The scheduler takes every queued request, plans
-// the batch tables for them (the planner of the batched mode), uploads the
-// tables through a pinned staging buffer and launches the batched kernels on
-// a compute stream whose previous iteration has finished (when all three are
-// busy, on the one launched first, once it is done), recording one completion
-// event per iteration: at most three iterations are in flight and they
-// overlap on the device, and no iteration waits behind a long one while
-// another stream is free.
+// waits for that copy, then queues the request.  The scheduler takes every
+// queued request; a lone frame below 800 rows goes through the per-frame
+// kernels, any other set gets the batch tables (the planner of the batched
+// mode), uploaded through a pinned staging buffer, and the batched kernels.
+// Each iteration runs on a compute stream whose previous iteration has
+// finished (when all three are busy, on the one launched first, once it is
+// done), recording one completion event per iteration: at most three
+// iterations are in flight and they overlap on the device, and no iteration
+// waits behind a long one while another stream is free.
 // stixels_poll checks the request's iteration event, reads its status word,
 // copies the results out on the calling thread's stream (one wait) and
 // returns the slot's memory and status word.
@@ -177,10 +178,14 @@ void scheduler(stixels_server_t s)
                 if (s->launched[q] < s->launched[k]) k = q;
             cudaEventSynchronize(s->last[k]->done);
         }
-        // plan the iteration; halve it (returning the rest to the queue) while
-        // its tables do not fit the staging buffer
+        // a lone frame below 800 rows runs the per-frame kernels on its own
+        // buffers (no tables; a lone 1024x440 frame 121 -> 105 us, 640x240
+        // 60 -> 56 us); otherwise plan the iteration, halving it (returning
+        // the rest to the queue) while its tables do not fit the staging
+        // buffer
+        const bool lone = batch.size() == 1 && batch[0]->job.g.H < 800;
         BatchTables t;
-        for (;;) {
+        for (; !lone;) {
             std::vector<FrameJob> jobs;
             jobs.reserve(batch.size());
             for (auto& r : batch) jobs.push_back(r->job);
@@ -193,10 +198,15 @@ void scheduler(stixels_server_t s)
         }
         auto it = std::make_shared<Iteration>();
         cudaError_t e = cudaEventCreateWithFlags(&it->done, cudaEventDisableTiming);
-        if (e == cudaSuccess && t.host.size() > kTableBytes) e = cudaErrorInvalidValue;
-        if (e == cudaSuccess) {
-            memcpy(s->h_staging[k], t.host.data(), t.host.size());
-            e = cudaMemcpyAsync(s->d_tables[k], s->h_staging[k], t.host.size(), cudaMemcpyHostToDevice, s->streams[k]);
+        if (lone) {
+            if (e == cudaSuccess) e = launch_frame_job(batch[0]->job, s->streams[k]);
+        } else {
+            if (e == cudaSuccess && t.host.size() > kTableBytes) e = cudaErrorInvalidValue;
+            if (e == cudaSuccess) {
+                memcpy(s->h_staging[k], t.host.data(), t.host.size());
+                e = cudaMemcpyAsync(s->d_tables[k], s->h_staging[k], t.host.size(), cudaMemcpyHostToDevice,
+                                    s->streams[k]);
+            }
         }
         // the DP's launch shape: an iteration that holds a tall frame (800
         // rows or more) and at most three columns per SM runs faster with 16
@@ -204,7 +214,8 @@ void scheduler(stixels_server_t s)
         // us); every other one with 8 warps, two CTAs per SM (a lone 1024x440
         // frame 121 us, against 154 us)
         const bool tall = t.maxH >= 800 && t.nitems <= 3 * sm_count();
-        if (e == cudaSuccess && t.nlut > 0) e = enqueue_tables(t, s->d_tables[k], tall ? 16 : 8, tall ? 1 : 2, s->streams[k]);
+        if (!lone && e == cudaSuccess && t.nlut > 0)
+            e = enqueue_tables(t, s->d_tables[k], tall ? 16 : 8, tall ? 1 : 2, s->streams[k]);
         if (e == cudaSuccess) e = cudaEventRecord(it->done, s->streams[k]);
         const int launch_status = e == cudaSuccess ? STIXELS_OK : status_of(e);
         if (e != cudaSuccess && it->done) cudaEventRecord(it->done, s->streams[k]);   // polls must still return

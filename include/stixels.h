@@ -367,10 +367,13 @@ int stixels_batch_destroy(stixels_batch_t b);
 /*
  * A server admits frames from any number of camera handles as they arrive and
  * runs them with continuous batching: a scheduler thread takes every admitted
- * frame whose input has been copied in, runs them together as one batch (the
- * kernels of the batched mode, tables rebuilt per iteration), and alternates
- * between two CUDA streams, so frames admitted while another iteration is on
- * the GPU start in the next iteration and the two overlap on the device.
+ * frame whose input has been copied in and runs them together as one
+ * iteration -- a lone frame below 800 rows through the kernels of
+ * stixels_compute, any other set as one batch (the kernels of the batched
+ * mode, tables rebuilt per iteration, the DP's launch shape chosen by the
+ * iteration's size) -- on one of three CUDA streams whose previous iteration
+ * has finished, so frames admitted while iterations are on the GPU start in
+ * the next one and up to three overlap on the device.
  * Device memory comes from one arena of mem_budget_bytes allocated at
  * creation: a frame is admitted only if a slot and arena space for its input,
  * intermediates and outputs are free, else stixels_submit returns

@@ -80,6 +80,7 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
         la[i].H = f.g.H; la[i].P = f.g.P; la[i].F = m.dmax + 1; la[i].m = m; la[i].rows = rows;
         la[i].pd = f.pd; la[i].pg = f.pg; la[i].ps = f.ps; la[i].po = f.po;
         la[i].range_only = 1;
+        la[i].rows_per_cta = lut_rows_per_cta(m, 1);
         dp_frame_args(f.pd, f.pg, f.ps, f.po, f.g, m, rows, f.view.rp, f.view.pixel_floor, f.out, f.view.err, &da[i]);
         if (f.g.ncols == 0) continue;
         if (f.view.ground_estimate) {
@@ -93,7 +94,7 @@ void plan_tables(const std::vector<FrameJob>& jobs, BatchTables* t)
                 t->ground_ok = false;
             }
         }
-        t->max_groups = std::max(t->max_groups, lut_row_groups(m.dmax + 1));
+        t->max_groups = std::max(t->max_groups, lut_row_groups(m.dmax + 1, la[i].rows_per_cta));
         t->lut_smem = std::max(t->lut_smem, lut_shared_bytes(f.g.H, m));
         for (int c = 0; c < f.g.ncols; ++c) lut_items.push_back(make_int2(i, c));
         if (f.view.global_map) {

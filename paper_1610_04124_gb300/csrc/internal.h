@@ -206,6 +206,7 @@ struct LutArgs {
     // its rounded mean, round(min q / 16) .. round(max q / 16) (the mean of a
     // run of codes lies between their extremes); the DP reads no other row
     int32_t range_only;
+    int32_t rows_per_cta;       // LUT rows per CTA (lut_rows_per_cta)
 };
 
 // One frame's arguments for the DP kernel (per-frame launch or batch table entry).
@@ -258,7 +259,10 @@ cudaError_t launch_reduce(const float* disp, const FrameGeom& g, int dmax, int m
 cudaError_t launch_luts(const int16_t* q, const FrameGeom& g, const ModelDev& m, const RowsDev& r,
                         int32_t* pd, int32_t* pg, int32_t* ps, int32_t* po, cudaStream_t st, int range_only = 0);
 size_t lut_shared_bytes(int H, const ModelDev& m);
-int lut_row_groups(int F);
+// LUT rows per CTA: 48 where only the code range is written with the
+// default model (fewer CTAs that skip every row), else 32
+int lut_rows_per_cta(const ModelDev& m, int range_only);
+int lut_row_groups(int F, int rows_per_cta);
 cudaError_t launch_luts_batch(const LutArgs* d_frames, const int2* d_items, int nitems, int max_groups,
                               size_t smem, cudaStream_t st);
 cudaError_t launch_reduce_batch(const ReduceArgs* d_frames, const int4* d_tiles, int ntiles, int s, int mode,

@@ -16,7 +16,8 @@
 // entries for sigma = 1 px).
 //
 // Work split: one warp per LUT row (as in the paper's Sec. 5.2), 32 rows per
-// 256-thread CTA, grid = (ncols, ceil((dmax + 4) / 32)).  A lane owns 8
+// 256-thread CTA (48 when only the code range is written with the default
+// model), grid = (ncols, ceil((dmax + 4) / rows)).  A lane owns 8
 // consecutive outputs, so one chunk of the row is 256 entries: 7 in-register
 // adds, a 5-step shuffle scan of the lane totals, and two 16-byte stores per
 // lane.  Rows are padded to a multiple
@@ -29,7 +30,9 @@
 namespace stx {
 namespace {
 
-constexpr int kRowsPerCta = 32;
+constexpr int kRowsPerCta = 32;               // rows per CTA, whole tables
+constexpr int kRowsPerCtaRange = 48;          // rows per CTA, code range only (default model)
+constexpr int kMaxRowsPerCta = 48;
 constexpr int kLutThreads = 256;             // threads of every LUT CTA (8 warps)
 constexpr int kPerLane = 8;                    // consecutive outputs per lane
 constexpr int kChunk = 32 * kPerLane;          // outputs per warp iteration
@@ -93,7 +96,7 @@ __device__ __forceinline__ void scan_row(int32_t* __restrict__ out, const int32_
     }
 }
 
-// Rows [row0, row0 + kRowsPerCta) of column `col`'s LUTs (row f < F: object
+// Rows [row0, row0 + a.rows_per_cta) of column `col`'s LUTs (row f < F: object
 // at disparity f; F: disparities; F + 1: ground; F + 2: sky), by one CTA.
 // kIntGrid: codes are whole pixels and object costs come from the staged
 // window [f - r, f + r] of LUT_cost row f (d outside it is clamped to its
@@ -118,11 +121,12 @@ __device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const 
     const int E = m.emax + 1;
     int32_t* s_go = s_q + QP;                    // [ngo]   residual tables, clamped at saturation
     int32_t* s_gs = s_go + ngo;                  // [esat_sky + 1]
-    int32_t* s_lc = s_gs + m.esat_sky + 1;       // whole-pixel grid: [kRowsPerCta][2 r + 1] windows
+    int32_t* s_lc = s_gs + m.esat_sky + 1;       // whole-pixel grid: [rows per CTA][2 r + 1] windows
+    const int RC = a.rows_per_cta;
     const int R = F + 3;
     const int lr = lc_radius(m.esat_obj), lw = 2 * lr + 1;
 
-    if ((unsigned)(F + 1 - row0) < (unsigned)kRowsPerCta) {
+    if ((unsigned)(F + 1 - row0) < (unsigned)RC) {
         // the ground row reads its row tables, then its residual windows, at
         // every pixel: start bringing both into L2 now, behind the codes' loads
         const char* pb = reinterpret_cast<const char*>(rows.gpool);
@@ -137,7 +141,7 @@ __device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const 
     if (kIntGrid) {
         // the windows of the LUT_cost rows of this CTA's object disparities
         // (entries beyond [0, dmax] are never read: d is clamped to [0, dmax] first)
-        const int nf = min(kRowsPerCta, F - row0);
+        const int nf = min(RC, F - row0);
         for (int i = threadIdx.x; i < nf * lw; i += blockDim.x) {
             const int ff = row0 + i / lw, d = ff - lr + i % lw;
             s_lc[i] = (d >= 0 && d < F) ? __ldg(m.lut_cost + (size_t)ff * F + d) : m.c_out;
@@ -177,7 +181,7 @@ __device__ __forceinline__ void lut_rows(const LutArgs& a, const int col, const 
         f_lo = max((lo + 8) >> 4, 0);
         f_hi = min((hi + 8) >> 4, F - 1);
     }
-    for (int rr = warp; rr < kRowsPerCta; rr += 8) {
+    for (int rr = warp; rr < RC; rr += 8) {
         const int row = row0 + rr;
         if (row >= R) break;
         if (row < F && (row < f_lo || row > f_hi)) continue;     // never read
@@ -235,7 +239,7 @@ __global__ void __launch_bounds__(256, kVarSigma ? 6 : 8) prefix_lut_kernel(LutA
     extern __shared__ __align__(16) int32_t sm[];
     // the DP kernel that follows may be scheduled now (it waits for the tables)
     grid_dependents_may_launch();
-    lut_rows<kIntGrid, kVarSigma>(a, blockIdx.x, blockIdx.y * kRowsPerCta, sm);
+    lut_rows<kIntGrid, kVarSigma>(a, blockIdx.x, blockIdx.y * a.rows_per_cta, sm);
 }
 
 // Batch form: blockIdx.x indexes a list of (frame, column) items, blockIdx.y
@@ -250,8 +254,8 @@ __global__ void __launch_bounds__(256) prefix_lut_batch_kernel(const LutArgs* __
     int* dst = reinterpret_cast<int*>(&s_args);
     for (int i = threadIdx.x; i < (int)(sizeof(LutArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
     __syncthreads();
-    if ((int)blockIdx.y * kRowsPerCta >= s_args.F + 3) return;
-    const int row0 = blockIdx.y * kRowsPerCta;
+    if ((int)blockIdx.y * s_args.rows_per_cta >= s_args.F + 3) return;
+    const int row0 = blockIdx.y * s_args.rows_per_cta;
     if (s_args.m.var_sigma) {
         if (s_args.m.int_grid) lut_rows<true, true>(s_args, w.y, row0, sm);
         else lut_rows<false, true>(s_args, w.y, row0, sm);
@@ -267,12 +271,21 @@ size_t lut_shared_bytes(int H, const ModelDev& m)
 {
     const int P = lut_pitch(H);
     const int QP = (P + kChunk - 1) / kChunk * kChunk;
-    const size_t lc = m.int_grid ? (size_t)kRowsPerCta * (2 * lc_radius(m.esat_obj) + 1) : 0;
+    const size_t lc = m.int_grid ? (size_t)kMaxRowsPerCta * (2 * lc_radius(m.esat_obj) + 1) : 0;
     const size_t tabs = m.var_sigma ? (size_t)m.esat_sky + 1 : (size_t)m.esat_obj + m.esat_sky + 2;
     return sizeof(int32_t) * ((size_t)QP + tabs + lc);
 }
 
-int lut_row_groups(int F) { return (F + 3 + kRowsPerCta - 1) / kRowsPerCta; }
+// (measured with the code range written, 1024x440: 32 rows 106.8 us per
+// stixels_compute, 48 rows 105.5, 64 rows 107.1; 32 batched frames 14.67 /
+// 14.99 / 14.98 K frames/s; with whole tables, the whole-pixel grid or the
+// variable sigma 48 rows were slower: 18.4 -> 22.5 us per LUT launch)
+int lut_rows_per_cta(const ModelDev& m, int range_only)
+{
+    return range_only && !m.int_grid && !m.var_sigma ? kRowsPerCtaRange : kRowsPerCta;
+}
+
+int lut_row_groups(int F, int rows_per_cta) { return (F + 3 + rows_per_cta - 1) / rows_per_cta; }
 
 cudaError_t launch_luts(const int16_t* q, const FrameGeom& g, const ModelDev& m, const RowsDev& r,
                         int32_t* pd, int32_t* pg, int32_t* ps, int32_t* po, cudaStream_t st, int range_only)
@@ -282,7 +295,8 @@ cudaError_t launch_luts(const int16_t* q, const FrameGeom& g, const ModelDev& m,
     a.q = q; a.H = g.H; a.P = g.P; a.F = m.dmax + 1; a.m = m; a.rows = r;
     a.pd = pd; a.pg = pg; a.ps = ps; a.po = po;
     a.range_only = range_only;
-    dim3 grid(g.ncols, lut_row_groups(a.F));
+    a.rows_per_cta = lut_rows_per_cta(m, range_only);
+    dim3 grid(g.ncols, lut_row_groups(a.F, a.rows_per_cta));
     const size_t smem = lut_shared_bytes(g.H, m);
     // a programmatic dependent of the reduction before it on the stream
     if (m.var_sigma)

@@ -132,3 +132,28 @@ def test_batched_global_map_mixed_heights_equal_per_frame():
     b.close()
     for h in hs:
         h.close()
+
+
+def test_batched_global_map_ragged_heights_equal_oracle():
+    """Global-MAP frames of 1, 2, 31, 33 and 64 rows (a block of 32 rows
+    partly filled, one row, exactly two blocks) in one batched launch, against
+    the oracle frame by frame."""
+    specs = []
+    for H in (1, 2, 31, 33, 64):
+        cam = scenes.Camera(83, H, stixel_width=5, dmax=48, horizon_row=max(0, H // 3), baseline_m=0.4,
+                            camera_height_m=1.0)
+        kw = dict(global_map=1, cost_order=3.0, eps_order=-0.5)
+        specs.append((cam, kw, scenes.make_scene(cam, 8300 + H, n_obstacles=(1, 4), span_cols=(1, 6)).disparity))
+    hs = [S.Stixels(_lib_params(cam, kw)) for cam, kw, _ in specs]
+    b = S.Batch([(h, cam.height, cam.width) for h, (cam, _, _) in zip(hs, specs)])
+    for i, (_, _, d) in enumerate(specs):
+        b.set_input(i, cuda(d))
+    b.launch()
+    torch.cuda.synchronize()
+    for i, (h, (cam, kw, d)) in enumerate(zip(hs, specs)):
+        cap = h.params.max_stixels_per_col
+        fr = oracle.frame(_oracle_params(cam, kw), d, cap=cap)
+        assert_frame_equal(b.output(i), fr, cam.height, cap, _oracle_params(cam, kw))
+    b.close()
+    for h in hs:
+        h.close()

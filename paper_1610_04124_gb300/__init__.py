@@ -208,6 +208,7 @@ class Stixels:
         self._h = h
 
     def close(self):
+        self.__dict__.pop("_host_ptrs", None)
         if getattr(self, "_h", None):
             lib().stixels_destroy(self._h)
             self._h = None
@@ -293,8 +294,20 @@ class Stixels:
         H, W = d.shape
         ncols, cap = self.output_shape(H, W)
         st, counts, cost = out if out is not None else self.alloc_host_output(H, W)
-        rc = lib().stixels_compute_host(self._h, d.ctypes.data, H, W, st.ctypes.data, counts.ctypes.data,
-                                        cost.ctypes.data)
+        # the buffers' addresses, kept with references to the arrays they
+        # belong to (so those arrays stay alive and the addresses valid) for
+        # the next call with the same arrays
+        last = self.__dict__.get("_host_ptrs")
+        if last is not None and last[0] is d:
+            dp = last[1]
+        else:
+            dp = d.ctypes.data
+        if last is not None and last[2] is out and out is not None:
+            sp, cp, kp = last[3]
+        else:
+            sp, cp, kp = st.ctypes.data, counts.ctypes.data, cost.ctypes.data
+        self._host_ptrs = (d, dp, out, (sp, cp, kp))
+        rc = lib().stixels_compute_host(self._h, dp, H, W, sp, cp, kp)
         _check(rc, "stixels_compute_host", (OK, E_CAPACITY))
         return st[:ncols * cap].reshape(ncols, cap), counts[:ncols], cost[:ncols], rc
 

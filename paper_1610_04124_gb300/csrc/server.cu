@@ -38,6 +38,10 @@ namespace {
 constexpr int kStreams = 3;
 constexpr size_t kTableBytes = 8u << 20;      // per stream: device tables and pinned staging
 constexpr int kMaxBatchFrames = 512;
+// frames of this many rows or more are "tall": alone they keep the batched
+// kernels, whose 16-warp DP shape suits them (below, a lone frame takes the
+// per-frame kernels)
+constexpr int kTallRows = 800;
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -183,7 +187,7 @@ void scheduler(stixels_server_t s)
         // 60 -> 56 us); otherwise plan the iteration, halving it (returning
         // the rest to the queue) while its tables do not fit the staging
         // buffer
-        const bool lone = batch.size() == 1 && batch[0]->job.g.H < 800;
+        const bool lone = batch.size() == 1 && batch[0]->job.g.H < kTallRows;
         BatchTables t;
         for (; !lone;) {
             std::vector<FrameJob> jobs;
@@ -213,7 +217,7 @@ void scheduler(stixels_server_t s)
         // warps per column, one CTA per SM (a lone 2048x880 frame 693 -> 533
         // us); every other one with 8 warps, two CTAs per SM (a lone 1024x440
         // frame 121 us, against 154 us)
-        const bool tall = t.maxH >= 800 && t.nitems <= 3 * sm_count();
+        const bool tall = t.maxH >= kTallRows && t.nitems <= 3 * sm_count();
         if (!lone && e == cudaSuccess && t.nlut > 0)
             e = enqueue_tables(t, s->d_tables[k], tall ? 16 : 8, tall ? 1 : 2, s->streams[k]);
         if (e == cudaSuccess) e = cudaEventRecord(it->done, s->streams[k]);
